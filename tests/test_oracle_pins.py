@@ -1,0 +1,449 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these tests retypes the oracle's formula: each compares it with a
+worked example of the paper, a closed form, an invariant, a brute force over
+a tiny case, or a library routine.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden_raster():
+    rects, rows, in_img = [], [], False
+    with open(os.path.join(GOLDEN, "raster_8x8.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line == "image":
+                in_img = True
+            elif in_img:
+                rows.append([int(c) for c in line])
+            else:
+                rects.append([int(v) for v in line.split()[1:]])
+    return rects, np.array(rows, dtype=np.uint8)
+
+
+def test_raster_golden_8x8():
+    rects, expect = _read_golden_raster()
+    img = oracle.rasterize(32, 4, rects)
+    assert img.shape == (8, 8)
+    np.testing.assert_array_equal(img, expect)
+
+
+def _centres_in(lo, hi, p, N):
+    # closed form: number of i in [0, N) with lo <= p*i + p/2 < hi
+    first = -((-(2 * lo - p)) // (2 * p))          # ceil((2lo - p) / 2p)
+    last = -((-(2 * hi - p)) // (2 * p))           # ceil((2hi - p) / 2p)
+    return max(0, min(last, N) - max(first, 0))
+
+
+@pytest.mark.parametrize("p", [4, 3, 8])
+def test_raster_single_rect_closed_form(p):
+    rng = np.random.default_rng(7 + p)
+    W = 64 * p
+    N = W // p
+    for _ in range(200):
+        x0, x1 = sorted(rng.integers(0, W + 1, size=2))
+        y0, y1 = sorted(rng.integers(0, W + 1, size=2))
+        if x0 == x1 or y0 == y1:
+            continue
+        img = oracle.rasterize(W, p, [[x0, y0, x1, y1]])
+        assert int(img.sum()) == _centres_in(x0, x1, p, N) * _centres_in(y0, y1, p, N)
+
+
+def test_raster_union_of_overlaps():
+    # overlapping rectangles union (0/1 image), never sum
+    img = oracle.rasterize(64, 4, [[0, 0, 40, 40], [20, 20, 64, 64]])
+    assert img.max() == 1
+    a = oracle.rasterize(64, 4, [[0, 0, 40, 40]])
+    b = oracle.rasterize(64, 4, [[20, 20, 64, 64]])
+    np.testing.assert_array_equal(img, np.maximum(a, b))
+
+
+@pytest.mark.parametrize("N", [64, 128, 96])
+def test_corr_words_equals_pixel_loop(N):
+    rng = np.random.default_rng(N)
+    for t in range(6):
+        A = (rng.random((N, N)) < 0.3).astype(np.uint8)
+        B = (rng.random((N, N)) < 0.4).astype(np.uint8)
+        for dx, dy in [(0, 0), (1, 0), (0, -1), (-7, 5), (13, -9), (63, 2), (-64, 1), (65, -3)]:
+            assert oracle.corr_words(A, B, dx, dy) == oracle.corr_pixel(A, B, dx, dy)
+
+
+def test_corr_matches_numpy_correlation():
+    # c(s) = sum_x A(x) B(x - s): compare with an explicit numpy shift + sum
+    rng = np.random.default_rng(3)
+    N = 64
+    A = (rng.random((N, N)) < 0.5).astype(np.uint8)
+    B = (rng.random((N, N)) < 0.5).astype(np.uint8)
+    for dx, dy in [(3, -2), (-5, 4), (0, 7)]:
+        Bs = np.zeros_like(B)
+        # Bs(x) = B(x - s): move B by +s
+        ys, xs = np.nonzero(B)
+        ys2, xs2 = ys + dy, xs + dx
+        ok = (ys2 >= 0) & (ys2 < N) & (xs2 >= 0) & (xs2 < N)
+        Bs[ys2[ok], xs2[ok]] = 1
+        assert oracle.corr_pixel(A, B, dx, dy) == int((A.astype(int) * Bs).sum())
+
+
+def test_self_similarity_is_one_at_zero(small_set):
+    for c in range(0, 60, 7):
+        r = small_set.pair(c, c)
+        assert r["dx_dbu"] == 0 and r["dy_dbu"] == 0
+        assert r["score"] == small_set.pop(c)
+        assert abs(r["sim"] - 1.0) < 1e-15
+        assert r["pass_"] == 1
+
+
+def test_swap_symmetry_cosine(small_set):
+    rng = np.random.default_rng(11)
+    S = small_set.S
+    for _ in range(80):
+        a, b = (int(v) for v in rng.integers(0, small_set.n, size=2))
+        if a == b:
+            continue
+        r1 = small_set.pair(a, b, use_gates=False)
+        r2 = small_set.pair(b, a, use_gates=False)
+        assert r1["score"] == r2["score"]
+        assert abs(r1["sim"] - r2["sim"]) < 1e-12
+        assert r1["pass_"] == r2["pass_"]
+        if (r1["dx_dbu"], r1["dy_dbu"]) != (-r2["dx_dbu"], -r2["dy_dbu"]):
+            # tied maximum: the negated shift must still be a maximiser
+            cw = small_set.corr_window(b, a)
+            dx, dy = -r1["dx_dbu"] // small_set.p, -r1["dy_dbu"] // small_set.p
+            assert cw[dy + S, dx + S] == r2["score"]
+
+
+def _translate(rects, tx, ty):
+    return [[r[0] + tx, r[1] + ty, r[2] + tx, r[3] + ty] for r in rects]
+
+
+def test_pure_translate_gives_negated_shift_and_sim_one():
+    base = [[100, 120, 160, 180], [220, 300, 300, 330], [330, 90, 380, 250]]
+    for tx, ty in [(8, -12), (-32, 32), (4, 0), (0, -28)]:
+        wl = synth.from_lists([base, _translate(base, tx, ty)], 512, 4, 32)
+        cs = oracle.ClipSet(wl)
+        r = cs.pair(0, 1, use_gates=False)
+        assert (r["dx_dbu"], r["dy_dbu"]) == (-tx, -ty)
+        assert abs(r["sim"] - 1.0) < 1e-15 and r["pass_"] == 1
+
+
+def test_translation_invariance_of_pair():
+    rng = np.random.default_rng(5)
+    a = [[100, 100, 180, 150], [250, 260, 300, 400], [120, 300, 200, 340]]
+    b = [[106, 96, 190, 150], [250, 268, 296, 400], [128, 304, 200, 344]]
+    wl = synth.from_lists([a, b], 512, 4, 32)
+    ref = oracle.ClipSet(wl).pair(0, 1, use_gates=False)
+    for _ in range(4):
+        tx, ty = (int(4 * v) for v in rng.integers(-20, 21, size=2))
+        wl2 = synth.from_lists([_translate(a, tx, ty), _translate(b, tx, ty)], 512, 4, 32)
+        r = oracle.ClipSet(wl2).pair(0, 1, use_gates=False)
+        assert r["score"] == ref["score"] and abs(r["sim"] - ref["sim"]) < 1e-15
+        assert (r["dx_dbu"], r["dy_dbu"]) == (ref["dx_dbu"], ref["dy_dbu"])
+
+
+def test_tie_order_of_shifts():
+    # A: one pixel at x index 5; B: pixels at x indices 4 and 6 (same row).
+    # c(s) = B(5 - dx): maxima at dx = +1 and dx = -1 (both |s| = 1, dy = 0);
+    # the tie order (-c, |dx|+|dy|, dy, dx) picks dx = -1.
+    a = [[20, 20, 24, 24]]
+    b = [[16, 20, 20, 24], [24, 20, 28, 24]]
+    wl = synth.from_lists([a, b], 64, 4, 8)
+    r = oracle.ClipSet(wl).pair(0, 1, use_gates=False)
+    assert (r["dx_dbu"], r["dy_dbu"], r["score"]) == (-4, 0, 1)
+
+
+def test_tie_order_dy_then_length():
+    # vertical tie: B has pixels above and below A's pixel -> dy = -1 wins
+    a = [[20, 20, 24, 24]]
+    b = [[20, 16, 24, 20], [20, 24, 24, 28]]
+    r = oracle.ClipSet(synth.from_lists([a, b], 64, 4, 8)).pair(0, 1, use_gates=False)
+    assert (r["dx_dbu"], r["dy_dbu"]) == (0, -4)
+    # |dx|+|dy| before dy: candidates (dx, dy) = (0, 1) and (-1, -1) -> (0, 1)
+    b = [[20, 16, 24, 20], [24, 24, 28, 28]]
+    r = oracle.ClipSet(synth.from_lists([a, b], 64, 4, 8)).pair(0, 1, use_gates=False)
+    assert (r["dx_dbu"], r["dy_dbu"]) == (0, 4)
+
+
+def _translate_workload(seed, k=24):
+    """k random interior clips and, for each, a pure translate and a
+    one-pixel-edge variant: pairs that pass and need a non-zero shift."""
+    rng = np.random.default_rng(seed)
+    clips = []
+    for _ in range(k):
+        rects = []
+        while len(rects) < int(rng.integers(2, 6)):
+            x0, y0 = (int(40 + 10 * v) for v in rng.integers(0, 38, size=2))
+            w, h = (int(10 * v) for v in rng.integers(3, 9, size=2))
+            r = [x0, y0, x0 + w, y0 + h]
+            if all(r[2] + 20 <= q[0] or q[2] + 20 <= r[0] or r[3] + 20 <= q[1] or q[3] + 20 <= r[1]
+                   for q in rects):
+                rects.append(r)
+        tx, ty = (int(4 * v) for v in rng.integers(-8, 9, size=2))
+        var = [list(r) for r in rects]
+        var[0][2] += 4
+        clips += [rects, _translate(rects, tx, ty), _translate(var, -ty, tx)]
+    return synth.from_lists(clips, 512, 4, 32)
+
+
+def test_gates_keep_shifted_passing_pairs():
+    cs = oracle.ClipSet(_translate_workload(31))
+    n = cs.n
+    allp = np.array([(i, j) for i in range(n) for j in range(i + 1, n)], dtype=np.uint32)
+    brute = cs.match(allp, oracle.MODE_COSINE, use_gates=False)
+    passing = {(int(r["a"]), int(r["b"])) for r in brute if r["pass_"]}
+    assert len(passing) >= 2 * 24
+    kept, _ = cs.candidates(oracle.MODE_COSINE)
+    assert passing <= set(map(tuple, kept.tolist()))
+    for r in brute:
+        b = cs.gate_bounds(int(r["a"]), int(r["b"]))
+        assert (b >= r["score"]).all()
+
+
+def test_pcm_delta_on_cyclic_shift():
+    # Eqs. 3-5: g = f moved by (x0, y0) -> r = delta at the shift.  With the
+    # member B = A moved by t, the surface built from C = F_A conj(F_B)
+    # peaks at -t (the shift that re-aligns B).
+    rng = np.random.default_rng(2)
+    L = 48
+    A = (rng.random((L, L)) < 0.4).astype(np.uint8)
+    for tx, ty in [(5, -3), (-11, 7), (0, 0)]:
+        B = np.roll(np.roll(A, ty, axis=0), tx, axis=1)
+        r = oracle.pcm_surface(A, B, L)
+        iy, ix = np.unravel_index(np.argmax(r), r.shape)
+        assert (iy, ix) == ((-ty) % L, (-tx) % L)
+        assert abs(r[iy, ix] - 1.0) < 1e-9
+        r2 = r.copy()
+        r2[iy, ix] = 0
+        assert np.abs(r2).max() < 1e-9
+
+
+def test_pcm_peak_on_padded_translate_matches_exact_argmax():
+    base = [[100, 120, 160, 180], [220, 300, 300, 330], [330, 90, 380, 250]]
+    wl = synth.from_lists([base, _translate(base, 12, -20)], 512, 4, 32)
+    cs = oracle.ClipSet(wl)
+    w = cs.pcm_window(0, 1)
+    dx, dy = oracle.window_peak(w, cs.S)
+    assert (dx * 4, dy * 4) == (-12, 20)
+
+
+def test_decision_integer_rule_vs_float64():
+    rng = np.random.default_rng(9)
+    T = Fraction(95, 100)
+    n_checked = 0
+    for _ in range(20000):
+        pa, pb = (int(v) for v in rng.integers(1, 65536, size=2))
+        c = int(rng.integers(0, min(pa, pb) + 1))
+        sim = c / np.sqrt(float(pa) * float(pb))
+        if abs(sim - 0.95) < 1e-9:
+            continue
+        assert oracle.cos_exceeds(c, pa, pb, 95, 100) == (sim > float(T))
+        n_checked += 1
+    assert n_checked > 19000
+    # exact tie: sim = 0.95 exactly is not "> T" (strict, Eq. 2)
+    assert not oracle.cos_exceeds(95, 100, 100, 95, 100)
+    assert oracle.cos_exceeds(96, 100, 100, 95, 100)
+    assert not oracle.cos_exceeds(0, 0, 0, 95, 100)
+
+
+def _golden_minmax():
+    vals = {}
+    with open(os.path.join(GOLDEN, "minmax_worked_example.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = int(v)
+    return vals
+
+
+def test_minmax_worked_example():
+    g = _golden_minmax()
+    d = [g["d_min"], 5, 7, g["d_max"]]
+    T, E = oracle.minmax_closed(d, 64)
+    assert (T, E) == (g["T_opt"], g["E_min"])
+    e, lo, hi = oracle.minmax_scan(d, 64)
+    assert e == g["E_min"] and lo == hi == g["T_opt"]
+
+
+def test_minmax_closed_form_equals_brute_force():
+    rng = np.random.default_rng(4)
+    for _ in range(500):
+        n = int(rng.integers(1, 12))
+        M = int(rng.integers(0, 40))
+        d = rng.integers(-60, 61, size=n).astype(np.int32)
+        T, E = oracle.minmax_closed(d, M)
+        e, lo, hi = oracle.minmax_scan(d, M)
+        assert E == e
+        assert lo <= T <= hi
+        assert T == -oracle.minmax_closed(-d, M)[0]   # odd symmetry of trunc
+
+
+def test_minmax_linf_separable_2d():
+    # L_inf separability (Sec. 3.2.2): the 2-D optimum of max_i ||d_i - T||_inf
+    # equals the larger of the two 1-D optima.
+    rng = np.random.default_rng(8)
+    for _ in range(60):
+        n = int(rng.integers(1, 6))
+        dx = rng.integers(-15, 16, size=n)
+        dy = rng.integers(-15, 16, size=n)
+        M = 16
+        best = min(max(max(abs(dx - tx)), max(abs(dy - ty)))
+                   for tx in range(-M, M + 1) for ty in range(-M, M + 1))
+        _, ex = oracle.minmax_closed(dx, M)
+        _, ey = oracle.minmax_closed(dy, M)
+        assert best == max(ex, ey)
+
+
+def _edge_pair(a_rects, b_rects, tol, W=512, M=32):
+    wl = synth.from_lists([a_rects, b_rects], W, 4, M)
+    return oracle.ClipSet(wl).pair(0, 1, mode=oracle.MODE_EDGE, edge_tol_dbu=tol)
+
+
+def test_edge_worked_example_pair():
+    # member edges displaced so that d = e_A - e_B is 2 (left) and 10 (right):
+    # interval [2, 10] -> T = 6, E = 4 (Sec. 3.2.2); passes at tol 4 only.
+    a = [[100, 100, 200, 180]]
+    b = [[98, 100, 190, 180]]
+    r = _edge_pair(a, b, 4)
+    assert (r["dx_dbu"], r["dy_dbu"], r["score"], r["pass_"]) == (6, 0, 4, 1)
+    assert _edge_pair(a, b, 3)["pass_"] == 0
+
+
+def test_edge_exactly_one_overlap_rule():
+    # Sec. 2.2.2 condition 1: a polygon of the smaller pattern overlapping two
+    # polygons of the other fails; overlapping exactly one passes.
+    a = [[100, 100, 300, 140]]
+    b_two = [[100, 100, 190, 140], [210, 100, 300, 140]]
+    r = _edge_pair(a, b_two, 4)
+    assert r["pass_"] == 0 and (r["flags"] & 15) == oracle.GATE_E1_MATCH
+    b_one = [[102, 100, 300, 141], [400, 400, 450, 450]]
+    r = _edge_pair(a, b_one, 4)
+    assert r["pass_"] == 1
+
+
+def test_edge_swap_symmetry(small_set):
+    rng = np.random.default_rng(12)
+    hits = 0
+    for _ in range(400):
+        a, b = (int(v) for v in rng.integers(0, small_set.n, size=2))
+        if a == b:
+            continue
+        r1 = small_set.pair(a, b, mode=oracle.MODE_EDGE)
+        r2 = small_set.pair(b, a, mode=oracle.MODE_EDGE)
+        assert r1["pass_"] == r2["pass_"]
+        assert (r1["flags"] & 15) == (r2["flags"] & 15)
+        if r1["flags"] & oracle.F_ALIGNED:
+            hits += 1
+            assert (r1["dx_dbu"], r1["dy_dbu"]) == (-r2["dx_dbu"], -r2["dy_dbu"])
+            assert r1["score"] == r2["score"]
+    assert hits > 0
+
+
+def test_edge_empty_cases():
+    assert _edge_pair([], [], 4)["pass_"] == 1
+    r = _edge_pair([], [[10, 10, 50, 50]], 4)
+    assert r["pass_"] == 0 and (r["flags"] & 15) == oracle.GATE_E1_MATCH
+
+
+def test_cosine_empty_cases():
+    wl = synth.from_lists([[], [], [[10, 10, 50, 50]]], 512, 4, 32)
+    cs = oracle.ClipSet(wl)
+    r = cs.pair(0, 1)
+    assert r["pass_"] == 1 and r["sim"] == 1.0 and r["flags"] & oracle.F_EMPTY
+    r = cs.pair(0, 2)
+    assert r["pass_"] == 0
+
+
+def test_gates_are_lossless_on_subset(small_wl):
+    sub = small_wl.subset(np.arange(220))
+    cs = oracle.ClipSet(sub)
+    n = cs.n
+    allp = np.array([(i, j) for i in range(n) for j in range(i + 1, n)], dtype=np.uint32)
+    for mode in (oracle.MODE_COSINE, oracle.MODE_EDGE):
+        kept, counts = cs.candidates(mode)
+        assert int(counts.sum()) == len(allp)
+        brute = cs.match(allp, mode, use_gates=False)
+        keep = set(map(tuple, kept.tolist()))
+        passing = {(int(r["a"]), int(r["b"])) for r in brute if r["pass_"]}
+        assert passing <= keep
+
+
+def test_gate_bounds_dominate_every_shift(small_set):
+    # the profile and density bounds hold for every shift of the window, not
+    # only the best one; G1's sqrt(min/max) bounds the similarity itself
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        a, b = (int(v) for v in rng.integers(0, small_set.n, size=2))
+        cw = small_set.corr_window(a, b)
+        sa, sb = small_set.signature(a), small_set.signature(b)
+        S = small_set.S
+        N = small_set.N
+        # independent restatement of the row-profile bound per dy
+        for dy in range(-S, S + 1):
+            ub = sum(min(sa["rows"][j], sb["rows"][j - dy]) for j in range(N) if 0 <= j - dy < N)
+            assert cw[dy + S].max() <= ub
+        for dx in range(-S, S + 1):
+            ub = sum(min(sa["cols"][i], sb["cols"][i - dx]) for i in range(N) if 0 <= i - dx < N)
+            assert cw[:, dx + S].max() <= ub
+        pa, pb = small_set.pop(a), small_set.pop(b)
+        assert cw.max() <= min(pa, pb)
+
+
+def test_signature_consistency(small_set):
+    for c in range(0, 50, 5):
+        img = small_set.image(c)
+        sg = small_set.signature(c)
+        np.testing.assert_array_equal(sg["rows"], img.sum(axis=1))
+        np.testing.assert_array_equal(sg["cols"], img.sum(axis=0))
+        nb = img.shape[0] // 16
+        np.testing.assert_array_equal(sg["blk"], img.reshape(nb, 16, nb, 16).sum(axis=(1, 3)))
+
+
+# ---------------------------------------------------------------- set cover
+
+def test_surprisal_scores_by_hand():
+    # Graph: 0-{1,2,3}; {1,2,3} x {7,8,9}; 4-{5,6}.  Eqs. 7-9 in 2^32 fixed
+    # point: f = 1 + deg; S = floor(2^32 / f).
+    edges = [(0, 1), (0, 2), (0, 3), (4, 5), (4, 6)]
+    edges += [(u, v) for u in (1, 2, 3) for v in (7, 8, 9)]
+    unc = np.ones(10, bool)
+    assert oracle.score_of(10, edges, unc, 4) == 1431655765 + 2 * 2147483648
+    assert oracle.score_of(10, edges, unc, 1) == 858993459 + 4 * 1073741824
+    order, rep = oracle.setcover_eager(10, edges)
+    # surprisal prefers the rare pair {5, 6} (a count-based greedy would take 1)
+    assert order == [4, 1, 2, 3]
+    assert rep.tolist() == [1, 1, 2, 3, 4, 4, 4, 1, 1, 1]
+
+
+def test_setcover_path_graph():
+    order, rep = oracle.setcover_eager(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
+    assert order == [1, 3]
+    assert rep.tolist() == [1, 1, 1, 3, 3]
+
+
+def test_cluster_loop_invariants(small_set):
+    pairs, _ = small_set.candidates(oracle.MODE_EDGE, edge_tol_dbu=6)
+    rec = small_set.match(pairs, oracle.MODE_EDGE, edge_tol_dbu=6)
+    verified = (rec["flags"] & oracle.F_ALIGNED) > 0
+    verified &= (rec["flags"] & oracle.F_EDGE_VERIFY_FAIL) == 0
+    strict = verified & (rec["score"] <= 4)
+    relaxed = verified & (rec["score"] <= 6)
+    rep_of, ncl, rounds = oracle.cluster_loop(small_set.n, pairs, strict, relaxed)
+    assert (rep_of >= 0).all()
+    reps = set(np.unique(rep_of).tolist())
+    assert len(reps) == ncl
+    assert all(rep_of[r] == r for r in reps)
+    ok = {(int(a), int(b)) for (a, b), s in zip(pairs.tolist(), strict) if s}
+    for k, r in enumerate(rep_of.tolist()):
+        if k != r:
+            assert (min(k, r), max(k, r)) in ok
+    assert rounds >= 1
