@@ -360,7 +360,8 @@ void orc_cosine_pair(const orc_set *s, int a, int b, const orc_params *P, orc_re
     out->dx_dbu = bdx * s->p;
     out->dy_dbu = bdy * s->p;
     out->score = bc;
-    out->sim = (double)bc / sqrt((double)pa * (double)pb);
+    /* a zero vector has cosine 0 with anything (one clip empty) */
+    out->sim = (pa > 0 && pb > 0) ? (double)bc / sqrt((double)pa * (double)pb) : 0.0;
     out->pass = cos_exceeds(bc, pa, pb, P->cos_num, P->cos_den);
     out->flags = ORC_F_ALIGNED;
 }

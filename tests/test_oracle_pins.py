@@ -361,6 +361,8 @@ def test_cosine_empty_cases():
     assert r["pass_"] == 1 and r["sim"] == 1.0 and r["flags"] & oracle.F_EMPTY
     r = cs.pair(0, 2)
     assert r["pass_"] == 0
+    r = cs.pair(0, 2, use_gates=False)
+    assert r["pass_"] == 0 and r["sim"] == 0.0
 
 
 def test_gates_are_lossless_on_subset(small_wl):
