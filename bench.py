@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: aligned pair-similarities per second of the pairwise
+optimal-alignment similarity path on one GB300 (or N of them, weak scaling).
+
+A step is one pass of the whole path over one clip set resident in HBM:
+rasterisation + signatures, the cosine candidate screen (area band join with
+G3/G2 bounds), the edge candidate screen (E2 bbox + E1 correspondence over all
+pairs), FFT phase-correlation cosine matching of the cosine candidates
+(including the forward FFTs of the clips they reference) and Min-Max matching
+of the edge candidates, and the compaction of the pass lists.
+
+  value  = pairs that reached an alignment engine per second (cosine FFT-PCM
+           + edge Min-Max), summed over ranks / max step time over ranks
+  e2e    = the same through the public API from pinned host rectangles
+           (host->device copy of the clip set and device->host read of the
+           pass lists inside the timed region)
+
+Workload: the synthetic "scale" clip set (100,000 clips of 1024 x 1024 dbu,
+256^2 px at 4 dbu/px, 5-40 rectangles, 70% perturbed copies of 5,000 seeds,
+marker +/-64 dbu, cosine 0.95, edge tolerance 4 dbu).  Inputs exceed L2 and
+L2 is also flushed between timed steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "aligned pair-similarities/sec at oracle-exact decisions"
+UNIT = "pairs/s"
+COS_NUM, COS_DEN, TOL = 95, 100, 4
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="scale", choices=["scale", "small"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="clips in the oracle sample (0: auto)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+def alu_peak_tops(sm_mhz: float) -> float:
+    # 152 SMs x 128 INT32/FP32 lanes per SM per clock
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(config: str, seed: int):
+    import synth
+    return synth.preset(config, seed=seed)
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def oracle_sample(wl, n_clips: int):
+    """Time the CPU oracle, as it stands, on the first n_clips clips of the
+    workload: rasters + signatures, exhaustive gate screens of both modes,
+    brute-force alignment of the survivors.  Returns (aligned pairs, seconds,
+    threads)."""
+    import oracle
+    sub = wl.subset(np.arange(min(n_clips, wl.n)))
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    cs = oracle.ClipSet(sub)
+    pc, _ = cs.candidates(oracle.MODE_COSINE, threads=threads)
+    pe, _ = cs.candidates(oracle.MODE_EDGE, threads=threads)
+    rc = cs.match(pc, oracle.MODE_COSINE, threads=threads)
+    re_ = cs.match(pe, oracle.MODE_EDGE, threads=threads)
+    dt = time.perf_counter() - t0
+    aligned = int(((rc["flags"] & oracle.F_ALIGNED) > 0).sum() + ((re_["flags"] & oracle.F_ALIGNED) > 0).sum())
+    return aligned, dt, threads
+
+
+def default_sample(config: str) -> int:
+    return 4000 if config == "scale" else 1000
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workload(args.config, args.seed)
+    n_s = args.cpu_sample or default_sample(args.config)
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_s)
+    tot_a, tot_t, thr = 0, 0.0, 1
+    for _ in range(args.steps):
+        a, t, thr = oracle_sample(wl, n_s)
+        tot_a += a
+        tot_t += t
+    value = tot_a / tot_t if tot_t > 0 else 0.0
+    sample = f"first {n_s} clips of the {args.config} set: all pairs screened, survivors aligned"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
+        "data": "synthetic", "config": {"workload": f"{args.config} (oracle sample)", "sample_clips": n_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2512_13133_gb300 as pcl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = workload(args.config, args.seed + rank)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL)
+    ctx = pcl.Context(local_rank)
+    h_off = torch.from_numpy(wl.rect_off.view(np.int32).copy()).pin_memory()
+    h_rects = torch.from_numpy(wl.rects.reshape(-1).copy()).pin_memory()
+    d_off = h_off.to(dev)
+    d_rects = h_rects.to(dev)
+    cs = pcl.alloc_clipset(P, d_off, d_rects)
+    cap_c, cap_e = 1 << 22, 1 << 25
+    pc = torch.empty((cap_c, 2), dtype=torch.int32, device=dev)
+    pe = torch.empty((cap_e, 2), dtype=torch.int32, device=dev)
+    rc = torch.empty((cap_c, 40), dtype=torch.uint8, device=dev)
+    re_ = torch.empty((cap_e, 40), dtype=torch.uint8, device=dev)
+    qc = torch.empty((cap_c, 2), dtype=torch.int32, device=dev)
+    qe = torch.empty((cap_e, 2), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev)     # cand cos, cand edge, pass cos, pass edge
+    gates = torch.zeros((2, 16), dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stages = ["raster", "cand_cos", "cand_edge", "match_cos", "match_edge", "compact"]
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record()
+        mark(0)
+        pcl.pcl_rasterize(ctx, P, cs)
+        mark(1)
+        pcl.pcl_candidates(ctx, P, pcl.MODE_COSINE, cs, pc, cnt[0:1], gates[0])
+        mark(2)
+        pcl.pcl_candidates(ctx, P, pcl.MODE_EDGE, cs, pe, cnt[1:2], gates[1])
+        mark(3)
+        pcl.pcl_match_pairs(ctx, P, pcl.MODE_COSINE, cs, cs, pc, rc, d_n=cnt[0:1])
+        mark(4)
+        pcl.pcl_match_pairs(ctx, P, pcl.MODE_EDGE, cs, cs, pe, re_, d_n=cnt[1:2])
+        mark(5)
+        pcl.pcl_compact_pass(ctx, rc, qc, cnt[2:3], d_n=cnt[0:1])
+        pcl.pcl_compact_pass(ctx, re_, qe, cnt[3:4], d_n=cnt[1:2])
+        mark(6)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    if c[0] > cap_c or c[1] > cap_e:
+        raise RuntimeError(f"candidate capacity exceeded: {c[:2]}")
+    aligned = int(c[0] + c[1])
+    g = (gates.cpu().numpy() // max(args.warmup, 1))
+    n = wl.n
+    total_pairs = n * (n - 1) // 2
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    st_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
+    ms_step = float(st_ms.sum(axis=1).mean())
+    per_stage = {s: float(st_ms[:, i].mean()) for i, s in enumerate(stages)}
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h_cnt = torch.zeros(4, dtype=torch.int64).pin_memory()
+        e2e_ms, bi, bo = [], 0, 0
+        for k in range(max(args.steps, 1)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d_off.copy_(h_off, non_blocking=True)
+            d_rects.copy_(h_rects, non_blocking=True)
+            step()
+            h_cnt.copy_(cnt, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            m_c, m_e = int(h_cnt[2]), int(h_cnt[3])
+            out_c = qc[:m_c].cpu()
+            out_e = qe[:m_e].cpu()
+            e1.record()
+            torch.cuda.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+            bi = h_off.numel() * 4 + h_rects.numel() * 4
+            bo = 32 + (out_c.numel() + out_e.numel()) * 4
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+               "ms_per_step": float(np.mean(e2e_ms))}
+
+    # ---- reduce over ranks
+    tot_aligned = aligned
+    ms_max = ms_step
+    e2e_max = e2e["ms_per_step"] if e2e else 0.0
+    if world > 1:
+        t = torch.tensor([float(aligned), ms_step, e2e_max], dtype=torch.float64, device=dev)
+        a = t.clone()
+        torch.distributed.all_reduce(a[0:1])
+        torch.distributed.all_reduce(t[1:3], op=torch.distributed.ReduceOp.MAX)
+        tot_aligned, ms_max, e2e_max = int(a[0].item()), float(t[1].item()), float(t[2].item())
+    if rank != 0:
+        return
+    value = tot_aligned / (ms_max / 1e3)
+    if e2e:
+        e2e["value"] = tot_aligned / (e2e_max / 1e3)
+        e2e["ms_per_step"] = e2e_max
+
+    # ---- roofline of the dominant stage
+    pk, pk_kind = peaks()
+    dom = max(per_stage, key=per_stage.get)
+    N, nb = cs.N, cs.N // 16
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    if dom == "raster":
+        byts = n * (N * N / 8 + 4 + 4 * N + 4 * nb * nb + 32) + wl.rects.nbytes + wl.rect_off.nbytes
+        ach = byts / (per_stage[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    elif dom == "cand_cos":
+        band = int(g[0][0] + g[0][2] + g[0][3])
+        ops = band * 4 * nb * nb
+        ach = ops / (per_stage[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak_tops(2070.0), "unit": "Tops/s"}
+    elif dom == "cand_edge":
+        # algorithmic work: every pair's E2/pre-alignment arithmetic (~24 int ops)
+        ops = total_pairs * 24
+        ach = ops / (per_stage[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak_tops(2070.0), "unit": "Tops/s"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": alu_peak_tops(2070.0), "unit": "Tops/s"}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["peak_source"] = pk_kind
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64/i32/f32", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {n} clips, {N}x{N} px, W={wl.window_dbu} dbu, "
+                               f"M={wl.marker_dbu} dbu, T=0.95, tol=4 dbu, both modes",
+                   "l2": "inputs > L2 and 512 MB flush between timed steps",
+                   "pairs_screened": total_pairs, "aligned_cosine": int(c[0]), "aligned_edge": int(c[1]),
+                   "passed_cosine": int(c[2]), "passed_edge": int(c[3]),
+                   "gates_cosine": {"G1": int(g[0][1]), "G3": int(g[0][3]), "G2": int(g[0][2])},
+                   "gates_edge": {"E2": int(g[1][5]), "E1": int(g[1][4])},
+                   "stage_ms": per_stage, "screened_pairs_per_s": 2 * total_pairs * world / (ms_max / 1e3),
+                   "wall_s_timed": wall},
+        "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None,
+    }
+    # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
+    # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2
+    line["gpu_launches"] = args.steps * (1 + 5 + 1 + 3 + 1 + 2)
+    if not args.no_cpu_baseline and world == 1:
+        n_s = args.cpu_sample or default_sample(args.config)
+        a, t, thr = oracle_sample(wl, n_s)
+        line["cpu_baseline"] = {"value": a / t, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"first {n_s} clips of the {args.config} set ({n_s*(n_s-1)//2} pairs "
+                                          f"screened both modes, {a} aligned), {t:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

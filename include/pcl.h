@@ -1,0 +1,271 @@
+/*
+ * pcl.h -- C ABI of the GB300 pairwise optimal-alignment similarity library.
+ *
+ * The library implements the data-parallel hot path of the layout-pattern
+ * clustering method of "An Optimal Alignment-Driven Iterative Closed-Loop
+ * Convergence Framework for High-Performance Ultra-Large Scale Layout Pattern
+ * Clustering" (arXiv 2512.13133): rasterisation of Manhattan clips
+ * (Sec. 2.2.1), the multi-stage lossless pre-screening (Sec. 3.1 stage 1),
+ * FFT phase correlation with the cosine test at the optimal shift
+ * (Sec. 3.2.1, Eqs. 2-5), the geometric Min-Max edge-displacement alignment
+ * (Sec. 3.2.2, Eq. 6), and the surprisal lazy-greedy set cover with the
+ * coarse-to-fine loop as host code (Sec. 3.3, Eqs. 7-9; Sec. 3.1 stages 2-4).
+ *
+ * Conventions shared by every call
+ *  - Every call returns pcl_status; no C++ exception crosses the ABI.
+ *    pcl_last_error(ctx) gives a message owned by the context.
+ *  - "d_" pointers are device pointers (any allocator: cudaMalloc, PyTorch,
+ *    ...), "h_" pointers are host pointers.  The caller owns every buffer it
+ *    passes and keeps it alive until the stream has passed the call.
+ *  - Device work is enqueued on the caller's stream and is asynchronous;
+ *    results are valid once the stream has reached the call.  Calls that
+ *    return counts write them to device memory for the same reason.
+ *  - A context is used by one host thread at a time.
+ *  - Geometry is integer dbu.  A clip is a W x W window; its rectangles
+ *    (x0, y0, x1, y1) are window-relative with x0 < x1, y0 < y1.  Manhattan
+ *    polygons enter as rectangle decompositions.
+ *  - Raster: N = W / p pixels per side; pixel (i, j) is 1 iff its centre
+ *    (p*i + p/2, p*j + p/2) lies in some rectangle (half-open), i.e. the
+ *    union of the rectangles sampled at pixel centres.
+ *  - Shift: s = (dx, dy) moves the member B onto the representative A;
+ *    c(s) = sum_x A(x) B(x - s) counts overlapping pixels (B is zero outside
+ *    its window).  Shifts are searched over the marker window
+ *    |dx|, |dy| <= S = M / p and reported in dbu.
+ */
+#ifndef PCL_H
+#define PCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pcl_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum pcl_status {
+    PCL_OK = 0,
+    PCL_ERR_INVALID = 1,     /* bad argument or parameter combination */
+    PCL_ERR_OOM = 2,         /* a library-owned allocation failed */
+    PCL_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    PCL_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    PCL_ERR_BUSY = 5,        /* output capacity too small / not admitted */
+    PCL_ERR_UNSUPPORTED = 6  /* valid request outside what the kernels cover */
+} pcl_status;
+
+enum { PCL_MODE_COSINE = 1, PCL_MODE_EDGE = 2 };
+enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1 };
+enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
+
+/* pcl_params.flags */
+enum {
+    PCL_P_NO_GATES = 1u << 0, /* match every listed pair without the lossless gates */
+    PCL_P_NO_PCM = 1u << 1    /* FFT engine: skip the phase-correlation surface */
+};
+
+/*
+ * Method parameters (Sec. 2: pattern window, marker region, cosine threshold
+ * T_cos of Eq. 2, edge tolerance T_edge of Sec. 2.2.2).
+ *   pitch_dbu    raster pitch p (dbu per pixel)
+ *   window_dbu   W, a multiple of p with N = W/p in {64, 128, 256, 512}
+ *   marker_dbu   M, shift half-range, a multiple of p; S = M/p <= N/16 for
+ *                the cosine engines (edge mode accepts any M >= 0)
+ *   cos_num/den  T_cos = num/den as an exact rational, 0 < num < den <= 65535
+ *   edge_tol_dbu T_edge >= 0 ("must not exceed")
+ *   cos_engine   PCL_ENGINE_*; shift_rule PCL_SHIFT_*
+ *   near_band    |sim - T| below which the cosine is re-evaluated in FP64
+ *   flags        PCL_P_*
+ */
+typedef struct pcl_params {
+    int32_t pitch_dbu;
+    int32_t window_dbu;
+    int32_t marker_dbu;
+    uint32_t cos_num;
+    uint32_t cos_den;
+    int32_t edge_tol_dbu;
+    uint32_t cos_engine;
+    uint32_t shift_rule;
+    float near_band;
+    uint32_t flags;
+} pcl_params;
+
+typedef struct pcl_pair {
+    uint32_t a, b; /* representative index (set A), member index (set B) */
+} pcl_pair;
+
+/* record flags: low 4 bits = rejecting gate (0 = none) */
+enum {
+    PCL_GATE_NONE = 0,
+    PCL_GATE_G1_AREA = 1,     /* sqrt(min|A|,|B| / max) <= T */
+    PCL_GATE_G2_PROFILE = 2,  /* row/column projection bound */
+    PCL_GATE_G3_DENSITY = 3,  /* 16x16 block-density bound */
+    PCL_GATE_E1_MATCH = 4,    /* no polygon correspondence at the pre-alignment */
+    PCL_GATE_E2_BBOX = 5,     /* bbox size differs by more than 2*tol */
+    PCL_GATE_BAD_INDEX = 15,  /* pair index outside its clip set (no work done) */
+    PCL_F_NEAR_BAND = 1u << 4,
+    PCL_F_FFT_GUARD = 1u << 5,   /* FFT residual too large: exact scan used */
+    PCL_F_PCM_AGREES = 1u << 6,  /* phase-correlation peak == exact argmax */
+    PCL_F_EDGE_VERIFY_FAIL = 1u << 7,
+    PCL_F_EMPTY = 1u << 8,       /* both clips empty: similar by definition */
+    PCL_F_ALIGNED = 1u << 9      /* the pair reached the alignment engine */
+};
+
+/*
+ * One record per matched pair (40 bytes).
+ *   cosine: dx/dy = best shift (dbu) applied to b, sim = c_best / sqrt(|A||B|) (FP32,
+ *           FP64-evaluated inside the near band), score = c_best (overlap pixels),
+ *           pcm_dx/dy = phase-correlation peak (dbu)
+ *   edge:   dx/dy = Min-Max translation T (dbu), sim = score = max(E_x, E_y)
+ *   pass:   the exact decision (integer rule), mode: PCL_MODE_*
+ */
+typedef struct pcl_record {
+    uint32_t a, b;
+    int32_t dx_dbu, dy_dbu;
+    float sim;
+    uint32_t score;
+    int32_t pcm_dx_dbu, pcm_dy_dbu;
+    uint16_t flags;
+    uint8_t pass;
+    uint8_t mode;
+    uint32_t reserved;
+} pcl_record;
+
+/*
+ * A clip set: the caller allocates every buffer (device memory, sizes from
+ * pcl_clipset_sizes) and fills rect_off/rects; the library fills the rest.
+ *   rect_off [n+1] u32   clip i owns rects[4*rect_off[i] .. 4*rect_off[i+1])
+ *   rects    [4R]  i32   x0, y0, x1, y1 (window-relative dbu)
+ *   bits     [n][N][N/64] u64   raster rows; bit t of word w = pixel 64w+t
+ *   pop      [n] u32     |A| (ones of the raster)
+ *   prof     [n][2N] u16 row counts r(j), then column counts q(i)
+ *   blk      [n][2*nb*nb] u16  16x16 block counts, then their neighbourhood
+ *                        sums over (2*ceil(S/16)+1)^2 blocks (nb = N/16)
+ *   esig     [n][8] i32  edge signature: n_rects, has_x, lo_x, hi_x, has_y,
+ *                        lo_y, hi_y, touches_border (non-border edges only)
+ *   spec     [n][L][Ls] float2 or NULL   cached R2C spectrum of the raster
+ *                        zero-padded to L = 9N/8 (rows ky, columns kx < L/2+1)
+ *   spec_state [n] u8 or NULL            1 once spec[i] holds the spectrum
+ */
+typedef struct pcl_clipset {
+    uint32_t n_clips;
+    uint32_t reserved;
+    const uint32_t *rect_off;
+    const int32_t *rects;
+    uint64_t *bits;
+    uint32_t *pop;
+    uint16_t *prof;
+    uint16_t *blk;
+    int32_t *esig;
+    void *spec;
+    uint8_t *spec_state;
+} pcl_clipset;
+
+/* bytes of each clip-set buffer for n clips (spec may be sized 0 by the
+   caller when the cosine FFT engine is not used) */
+typedef struct pcl_clipset_sizes {
+    uint64_t bits, pop, prof, blk, esig, spec, spec_state;
+    int32_t N, S, L, Ls; /* raster side, shift half-range, FFT side, FFT row stride */
+} pcl_clipset_sizes;
+
+typedef struct pcl_ctx pcl_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device` (made current on every
+   call).  Errors: PCL_ERR_INVALID (NULL out / no such device). */
+pcl_status pcl_create(pcl_ctx **out, int device);
+/* Destroy; frees the context's grow-only device workspace.  NULL is a no-op. */
+void pcl_destroy(pcl_ctx *ctx);
+/* Message of the last failed call on ctx ("" if none); owned by ctx. */
+const char *pcl_last_error(const pcl_ctx *ctx);
+const char *pcl_status_string(pcl_status s);
+
+/* Check a parameter block (rules listed at pcl_params). */
+pcl_status pcl_params_validate(const pcl_params *P);
+
+/* Buffer sizes of a clip set of n clips under P.  Errors: PCL_ERR_INVALID. */
+pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n_clips, pcl_clipset_sizes *out);
+
+/* ---- a1: rasterisation + signatures (Sec. 2.2.1 step 1) --------------------
+   Fills bits, pop, prof, blk, esig of every clip from rect_off/rects and
+   clears spec_state.  One CTA per clip.  Errors: PCL_ERR_INVALID (params or
+   NULL buffer), PCL_ERR_CUDA (launch). */
+pcl_status pcl_rasterize(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, pcl_stream stream);
+
+/* ---- a3: forward FFT cache (Sec. 3.2.1, Eq. 3) ---------------------------
+   Computes spec[i] for every clip i with spec_state[i] == 0 (or, with
+   d_list != NULL, for the n_list listed clips) and sets spec_state[i] = 1.
+   Requires cs->spec and cs->spec_state.  Errors: PCL_ERR_INVALID,
+   PCL_ERR_UNSUPPORTED (S > N/16), PCL_ERR_CUDA. */
+pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const uint32_t *d_list,
+                       uint32_t n_list, pcl_stream stream);
+
+/* ---- a2: lossless pre-screening + candidate generation (Sec. 3.1 stage 1) --
+   Self-join of cs: emits every pair (a < b) that no gate of `mode` rejects.
+   COSINE: area-sorted band join (exactly the G1 survivors), then G3 density
+   and G2 profile bounds.  EDGE: all pairs, E2 bbox then E1 correspondence at
+   the pre-alignment.  Pairs are written to d_out[0 .. min(count, cap)) in
+   unspecified order; *d_count (u64, device) receives the survivor count,
+   which may exceed cap (then re-run with a larger buffer).  d_gate_counts
+   (u64[16], device, may be NULL) is incremented: [0] survivors, [g] pairs
+   rejected by gate g.  Uses the context workspace.
+   Errors: PCL_ERR_INVALID, PCL_ERR_OOM (workspace), PCL_ERR_CUDA. */
+pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
+                          pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
+                          pcl_stream stream);
+
+/* ---- a4-a7: alignment + decision for listed pairs ------------------------
+   One record per pair, in list order, pair (a, b) = (clip a of set A, clip b
+   of set B).  Gates of the mode run first unless PCL_P_NO_GATES.
+   COSINE (Sec. 3.2.1 + Eq. 2): cross-power spectrum of the cached spectra,
+   one packed inverse FFT pruned to the marker window giving the phase-
+   correlation surface (Eq. 5) and the correlation c(s); exact integer argmax
+   with the tie order (-c, |dx|+|dy|, dy, dx); c_best verified by popcount;
+   decision den^2 c_best^2 > num^2 |A||B|.  Spectra of referenced clips are
+   computed first when missing (spec_state == 0).
+   EDGE (Sec. 2.2.2 + Eq. 6): pre-alignment, correspondence, per-axis
+   d_min/d_max of matched non-border edges, T = trunc((d_min+d_max)/2)
+   clamped to +/-M, E = max(T - d_min, d_max - T), re-check at T,
+   pass iff E_x, E_y <= tol.
+   d_n (u64, device, may be NULL): when given, only the first min(n, *d_n)
+   pairs are processed, so a candidate list can be matched without reading
+   its length back to the host; records past that count are not written.
+   Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED, PCL_ERR_CUDA. */
+pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl_clipset *a,
+                           pcl_clipset *b, const pcl_pair *d_pairs, uint64_t n, const uint64_t *d_n,
+                           pcl_record *d_out, pcl_stream stream);
+
+/* Passing pairs of d_rec[0..min(n, *d_n)) as (a, b), order unspecified
+   (d_n as in pcl_match_pairs, may be NULL); *d_count (u64, device) receives
+   the count (may exceed cap).  Errors: PCL_ERR_INVALID, PCL_ERR_CUDA. */
+pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,
+                            pcl_pair *d_out, uint64_t cap, uint64_t *d_count, pcl_stream stream);
+
+/* ---- a11: host set cover + coarse-to-fine loop (Sec. 3.3, Sec. 3.1) -------
+   Surprisal lazy greedy over the undirected graph h_edges[0..n_edges) on
+   n_nodes nodes: f_i = 1 + deg(i), S_i = floor(2^32 / f_i), Score_j =
+   S_j + sum of S_k over uncovered neighbours (Eqs. 7-9); candidates are the
+   uncovered nodes; ties: higher score, then lower index.  h_order receives
+   the selected representatives in selection order (*n_selected of them),
+   h_rep_of[i] the representative that first covered i.  Pure host code.
+   Errors: PCL_ERR_INVALID (edge index out of range / NULL). */
+pcl_status pcl_setcover(const pcl_pair *h_edges, uint64_t n_edges, uint32_t n_nodes,
+                        uint32_t *h_rep_of, uint32_t *h_order, uint32_t *n_selected);
+
+/* Coarse-to-fine loop over candidate pairs h_pairs[0..m) with per-pair
+   strict and relaxed decisions (u8 0/1): each round runs the set cover on
+   the relaxed graph of the remaining clips, accepts members that pass the
+   strict test against their representative, lets orphans try the
+   representatives so far in index order, and re-injects the rest.  Ends
+   when every clip is assigned.  h_rep_of[n_nodes] out; *n_clusters,
+   *n_rounds out.  Pure host code.  Errors: PCL_ERR_INVALID. */
+pcl_status pcl_cluster_loop(const pcl_pair *h_pairs, const uint8_t *h_strict,
+                            const uint8_t *h_relaxed, uint64_t m, uint32_t n_nodes,
+                            uint32_t *h_rep_of, uint32_t *n_clusters, uint32_t *n_rounds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCL_H */

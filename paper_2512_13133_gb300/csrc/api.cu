@@ -1,0 +1,298 @@
+// C ABI of the pcl library: context, parameter checks, clip-set sizes and the
+// entry points of include/pcl.h.  Kernels live in raster.cu, gates.cu,
+// edge.cu and fft.cu; the host set cover and loop in host_scp.cpp.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+namespace pcl {
+cudaError_t launch_raster(const pcl_params &, const pcl_clipset &, cudaStream_t);
+size_t band_join_workspace(const Geo &, uint32_t);
+cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
+                             unsigned long long *, unsigned long long *, int, cudaStream_t);
+cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
+                               unsigned long long *, unsigned long long *, cudaStream_t);
+cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
+                              uint64_t, const unsigned long long *, pcl_record *, cudaStream_t);
+cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool,
+                           cudaStream_t);
+cudaError_t launch_mark(const pcl_pair *, uint64_t, const unsigned long long *, pcl_clipset &, pcl_clipset &,
+                        cudaStream_t);
+cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
+                            uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
+cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
+                           unsigned long long *, cudaStream_t);
+}  // namespace pcl
+
+struct pcl_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+using namespace pcl;
+
+namespace {
+
+pcl_status fail(pcl_ctx *ctx, pcl_status s, const char *fmt, const char *a = "", long long b = 0) {
+    if (ctx) {
+        char buf[512];
+        snprintf(buf, sizeof buf, fmt, a, b);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+pcl_status cuda_fail(pcl_ctx *ctx, cudaError_t e, const char *where) {
+    if (ctx) ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return PCL_ERR_CUDA;
+}
+
+pcl_status enter(pcl_ctx *ctx) {
+    if (!ctx) return PCL_ERR_INVALID;
+    ctx->err.clear();
+    const cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return PCL_OK;
+}
+
+pcl_status ensure_ws(pcl_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return PCL_OK;
+    if (ctx->ws) {
+        cudaFree(ctx->ws);  // synchronises the device: no kernel still uses it
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    const size_t want = bytes + bytes / 4 + 4096;
+    const cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return fail(ctx, PCL_ERR_OOM, "workspace allocation of %s%lld bytes failed", "", (long long)want);
+    }
+    ctx->ws_bytes = want;
+    return PCL_OK;
+}
+
+bool pow2_raster(int N) { return N == 64 || N == 128 || N == 256 || N == 512; }
+
+pcl_status check_clipset(pcl_ctx *ctx, const pcl_clipset *cs, bool need_edge_or_raster) {
+    if (!cs) return fail(ctx, PCL_ERR_INVALID, "clip set is NULL%s%lld");
+    if (cs->n_clips && (!cs->rect_off || !cs->rects || !cs->bits || !cs->pop || !cs->prof || !cs->blk ||
+                        (need_edge_or_raster && !cs->esig)))
+        return fail(ctx, PCL_ERR_INVALID, "clip set has a NULL buffer%s%lld");
+    return PCL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pcl_status_string(pcl_status s) {
+    switch (s) {
+        case PCL_OK: return "ok";
+        case PCL_ERR_INVALID: return "invalid argument";
+        case PCL_ERR_OOM: return "out of device memory";
+        case PCL_ERR_CUDA: return "CUDA error";
+        case PCL_ERR_TIMEOUT: return "device wait timed out";
+        case PCL_ERR_BUSY: return "busy / capacity too small";
+        case PCL_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+pcl_status pcl_create(pcl_ctx **out, int device) {
+    if (!out) return PCL_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return PCL_ERR_INVALID;
+    }
+    pcl_ctx *c = new (std::nothrow) pcl_ctx;
+    if (!c) return PCL_ERR_OOM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PCL_ERR_CUDA;
+    }
+    *out = c;
+    return PCL_OK;
+}
+
+void pcl_destroy(pcl_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->ws) {
+        cudaSetDevice(ctx->device);
+        cudaFree(ctx->ws);
+    }
+    delete ctx;
+}
+
+const char *pcl_last_error(const pcl_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+pcl_status pcl_params_validate(const pcl_params *P) {
+    if (!P) return PCL_ERR_INVALID;
+    if (P->pitch_dbu <= 0 || P->window_dbu <= 0 || P->window_dbu % P->pitch_dbu) return PCL_ERR_INVALID;
+    if (!pow2_raster(P->window_dbu / P->pitch_dbu)) return PCL_ERR_INVALID;
+    if (P->marker_dbu < 0 || P->marker_dbu % P->pitch_dbu) return PCL_ERR_INVALID;
+    if (P->marker_dbu / P->pitch_dbu > 64) return PCL_ERR_INVALID;
+    if (P->cos_den == 0 || P->cos_den > 65535 || P->cos_num == 0 || P->cos_num >= P->cos_den)
+        return PCL_ERR_INVALID;
+    if (P->edge_tol_dbu < 0) return PCL_ERR_INVALID;
+    if (P->cos_engine > PCL_ENGINE_TC_DIRECT || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
+    if (!(P->near_band >= 0.0f)) return PCL_ERR_INVALID;
+    return PCL_OK;
+}
+
+pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n, pcl_clipset_sizes *o) {
+    if (!o || pcl_params_validate(P) != PCL_OK) return PCL_ERR_INVALID;
+    const Geo g = make_geo(*P);
+    o->bits = 8ull * n * g.N * g.nw;
+    o->pop = 4ull * n;
+    o->prof = 2ull * n * 2 * g.N;
+    o->blk = 2ull * n * 2 * g.nb * g.nb;
+    o->esig = 32ull * n;
+    o->spec = 8ull * n * g.L * g.Ls;
+    o->spec_state = n;
+    o->N = g.N;
+    o->S = g.S;
+    o->L = g.L;
+    o->Ls = g.Ls;
+    return PCL_OK;
+}
+
+pcl_status pcl_rasterize(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, pcl_stream stream) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    if ((s = check_clipset(ctx, cs, true))) return s;
+    const cudaError_t e = launch_raster(*P, *cs, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "raster kernel");
+}
+
+pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const uint32_t *d_list,
+                       uint32_t n_list, pcl_stream stream) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    if ((s = check_clipset(ctx, cs, false))) return s;
+    if (!cs->spec || !cs->spec_state) return fail(ctx, PCL_ERR_INVALID, "spec / spec_state buffers missing%s%lld");
+    const Geo g = make_geo(*P);
+    if (g.N > 256) return fail(ctx, PCL_ERR_UNSUPPORTED, "FFT engine covers N <= 256 (got N = %s%lld)", "", g.N);
+    const cudaError_t e = launch_spectra(*P, *cs, d_list, n_list, false, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "spectra kernel");
+}
+
+pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
+                          pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
+                          pcl_stream stream) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    if ((s = check_clipset(ctx, cs, mode == PCL_MODE_EDGE))) return s;
+    if (!d_count || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL output%s%lld");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    auto *cnt = reinterpret_cast<unsigned long long *>(d_count);
+    auto *gates = reinterpret_cast<unsigned long long *>(d_gate_counts);
+    if (mode == PCL_MODE_COSINE) {
+        const Geo g = make_geo(*P);
+        if (g.S > g.N / 16) return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine gates need S <= N/16%s%lld");
+        const size_t need = band_join_workspace(g, cs->n_clips);
+        if ((s = ensure_ws(ctx, need))) return s;
+        e = launch_band_join(*P, *cs, ctx->ws, ctx->ws_bytes, d_out, cap, cnt, gates, ctx->num_sms, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "band join");
+    }
+    if (mode == PCL_MODE_EDGE) {
+        e = launch_edge_screen(*P, *cs, d_out, cap, cnt, gates, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge screen");
+    }
+    return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
+}
+
+pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl_clipset *a, pcl_clipset *b,
+                           const pcl_pair *d_pairs, uint64_t n, const uint64_t *d_n, pcl_record *d_out,
+                           pcl_stream stream) {
+    const auto *dn = reinterpret_cast<const unsigned long long *>(d_n);
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    if ((s = check_clipset(ctx, a, mode == PCL_MODE_EDGE)) || (s = check_clipset(ctx, b, mode == PCL_MODE_EDGE)))
+        return s;
+    if (n && (!d_pairs || !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL pair list or output%s%lld");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (mode == PCL_MODE_EDGE) {
+        e = launch_edge_match(*P, *a, *b, d_pairs, n, dn, d_out, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge match");
+    }
+    if (mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
+    const Geo g = make_geo(*P);
+    if (P->cos_engine != PCL_ENGINE_FFT_PCM)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine engine %s%lld not built", "", P->cos_engine);
+    if (g.N > 256 || g.S > g.N / 16)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "FFT engine covers N <= 256 and S <= N/16%s%lld");
+    if (!a->spec || !a->spec_state || !b->spec || !b->spec_state)
+        return fail(ctx, PCL_ERR_INVALID, "spec / spec_state buffers missing%s%lld");
+    if ((e = launch_mark(d_pairs, n, dn, *a, *b, st)) != cudaSuccess) return cuda_fail(ctx, e, "mark");
+    if ((e = launch_spectra(*P, *a, nullptr, 0, true, st)) != cudaSuccess) return cuda_fail(ctx, e, "spectra");
+    if (b->spec_state != a->spec_state &&
+        (e = launch_spectra(*P, *b, nullptr, 0, true, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "spectra");
+    e = launch_pair_fft(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "pair fft");
+}
+
+pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,
+                            pcl_pair *d_out, uint64_t cap, uint64_t *d_count, pcl_stream stream) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (!d_count || (n && !d_rec) || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL argument%s%lld");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st);
+    if (e == cudaSuccess)
+        e = launch_compact(d_rec, n, reinterpret_cast<const unsigned long long *>(d_n), d_out, cap,
+                           reinterpret_cast<unsigned long long *>(d_count), st);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "compact");
+}
+
+}  // extern "C"
+
+namespace pcl {
+namespace {
+__global__ void compact_kernel(const pcl_record *rec, uint64_t n, const unsigned long long *d_n, pcl_pair *out,
+                               uint64_t cap, unsigned long long *count) {
+    if (d_n && *d_n < n) n = *d_n;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = base + threadIdx.x;
+        const bool keep = t < n && rec[t].pass;
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (!mask) continue;
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        unsigned long long b0 = 0;
+        if (lane == leader) b0 = atomicAdd(count, (unsigned long long)__popc(mask));
+        b0 = __shfl_sync(0xffffffffu, b0, leader);
+        if (keep) {
+            const unsigned long long idx = b0 + __popc(mask & ((1u << lane) - 1u));
+            if (idx < cap) out[idx] = pcl_pair{rec[t].a, rec[t].b};
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_compact(const pcl_record *rec, uint64_t n, const unsigned long long *d_n, pcl_pair *out,
+                           uint64_t cap, unsigned long long *count, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    compact_kernel<<<1024, 256, 0, st>>>(rec, n, d_n, out, cap, count);
+    return cudaGetLastError();
+}
+}  // namespace pcl

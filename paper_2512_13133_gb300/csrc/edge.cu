@@ -1,0 +1,269 @@
+// a2 (edge gates) and a7: edge-displacement mode (Sec. 2.2.2) with the
+// geometric Min-Max closed form of Sec. 3.2.2 (Eq. 6).
+//
+// Integer dbu throughout.  One thread evaluates one pair: the polygon lists
+// are short (tens of rectangles) and the procedure is a handful of O(n_A n_B)
+// scans with early exits, so per-thread evaluation keeps every lane busy on
+// its own pair instead of idling lanes on small clips.  Partners are
+// recomputed by scanning rather than stored, so no per-thread arrays are
+// needed for any polygon count.
+#include <climits>
+
+#include "common.cuh"
+
+namespace pcl {
+
+namespace {
+
+struct EdgeOut {
+    int gate;      // PCL_GATE_* (0: passed the gates)
+    int tx, ty;    // translation applied to B (dbu)
+    int E;         // max(E_x, E_y)
+    bool verified; // correspondence unchanged at T
+    bool pass;
+    bool empty;
+};
+
+__device__ __forceinline__ bool ovl(const int4 a, const int4 b, int tx, int ty) {
+    return a.x < b.z + tx && b.x + tx < a.z && a.y < b.w + ty && b.y + ty < a.w;
+}
+
+// partner of small-side polygon k at shift (tx, ty): index in the large list,
+// -1 if none, -2 if more than one.
+__device__ __forceinline__ int partner(const int4 *__restrict__ rs, const int4 *__restrict__ rl, int nl,
+                                       bool small_is_a, int k, int tx, int ty) {
+    const int4 s = __ldg(rs + k);
+    int who = -1;
+    for (int m = 0; m < nl; ++m) {
+        const int4 l = __ldg(rl + m);
+        const bool hit = small_is_a ? ovl(s, l, tx, ty) : ovl(l, s, tx, ty);
+        if (hit) {
+            if (who >= 0) return -2;
+            who = m;
+        }
+    }
+    return who;
+}
+
+// correspondence (Sec. 2.2.2 condition 1) at shift t, with injectivity
+__device__ bool correspond(const int4 *rs, int ns, const int4 *rl, int nl, bool small_is_a, int tx,
+                           int ty) {
+    for (int k = 0; k < ns; ++k)
+        if (partner(rs, rl, nl, small_is_a, k, tx, ty) < 0) return false;
+    // every small polygon has exactly one partner; the map is injective iff no
+    // large polygon overlaps two small polygons
+    for (int m = 0; m < nl; ++m) {
+        const int4 l = __ldg(rl + m);
+        int cnt = 0;
+        for (int k = 0; k < ns && cnt < 2; ++k) {
+            const int4 s = __ldg(rs + k);
+            cnt += (small_is_a ? ovl(s, l, tx, ty) : ovl(l, s, tx, ty)) ? 1 : 0;
+        }
+        if (cnt > 1) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Gates E2 and E1 and, unless screen_only, the full Min-Max procedure.
+__device__ EdgeOut edge_eval(const int4 *ra, const int32_t *ea, const int4 *rb, const int32_t *eb,
+                             int W, int M, int tol, bool gates, bool screen_only) {
+    EdgeOut o{};
+    const int na = ea[ES_N], nb = eb[ES_N];
+    if (na == 0 && nb == 0) {
+        o.empty = true;
+        o.pass = true;
+        o.verified = true;
+        return o;
+    }
+    if (na == 0 || nb == 0) {
+        o.gate = PCL_GATE_E1_MATCH;
+        return o;
+    }
+    const int lxa = ea[ES_LOX], uxa = ea[ES_HIX], lya = ea[ES_LOY], uya = ea[ES_HIY];
+    const int lxb = eb[ES_LOX], uxb = eb[ES_HIX], lyb = eb[ES_LOY], uyb = eb[ES_HIY];
+    if (gates && na == nb && !ea[ES_BORDER] && !eb[ES_BORDER]) {
+        // E2: with a bijection and no border edges every displacement lies in
+        // [T - tol, T + tol], so the bbox sizes differ by at most 2 tol
+        if (abs((uxa - lxa) - (uxb - lxb)) > 2 * tol || abs((uya - lya) - (uyb - lyb)) > 2 * tol) {
+            o.gate = PCL_GATE_E2_BBOX;
+            return o;
+        }
+    }
+    // pre-alignment: difference of the bbox centres (doubled centres halved,
+    // truncated toward zero), clamped to the marker window
+    const int s0x = (ea[ES_HASX] && eb[ES_HASX]) ? clampi(((lxa + uxa) - (lxb + uxb)) / 2, -M, M) : 0;
+    const int s0y = (ea[ES_HASY] && eb[ES_HASY]) ? clampi(((lya + uya) - (lyb + uyb)) / 2, -M, M) : 0;
+    const bool small_is_a = na <= nb;
+    const int4 *rs = small_is_a ? ra : rb;
+    const int4 *rl = small_is_a ? rb : ra;
+    const int ns = small_is_a ? na : nb, nl = small_is_a ? nb : na;
+    o.tx = s0x;
+    o.ty = s0y;
+    if (!correspond(rs, ns, rl, nl, small_is_a, s0x, s0y)) {
+        o.gate = PCL_GATE_E1_MATCH;
+        return o;
+    }
+    if (screen_only) return o;
+    // displacements d = e_A - e_B of matched edges off the window border
+    int cx = 0, cy = 0, dminx = INT_MAX, dmaxx = INT_MIN, dminy = INT_MAX, dmaxy = INT_MIN;
+    for (int k = 0; k < ns; ++k) {
+        const int m = partner(rs, rl, nl, small_is_a, k, s0x, s0y);
+        const int4 pa = __ldg(small_is_a ? ra + k : ra + m);
+        const int4 pb = __ldg(small_is_a ? rb + m : rb + k);
+        if (pa.x != 0 && pb.x != 0) { const int d = pa.x - pb.x; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
+        if (pa.z != W && pb.z != W) { const int d = pa.z - pb.z; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
+        if (pa.y != 0 && pb.y != 0) { const int d = pa.y - pb.y; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
+        if (pa.w != W && pb.w != W) { const int d = pa.w - pb.w; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
+    }
+    // Eq. 6 per separable axis: midpoint (trunc toward zero), clamped
+    const int Tx = cx ? clampi((dminx + dmaxx) / 2, -M, M) : s0x;
+    const int Ty = cy ? clampi((dminy + dmaxy) / 2, -M, M) : s0y;
+    const int Ex = cx ? max(Tx - dminx, dmaxx - Tx) : 0;
+    const int Ey = cy ? max(Ty - dminy, dmaxy - Ty) : 0;
+    // the correspondence must hold at T with the same partners
+    bool ok = true;
+    for (int k = 0; k < ns && ok; ++k) {
+        const int m0 = partner(rs, rl, nl, small_is_a, k, s0x, s0y);
+        const int m1 = partner(rs, rl, nl, small_is_a, k, Tx, Ty);
+        ok = (m0 == m1);
+    }
+    o.tx = Tx;
+    o.ty = Ty;
+    o.E = max(Ex, Ey);
+    o.verified = ok;
+    o.pass = ok && Ex <= tol && Ey <= tol;
+    return o;
+}
+
+__device__ __forceinline__ void emit_pair(pcl_pair *out, uint64_t cap, unsigned long long *count,
+                                          bool keep, uint32_t a, uint32_t b) {
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep) {
+        const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+        if (idx < cap) out[idx] = pcl_pair{a, b};
+    }
+}
+
+constexpr int kTileI = 8;
+
+// Self-join screen: block (bx, by) covers rows i in [kTileI bx, kTileI bx +
+// kTileI) and columns j in [256 by, 256 by + 256); pairs with i < j only.
+__global__ void __launch_bounds__(256) edge_screen_kernel(pcl_params prm, pcl_clipset cs,
+                                                          pcl_pair *out, uint64_t cap,
+                                                          unsigned long long *count,
+                                                          unsigned long long *gates) {
+    const uint32_t n = cs.n_clips;
+    const uint32_t j = blockIdx.y * 256u + threadIdx.x;
+    const uint32_t i0 = blockIdx.x * kTileI;
+    if (i0 >= n || i0 > blockIdx.y * 256u + 255u) return;  // whole block below the diagonal
+    const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
+    const bool jv = j < n;
+    int32_t eb[8];
+    const int4 *rb = nullptr;
+    if (jv) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) eb[k] = __ldg(cs.esig + (size_t)j * 8 + k);
+        rb = reinterpret_cast<const int4 *>(cs.rects) + __ldg(cs.rect_off + j);
+    }
+    uint32_t g_e1 = 0, g_e2 = 0, kept = 0;
+    for (int t = 0; t < kTileI; ++t) {
+        const uint32_t i = i0 + t;
+        bool keep = false;
+        if (jv && i < n && i < j) {
+            int32_t ea[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ea[k] = __ldg(cs.esig + (size_t)i * 8 + k);
+            const int4 *ra = reinterpret_cast<const int4 *>(cs.rects) + __ldg(cs.rect_off + i);
+            const EdgeOut o = edge_eval(ra, ea, rb, eb, W, M, tol, true, true);
+            if (o.gate == PCL_GATE_E1_MATCH) ++g_e1;
+            else if (o.gate == PCL_GATE_E2_BBOX) ++g_e2;
+            else { keep = true; ++kept; }
+        }
+        emit_pair(out, cap, count, keep, i, j);
+    }
+    // gate counters: one atomic per warp and counter
+    g_e1 = __reduce_add_sync(0xffffffffu, g_e1);
+    g_e2 = __reduce_add_sync(0xffffffffu, g_e2);
+    kept = __reduce_add_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && gates) {
+        if (kept) atomicAdd(gates + 0, (unsigned long long)kept);
+        if (g_e1) atomicAdd(gates + PCL_GATE_E1_MATCH, (unsigned long long)g_e1);
+        if (g_e2) atomicAdd(gates + PCL_GATE_E2_BBOX, (unsigned long long)g_e2);
+    }
+}
+
+__global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
+                                                         const pcl_pair *pairs, uint64_t n,
+                                                         const unsigned long long *d_n, pcl_record *out) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d_n && *d_n < n) n = *d_n;
+    if (t >= n) return;
+    const pcl_pair pr = pairs[t];
+    pcl_record r{};
+    r.a = pr.a;
+    r.b = pr.b;
+    r.mode = PCL_MODE_EDGE;
+    if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
+        r.flags = PCL_GATE_BAD_INDEX;
+        out[t] = r;
+        return;
+    }
+    int32_t ea[8], eb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        ea[k] = __ldg(A.esig + (size_t)pr.a * 8 + k);
+        eb[k] = __ldg(B.esig + (size_t)pr.b * 8 + k);
+    }
+    const int4 *ra = reinterpret_cast<const int4 *>(A.rects) + __ldg(A.rect_off + pr.a);
+    const int4 *rb = reinterpret_cast<const int4 *>(B.rects) + __ldg(B.rect_off + pr.b);
+    const bool gates = !(prm.flags & PCL_P_NO_GATES);
+    const EdgeOut o = edge_eval(ra, ea, rb, eb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu,
+                                gates, false);
+    r.dx_dbu = o.tx;
+    r.dy_dbu = o.ty;
+    if (o.empty) {
+        r.flags = PCL_F_EMPTY;
+        r.pass = 1;
+    } else if (o.gate) {
+        r.flags = (uint16_t)o.gate;
+    } else {
+        r.flags = PCL_F_ALIGNED | (o.verified ? 0 : PCL_F_EDGE_VERIFY_FAIL);
+        r.score = (uint32_t)o.E;
+        r.sim = (float)o.E;
+        r.pass = o.pass ? 1 : 0;
+    }
+    out[t] = r;
+}
+
+}  // namespace
+
+cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl_pair *out,
+                               uint64_t cap, unsigned long long *count, unsigned long long *gates,
+                               cudaStream_t st) {
+    const uint32_t n = cs.n_clips;
+    if (n < 2) return cudaSuccess;
+    dim3 grid((n + kTileI - 1) / kTileI, (n + 255) / 256);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    edge_screen_kernel<<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_match(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
+                              const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
+                              cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    edge_match_kernel<<<(unsigned)blocks, 256, 0, st>>>(prm, a, b, pairs, n, d_n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pcl

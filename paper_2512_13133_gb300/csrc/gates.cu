@@ -1,0 +1,186 @@
+// a2: lossless multi-stage pre-screening for cosine mode (Sec. 3.1 stage 1)
+// and the area-sorted band join that generates candidate pairs.
+//
+// Every gate is an upper bound on the overlap c(s) for all shifts of the
+// marker window, compared with the exact integer threshold rule of Eq. 2, so
+// a rejected pair can never pass:
+//   G1 area     c(s) <= min(|A|, |B|)  ->  den^2 min > num^2 max required
+//   G3 density  the ones of A in a 16x16 block can only meet ones of B in the
+//               block's neighbourhood: c <= sum_k min(cnt_A(k), nbr_B(k)),
+//               taken both ways
+//   G2 profile  c(dx, dy) <= sum_j min(r_A(j), r_B(j - dy)); the best dy
+//               bounds every shift; same with column counts
+// Evaluation order G1 -> G3 -> G2 (cheapest first); a rejected pair records
+// the first gate that rejects it.
+//
+// Candidate generation: G1 passes exactly when the larger area is below
+// den^2/num^2 times the smaller one, so after a counting sort of the clips by
+// area every G1 survivor (i, j) lies in the band of positions
+// (p, end_p) with end_p = #{clips with area <= floor((den^2 a_p - 1)/num^2)}.
+// Warps take positions p from a global counter and test G3 and G2 on every
+// band member with the whole warp.
+#include "gates.cuh"
+
+namespace pcl {
+
+namespace {
+
+__global__ void hist_kernel(const uint32_t *pop, uint32_t n, uint32_t *hist) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(hist + pop[i], 1u);
+}
+
+// exclusive scan of v[0..m) into v (single CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *v, uint32_t m) {
+    __shared__ uint32_t wsum[32];
+    const uint32_t per = (m + 1023) / 1024;
+    const uint32_t lo = threadIdx.x * per, hi = min(m, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += v[i];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (wid ? wsum[wid - 1] : 0u);
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t t = v[i];
+        v[i] = run;
+        run += t;
+    }
+}
+
+__global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *cum, uint32_t *fill,
+                               uint32_t *order, uint32_t *spop) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = pop[i];
+        const uint32_t pos = cum[v] + atomicAdd(fill + v, 1u);
+        order[pos] = i;
+        spop[pos] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
+                                                        const uint32_t *spop, const uint32_t *cum,
+                                                        uint32_t vmax_all, pcl_pair *out, uint64_t cap,
+                                                        unsigned long long *count,
+                                                        unsigned long long *local_gates,
+                                                        unsigned int *next_pos) {
+    const Geo g = make_geo(prm);
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = cs.n_clips;
+    const uint64_t num2 = (uint64_t)prm.cos_num * prm.cos_num, den2 = (uint64_t)prm.cos_den * prm.cos_den;
+    unsigned long long kept = 0, g2 = 0, g3 = 0;
+    for (;;) {
+        uint32_t p = 0;
+        if (lane == 0) p = atomicAdd(next_pos, 1u);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= n) break;
+        const uint32_t a = order[p];
+        const uint64_t pa = spop[p];
+        uint64_t vmax = pa == 0 ? 0 : (den2 * pa - 1) / num2;
+        if (vmax > vmax_all) vmax = vmax_all;
+        const uint32_t end = cum[vmax + 1];
+        for (uint32_t q = p + 1; q < end; ++q) {
+            const uint32_t b = order[q];
+            const uint64_t pb = spop[q];
+            bool keep = true;
+            if (!(pa == 0 && pb == 0)) {
+                const int nb2 = g.nb * g.nb;
+                const uint32_t u3 =
+                    warp_g3(cs.blk + (size_t)a * 2 * nb2, cs.blk + (size_t)b * 2 * nb2, nb2, lane);
+                if (!cos_exceeds(u3, pa, pb, prm.cos_num, prm.cos_den)) {
+                    ++g3;
+                    continue;
+                }
+                const uint32_t u2 = warp_g2(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)b * 2 * g.N,
+                                            g.N, g.S, lane);
+                if (!cos_exceeds(u2, pa, pb, prm.cos_num, prm.cos_den)) {
+                    ++g2;
+                    continue;
+                }
+            }
+            if (keep) {
+                ++kept;
+                if (lane == 0) {
+                    const unsigned long long idx = atomicAdd(count, 1ull);
+                    if (idx < cap) out[idx] = pcl_pair{min(a, b), max(a, b)};
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        if (kept) atomicAdd(local_gates + 0, kept);
+        if (g2) atomicAdd(local_gates + PCL_GATE_G2_PROFILE, g2);
+        if (g3) atomicAdd(local_gates + PCL_GATE_G3_DENSITY, g3);
+    }
+}
+
+// add this call's gate counts to the caller's array; G1 = all pairs minus the
+// pairs the band join enumerated
+__global__ void finish_gates_kernel(const unsigned long long *local, unsigned long long *gates,
+                                    unsigned long long total) {
+    if (threadIdx.x == 0 && gates) {
+        const unsigned long long seen =
+            local[0] + local[PCL_GATE_G2_PROFILE] + local[PCL_GATE_G3_DENSITY];
+        gates[0] += local[0];
+        gates[PCL_GATE_G1_AREA] += total - seen;
+        gates[PCL_GATE_G2_PROFILE] += local[PCL_GATE_G2_PROFILE];
+        gates[PCL_GATE_G3_DENSITY] += local[PCL_GATE_G3_DENSITY];
+    }
+}
+
+}  // namespace
+
+// workspace bytes for the band join of n clips under g
+size_t band_join_workspace(const Geo &g, uint32_t n) {
+    const size_t V = (size_t)g.N * g.N + 2;  // areas 0..N^2, plus the end slot
+    return 4 * (2 * V + 2 * (size_t)n) + 8 * 16 + 64;
+}
+
+cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void *ws, size_t ws_bytes,
+                             pcl_pair *out, uint64_t cap, unsigned long long *count,
+                             unsigned long long *gates, int num_sms, cudaStream_t st) {
+    const Geo g = make_geo(prm);
+    const uint32_t n = cs.n_clips;
+    if (ws_bytes < band_join_workspace(g, n)) return cudaErrorInvalidValue;
+    const uint32_t V = (uint32_t)g.N * g.N + 2;
+    char *w = static_cast<char *>(ws);
+    unsigned long long *local = reinterpret_cast<unsigned long long *>(w);
+    unsigned int *next_pos = reinterpret_cast<unsigned int *>(w + 8 * 16);
+    uint32_t *cum = reinterpret_cast<uint32_t *>(w + 8 * 16 + 64);
+    uint32_t *fill = cum + V;
+    uint32_t *order = fill + V;
+    uint32_t *spop = order + n;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w, 0, 8 * 16 + 64 + 4 * (size_t)2 * V, st)) != cudaSuccess) return e;
+    if (n == 0) {
+        finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, 0ull);
+        return cudaGetLastError();
+    }
+    hist_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum);
+    scan_kernel<<<1, 1024, 0, st>>>(cum, V);
+    scatter_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum, fill, order, spop);
+    band_join_kernel<<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, (uint32_t)g.N * g.N, out,
+                                                  cap, count, local, next_pos);
+    const unsigned long long total = (unsigned long long)n * (n - 1) / 2;
+    finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, total);
+    return cudaGetLastError();
+}
+
+}  // namespace pcl

@@ -1,0 +1,171 @@
+// a1: rasterisation of Manhattan clips and the per-clip signatures read by the
+// lossless gates (Sec. 2.2.1 step 1; signatures for the pre-screening of
+// Sec. 3.1 stage 1).
+//
+// One CTA per clip, one thread per raster row (blockDim = N <= 512).  The
+// clip's rectangles are staged in shared memory in chunks; each thread ORs
+// the pixel-centre runs of the rectangles that cover its row centre into its
+// row words (registers), then the CTA derives the popcount, row/column
+// profiles and the 16x16 block counts from the row words in shared memory.
+#include "common.cuh"
+
+namespace pcl {
+
+namespace {
+
+constexpr int kRectChunk = 256;
+
+__device__ __forceinline__ int ceil_div_i(long long a, long long b) {  // b > 0
+    long long q = a / b;
+    if (a % b != 0 && a > 0) ++q;
+    return (int)q;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset cs) {
+    const Geo g = make_geo(prm);
+    const int c = blockIdx.x;
+    const int j = threadIdx.x;  // row (y index)
+    const int N = g.N;
+    __shared__ int4 rs[kRectChunk];
+    __shared__ uint64_t rows[512 * NW];
+    __shared__ uint32_t red[32];
+
+    const uint32_t r0 = cs.rect_off[c], r1 = cs.rect_off[c + 1];
+    const long long p = g.p;
+    // pixel centre of row j in doubled coordinates: 2 p j + p
+    const long long Y2 = 2 * p * j + p;
+    uint64_t w[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = 0ull;
+
+    for (uint32_t base = r0; base < r1; base += kRectChunk) {
+        const uint32_t cnt = min((uint32_t)kRectChunk, r1 - base);
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x)
+            rs[t] = reinterpret_cast<const int4 *>(cs.rects)[base + t];
+        __syncthreads();
+        if (j < N) {
+            for (uint32_t t = 0; t < cnt; ++t) {
+                const int4 q = rs[t];
+                if (!(2LL * q.y <= Y2 && Y2 < 2LL * q.w)) continue;
+                // columns i with 2 x0 <= 2 p i + p < 2 x1
+                int i0 = ceil_div_i(2LL * q.x - p, 2 * p);
+                int i1 = ceil_div_i(2LL * q.z - p, 2 * p);
+                i0 = max(i0, 0);
+                i1 = min(i1, N);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    const int lo = max(i0, 64 * k), hi = min(i1, 64 * k + 64);
+                    if (lo < hi) {
+                        const int len = hi - lo;
+                        const uint64_t m = (len == 64) ? ~0ull : (((1ull << len) - 1ull) << (lo - 64 * k));
+                        w[k] |= m;
+                    }
+                }
+            }
+        }
+    }
+    uint32_t rowpop = 0;
+    if (j < N) {
+        uint64_t *dst = cs.bits + ((size_t)c * N + j) * NW;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            dst[k] = w[k];
+            rows[j * NW + k] = w[k];
+            rowpop += (uint32_t)__popcll(w[k]);
+        }
+        cs.prof[(size_t)c * 2 * N + j] = (uint16_t)rowpop;
+    }
+    // total popcount
+    uint32_t tot = __reduce_add_sync(0xffffffffu, rowpop);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) s += red[k];
+        cs.pop[c] = s;
+    }
+    // column counts: thread i counts bit i over all rows
+    if (j < N) {
+        const int i = j;
+        const int k = i >> 6, b = i & 63;
+        uint32_t q = 0;
+        for (int jj = 0; jj < N; ++jj) q += (uint32_t)((rows[jj * NW + k] >> b) & 1ull);
+        cs.prof[(size_t)c * 2 * N + N + i] = (uint16_t)q;
+    }
+    // 16x16 block counts, then neighbourhood sums
+    const int nb = g.nb, nb2 = nb * nb;
+    uint16_t *blk = cs.blk + (size_t)c * 2 * nb2;
+    __shared__ uint16_t cnt_s[32 * 32];
+    for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+        const int by = t / nb, bx = t % nb;
+        const int k = bx >> 2, sh = (bx & 3) * 16;
+        uint32_t s = 0;
+        for (int jj = 0; jj < 16; ++jj) s += (uint32_t)__popcll((rows[(by * 16 + jj) * NW + k] >> sh) & 0xffffull);
+        cnt_s[t] = (uint16_t)s;
+        blk[t] = (uint16_t)s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+        const int by = t / nb, bx = t % nb;
+        uint32_t s = 0;
+        for (int oy = -g.rb; oy <= g.rb; ++oy)
+            for (int ox = -g.rb; ox <= g.rb; ++ox) {
+                const int yy = by + oy, xx = bx + ox;
+                if (yy >= 0 && yy < nb && xx >= 0 && xx < nb) s += cnt_s[yy * nb + xx];
+            }
+        blk[nb2 + t] = (uint16_t)min(s, 65535u);
+    }
+    // edge signature (warp 0): bbox over edges that are not on the window border
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int W = g.W;
+        int hasx = 0, hasy = 0, border = 0;
+        int lox = INT_MAX, hix = INT_MIN, loy = INT_MAX, hiy = INT_MIN;
+        for (uint32_t t = r0 + lane; t < r1; t += 32) {
+            const int4 q = reinterpret_cast<const int4 *>(cs.rects)[t];
+            if (q.x != 0) { hasx = 1; lox = min(lox, q.x); hix = max(hix, q.x); } else border = 1;
+            if (q.z != W) { hasx = 1; lox = min(lox, q.z); hix = max(hix, q.z); } else border = 1;
+            if (q.y != 0) { hasy = 1; loy = min(loy, q.y); hiy = max(hiy, q.y); } else border = 1;
+            if (q.w != W) { hasy = 1; loy = min(loy, q.w); hiy = max(hiy, q.w); } else border = 1;
+        }
+        hasx = __reduce_or_sync(0xffffffffu, hasx);
+        hasy = __reduce_or_sync(0xffffffffu, hasy);
+        border = __reduce_or_sync(0xffffffffu, border);
+        lox = __reduce_min_sync(0xffffffffu, lox);
+        hix = __reduce_max_sync(0xffffffffu, hix);
+        loy = __reduce_min_sync(0xffffffffu, loy);
+        hiy = __reduce_max_sync(0xffffffffu, hiy);
+        if (lane == 0) {
+            int32_t *e = cs.esig + (size_t)c * 8;
+            e[ES_N] = (int32_t)(r1 - r0);
+            e[ES_HASX] = hasx;
+            e[ES_LOX] = hasx ? lox : 0;
+            e[ES_HIX] = hasx ? hix : 0;
+            e[ES_HASY] = hasy;
+            e[ES_LOY] = hasy ? loy : 0;
+            e[ES_HIY] = hasy ? hiy : 0;
+            e[ES_BORDER] = border;
+        }
+    }
+    if (threadIdx.x == 0 && cs.spec_state) cs.spec_state[c] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_raster(const pcl_params &prm, const pcl_clipset &cs, cudaStream_t st) {
+    const Geo g = make_geo(prm);
+    if (cs.n_clips == 0) return cudaSuccess;
+    dim3 grid(cs.n_clips), block(g.N);
+    switch (g.nw) {
+        case 1: raster_kernel<1><<<grid, block, 0, st>>>(prm, cs); break;
+        case 2: raster_kernel<2><<<grid, block, 0, st>>>(prm, cs); break;
+        case 4: raster_kernel<4><<<grid, block, 0, st>>>(prm, cs); break;
+        case 8: raster_kernel<8><<<grid, block, 0, st>>>(prm, cs); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pcl
