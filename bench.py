@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="clips in the oracle sample (0: auto)")
+    ap.add_argument("--clips", type=int, default=0,
+                    help="override the clip count (seeds and copies scale with it; profiling runs)")
+    ap.add_argument("--no-fft-engine", action="store_true")
     return ap.parse_args()
 
 
@@ -121,9 +124,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(config: str, seed: int):
+def workload(config: str, seed: int, clips: int = 0):
     import synth
-    return synth.preset(config, seed=seed)
+    if not clips:
+        return synth.preset(config, seed=seed)
+    base = synth.PRESETS[config]
+    f = clips / base["n_clips"]
+    return synth.preset(config, seed=seed, n_clips=clips, n_seeds=max(1, int(base["n_seeds"] * f)),
+                        n_copies=int(base["n_copies"] * f))
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -154,7 +162,7 @@ def default_sample(config: str) -> int:
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = workload(args.config, args.seed)
+    wl = workload(args.config, args.seed, args.clips)
     n_s = args.cpu_sample or default_sample(args.config)
     for _ in range(args.warmup):
         oracle_sample(wl, n_s)
@@ -187,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = workload(args.config, args.seed + rank)
+    wl = workload(args.config, args.seed + rank, args.clips)
     P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL)
     ctx = pcl.Context(local_rank)
     h_off = torch.from_numpy(wl.rect_off.view(np.int32).copy()).pin_memory()
@@ -255,6 +263,56 @@ def run_ours(args, rank, world, local_rank):
     st_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
     ms_step = float(st_ms.sum(axis=1).mean())
     per_stage = {s: float(st_ms[:, i].mean()) for i, s in enumerate(stages)}
+
+    # ---- FFT phase-correlation engine on a fixed pair list: the same-seed
+    # pairs of the workload (the pairs a looser coarse threshold would send
+    # to alignment), gates off, spectra cached beforehand
+    fft = None
+    if not args.no_fft_engine:
+        lab = wl.label
+        order = np.argsort(lab, kind="stable")
+        ls = lab[order]
+        fp = []
+        for s0 in np.flatnonzero(np.r_[True, ls[1:] != ls[:-1]]):
+            e0 = s0
+            while e0 < len(ls) and ls[e0] == ls[s0]:
+                e0 += 1
+            if ls[s0] < 0:
+                continue
+            grp = order[s0:e0]
+            for x in range(len(grp)):
+                for y in range(x + 1, len(grp)):
+                    fp.append((min(grp[x], grp[y]), max(grp[x], grp[y])))
+        fp = np.array(sorted(fp), dtype=np.int32).reshape(-1, 2)
+        Pn = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL, flags=pcl.P_NO_GATES)
+        tfp = torch.from_numpy(fp).to(dev)
+        rfp = torch.empty((len(fp), 40), dtype=torch.uint8, device=dev)
+        pcl.pcl_spectra(ctx, Pn, cs)
+        for _ in range(2):
+            pcl.pcl_match_pairs(ctx, Pn, pcl.MODE_COSINE, cs, cs, tfp, rfp)
+        torch.cuda.synchronize()
+        f_ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            pcl.pcl_match_pairs(ctx, Pn, pcl.MODE_COSINE, cs, cs, tfp, rfp)
+            a1.record()
+            torch.cuda.synchronize()
+            f_ms.append(a0.elapsed_time(a1))
+        recs = pcl.records_to_numpy(rfp)
+        fms = float(np.mean(f_ms))
+        L, Ls = cs.L, cs.Ls
+        spec_b = L * Ls * 8
+        fft = {"pairs": int(len(fp)), "ms": fms, "pairs_per_s": len(fp) / (fms / 1e3),
+               "hbm_gbs_b_spectrum": len(fp) * spec_b / (fms / 1e3) / 1e9,
+               "guard_rate": float(((recs["flags"] & pcl.F_FFT_GUARD) > 0).mean()) if len(recs) else 0.0,
+               "pcm_agree_rate": float(((recs["flags"] & pcl.F_PCM_AGREES) > 0).mean()) if len(recs) else 0.0,
+               "pass": int(recs["pass_"].sum())}
+        # spectra are per-step work of the main path again
+        pcl.pcl_rasterize(ctx, P, cs)
+        torch.cuda.synchronize()
 
     # ---- end to end through the public API from pinned host memory
     e2e = None
@@ -339,7 +397,7 @@ def run_ours(args, rank, world, local_rank):
                    "gates_edge": {"E2": int(g[1][5]), "E1": int(g[1][4])},
                    "stage_ms": per_stage, "screened_pairs_per_s": 2 * total_pairs * world / (ms_max / 1e3),
                    "wall_s_timed": wall},
-        "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None,
+        "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
     # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2

@@ -22,8 +22,9 @@
  *    return counts write them to device memory for the same reason.
  *  - A context is used by one host thread at a time.
  *  - Geometry is integer dbu.  A clip is a W x W window; its rectangles
- *    (x0, y0, x1, y1) are window-relative with x0 < x1, y0 < y1.  Manhattan
- *    polygons enter as rectangle decompositions.
+ *    (x0, y0, x1, y1) are window-relative with x0 < x1, y0 < y1 (results for
+ *    a clip holding a degenerate rectangle are unspecified; no call faults on
+ *    one).  Manhattan polygons enter as rectangle decompositions.
  *  - Raster: N = W / p pixels per side; pixel (i, j) is 1 iff its centre
  *    (p*i + p/2, p*j + p/2) lies in some rectangle (half-open), i.e. the
  *    union of the rectangles sampled at pixel centres.
@@ -143,6 +144,11 @@ typedef struct pcl_record {
  *                        sums over (2*ceil(S/16)+1)^2 blocks (nb = N/16)
  *   esig     [n][8] i32  edge signature: n_rects, has_x, lo_x, hi_x, has_y,
  *                        lo_y, hi_y, touches_border (non-border edges only)
+ *   occ      [n][64] u64 64 x 64 occupancy grid of the rectangles (cell side
+ *                        W/64 dbu; bit cx of row cy set iff some rectangle's
+ *                        interior meets the cell), for the edge screen
+ *   rorder   [R] u16     per clip, local rectangle indices by ascending area
+ *                        (ties by index), parallel to rects
  *   spec     [n][L][Ls] float2 or NULL   cached R2C spectrum of the raster
  *                        zero-padded to L = 9N/8 (rows ky, columns kx < L/2+1)
  *   spec_state [n] u8 or NULL            1 once spec[i] holds the spectrum
@@ -157,14 +163,16 @@ typedef struct pcl_clipset {
     uint16_t *prof;
     uint16_t *blk;
     int32_t *esig;
+    uint64_t *occ;
+    uint16_t *rorder;
     void *spec;
     uint8_t *spec_state;
 } pcl_clipset;
 
-/* bytes of each clip-set buffer for n clips (spec may be sized 0 by the
-   caller when the cosine FFT engine is not used) */
+/* bytes of each clip-set buffer for n clips holding R rectangles in total
+   (spec may be sized 0 by the caller when the cosine FFT engine is not used) */
 typedef struct pcl_clipset_sizes {
-    uint64_t bits, pop, prof, blk, esig, spec, spec_state;
+    uint64_t bits, pop, prof, blk, esig, occ, rorder, spec, spec_state;
     int32_t N, S, L, Ls; /* raster side, shift half-range, FFT side, FFT row stride */
 } pcl_clipset_sizes;
 
@@ -184,12 +192,14 @@ const char *pcl_status_string(pcl_status s);
 /* Check a parameter block (rules listed at pcl_params). */
 pcl_status pcl_params_validate(const pcl_params *P);
 
-/* Buffer sizes of a clip set of n clips under P.  Errors: PCL_ERR_INVALID. */
-pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n_clips, pcl_clipset_sizes *out);
+/* Buffer sizes of a clip set of n clips with R rectangles under P.
+   Errors: PCL_ERR_INVALID. */
+pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n_clips, uint64_t n_rects,
+                                 pcl_clipset_sizes *out);
 
 /* ---- a1: rasterisation + signatures (Sec. 2.2.1 step 1) --------------------
-   Fills bits, pop, prof, blk, esig of every clip from rect_off/rects and
-   clears spec_state.  One CTA per clip.  Errors: PCL_ERR_INVALID (params or
+   Fills bits, pop, prof, blk, esig, occ, rorder of every clip from
+   rect_off/rects and clears spec_state.  One CTA per clip.  Errors: PCL_ERR_INVALID (params or
    NULL buffer), PCL_ERR_CUDA (launch). */
 pcl_status pcl_rasterize(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, pcl_stream stream);
 
@@ -205,7 +215,9 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
    Self-join of cs: emits every pair (a < b) that no gate of `mode` rejects.
    COSINE: area-sorted band join (exactly the G1 survivors), then G3 density
    and G2 profile bounds.  EDGE: all pairs, E2 bbox then E1 correspondence at
-   the pre-alignment.  Pairs are written to d_out[0 .. min(count, cap)) in
+   the pre-alignment (each polygon of the smaller clip, smallest first, is
+   first checked against the other clip's occupancy grid: no occupied cell
+   under it means no overlap, so E1 fails without scanning rectangles).  Pairs are written to d_out[0 .. min(count, cap)) in
    unspecified order; *d_count (u64, device) receives the survivor count,
    which may exceed cap (then re-run with a larger buffer).  d_gate_counts
    (u64[16], device, may be NULL) is incremented: [0] survivors, [g] pairs

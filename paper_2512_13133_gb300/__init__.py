@@ -80,13 +80,14 @@ class _Clipset(ctypes.Structure):
     _fields_ = [("n_clips", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("rect_off", ctypes.c_void_p), ("rects", ctypes.c_void_p),
                 ("bits", ctypes.c_void_p), ("pop", ctypes.c_void_p), ("prof", ctypes.c_void_p),
-                ("blk", ctypes.c_void_p), ("esig", ctypes.c_void_p), ("spec", ctypes.c_void_p),
-                ("spec_state", ctypes.c_void_p)]
+                ("blk", ctypes.c_void_p), ("esig", ctypes.c_void_p), ("occ", ctypes.c_void_p),
+                ("rorder", ctypes.c_void_p), ("spec", ctypes.c_void_p), ("spec_state", ctypes.c_void_p)]
 
 
 class _Sizes(ctypes.Structure):
     _fields_ = [("bits", ctypes.c_uint64), ("pop", ctypes.c_uint64), ("prof", ctypes.c_uint64),
-                ("blk", ctypes.c_uint64), ("esig", ctypes.c_uint64), ("spec", ctypes.c_uint64),
+                ("blk", ctypes.c_uint64), ("esig", ctypes.c_uint64), ("occ", ctypes.c_uint64),
+                ("rorder", ctypes.c_uint64), ("spec", ctypes.c_uint64),
                 ("spec_state", ctypes.c_uint64), ("N", ctypes.c_int32), ("S", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("Ls", ctypes.c_int32)]
 
@@ -122,7 +123,7 @@ def load(build_if_missing: bool = True):
         "pcl_last_error": ([_VP], ctypes.c_char_p),
         "pcl_status_string": ([st], ctypes.c_char_p),
         "pcl_params_validate": ([ctypes.POINTER(Params)], st),
-        "pcl_clipset_sizes_get": ([ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Sizes)], st),
+        "pcl_clipset_sizes_get": ([ctypes.POINTER(Params), ctypes.c_uint32, _U64, ctypes.POINTER(_Sizes)], st),
         "pcl_rasterize": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP], st),
         "pcl_spectra": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, ctypes.c_uint32, _VP], st),
         "pcl_candidates": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset), _VP, _U64,
@@ -211,19 +212,21 @@ class ClipSet:
     prof: object
     blk: object
     esig: object
+    occ: object
+    rorder: object
     spec: object
     spec_state: object
 
     def cstruct(self) -> _Clipset:
         return _Clipset(self.n, 0, _ptr(self.rect_off), _ptr(self.rects), _ptr(self.bits), _ptr(self.pop),
-                        _ptr(self.prof), _ptr(self.blk), _ptr(self.esig), _ptr(self.spec),
-                        _ptr(self.spec_state))
+                        _ptr(self.prof), _ptr(self.blk), _ptr(self.esig), _ptr(self.occ), _ptr(self.rorder),
+                        _ptr(self.spec), _ptr(self.spec_state))
 
 
-def clipset_sizes(P: Params, n: int) -> _Sizes:
+def clipset_sizes(P: Params, n: int, n_rects: int = 0) -> _Sizes:
     lib = load()
     sz = _Sizes()
-    s = lib.pcl_clipset_sizes_get(ctypes.byref(P), n, ctypes.byref(sz))
+    s = lib.pcl_clipset_sizes_get(ctypes.byref(P), n, n_rects, ctypes.byref(sz))
     if s != PCL_OK:
         raise PclError(s, "pcl_clipset_sizes_get: invalid parameters")
     return sz
@@ -241,7 +244,7 @@ def alloc_clipset(P: Params, rect_off, rects, device="cuda", with_spec: bool = T
             r = np.zeros(4, np.int32)
         rects = torch.from_numpy(r).to(device)
     n = int(rect_off.numel()) - 1
-    sz = clipset_sizes(P, n)
+    sz = clipset_sizes(P, n, int(rects.numel()) // 4)
 
     def buf(nbytes):
         return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
@@ -249,7 +252,7 @@ def alloc_clipset(P: Params, rect_off, rects, device="cuda", with_spec: bool = T
     spec = buf(sz.spec) if with_spec else None
     state = torch.zeros(max(int(sz.spec_state), 16), dtype=torch.uint8, device=device) if with_spec else None
     return ClipSet(n, sz.N, sz.S, sz.L, sz.Ls, rect_off, rects, buf(sz.bits), buf(sz.pop), buf(sz.prof),
-                   buf(sz.blk), buf(sz.esig), spec, state)
+                   buf(sz.blk), buf(sz.esig), buf(sz.occ), buf(sz.rorder), spec, state)
 
 
 # ---------------------------------------------------------------- entry points

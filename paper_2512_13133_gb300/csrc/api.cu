@@ -84,7 +84,7 @@ bool pow2_raster(int N) { return N == 64 || N == 128 || N == 256 || N == 512; }
 pcl_status check_clipset(pcl_ctx *ctx, const pcl_clipset *cs, bool need_edge_or_raster) {
     if (!cs) return fail(ctx, PCL_ERR_INVALID, "clip set is NULL%s%lld");
     if (cs->n_clips && (!cs->rect_off || !cs->rects || !cs->bits || !cs->pop || !cs->prof || !cs->blk ||
-                        (need_edge_or_raster && !cs->esig)))
+                        (need_edge_or_raster && (!cs->esig || !cs->occ || !cs->rorder))))
         return fail(ctx, PCL_ERR_INVALID, "clip set has a NULL buffer%s%lld");
     return PCL_OK;
 }
@@ -152,7 +152,7 @@ pcl_status pcl_params_validate(const pcl_params *P) {
     return PCL_OK;
 }
 
-pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n, pcl_clipset_sizes *o) {
+pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n, uint64_t n_rects, pcl_clipset_sizes *o) {
     if (!o || pcl_params_validate(P) != PCL_OK) return PCL_ERR_INVALID;
     const Geo g = make_geo(*P);
     o->bits = 8ull * n * g.N * g.nw;
@@ -160,6 +160,8 @@ pcl_status pcl_clipset_sizes_get(const pcl_params *P, uint32_t n, pcl_clipset_si
     o->prof = 2ull * n * 2 * g.N;
     o->blk = 2ull * n * 2 * g.nb * g.nb;
     o->esig = 32ull * n;
+    o->occ = 8ull * 64 * n;
+    o->rorder = 2ull * n_rects;
     o->spec = 8ull * n * g.L * g.Ls;
     o->spec_state = n;
     o->N = g.N;

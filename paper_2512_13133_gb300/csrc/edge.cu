@@ -66,9 +66,38 @@ __device__ bool correspond(const int4 *rs, int ns, const int4 *rl, int nl, bool 
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+__device__ __forceinline__ int cell_of(int v, int csz) {
+    const int q = v >= 0 ? v / csz : -((-v + csz - 1) / csz);
+    return q < 0 ? 0 : (q > 63 ? 63 : q);
+}
+
+// Does rectangle [x0,x1) x [y0,y1) (in the frame of the clip owning occ) meet
+// a marked cell of its occupancy grid?  Positive-area overlap with any of the
+// clip's rectangles implies a shared marked cell, so "false" proves that the
+// rectangle overlaps none of them.
+__device__ __forceinline__ bool grid_hit(const uint64_t *__restrict__ occ, int x0, int y0, int x1, int y1,
+                                         int csz) {
+    if (x1 <= x0 || y1 <= y0) return true;  // degenerate input: no pruning
+    const int cx0 = cell_of(x0, csz), cx1 = cell_of(x1 - 1, csz);
+    const int cy0 = cell_of(y0, csz), cy1 = cell_of(y1 - 1, csz);
+    const uint64_t m = (~0ull >> (63 - (cx1 - cx0))) << cx0;
+    for (int cy = cy0; cy <= cy1; ++cy)
+        if (__ldg(occ + cy) & m) return true;
+    return false;
+}
+
+struct ClipView {
+    const int4 *r;       // rectangles
+    const int32_t *e;    // edge signature
+    const uint16_t *ro;  // rectangles by ascending area
+    const uint64_t *occ; // occupancy grid
+};
+
 // Gates E2 and E1 and, unless screen_only, the full Min-Max procedure.
-__device__ EdgeOut edge_eval(const int4 *ra, const int32_t *ea, const int4 *rb, const int32_t *eb,
-                             int W, int M, int tol, bool gates, bool screen_only) {
+__device__ EdgeOut edge_eval(const ClipView &A, const ClipView &B, int W, int M, int tol, bool gates,
+                             bool screen_only) {
+    const int4 *ra = A.r, *rb = B.r;
+    const int32_t *ea = A.e, *eb = B.e;
     EdgeOut o{};
     const int na = ea[ES_N], nb = eb[ES_N];
     if (na == 0 && nb == 0) {
@@ -101,6 +130,22 @@ __device__ EdgeOut edge_eval(const int4 *ra, const int32_t *ea, const int4 *rb, 
     const int ns = small_is_a ? na : nb, nl = small_is_a ? nb : na;
     o.tx = s0x;
     o.ty = s0y;
+    // occupancy pre-check of E1, smallest polygons first (most likely to meet
+    // nothing): a small polygon over empty cells of the other clip has no partner
+    {
+        const uint16_t *ro = small_is_a ? A.ro : B.ro;
+        const uint64_t *occ_l = small_is_a ? B.occ : A.occ;
+        const int csz = W / 64;
+        // small polygon in the large clip's frame: a - t (small is A) or b + t
+        const int sx = small_is_a ? -s0x : s0x, sy = small_is_a ? -s0y : s0y;
+        for (int k = 0; k < ns; ++k) {
+            const int4 q = __ldg(rs + __ldg(ro + k));
+            if (!grid_hit(occ_l, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz)) {
+                o.gate = PCL_GATE_E1_MATCH;
+                return o;
+            }
+        }
+    }
     if (!correspond(rs, ns, rl, nl, small_is_a, s0x, s0y)) {
         o.gate = PCL_GATE_E1_MATCH;
         return o;
@@ -167,11 +212,15 @@ __global__ void __launch_bounds__(256) edge_screen_kernel(pcl_params prm, pcl_cl
     const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
     const bool jv = j < n;
     int32_t eb[8];
-    const int4 *rb = nullptr;
+    ClipView B{};
     if (jv) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) eb[k] = __ldg(cs.esig + (size_t)j * 8 + k);
-        rb = reinterpret_cast<const int4 *>(cs.rects) + __ldg(cs.rect_off + j);
+        const uint32_t o = __ldg(cs.rect_off + j);
+        B.r = reinterpret_cast<const int4 *>(cs.rects) + o;
+        B.ro = cs.rorder + o;
+        B.occ = cs.occ + (size_t)j * 64;
+        B.e = eb;
     }
     uint32_t g_e1 = 0, g_e2 = 0, kept = 0;
     for (int t = 0; t < kTileI; ++t) {
@@ -181,8 +230,10 @@ __global__ void __launch_bounds__(256) edge_screen_kernel(pcl_params prm, pcl_cl
             int32_t ea[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) ea[k] = __ldg(cs.esig + (size_t)i * 8 + k);
-            const int4 *ra = reinterpret_cast<const int4 *>(cs.rects) + __ldg(cs.rect_off + i);
-            const EdgeOut o = edge_eval(ra, ea, rb, eb, W, M, tol, true, true);
+            const uint32_t oa = __ldg(cs.rect_off + i);
+            const ClipView A{reinterpret_cast<const int4 *>(cs.rects) + oa, ea, cs.rorder + oa,
+                             cs.occ + (size_t)i * 64};
+            const EdgeOut o = edge_eval(A, B, W, M, tol, true, true);
             if (o.gate == PCL_GATE_E1_MATCH) ++g_e1;
             else if (o.gate == PCL_GATE_E2_BBOX) ++g_e2;
             else { keep = true; ++kept; }
@@ -222,11 +273,11 @@ __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_cli
         ea[k] = __ldg(A.esig + (size_t)pr.a * 8 + k);
         eb[k] = __ldg(B.esig + (size_t)pr.b * 8 + k);
     }
-    const int4 *ra = reinterpret_cast<const int4 *>(A.rects) + __ldg(A.rect_off + pr.a);
-    const int4 *rb = reinterpret_cast<const int4 *>(B.rects) + __ldg(B.rect_off + pr.b);
+    const uint32_t oa = __ldg(A.rect_off + pr.a), ob = __ldg(B.rect_off + pr.b);
+    const ClipView va{reinterpret_cast<const int4 *>(A.rects) + oa, ea, A.rorder + oa, A.occ + (size_t)pr.a * 64};
+    const ClipView vb{reinterpret_cast<const int4 *>(B.rects) + ob, eb, B.rorder + ob, B.occ + (size_t)pr.b * 64};
     const bool gates = !(prm.flags & PCL_P_NO_GATES);
-    const EdgeOut o = edge_eval(ra, ea, rb, eb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu,
-                                gates, false);
+    const EdgeOut o = edge_eval(va, vb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu, gates, false);
     r.dx_dbu = o.tx;
     r.dy_dbu = o.ty;
     if (o.empty) {

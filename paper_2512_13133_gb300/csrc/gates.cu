@@ -102,9 +102,8 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
             bool keep = true;
             if (!(pa == 0 && pb == 0)) {
                 const int nb2 = g.nb * g.nb;
-                const uint32_t u3 =
-                    warp_g3(cs.blk + (size_t)a * 2 * nb2, cs.blk + (size_t)b * 2 * nb2, nb2, lane);
-                if (!cos_exceeds(u3, pa, pb, prm.cos_num, prm.cos_den)) {
+                if (warp_g3_rejects(cs.blk + (size_t)a * 2 * nb2, cs.blk + (size_t)b * 2 * nb2, nb2, pa, pb,
+                                    prm.cos_num, prm.cos_den, lane)) {
                     ++g3;
                     continue;
                 }

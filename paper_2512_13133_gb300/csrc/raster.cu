@@ -15,6 +15,12 @@ namespace {
 
 constexpr int kRectChunk = 256;
 
+// grid cell of coordinate v (floor division, clamped to the 64 cells)
+__device__ __forceinline__ int cell_of(int v, int csz) {
+    const int q = v >= 0 ? v / csz : -((-v + csz - 1) / csz);
+    return q < 0 ? 0 : (q > 63 ? 63 : q);
+}
+
 __device__ __forceinline__ int ceil_div_i(long long a, long long b) {  // b > 0
     long long q = a / b;
     if (a % b != 0 && a > 0) ++q;
@@ -148,6 +154,36 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
             e[ES_HIY] = hasy ? hiy : 0;
             e[ES_BORDER] = border;
         }
+    }
+    // 64 x 64 occupancy grid (cell side W/64): a cell is marked when it holds an
+    // integer point of some rectangle's interior, so two rectangles that
+    // overlap with positive area always share a marked cell
+    const int csz = g.W / 64;
+    const int4 *r4 = reinterpret_cast<const int4 *>(cs.rects);
+    for (int cy = threadIdx.x; cy < 64; cy += blockDim.x) {
+        uint64_t m = 0ull;
+        for (uint32_t t = r0; t < r1; ++t) {
+            const int4 q = r4[t];
+            if (q.z <= q.x || q.w <= q.y) continue;
+            const int y0 = cell_of(q.y, csz), y1 = cell_of(q.w - 1, csz);
+            if (cy < y0 || cy > y1) continue;
+            const int x0 = cell_of(q.x, csz), x1 = cell_of(q.z - 1, csz);
+            m |= (~0ull >> (63 - (x1 - x0))) << x0;
+        }
+        cs.occ[(size_t)c * 64 + cy] = m;
+    }
+    // rectangles by ascending area (ties by index): rank by counting
+    const uint32_t nr = r1 - r0;
+    for (uint32_t t = threadIdx.x; t < nr; t += blockDim.x) {
+        const int4 q = r4[r0 + t];
+        const long long at = (long long)(q.z - q.x) * (long long)(q.w - q.y);
+        uint32_t rank = 0;
+        for (uint32_t m = 0; m < nr; ++m) {
+            const int4 u = r4[r0 + m];
+            const long long am = (long long)(u.z - u.x) * (long long)(u.w - u.y);
+            rank += (am < at || (am == at && m < t)) ? 1u : 0u;
+        }
+        cs.rorder[r0 + rank] = (uint16_t)t;
     }
     if (threadIdx.x == 0 && cs.spec_state) cs.spec_state[c] = 0;
 }
