@@ -221,14 +221,21 @@ __device__ __forceinline__ uint32_t warp_corr_exact(const uint64_t *__restrict__
     return __reduce_add_sync(0xffffffffu, acc);
 }
 
-// integer cosine threshold test of Eq. 2 (strict >): den^2 c^2 > num^2 pa pb
+// a * b as a 128-bit (hi, lo) pair
+__device__ __forceinline__ void mul128(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo) {
+    lo = a * b;
+    hi = __umul64hi(a, b);
+}
+
+// integer cosine threshold test of Eq. 2 (strict >): den^2 c^2 > num^2 pa pb,
+// exact for c, pa, pb < 2^32 and den < 2^16 (128-bit products)
 __device__ __forceinline__ bool cos_exceeds(uint64_t c, uint64_t pa, uint64_t pb, uint32_t num,
                                             uint32_t den) {
     if (c == 0) return false;
-    // den^2 c^2 <= 2^32 * 2^36 overflows 64 bits: compare in 128 bits
-    const unsigned __int128 lhs = (unsigned __int128)((uint64_t)den * den) * (c * c);
-    const unsigned __int128 rhs = (unsigned __int128)((uint64_t)num * num) * (pa * pb);
-    return lhs > rhs;
+    uint64_t lh, ll, rh, rl;
+    mul128((uint64_t)den * den, c * c, lh, ll);
+    mul128((uint64_t)num * num, pa * pb, rh, rl);
+    return lh > rh || (lh == rh && ll > rl);
 }
 
 }  // namespace pcl

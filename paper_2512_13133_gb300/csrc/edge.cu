@@ -66,9 +66,11 @@ __device__ bool correspond(const int4 *rs, int ns, const int4 *rl, int nl, bool 
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-__device__ __forceinline__ int cell_of(int v, int csz) {
-    const int q = v >= 0 ? v / csz : -((-v + csz - 1) / csz);
-    return q < 0 ? 0 : (q > 63 ? 63 : q);
+// grid cell of coordinate v: floor(v / csz) clamped to the 64 cells; csh >= 0
+// is log2(csz) when csz is a power of two (arithmetic shift = floor division)
+__device__ __forceinline__ int cell_of(int v, int csz, int csh) {
+    const int q = csh >= 0 ? (v >> csh) : (v >= 0 ? v / csz : -((-v + csz - 1) / csz));
+    return min(max(q, 0), 63);
 }
 
 // Does rectangle [x0,x1) x [y0,y1) (in the frame of the clip owning occ) meet
@@ -76,10 +78,10 @@ __device__ __forceinline__ int cell_of(int v, int csz) {
 // clip's rectangles implies a shared marked cell, so "false" proves that the
 // rectangle overlaps none of them.
 __device__ __forceinline__ bool grid_hit(const uint64_t *__restrict__ occ, int x0, int y0, int x1, int y1,
-                                         int csz) {
+                                         int csz, int csh) {
     if (x1 <= x0 || y1 <= y0) return true;  // degenerate input: no pruning
-    const int cx0 = cell_of(x0, csz), cx1 = cell_of(x1 - 1, csz);
-    const int cy0 = cell_of(y0, csz), cy1 = cell_of(y1 - 1, csz);
+    const int cx0 = cell_of(x0, csz, csh), cx1 = cell_of(x1 - 1, csz, csh);
+    const int cy0 = cell_of(y0, csz, csh), cy1 = cell_of(y1 - 1, csz, csh);
     const uint64_t m = (~0ull >> (63 - (cx1 - cx0))) << cx0;
     for (int cy = cy0; cy <= cy1; ++cy)
         if (__ldg(occ + cy) & m) return true;
@@ -136,11 +138,12 @@ __device__ EdgeOut edge_eval(const ClipView &A, const ClipView &B, int W, int M,
         const uint16_t *ro = small_is_a ? A.ro : B.ro;
         const uint64_t *occ_l = small_is_a ? B.occ : A.occ;
         const int csz = W / 64;
+        const int csh = (csz & (csz - 1)) == 0 ? __ffs(csz) - 1 : -1;
         // small polygon in the large clip's frame: a - t (small is A) or b + t
         const int sx = small_is_a ? -s0x : s0x, sy = small_is_a ? -s0y : s0y;
         for (int k = 0; k < ns; ++k) {
             const int4 q = __ldg(rs + __ldg(ro + k));
-            if (!grid_hit(occ_l, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz)) {
+            if (!grid_hit(occ_l, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz, csh)) {
                 o.gate = PCL_GATE_E1_MATCH;
                 return o;
             }

@@ -75,6 +75,33 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
     }
 }
 
+// G3 for one band member b of representative a with a's block words held in
+// registers (WPL u32 words per lane = two 16-bit blocks each); deficits are
+// accumulated as packed 16-bit halves (min <= value, so no borrow crosses
+// halves) and checked after every 32-lane chunk.
+template <int WPL>
+__device__ __forceinline__ bool g3_rejects_reg(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+                                               const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
+                                               int words, uint64_t pa, uint64_t pb, uint32_t num, uint32_t den,
+                                               int lane) {
+    uint32_t pda = 0, pdb = 0;
+#pragma unroll
+    for (int c = 0; c < WPL; ++c) {
+        const int t = c * 32 + lane;
+        if (t < words) {
+            const uint32_t b = __ldg(cb + t);
+            pda += ca[c] - __vminu2(ca[c], __ldg(db + t));
+            pdb += b - __vminu2(b, da[c]);
+        }
+        const uint64_t DA = __reduce_add_sync(0xffffffffu, (pda & 0xffffu) + (pda >> 16));
+        const uint64_t DB = __reduce_add_sync(0xffffffffu, (pdb & 0xffffu) + (pdb >> 16));
+        const uint64_t ua = pa - DA, ub = pb - DB;
+        if (!cos_exceeds(ua < ub ? ua : ub, pa, pb, num, den)) return true;
+    }
+    return false;
+}
+
+template <int WPL>
 __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
                                                         const uint32_t *spop, const uint32_t *cum,
                                                         uint32_t vmax_all, pcl_pair *out, uint64_t cap,
@@ -84,6 +111,7 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
     const Geo g = make_geo(prm);
     const int lane = threadIdx.x & 31;
     const uint32_t n = cs.n_clips;
+    const int nb2 = g.nb * g.nb, words = nb2 / 2;
     const uint64_t num2 = (uint64_t)prm.cos_num * prm.cos_num, den2 = (uint64_t)prm.cos_den * prm.cos_den;
     unsigned long long kept = 0, g2 = 0, g3 = 0;
     for (;;) {
@@ -96,14 +124,21 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
         uint64_t vmax = pa == 0 ? 0 : (den2 * pa - 1) / num2;
         if (vmax > vmax_all) vmax = vmax_all;
         const uint32_t end = cum[vmax + 1];
+        const uint32_t *cwa = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)a * 2 * nb2);
+        uint32_t ca[WPL], da[WPL];
+#pragma unroll
+        for (int c = 0; c < WPL; ++c) {
+            const int t = c * 32 + lane;
+            ca[c] = t < words ? cwa[t] : 0u;
+            da[c] = t < words ? cwa[words + t] : 0u;
+        }
         for (uint32_t q = p + 1; q < end; ++q) {
             const uint32_t b = order[q];
             const uint64_t pb = spop[q];
-            bool keep = true;
             if (!(pa == 0 && pb == 0)) {
-                const int nb2 = g.nb * g.nb;
-                if (warp_g3_rejects(cs.blk + (size_t)a * 2 * nb2, cs.blk + (size_t)b * 2 * nb2, nb2, pa, pb,
-                                    prm.cos_num, prm.cos_den, lane)) {
+                const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)b * 2 * nb2);
+                if (g3_rejects_reg<WPL>(ca, da, cwb, cwb + words, words, pa, pb, prm.cos_num, prm.cos_den,
+                                        lane)) {
                     ++g3;
                     continue;
                 }
@@ -114,12 +149,10 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
                     continue;
                 }
             }
-            if (keep) {
-                ++kept;
-                if (lane == 0) {
-                    const unsigned long long idx = atomicAdd(count, 1ull);
-                    if (idx < cap) out[idx] = pcl_pair{min(a, b), max(a, b)};
-                }
+            ++kept;
+            if (lane == 0) {
+                const unsigned long long idx = atomicAdd(count, 1ull);
+                if (idx < cap) out[idx] = pcl_pair{min(a, b), max(a, b)};
             }
         }
     }
@@ -175,8 +208,16 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     hist_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum);
     scan_kernel<<<1, 1024, 0, st>>>(cum, V);
     scatter_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum, fill, order, spop);
-    band_join_kernel<<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, (uint32_t)g.N * g.N, out,
-                                                  cap, count, local, next_pos);
+    const uint32_t vall = (uint32_t)g.N * g.N;
+    switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
+        case 1: band_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
+                                                                 local, next_pos); break;
+        case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
+                                                                 local, next_pos); break;
+        case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
+                                                                   local, next_pos); break;
+        default: return cudaErrorInvalidValue;
+    }
     const unsigned long long total = (unsigned long long)n * (n - 1) / 2;
     finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, total);
     return cudaGetLastError();
