@@ -227,6 +227,24 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
                           pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
                           pcl_stream stream);
 
+/* Cosine candidate generation without any device allocation (the paper has
+   no counterpart; this serves callers that cannot allocate device memory,
+   e.g. when another allocator owns the device's memory under a fixed budget,
+   or in a service loop where cudaMalloc/cudaFree would synchronise the device
+   mid-request).  Same results and arguments as pcl_candidates with
+   mode = PCL_MODE_COSINE, but the scratch (area histogram, sorted order) is a
+   fixed 8 MiB array in the library's device memory instead of the context
+   workspace: 8 (N^2 + 2) + 8 n + 192 bytes must fit, otherwise
+   PCL_ERR_INVALID with the required size in pcl_last_error.  The first call
+   on a device looks up the array's device address (cudaGetSymbolAddress);
+   make that first call before any stream capture.  All calls share the one
+   array: calls whose work overlaps on the GPU (other streams, other host
+   threads) race on it and must be serialised by the caller.
+   Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (S > N/16), PCL_ERR_CUDA. */
+pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *cs,
+                                         pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
+                                         uint64_t *d_gate_counts, pcl_stream stream);
+
 /* ---- a4-a7: alignment + decision for listed pairs ------------------------
    One record per pair, in list order, pair (a, b) = (clip a of set A, clip b
    of set B).  Gates of the mode run first unless PCL_P_NO_GATES.

@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True):
         "pcl_spectra": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, ctypes.c_uint32, _VP], st),
         "pcl_candidates": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset), _VP, _U64,
                             _VP, _VP, _VP], st),
+        "pcl_candidates_cosine_noalloc": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, _U64,
+                                           _VP, _VP, _VP], st),
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
@@ -278,6 +280,20 @@ def pcl_candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, out_pairs, d
     cap = 0 if out_pairs is None else int(out_pairs.shape[0])
     ctx.check(ctx.lib.pcl_candidates(ctx.h, ctypes.byref(P), mode, ctypes.byref(c), _ptr(out_pairs), cap,
                                      _ptr(d_count), _ptr(d_gates), _stream_ptr(stream)), "pcl_candidates")
+
+
+def pcl_candidates_cosine_noalloc(ctx: Context, P: Params, cs: ClipSet, out_pairs, d_count, d_gates=None,
+                                  stream=None, n_clips: int | None = None) -> None:
+    """Cosine candidates without device allocation (fixed library scratch);
+    arguments as pcl_candidates.  n_clips overrides the clip count passed
+    across the ABI (used to exercise the size limit)."""
+    c = cs.cstruct()
+    if n_clips is not None:
+        c.n_clips = n_clips
+    cap = 0 if out_pairs is None else int(out_pairs.shape[0])
+    ctx.check(ctx.lib.pcl_candidates_cosine_noalloc(ctx.h, ctypes.byref(P), ctypes.byref(c), _ptr(out_pairs), cap,
+                                                    _ptr(d_count), _ptr(d_gates), _stream_ptr(stream)),
+              "pcl_candidates_cosine_noalloc")
 
 
 def pcl_match_pairs(ctx: Context, P: Params, mode: int, a: ClipSet, b: ClipSet, pairs, out_rec,

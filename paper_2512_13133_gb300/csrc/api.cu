@@ -27,13 +27,7 @@ cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long lon
                            unsigned long long *, cudaStream_t);
 }  // namespace pcl
 
-struct pcl_ctx {
-    int device = 0;
-    int num_sms = 0;
-    std::string err;
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-};
+#include "ctx.h"
 
 using namespace pcl;
 

@@ -1,0 +1,12 @@
+// Private definition of the library context (shared by the C-ABI sources).
+#pragma once
+
+#include <string>
+
+struct pcl_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};

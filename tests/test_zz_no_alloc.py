@@ -1,0 +1,72 @@
+"""The allocation-free cosine candidate entry point against pcl_candidates.
+
+pcl_candidates_cosine_noalloc exists for callers that cannot let the library
+call cudaMalloc (device memory owned by another allocator with a fixed
+budget, or a service loop that must not synchronise the device to allocate).
+It must return exactly what the regular entry point returns -- the candidate
+pairs and the gate counts are integers, so the comparison is exact -- and
+keep doing so on consecutive calls, since its scratch array persists between
+calls.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _pairs(t):
+    return set(map(tuple, t.cpu().numpy().astype(np.int64).tolist()))
+
+
+@pytest.mark.parametrize("preset,clips", [("small", 1000), ("scale", 20000)])
+def test_noalloc_matches_regular_entry_point_twice(torch_cuda, preset, clips):
+    import paper_2512_13133_gb300 as pcl
+    torch = torch_cuda
+    base = synth.PRESETS[preset]
+    f = clips / base["n_clips"]
+    wl = synth.preset(preset, seed=5, n_clips=clips, n_seeds=max(1, int(base["n_seeds"] * f)),
+                      n_copies=int(base["n_copies"] * f))
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu)
+    ctx = pcl.Context(0)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    ref_pairs, ref_gates = pcl.candidates(ctx, P, pcl.MODE_COSINE, cs, cap=1 << 22)
+    cap = max(int(ref_pairs.shape[0]), 1)
+    for _ in range(2):
+        out = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        gates = torch.zeros(16, dtype=torch.int64, device="cuda")
+        pcl.pcl_candidates_cosine_noalloc(ctx, P, cs, out, cnt, gates)
+        m = int(cnt.item())
+        assert m == ref_pairs.shape[0]
+        assert _pairs(out[:m]) == _pairs(ref_pairs)
+        np.testing.assert_array_equal(gates.cpu().numpy(), ref_gates)
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_above_its_scratch(torch_cuda):
+    import paper_2512_13133_gb300 as pcl
+    torch = torch_cuda
+    wl = synth.preset("small", seed=2, n_clips=50, n_seeds=5, n_copies=20)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu)
+    ctx = pcl.Context(0)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    out = torch.empty((16, 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # the size check happens before any kernel touches the buffers
+    with pytest.raises(pcl.PclError) as e:
+        pcl.pcl_candidates_cosine_noalloc(ctx, P, cs, out, cnt, None, n_clips=5_000_000)
+    assert e.value.status == pcl.PCL_ERR_INVALID
+    assert "8 MiB" in str(e.value)
+    ctx.close()
