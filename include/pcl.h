@@ -272,6 +272,60 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
 pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,
                             pcl_pair *d_out, uint64_t cap, uint64_t *d_count, pcl_stream stream);
 
+/* ---- a10: serving loop ----------------------------------------------------
+   A resident representative library and continuously batched query requests
+   (cosine mode, FFT phase-correlation engine).  pcl_server_create computes
+   the library's spectra (all clips; the library must be rasterised and own
+   spec/spec_state buffers) and sorts it by area, then allocates max_inflight
+   request slots (one stream each, pinned staging) and one device arena of
+   mem_budget bytes.  pcl_server_submit admits a request of n_clips query
+   clips (host rectangles, copied before return) when a slot is free and its
+   device footprint (its clip set, candidate/record buffers of cand_per_query
+   entries per clip) fits in the arena, else returns PCL_ERR_BUSY at once
+   (resubmit after a poll/release); the request then runs asynchronously:
+   rasterisation, query x library band join with the G1/G3/G2 gates,
+   spectra of the referenced query clips, phase-correlation matching with
+   the exact decision, pass compaction and the copy of the pass list back.
+   pcl_server_poll returns finished requests (pass pairs are
+   (query index, library index), in server-owned host memory valid until
+   pcl_server_release frees the request's slot and arena region); a request
+   whose candidates exceeded its capacity completes with PCL_ERR_BUSY.
+   Timestamps are steady-clock nanoseconds: submit, and device completion as
+   stamped by a host callback on the request's stream.  One host thread at a
+   time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (N > 256 or
+   S > N/16), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not admitted). */
+typedef struct pcl_server pcl_server;
+
+typedef struct pcl_server_cfg {
+    uint32_t max_inflight;     /* request slots, 1..64 */
+    uint32_t max_query_clips;  /* clips per request */
+    uint64_t max_query_rects;  /* rectangles per request */
+    uint32_t cand_per_query;   /* candidate capacity per query clip */
+    uint32_t pass_copy;        /* pass pairs copied back without a second copy */
+    uint64_t mem_budget;       /* device bytes for in-flight requests */
+} pcl_server_cfg;
+
+typedef struct pcl_completion {
+    uint64_t request_id;
+    int32_t status;        /* PCL_OK or PCL_ERR_BUSY (candidate capacity exceeded) */
+    uint32_t n_queries;
+    uint64_t n_candidates; /* pairs that reached the alignment engine */
+    uint64_t n_pass;
+    const pcl_pair *pass;  /* (query, library) pairs, valid until pcl_server_release */
+    int64_t t_submit_ns, t_done_ns;
+} pcl_completion;
+
+pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *library,
+                             const pcl_server_cfg *cfg, pcl_server **out);
+pcl_status pcl_server_submit(pcl_server *srv, const uint32_t *h_rect_off, const int32_t *h_rects,
+                             uint32_t n_clips, uint64_t request_id);
+pcl_status pcl_server_poll(pcl_server *srv, pcl_completion *out, uint32_t cap, uint32_t *n_out);
+pcl_status pcl_server_release(pcl_server *srv, uint64_t request_id);
+/* requests holding a slot, and free arena bytes (admission state) */
+pcl_status pcl_server_stats(pcl_server *srv, uint32_t *inflight, uint64_t *free_bytes);
+/* waits for in-flight work, frees the slots, arena and library index */
+void pcl_server_destroy(pcl_server *srv);
+
 /* ---- a11: host set cover + coarse-to-fine loop (Sec. 3.3, Sec. 3.1) -------
    Surprisal lazy greedy over the undirected graph h_edges[0..n_edges) on
    n_nodes nodes: f_i = 1 + deg(i), S_i = floor(2^32 / f_i), Score_j =

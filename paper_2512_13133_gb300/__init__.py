@@ -96,6 +96,18 @@ class _Pair(ctypes.Structure):
     _fields_ = [("a", ctypes.c_uint32), ("b", ctypes.c_uint32)]
 
 
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_uint32), ("max_query_clips", ctypes.c_uint32),
+                ("max_query_rects", ctypes.c_uint64), ("cand_per_query", ctypes.c_uint32),
+                ("pass_copy", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_queries", ctypes.c_uint32),
+                ("n_candidates", ctypes.c_uint64), ("n_pass", ctypes.c_uint64), ("pass_", ctypes.c_void_p),
+                ("t_submit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _U64 = ctypes.c_uint64
@@ -133,6 +145,13 @@ def load(build_if_missing: bool = True):
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
+        "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
+                               ctypes.POINTER(_VP)], st),
+        "pcl_server_submit": ([_VP, _VP, _VP, ctypes.c_uint32, _U64], st),
+        "pcl_server_poll": ([_VP, ctypes.POINTER(_Completion), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], st),
+        "pcl_server_release": ([_VP, _U64], st),
+        "pcl_server_stats": ([_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_U64)], st),
+        "pcl_server_destroy": ([_VP], None),
         "pcl_setcover": ([_VP, _U64, ctypes.c_uint32, _VP, _VP, ctypes.POINTER(ctypes.c_uint32)], st),
         "pcl_cluster_loop": ([_VP, _VP, _VP, _U64, ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_uint32),
                               ctypes.POINTER(ctypes.c_uint32)], st),
@@ -395,3 +414,68 @@ def match(ctx: Context, P: Params, mode: int, a: ClipSet, b: ClipSet, pairs, str
     out = torch.empty((int(pairs.shape[0]), 40), dtype=torch.uint8, device=pairs.device)
     pcl_match_pairs(ctx, P, mode, a, b, pairs.contiguous(), out, None, stream)
     return out
+
+
+class Server:
+    """pcl_server_*: resident library + continuously batched query requests."""
+
+    def __init__(self, ctx: Context, P: Params, library: ClipSet, max_inflight: int = 8,
+                 max_query_clips: int = 4096, max_query_rects: int = 4096 * 48, cand_per_query: int = 256,
+                 pass_copy: int = 1 << 16, mem_budget: int = 8 << 30):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.library = library  # keeps the library buffers alive
+        self._cl = library.cstruct()
+        cfg = _ServerCfg(max_inflight, max_query_clips, max_query_rects, cand_per_query, pass_copy, mem_budget)
+        h = _VP()
+        ctx.check(self.lib.pcl_server_create(ctx.h, ctypes.byref(P), ctypes.byref(self._cl), ctypes.byref(cfg),
+                                             ctypes.byref(h)), "pcl_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, rect_off: np.ndarray, rects: np.ndarray, request_id: int) -> bool:
+        """True if admitted, False if busy (no slot or memory); raises on errors."""
+        off = np.ascontiguousarray(rect_off, dtype=np.uint32)
+        r = np.ascontiguousarray(rects, dtype=np.int32).reshape(-1)
+        st = self.lib.pcl_server_submit(self.h, off.ctypes.data, r.ctypes.data if r.size else None,
+                                        off.shape[0] - 1, request_id)
+        if st == PCL_ERR_BUSY:
+            return False
+        self.ctx.check(st, "pcl_server_submit")
+        return True
+
+    def poll(self, cap: int = 64) -> list[dict]:
+        """Finished requests; their pass lists are copied out and the slots released."""
+        arr = (_Completion * cap)()
+        n = ctypes.c_uint32()
+        self.ctx.check(self.lib.pcl_server_poll(self.h, arr, cap, ctypes.byref(n)), "pcl_server_poll")
+        out = []
+        for c in arr[: n.value]:
+            k = int(c.n_pass)
+            if k:
+                buf = (ctypes.c_uint32 * (2 * k)).from_address(c.pass_)
+                pairs = np.frombuffer(buf, dtype=np.uint32).reshape(k, 2).copy()
+            else:
+                pairs = np.zeros((0, 2), np.uint32)
+            out.append(dict(id=int(c.request_id), status=int(c.status), n_queries=int(c.n_queries),
+                            n_candidates=int(c.n_candidates), pass_pairs=pairs, t_submit_ns=int(c.t_submit_ns),
+                            t_done_ns=int(c.t_done_ns)))
+            self.ctx.check(self.lib.pcl_server_release(self.h, c.request_id), "pcl_server_release")
+        return out
+
+    def stats(self):
+        k = ctypes.c_uint32()
+        f = _U64()
+        self.ctx.check(self.lib.pcl_server_stats(self.h, ctypes.byref(k), ctypes.byref(f)), "pcl_server_stats")
+        return int(k.value), int(f.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pcl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

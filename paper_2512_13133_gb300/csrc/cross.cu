@@ -1,0 +1,181 @@
+// a2 for two clip sets: cosine candidates between a query set Q and a
+// resident library L (Sec. 3.1 stage 1), used by the serving loop.
+//
+// The library is sorted by area once (launch_area_sort).  For a query of
+// area a the G1 survivors are exactly the library clips with area in
+// [floor(num^2 a / den^2) + 1, floor((den^2 a - 1) / num^2)], a contiguous range
+// of the sorted order.  Each query's range is cut into chunks of kChunk
+// positions; warps take (query, chunk) items from a global counter and test
+// G3 and G2 on every member with the whole warp, as in the self-join.
+#include "gates.cuh"
+
+namespace pcl {
+
+namespace {
+
+constexpr uint32_t kChunk = 1024;
+
+// per query: first sorted position, end position, chunk count
+__global__ void cross_prep_kernel(const uint32_t *qpop, uint32_t nq, const uint32_t *lib_cum, uint32_t vmax_all,
+                                  uint32_t num, uint32_t den, uint32_t *beg, uint32_t *end, uint32_t *nch) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const uint64_t a = qpop[q];
+    const uint64_t n2 = (uint64_t)num * num, d2 = (uint64_t)den * den;
+    uint64_t lo, hi;
+    if (a == 0) {
+        lo = 0;
+        hi = 0;
+    } else {
+        lo = n2 * a / d2 + 1;
+        hi = (d2 * a - 1) / n2;
+    }
+    if (hi > vmax_all) hi = vmax_all;
+    uint32_t b = 0, e = 0;
+    if (lo <= hi) {
+        b = lib_cum[lo];
+        e = lib_cum[hi + 1];
+    }
+    beg[q] = b;
+    end[q] = e;
+    nch[q] = (e - b + kChunk - 1) / kChunk;
+}
+
+// exclusive scan of v[0..m) into out[0..m], out[m] = total (single CTA)
+__global__ void __launch_bounds__(1024) scan_items_kernel(const uint32_t *v, uint32_t m, uint32_t *out) {
+    __shared__ uint32_t wsum[32];
+    const uint32_t per = (m + 1023) / 1024;
+    const uint32_t lo = threadIdx.x * per, hi = min(m, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += v[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (wid ? wsum[wid - 1] : 0u);
+    for (uint32_t i = lo; i < hi; ++i) {
+        out[i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 1023) out[m] = run;
+}
+
+__global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
+                                                         const uint32_t *lib_order, const uint32_t *lib_spop,
+                                                         const uint32_t *beg, const uint32_t *item_off,
+                                                         pcl_pair *out, uint64_t cap, unsigned long long *count,
+                                                         unsigned long long *local, unsigned int *next_item) {
+    const Geo g = make_geo(prm);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nq = Q.n_clips;
+    const uint32_t total = item_off[nq];
+    const int nb2 = g.nb * g.nb;
+    unsigned long long kept = 0, g2 = 0, g3 = 0;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(next_item, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        // query of item t: last q with item_off[q] <= t
+        uint32_t lo = 0, hi = nq;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (item_off[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t q = lo;
+        const uint32_t bend = item_off[nq + 1 + q];  // end of q's band
+        const uint32_t p0 = beg[q] + (t - item_off[q]) * kChunk;
+        const uint32_t p1 = min(p0 + kChunk, bend);
+        const uint64_t pa = Q.pop[q];
+        for (uint32_t pos = p0; pos < p1; ++pos) {
+            const uint32_t b = lib_order[pos];
+            const uint64_t pb = lib_spop[pos];
+            if (!(pa == 0 && pb == 0)) {
+                if (warp_g3_rejects(Q.blk + (size_t)q * 2 * nb2, L.blk + (size_t)b * 2 * nb2, nb2, pa, pb, prm.cos_num,
+                                    prm.cos_den, lane)) {
+                    ++g3;
+                    continue;
+                }
+                const uint32_t u2 =
+                    warp_g2(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)b * 2 * g.N, g.N, g.S, lane);
+                if (!cos_exceeds(u2, pa, pb, prm.cos_num, prm.cos_den)) {
+                    ++g2;
+                    continue;
+                }
+            }
+            ++kept;
+            if (lane == 0) {
+                const unsigned long long idx = atomicAdd(count, 1ull);
+                if (idx < cap) out[idx] = pcl_pair{q, b};
+            }
+        }
+    }
+    if (lane == 0) {
+        if (kept) atomicAdd(local + 0, kept);
+        if (g2) atomicAdd(local + PCL_GATE_G2_PROFILE, g2);
+        if (g3) atomicAdd(local + PCL_GATE_G3_DENSITY, g3);
+    }
+}
+
+__global__ void cross_finish_kernel(const unsigned long long *local, unsigned long long *gates,
+                                    unsigned long long total) {
+    if (threadIdx.x == 0 && gates) {
+        const unsigned long long seen = local[0] + local[PCL_GATE_G2_PROFILE] + local[PCL_GATE_G3_DENSITY];
+        gates[0] += local[0];
+        gates[PCL_GATE_G1_AREA] += total - seen;
+        gates[PCL_GATE_G2_PROFILE] += local[PCL_GATE_G2_PROFILE];
+        gates[PCL_GATE_G3_DENSITY] += local[PCL_GATE_G3_DENSITY];
+    }
+}
+
+}  // namespace
+
+// workspace of the cross join for nq queries: 16 u64 counters + next item
+// (64 B) + beg[nq] + nch[nq] + item offsets [nq + 1] + band ends [nq]
+size_t cross_join_workspace(uint32_t nq) { return 8 * 16 + 64 + 4 * (4 * (size_t)nq + 2); }
+
+cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const pcl_clipset &L,
+                              const uint32_t *lib_order, const uint32_t *lib_spop, const uint32_t *lib_cum,
+                              void *ws, size_t ws_bytes, pcl_pair *out, uint64_t cap, unsigned long long *count,
+                              unsigned long long *gates, int num_sms, cudaStream_t st) {
+    const Geo g = make_geo(prm);
+    const uint32_t nq = Q.n_clips;
+    if (ws_bytes < cross_join_workspace(nq)) return cudaErrorInvalidValue;
+    char *w = static_cast<char *>(ws);
+    unsigned long long *local = reinterpret_cast<unsigned long long *>(w);
+    unsigned int *next_item = reinterpret_cast<unsigned int *>(w + 8 * 16);
+    uint32_t *beg = reinterpret_cast<uint32_t *>(w + 8 * 16 + 64);
+    uint32_t *nch = beg + nq;
+    // item_off[0..nq] then band ends at item_off[nq + 1 + q]
+    uint32_t *item_off = nch + nq;
+    uint32_t *endp = item_off + nq + 1;
+    cudaError_t e = cudaMemsetAsync(w, 0, 8 * 16 + 64, st);
+    if (e != cudaSuccess) return e;
+    if (nq) {
+        cross_prep_kernel<<<(nq + 255) / 256, 256, 0, st>>>(Q.pop, nq, lib_cum, (uint32_t)g.N * g.N, prm.cos_num,
+                                                             prm.cos_den, beg, endp, nch);
+        scan_items_kernel<<<1, 1024, 0, st>>>(nch, nq, item_off);
+        cross_join_kernel<<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off, out, cap,
+                                                       count, local, next_item);
+    }
+    cross_finish_kernel<<<1, 32, 0, st>>>(local, gates, (unsigned long long)nq * L.n_clips);
+    return cudaGetLastError();
+}
+
+}  // namespace pcl

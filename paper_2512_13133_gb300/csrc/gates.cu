@@ -179,6 +179,19 @@ __global__ void finish_gates_kernel(const unsigned long long *local, unsigned lo
 
 }  // namespace
 
+// counting sort of n clips by area: cum[v] = #clips with area < v (V entries),
+// order/spop = clip indices and areas in ascending area order
+cudaError_t launch_area_sort(const uint32_t *pop, uint32_t n, uint32_t V, uint32_t *cum, uint32_t *fill,
+                             uint32_t *order, uint32_t *spop, int num_sms, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(cum, 0, 4 * (size_t)V, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, 4 * (size_t)V, st);
+    if (e != cudaSuccess) return e;
+    if (n) hist_kernel<<<num_sms * 4, 256, 0, st>>>(pop, n, cum);
+    scan_kernel<<<1, 1024, 0, st>>>(cum, V);
+    if (n) scatter_kernel<<<num_sms * 4, 256, 0, st>>>(pop, n, cum, fill, order, spop);
+    return cudaGetLastError();
+}
+
 // workspace bytes for the band join of n clips under g
 size_t band_join_workspace(const Geo &g, uint32_t n) {
     const size_t V = (size_t)g.N * g.N + 2;  // areas 0..N^2, plus the end slot

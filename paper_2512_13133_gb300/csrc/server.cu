@@ -1,0 +1,411 @@
+// a10: serving loop -- a resident representative library and continuously
+// batched query requests (cosine mode, FFT phase-correlation engine).
+//
+// The library's rasters, signatures and spectra stay in device memory, with
+// its clips sorted by area once.  Each admitted request gets a slot: its own
+// stream and a region of a fixed device arena holding the query clip set,
+// candidates and records.  Admission needs a free slot and room in the arena
+// (the memory budget), so requests that arrive while others run are admitted
+// as slots and memory free up, and their kernels overlap on the device.  A
+// request's work: host->device copy of its rectangles, rasterisation,
+// query x library candidate join, spectra of the referenced query clips,
+// phase-correlation matching, pass compaction, device->host copy of the pass
+// list; a host callback on the stream stamps the completion time.
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace pcl {
+cudaError_t launch_raster(const pcl_params &, const pcl_clipset &, cudaStream_t);
+cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool, cudaStream_t);
+cudaError_t launch_mark(const pcl_pair *, uint64_t, const unsigned long long *, pcl_clipset &, pcl_clipset &,
+                        cudaStream_t);
+cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                            const unsigned long long *, pcl_record *, int, cudaStream_t);
+cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
+                           unsigned long long *, cudaStream_t);
+cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
+                             int, cudaStream_t);
+size_t cross_join_workspace(uint32_t);
+cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
+                              const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
+                              unsigned long long *, unsigned long long *, int, cudaStream_t);
+}  // namespace pcl
+
+namespace {
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// first-fit allocator over one device region, 256-byte granules
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0;
+    std::map<size_t, size_t> free_;  // offset -> size
+    void init(char *b, size_t n) {
+        base = b;
+        bytes = n;
+        free_.clear();
+        free_[0] = n;
+    }
+    bool alloc(size_t n, size_t *off) {
+        n = align256(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n, at = it->first + n;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = align256(n);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Slot {
+    bool busy = false, done = false;
+    uint64_t id = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    size_t off = 0, bytes = 0;
+    uint32_t nq = 0;
+    uint64_t cap = 0;
+    pcl_clipset q{};
+    pcl_pair *cand = nullptr, *pass = nullptr;
+    pcl_record *rec = nullptr;
+    unsigned long long *counts = nullptr;  // [0] candidates, [1] pass
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    // pinned host staging
+    uint32_t *h_off = nullptr;
+    int32_t *h_rects = nullptr;
+    pcl_pair *h_pass = nullptr;
+    unsigned long long *h_counts = nullptr;
+    std::vector<pcl_pair> overflow;
+    int64_t t_submit = 0;
+    int64_t t_done = 0;  // written by the stream's host callback
+    pcl_completion comp{};
+};
+
+void CUDART_CB stamp_done(void *p) { static_cast<Slot *>(p)->t_done = now_ns(); }
+
+}  // namespace
+
+struct pcl_server {
+    pcl_ctx *ctx = nullptr;
+    pcl_params P{};
+    pcl::Geo g{};
+    pcl_server_cfg cfg{};
+    pcl_clipset lib{};
+    uint32_t *lib_cum = nullptr, *lib_fill = nullptr, *lib_order = nullptr, *lib_spop = nullptr;
+    char *arena_mem = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::mutex mu;
+};
+
+namespace {
+
+// device bytes of one request of nq clips and R rectangles with candidate capacity cap
+size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap) {
+    size_t b = 0;
+    b += align256(4ull * (nq + 1));                 // rect_off
+    b += align256(16ull * (R ? R : 1));             // rects
+    b += align256(8ull * nq * g.N * g.nw);          // bits
+    b += align256(4ull * nq);                       // pop
+    b += align256(4ull * nq * g.N);                 // prof
+    b += align256(4ull * nq * g.nb * g.nb);         // blk
+    b += align256(32ull * nq);                      // esig
+    b += align256(512ull * nq);                     // occ
+    b += align256(2ull * (R ? R : 1));              // rorder
+    b += align256(8ull * nq * g.L * g.Ls);          // spec
+    b += align256(nq);                              // spec_state
+    b += align256(8ull * cap) * 2;                  // cand, pass
+    b += align256(40ull * cap);                     // records
+    b += align256(64);                              // counts
+    b += align256(pcl::cross_join_workspace(nq));   // join workspace
+    return b;
+}
+
+void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint64_t cap) {
+    char *p = base;
+    auto take = [&](size_t n) {
+        char *r = p;
+        p += align256(n);
+        return r;
+    };
+    s.q.n_clips = nq;
+    s.q.rect_off = reinterpret_cast<uint32_t *>(take(4ull * (nq + 1)));
+    s.q.rects = reinterpret_cast<int32_t *>(take(16ull * (R ? R : 1)));
+    s.q.bits = reinterpret_cast<uint64_t *>(take(8ull * nq * g.N * g.nw));
+    s.q.pop = reinterpret_cast<uint32_t *>(take(4ull * nq));
+    s.q.prof = reinterpret_cast<uint16_t *>(take(4ull * nq * g.N));
+    s.q.blk = reinterpret_cast<uint16_t *>(take(4ull * nq * g.nb * g.nb));
+    s.q.esig = reinterpret_cast<int32_t *>(take(32ull * nq));
+    s.q.occ = reinterpret_cast<uint64_t *>(take(512ull * nq));
+    s.q.rorder = reinterpret_cast<uint16_t *>(take(2ull * (R ? R : 1)));
+    s.q.spec = take(8ull * nq * g.L * g.Ls);
+    s.q.spec_state = reinterpret_cast<uint8_t *>(take(nq));
+    s.cand = reinterpret_cast<pcl_pair *>(take(8ull * cap));
+    s.pass = reinterpret_cast<pcl_pair *>(take(8ull * cap));
+    s.rec = reinterpret_cast<pcl_record *>(take(40ull * cap));
+    s.counts = reinterpret_cast<unsigned long long *>(take(64));
+    s.ws_bytes = pcl::cross_join_workspace(nq);
+    s.ws = take(s.ws_bytes);
+}
+
+pcl_status fail(pcl_ctx *ctx, pcl_status s, const std::string &m) {
+    if (ctx) ctx->err = m;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *library,
+                             const pcl_server_cfg *cfg, pcl_server **out) {
+    if (!ctx || !out) return PCL_ERR_INVALID;
+    *out = nullptr;
+    ctx->err.clear();
+    if (pcl_params_validate(P) != PCL_OK) return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: invalid parameters");
+    if (!cfg || !library || cfg->max_inflight == 0 || cfg->max_inflight > 64 || cfg->max_query_clips == 0 ||
+        cfg->cand_per_query == 0)
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: invalid configuration");
+    if (!library->spec || !library->spec_state || !library->pop || !library->blk || !library->prof ||
+        !library->bits)
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters, signatures and spectra");
+    const pcl::Geo g = pcl::make_geo(*P);
+    if (g.N > 256 || g.S > g.N / 16)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(ctx, PCL_ERR_CUDA, "cudaSetDevice");
+    pcl_server *s = new (std::nothrow) pcl_server;
+    if (!s) return PCL_ERR_OOM;
+    s->ctx = ctx;
+    s->P = *P;
+    s->g = g;
+    s->cfg = *cfg;
+    s->lib = *library;
+    const uint32_t V = (uint32_t)g.N * g.N + 2;
+    const uint32_t nl = library->n_clips;
+    auto cleanup = [&](pcl_status st, const std::string &m) {
+        pcl_server_destroy(s);
+        return fail(ctx, st, m);
+    };
+    if (cudaMalloc(&s->lib_cum, 4ull * V) || cudaMalloc(&s->lib_fill, 4ull * V) ||
+        cudaMalloc(&s->lib_order, 4ull * (nl ? nl : 1)) || cudaMalloc(&s->lib_spop, 4ull * (nl ? nl : 1)) ||
+        cudaMalloc(&s->arena_mem, cfg->mem_budget ? cfg->mem_budget : 1)) {
+        cudaGetLastError();
+        return cleanup(PCL_ERR_OOM, "pcl_server_create: device allocation failed");
+    }
+    s->arena.init(s->arena_mem, cfg->mem_budget);
+    // resident library: spectra of every clip and the area order, once
+    e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
+    if (e == cudaSuccess)
+        e = pcl::launch_area_sort(library->pop, nl, V, s->lib_cum, s->lib_fill, s->lib_order, s->lib_spop,
+                                  ctx->num_sms, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cleanup(PCL_ERR_CUDA, std::string("library preparation: ") + cudaGetErrorString(e));
+    s->slots.resize(cfg->max_inflight);
+    const uint64_t cap_max = (uint64_t)cfg->cand_per_query * cfg->max_query_clips + 64;
+    const uint32_t pass_copy = cfg->pass_copy ? cfg->pass_copy : 1;
+    for (auto &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) ||
+            cudaMallocHost(&sl.h_off, 4ull * (cfg->max_query_clips + 1)) ||
+            cudaMallocHost(&sl.h_rects, 16ull * (cfg->max_query_rects ? cfg->max_query_rects : 1)) ||
+            cudaMallocHost(&sl.h_pass, 8ull * pass_copy) || cudaMallocHost(&sl.h_counts, 64)) {
+            cudaGetLastError();
+            return cleanup(PCL_ERR_OOM, "pcl_server_create: stream / pinned allocation failed");
+        }
+    }
+    (void)cap_max;
+    *out = s;
+    return PCL_OK;
+}
+
+pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const int32_t *h_rects, uint32_t n_clips,
+                             uint64_t request_id) {
+    if (!s) return PCL_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    pcl_ctx *ctx = s->ctx;
+    ctx->err.clear();
+    if (n_clips == 0 || n_clips > s->cfg.max_query_clips || !h_rect_off)
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_submit: clip count out of range");
+    const uint64_t R = h_rect_off[n_clips];
+    if (R > s->cfg.max_query_rects || (R && !h_rects))
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_submit: rectangle count out of range");
+    Slot *sl = nullptr;
+    for (auto &x : s->slots)
+        if (!x.busy) {
+            sl = &x;
+            break;
+        }
+    if (!sl) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: no free slot");
+    const uint64_t cap = (uint64_t)s->cfg.cand_per_query * n_clips + 64;
+    const size_t bytes = footprint(s->g, n_clips, R, cap);
+    size_t off = 0;
+    if (!s->arena.alloc(bytes, &off)) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: memory budget full");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    sl->busy = true;
+    sl->done = false;
+    sl->id = request_id;
+    sl->off = off;
+    sl->bytes = bytes;
+    sl->nq = n_clips;
+    sl->cap = cap;
+    sl->overflow.clear();
+    sl->t_done = 0;
+    sl->t_submit = now_ns();
+    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap);
+    std::memcpy(sl->h_off, h_rect_off, 4ull * (n_clips + 1));
+    if (R) std::memcpy(sl->h_rects, h_rects, 16ull * R);
+    cudaStream_t st = sl->st;
+    // rect offsets of the request relative to its own rectangle array
+    const uint32_t base = h_rect_off[0];
+    if (base)
+        for (uint32_t i = 0; i <= n_clips; ++i) sl->h_off[i] -= base;
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void *)sl->q.rect_off, sl->h_off, 4ull * (n_clips + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && R)
+        e = cudaMemcpyAsync((void *)sl->q.rects, sl->h_rects, 16ull * R, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl->counts, 0, 64, st);
+    if (e == cudaSuccess) e = pcl::launch_raster(s->P, sl->q, st);
+    if (e == cudaSuccess)
+        e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws, sl->ws_bytes,
+                                   sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
+    if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
+    if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
+    if (e == cudaSuccess)
+        e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
+    if (e == cudaSuccess) e = pcl::launch_compact(sl->rec, cap, sl->counts + 0, sl->pass, cap, sl->counts + 1, st);
+    const uint32_t pass_copy = s->cfg.pass_copy ? s->cfg.pass_copy : 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_counts, sl->counts, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl->h_pass, sl->pass, 8ull * (pass_copy < cap ? pass_copy : cap), cudaMemcpyDeviceToHost,
+                            st);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(st, stamp_done, sl);
+    if (e == cudaSuccess) e = cudaEventRecord(sl->ev, st);
+    if (e != cudaSuccess) {
+        // the slot keeps its memory until its stream is idle
+        cudaStreamSynchronize(st);
+        s->arena.release(sl->off, sl->bytes);
+        sl->busy = false;
+        return fail(ctx, PCL_ERR_CUDA, std::string("pcl_server_submit: ") + cudaGetErrorString(e));
+    }
+    return PCL_OK;
+}
+
+pcl_status pcl_server_poll(pcl_server *s, pcl_completion *out, uint32_t cap, uint32_t *n_out) {
+    if (!s || !n_out || (cap && !out)) return PCL_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    *n_out = 0;
+    cudaSetDevice(s->ctx->device);
+    const uint32_t pass_copy = s->cfg.pass_copy ? s->cfg.pass_copy : 1;
+    for (auto &sl : s->slots) {
+        if (!sl.busy || sl.done || *n_out >= cap) continue;
+        const cudaError_t q = cudaEventQuery(sl.ev);
+        if (q == cudaErrorNotReady) continue;
+        pcl_completion &c = sl.comp;
+        c = pcl_completion{};
+        c.request_id = sl.id;
+        c.n_queries = sl.nq;
+        c.t_submit_ns = sl.t_submit;
+        c.t_done_ns = sl.t_done;
+        if (q != cudaSuccess) {
+            c.status = PCL_ERR_CUDA;
+        } else {
+            c.n_candidates = sl.h_counts[0];
+            const uint64_t np = sl.h_counts[1];
+            c.status = (c.n_candidates > sl.cap) ? PCL_ERR_BUSY : PCL_OK;
+            const uint64_t got = np < sl.cap ? np : sl.cap;
+            c.n_pass = got;
+            if (got <= pass_copy) {
+                c.pass = sl.h_pass;
+            } else {
+                sl.overflow.resize(got);
+                cudaMemcpy(sl.overflow.data(), sl.pass, 8ull * got, cudaMemcpyDeviceToHost);
+                c.pass = sl.overflow.data();
+            }
+        }
+        sl.done = true;
+        out[(*n_out)++] = c;
+    }
+    return PCL_OK;
+}
+
+pcl_status pcl_server_release(pcl_server *s, uint64_t request_id) {
+    if (!s) return PCL_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto &sl : s->slots) {
+        if (sl.busy && sl.done && sl.id == request_id) {
+            s->arena.release(sl.off, sl.bytes);
+            sl.busy = false;
+            sl.done = false;
+            return PCL_OK;
+        }
+    }
+    return fail(s->ctx, PCL_ERR_INVALID, "pcl_server_release: no completed request with that id");
+}
+
+pcl_status pcl_server_stats(pcl_server *s, uint32_t *inflight, uint64_t *free_bytes) {
+    if (!s) return PCL_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    uint32_t k = 0;
+    for (auto &sl : s->slots) k += sl.busy ? 1u : 0u;
+    uint64_t f = 0;
+    for (auto &kv : s->arena.free_) f += kv.second;
+    if (inflight) *inflight = k;
+    if (free_bytes) *free_bytes = f;
+    return PCL_OK;
+}
+
+void pcl_server_destroy(pcl_server *s) {
+    if (!s) return;
+    cudaSetDevice(s->ctx->device);
+    for (auto &sl : s->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+        if (sl.h_off) cudaFreeHost(sl.h_off);
+        if (sl.h_rects) cudaFreeHost(sl.h_rects);
+        if (sl.h_pass) cudaFreeHost(sl.h_pass);
+        if (sl.h_counts) cudaFreeHost(sl.h_counts);
+    }
+    cudaFree(s->lib_cum);
+    cudaFree(s->lib_fill);
+    cudaFree(s->lib_order);
+    cudaFree(s->lib_spop);
+    cudaFree(s->arena_mem);
+    delete s;
+}
+
+}  // extern "C"

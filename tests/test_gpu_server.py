@@ -1,0 +1,150 @@
+"""Serving loop (a10): results of requests served against a resident library
+equal the oracle's, are the same alone and mixed with concurrent requests, and
+admission respects the slot count and the memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _translated_queries(lib, idx, rng, W):
+    """query clips: library clips moved by a few dbu (cut to the window)"""
+    clips = []
+    for i in idx:
+        r = lib.clip(int(i)).astype(np.int64).copy()
+        t = rng.integers(-8, 9, size=2)
+        r[:, [0, 2]] += t[0]
+        r[:, [1, 3]] += t[1]
+        r = np.clip(r, 0, W)
+        r = r[(r[:, 0] < r[:, 2]) & (r[:, 1] < r[:, 3])]
+        clips.append(r.tolist())
+    return synth.from_lists(clips, W, lib.pitch_dbu, lib.marker_dbu)
+
+
+def _wait_all(srv, ids, timeout=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < len(ids):
+        for c in srv.poll():
+            got[c["id"]] = c
+        if time.time() - t0 > timeout:
+            raise TimeoutError("server did not finish")
+        time.sleep(0.001)
+    return got
+
+
+def _pairset(a):
+    return set(map(tuple, np.asarray(a, dtype=np.int64).tolist()))
+
+
+@pytest.fixture(scope="module")
+def served(torch_cuda):
+    import paper_2512_13133_gb300 as pcl
+    lib = synth.preset("small", seed=4, n_clips=2000, n_seeds=200, n_copies=1200)
+    # a looser threshold than the benchmark's so that many pairs pass
+    P = pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, cos_num=80, cos_den=100)
+    ctx = pcl.Context(0)
+    cs = pcl.alloc_clipset(P, lib.rect_off, lib.rects)
+    pcl.pcl_rasterize(ctx, P, cs)
+    srv = pcl.Server(ctx, P, cs, max_inflight=4, max_query_clips=512, cand_per_query=2048,
+                     mem_budget=1 << 30)
+    rng = np.random.default_rng(9)
+    reqs = []
+    for k, n in enumerate([1, 7, 64, 200, 33, 512]):
+        idx = rng.choice(lib.n, n, replace=False)
+        reqs.append(_translated_queries(lib, idx, rng, lib.window_dbu))
+    return dict(pcl=pcl, lib=lib, P=P, ctx=ctx, cs=cs, srv=srv, reqs=reqs)
+
+
+def test_served_results_equal_oracle(served):
+    lib, srv, reqs = served["lib"], served["srv"], served["reqs"]
+    q = reqs[2]
+    assert srv.submit(q.rect_off, q.rects, 100)
+    res = _wait_all(srv, [100])[100]
+    assert res["status"] == 0
+    both = synth.from_lists([q.clip(i).tolist() for i in range(q.n)] +
+                            [lib.clip(i).tolist() for i in range(lib.n)], lib.window_dbu, lib.pitch_dbu,
+                            lib.marker_dbu)
+    orc = oracle.ClipSet(both)
+    pairs = np.array([(a, q.n + b) for a in range(q.n) for b in range(lib.n)], dtype=np.int64)
+    o = orc.match(pairs, oracle.MODE_COSINE, cos_num=80, cos_den=100)
+    cand = (o["flags"] & 15) == 0
+    assert res["n_candidates"] == int(cand.sum())
+    opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
+    assert _pairset(res["pass_pairs"]) == opass
+    assert len(opass) >= q.n  # every query passes against the clip it was moved from
+
+
+def test_same_alone_and_in_the_mix(served):
+    srv, reqs = served["srv"], served["reqs"]
+    alone = {}
+    for k, q in enumerate(reqs):
+        assert srv.submit(q.rect_off, q.rects, 1000 + k)
+        alone[k] = _wait_all(srv, [1000 + k])[1000 + k]
+    # all at once (up to four in flight), resubmitting when busy
+    pending = list(range(len(reqs))) * 2
+    ids, got, nid = {}, {}, 2000
+    t0 = time.time()
+    while pending or len(got) < len(ids):
+        while pending:
+            k = pending[0]
+            q = reqs[k]
+            if not srv.submit(q.rect_off, q.rects, nid):
+                break
+            ids[nid] = k
+            nid += 1
+            pending.pop(0)
+        for c in srv.poll():
+            got[c["id"]] = c
+        assert time.time() - t0 < 120
+    overlapped = 0
+    for rid, c in got.items():
+        a = alone[ids[rid]]
+        assert c["status"] == a["status"] == 0
+        assert c["n_candidates"] == a["n_candidates"]
+        assert _pairset(c["pass_pairs"]) == _pairset(a["pass_pairs"])
+    # requests did overlap in time on the device
+    spans = sorted((c["t_submit_ns"], c["t_done_ns"]) for c in got.values())
+    for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
+        overlapped += s1 < e0
+    assert overlapped > 0
+
+
+def test_admission_by_budget_and_slots(served):
+    pcl = served["pcl"]
+    lib, P, ctx, cs = served["lib"], served["P"], served["ctx"], served["cs"]
+    q = served["reqs"][5]  # 512 clips, about 105 MB of device footprint
+    # slots: two in flight at most (a slot frees only when its result is released)
+    a = pcl.Server(ctx, P, cs, max_inflight=2, max_query_clips=512, cand_per_query=2048, mem_budget=1 << 30)
+    admitted = [a.submit(q.rect_off, q.rects, i) for i in (1, 2, 3)]
+    assert admitted == [True, True, False]
+    done = _wait_all(a, [1, 2])
+    assert all(c["status"] == 0 for c in done.values())
+    assert a.stats() == (0, 1 << 30)
+    assert a.submit(q.rect_off, q.rects, 3)
+    _wait_all(a, [3])
+    a.close()
+    # memory: a 160 MB budget holds one such request, not two
+    b = pcl.Server(ctx, P, cs, max_inflight=4, max_query_clips=512, cand_per_query=2048, mem_budget=160 << 20)
+    assert b.submit(q.rect_off, q.rects, 1)
+    assert not b.submit(q.rect_off, q.rects, 2)
+    _wait_all(b, [1])
+    assert b.submit(q.rect_off, q.rects, 2)
+    _wait_all(b, [2])
+    with pytest.raises(pcl.PclError):
+        big = synth.from_lists([[[0, 0, 10, 10]]] * 600, lib.window_dbu, lib.pitch_dbu, lib.marker_dbu)
+        b.submit(big.rect_off, big.rects, 9)
+    b.close()
