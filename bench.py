@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--clips", type=int, default=0,
                     help="override the clip count (seeds and copies scale with it; profiling runs)")
     ap.add_argument("--no-fft-engine", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -156,6 +157,101 @@ def plain_e1_tests_per_pair(wl, n_sample: int = 20000, seed: int = 0) -> float:
             if hit.sum() != 1:
                 break
     return tot / n_sample
+
+
+def serving_requests(wl, n_req: int, seed: int = 7, max_clips: int = 4096):
+    """Query batches for the serving measurement: batch sizes log-uniform on
+    [1, max_clips]; each query clip is a library clip moved by U{-8..8} dbu
+    per axis and cut to the window (a new clip with matches in the library)."""
+    rng = np.random.default_rng(seed)
+    W = wl.window_dbu
+    off, R = wl.rect_off.astype(np.int64), wl.rects.astype(np.int64)
+    reqs = []
+    for _ in range(n_req):
+        k = int(np.exp(rng.uniform(0.0, np.log(max_clips))))
+        idx = rng.integers(0, wl.n, size=max(k, 1))
+        parts, counts = [], []
+        for i in idx:
+            r = R[off[i]:off[i + 1]].copy()
+            t = rng.integers(-8, 9, size=2)
+            r[:, [0, 2]] += t[0]
+            r[:, [1, 3]] += t[1]
+            np.clip(r, 0, W, out=r)
+            r = r[(r[:, 0] < r[:, 2]) & (r[:, 1] < r[:, 3])]
+            parts.append(r)
+            counts.append(len(r))
+        ro = np.zeros(len(parts) + 1, np.uint32)
+        ro[1:] = np.cumsum(counts)
+        reqs.append((ro, np.concatenate(parts).astype(np.int32) if parts else np.zeros((0, 4), np.int32)))
+    return reqs
+
+
+def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0):
+    """Continuous batching against the resident library: a closed-loop burst
+    gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it
+    give p50/p99 latency (arrival to device completion)."""
+    srv = pcl.Server(ctx, P, cs, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
+                     cand_per_query=64, mem_budget=24 << 30)
+    reqs = serving_requests(wl, 256)
+
+    def drive(arrivals):
+        """arrivals: monotonic ns per request (None: closed loop)"""
+        t0 = time.monotonic_ns()
+        queue, done, nxt = [], {}, 0
+        arr = {}
+        lat, pairs, clips = [], 0, 0
+        n_total = len(arrivals) if arrivals is not None else None
+        deadline = t0 + int(seconds * 1e9)
+        rid = 0
+        while True:
+            now = time.monotonic_ns()
+            if arrivals is None:
+                if now < deadline and len(queue) < 8:
+                    queue.append((rid, now))
+                    rid += 1
+            else:
+                while nxt < n_total and t0 + arrivals[nxt] <= now:
+                    queue.append((nxt, t0 + arrivals[nxt]))
+                    nxt += 1
+            while queue:
+                r, ta = queue[0]
+                ro, rr = reqs[r % len(reqs)]
+                if not srv.submit(ro, rr, r):
+                    break
+                arr[r] = ta
+                queue.pop(0)
+            for c in srv.poll():
+                lat.append((c["t_done_ns"] - arr[c["id"]]) / 1e6)
+                pairs += c["n_candidates"]
+                clips += c["n_queries"]
+                done[c["id"]] = c
+            if arrivals is None:
+                if now >= deadline and not queue and len(done) == rid:
+                    break
+            elif nxt >= n_total and not queue and len(done) == n_total:
+                break
+            time.sleep(0.0002)
+        wall = (time.monotonic_ns() - t0) / 1e9
+        return dict(requests=len(done), wall_s=wall, pairs_per_s=pairs / wall, query_clips_per_s=clips / wall,
+                    p50_ms=float(np.percentile(lat, 50)) if lat else None,
+                    p99_ms=float(np.percentile(lat, 99)) if lat else None)
+
+    drive(None)  # warm-up
+    sat = drive(None)
+    rps_sat = sat["requests"] / sat["wall_s"]
+    rng = np.random.default_rng(3)
+    out = {"library_clips": wl.n, "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
+    for frac in (0.5, 0.9):
+        lam = frac * rps_sat
+        n = max(8, int(lam * seconds))
+        gaps = rng.exponential(1.0 / lam, size=n)
+        arrivals = (np.cumsum(gaps) * 1e9).astype(np.int64)
+        r = drive(arrivals)
+        r["lambda_rps"] = lam
+        r["load"] = frac
+        out["poisson"].append(r)
+    srv.close()
+    return out
 
 
 def workload(config: str, seed: int, clips: int = 0):
@@ -348,6 +444,15 @@ def run_ours(args, rank, world, local_rank):
         pcl.pcl_rasterize(ctx, P, cs)
         torch.cuda.synchronize()
 
+    # ---- serving: continuous batching of query requests against the clip set
+    # as a resident library (p50/p99 latency beside throughput)
+    serving = None
+    if not args.no_serving and world == 1:
+        pcl.pcl_rasterize(ctx, P, cs)
+        serving = run_serving(pcl, ctx, P, cs, wl)
+        pcl.pcl_rasterize(ctx, P, cs)
+        torch.cuda.synchronize()
+
     # ---- end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -437,6 +542,7 @@ def run_ours(args, rank, world, local_rank):
                    "stage_ms": per_stage, "screened_pairs_per_s": 2 * total_pairs * world / (ms_max / 1e3),
                    "wall_s_timed": wall},
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
+        "serving": serving,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
     # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2
