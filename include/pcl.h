@@ -103,6 +103,7 @@ enum {
     PCL_GATE_G3_DENSITY = 3,  /* 16x16 block-density bound */
     PCL_GATE_E1_MATCH = 4,    /* no polygon correspondence at the pre-alignment */
     PCL_GATE_E2_BBOX = 5,     /* bbox size differs by more than 2*tol */
+    PCL_GATE_UNSUPPORTED = 14, /* size class outside the engine's range (no work done) */
     PCL_GATE_BAD_INDEX = 15,  /* pair index outside its clip set (no work done) */
     PCL_F_NEAR_BAND = 1u << 4,
     PCL_F_FFT_GUARD = 1u << 5,   /* FFT residual too large: exact scan used */
@@ -271,6 +272,36 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
    the count (may exceed cap).  Errors: PCL_ERR_INVALID, PCL_ERR_CUDA. */
 pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,
                             pcl_pair *d_out, uint64_t cap, uint64_t *d_count, pcl_stream stream);
+
+/* ---- a9: mixed batches in one persistent launch ---------------------------
+   One work item per pair: clip indices within the clip set of size class
+   `cls`, and the mode.  The list holds every PCL_MODE_COSINE item first
+   (n_cosine of them), then the PCL_MODE_EDGE items. */
+typedef struct pcl_work {
+    uint32_t a, b;
+    uint16_t cls;
+    uint16_t mode;
+} pcl_work;
+
+/* Launch parameters picked by the autotuner: fft_radix 2 or 4 (register DFT
+   of the FFT engine), ctas_per_sm (persistent CTAs per SM, 0 = as many as
+   fit). */
+typedef struct pcl_tuning {
+    uint32_t fft_radix;
+    uint32_t ctas_per_sm;
+} pcl_tuning;
+
+/* One record per work item, in list order, for n_classes (1..4) size classes
+   (params[c], sets[c]; a class's set serves as both sides of its pairs).
+   Spectra of referenced clips are computed first when missing; then a single
+   persistent kernel gates the cosine items a warp at a time, aligns the
+   survivors with the FFT engine of their class, and evaluates the edge items
+   one per thread.  Cosine items of a class with N > 256 or S > N/16 get
+   flags = PCL_GATE_UNSUPPORTED.  Uses 4 bytes of the context workspace.
+   Errors: PCL_ERR_INVALID, PCL_ERR_OOM, PCL_ERR_CUDA. */
+pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *sets, uint32_t n_classes,
+                           const pcl_work *d_work, uint64_t n_cosine, uint64_t n, pcl_record *d_out,
+                           const pcl_tuning *tune, pcl_stream stream);
 
 /* ---- a10: serving loop ----------------------------------------------------
    A resident representative library and continuously batched query requests

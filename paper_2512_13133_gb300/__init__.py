@@ -96,6 +96,14 @@ class _Pair(ctypes.Structure):
     _fields_ = [("a", ctypes.c_uint32), ("b", ctypes.c_uint32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("fft_radix", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+
+WORK_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("cls", "<u2"), ("mode", "<u2")])
+assert WORK_DTYPE.itemsize == 12
+
+
 class _ServerCfg(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_uint32), ("max_query_clips", ctypes.c_uint32),
                 ("max_query_rects", ctypes.c_uint64), ("cand_per_query", ctypes.c_uint32),
@@ -145,6 +153,7 @@ def load(build_if_missing: bool = True):
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
+        "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
                                ctypes.POINTER(_VP)], st),
         "pcl_server_submit": ([_VP, _VP, _VP, ctypes.c_uint32, _U64], st),
@@ -324,6 +333,19 @@ def pcl_match_pairs(ctx: Context, P: Params, mode: int, a: ClipSet, b: ClipSet, 
     ctx.check(ctx.lib.pcl_match_pairs(ctx.h, ctypes.byref(P), mode, ctypes.byref(ca), ctypes.byref(cb),
                                       _ptr(pairs), n, _ptr(d_n), _ptr(out_rec), _stream_ptr(stream)),
               "pcl_match_pairs")
+
+
+def pcl_match_mixed(ctx: Context, params_list, sets, work, n_cosine: int, out_rec, tune: Tuning | None = None,
+                    stream=None) -> None:
+    """params_list/sets: per size class; work: uint8 CUDA tensor [n, 12] of
+    pcl_work (cosine items first); out_rec: uint8 CUDA tensor [n, 40]."""
+    k = len(sets)
+    P_arr = (Params * k)(*params_list)
+    S_arr = (_Clipset * k)(*[c.cstruct() for c in sets])
+    n = int(work.shape[0])
+    ctx.check(ctx.lib.pcl_match_mixed(ctx.h, ctypes.cast(P_arr, _VP), ctypes.cast(S_arr, _VP), k, _ptr(work),
+                                      n_cosine, n, _ptr(out_rec), ctypes.byref(tune) if tune else None,
+                                      _stream_ptr(stream)), "pcl_match_mixed")
 
 
 def pcl_compact_pass(ctx: Context, rec, out_pairs, d_count, d_n=None, stream=None) -> None:

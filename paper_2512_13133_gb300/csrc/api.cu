@@ -25,6 +25,8 @@ cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_c
                             uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
                            unsigned long long *, cudaStream_t);
+cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
+                         pcl_record *, unsigned int *, uint32_t, uint32_t, int, cudaStream_t);
 }  // namespace pcl
 
 #include "ctx.h"
@@ -246,6 +248,28 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
         return cuda_fail(ctx, e, "spectra");
     e = launch_pair_fft(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "pair fft");
+}
+
+pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *sets, uint32_t n_classes,
+                           const pcl_work *d_work, uint64_t n_cosine, uint64_t n, pcl_record *d_out,
+                           const pcl_tuning *tune, pcl_stream stream) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (!params || !sets || n_classes == 0 || n_classes > 4 || n_cosine > n || (n && (!d_work || !d_out)))
+        return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: invalid arguments%s%lld");
+    for (uint32_t c = 0; c < n_classes; ++c) {
+        if (pcl_params_validate(&params[c])) return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: class %s%lld params", "", c);
+        if ((s = check_clipset(ctx, &sets[c], true))) return s;
+        if (n_cosine && (!sets[c].spec || !sets[c].spec_state))
+            return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: class %s%lld lacks spectra buffers", "", c);
+    }
+    const uint32_t radix = tune && tune->fft_radix == 4 ? 4 : 2;
+    const uint32_t ctas = tune ? tune->ctas_per_sm : 0;
+    if ((s = ensure_ws(ctx, 256))) return s;
+    const cudaError_t e = launch_mixed(params, sets, n_classes, d_work, n_cosine, n, d_out,
+                                       static_cast<unsigned int *>(ctx->ws), radix, ctas, ctx->num_sms,
+                                       (cudaStream_t)stream);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "mixed batch");
 }
 
 pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "pcl.h"
 
 namespace pcl {
@@ -136,6 +138,64 @@ __device__ __forceinline__ void dft_pow2(float2 (&v)[P]) {
         }
     }
     dft_stages<P, SIGN, 2>(v);
+}
+
+// ---- radix-4 decimation in frequency (natural input, digit-reversed output
+// reordered at compile time).  Radices: 4 while the block size is divisible
+// by 4, then one radix-2 step (P = 8, 32).
+__host__ __device__ constexpr int dif_freq(int p, int n) {
+    // frequency held at position p of a DIF transform of size n
+    return n == 1 ? 0
+         : (n % 4 == 0) ? 4 * dif_freq(p % (n / 4), n / 4) + p / (n / 4)
+                        : 2 * dif_freq(p % (n / 2), n / 2) + p / (n / 2);
+}
+
+template <int P, int SIGN, int BASE, int N>
+__device__ __forceinline__ void dif_block(float2 (&v)[P]) {
+    if constexpr (N == 2) {
+        const float2 a = v[BASE], b = v[BASE + 1];
+        v[BASE] = cadd(a, b);
+        v[BASE + 1] = csub(a, b);
+    } else if constexpr (N >= 4) {
+        constexpr int Q = N / 4;
+        [&]<int... J>(std::integer_sequence<int, J...>) {
+            ((void)([&] {
+                 const float2 a = v[BASE + J], b = v[BASE + J + Q], c = v[BASE + J + 2 * Q],
+                              d = v[BASE + J + 3 * Q];
+                 const float2 s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = csub(b, d);
+                 // SIGN * i * d1
+                 const float2 r = SIGN > 0 ? make_float2(-d1.y, d1.x) : make_float2(d1.y, -d1.x);
+                 v[BASE + J] = cadd(s0, s1);
+                 v[BASE + J + Q] = rot64<J * 1 * (64 / N), SIGN>(cadd(d0, r));
+                 v[BASE + J + 2 * Q] = rot64<J * 2 * (64 / N), SIGN>(csub(s0, s1));
+                 v[BASE + J + 3 * Q] = rot64<J * 3 * (64 / N), SIGN>(csub(d0, r));
+             }()),
+             ...);
+        }(std::make_integer_sequence<int, Q>{});
+        dif_block<P, SIGN, BASE, Q>(v);
+        dif_block<P, SIGN, BASE + Q, Q>(v);
+        dif_block<P, SIGN, BASE + 2 * Q, Q>(v);
+        dif_block<P, SIGN, BASE + 3 * Q, Q>(v);
+    }
+}
+
+// In-register DFT of length P by radix-4 DIF (same result as dft_pow2)
+template <int P, int SIGN>
+__device__ __forceinline__ void dft_pow2_r4(float2 (&v)[P]) {
+    static_assert(P >= 4 && P <= 64 && (P & (P - 1)) == 0, "P must be a power of two in [4, 64]");
+    dif_block<P, SIGN, 0, P>(v);
+    float2 t[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) t[dif_freq(p, P)] = v[p];
+#pragma unroll
+    for (int p = 0; p < P; ++p) v[p] = t[p];
+}
+
+// DFT of length P with the radix chosen at compile time (2 or 4)
+template <int P, int SIGN, int RADIX>
+__device__ __forceinline__ void dft_p(float2 (&v)[P]) {
+    if constexpr (RADIX == 4) dft_pow2_r4<P, SIGN>(v);
+    else dft_pow2<P, SIGN>(v);
 }
 
 // 3-point DFT, sign SIGN

@@ -7,183 +7,12 @@
 // its own pair instead of idling lanes on small clips.  Partners are
 // recomputed by scanning rather than stored, so no per-thread arrays are
 // needed for any polygon count.
-#include <climits>
-
-#include "common.cuh"
+#include "edge_dev.cuh"
 
 namespace pcl {
 
 namespace {
-
-struct EdgeOut {
-    int gate;      // PCL_GATE_* (0: passed the gates)
-    int tx, ty;    // translation applied to B (dbu)
-    int E;         // max(E_x, E_y)
-    bool verified; // correspondence unchanged at T
-    bool pass;
-    bool empty;
-};
-
-__device__ __forceinline__ bool ovl(const int4 a, const int4 b, int tx, int ty) {
-    return a.x < b.z + tx && b.x + tx < a.z && a.y < b.w + ty && b.y + ty < a.w;
-}
-
-// partner of small-side polygon k at shift (tx, ty): index in the large list,
-// -1 if none, -2 if more than one.
-__device__ __forceinline__ int partner(const int4 *__restrict__ rs, const int4 *__restrict__ rl, int nl,
-                                       bool small_is_a, int k, int tx, int ty) {
-    const int4 s = __ldg(rs + k);
-    int who = -1;
-    for (int m = 0; m < nl; ++m) {
-        const int4 l = __ldg(rl + m);
-        const bool hit = small_is_a ? ovl(s, l, tx, ty) : ovl(l, s, tx, ty);
-        if (hit) {
-            if (who >= 0) return -2;
-            who = m;
-        }
-    }
-    return who;
-}
-
-// correspondence (Sec. 2.2.2 condition 1) at shift t, with injectivity
-__device__ bool correspond(const int4 *rs, int ns, const int4 *rl, int nl, bool small_is_a, int tx,
-                           int ty) {
-    for (int k = 0; k < ns; ++k)
-        if (partner(rs, rl, nl, small_is_a, k, tx, ty) < 0) return false;
-    // every small polygon has exactly one partner; the map is injective iff no
-    // large polygon overlaps two small polygons
-    for (int m = 0; m < nl; ++m) {
-        const int4 l = __ldg(rl + m);
-        int cnt = 0;
-        for (int k = 0; k < ns && cnt < 2; ++k) {
-            const int4 s = __ldg(rs + k);
-            cnt += (small_is_a ? ovl(s, l, tx, ty) : ovl(l, s, tx, ty)) ? 1 : 0;
-        }
-        if (cnt > 1) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-
-// grid cell of coordinate v: floor(v / csz) clamped to the 64 cells; csh >= 0
-// is log2(csz) when csz is a power of two (arithmetic shift = floor division)
-__device__ __forceinline__ int cell_of(int v, int csz, int csh) {
-    const int q = csh >= 0 ? (v >> csh) : (v >= 0 ? v / csz : -((-v + csz - 1) / csz));
-    return min(max(q, 0), 63);
-}
-
-// Does rectangle [x0,x1) x [y0,y1) (in the frame of the clip owning occ) meet
-// a marked cell of its occupancy grid?  Positive-area overlap with any of the
-// clip's rectangles implies a shared marked cell, so "false" proves that the
-// rectangle overlaps none of them.
-__device__ __forceinline__ bool grid_hit(const uint64_t *__restrict__ occ, int x0, int y0, int x1, int y1,
-                                         int csz, int csh) {
-    if (x1 <= x0 || y1 <= y0) return true;  // degenerate input: no pruning
-    const int cx0 = cell_of(x0, csz, csh), cx1 = cell_of(x1 - 1, csz, csh);
-    const int cy0 = cell_of(y0, csz, csh), cy1 = cell_of(y1 - 1, csz, csh);
-    const uint64_t m = (~0ull >> (63 - (cx1 - cx0))) << cx0;
-    for (int cy = cy0; cy <= cy1; ++cy)
-        if (__ldg(occ + cy) & m) return true;
-    return false;
-}
-
-struct ClipView {
-    const int4 *r;       // rectangles
-    const int32_t *e;    // edge signature
-    const uint16_t *ro;  // rectangles by ascending area
-    const uint64_t *occ; // occupancy grid
-};
-
-// Gates E2 and E1 and, unless screen_only, the full Min-Max procedure.
-__device__ EdgeOut edge_eval(const ClipView &A, const ClipView &B, int W, int M, int tol, bool gates,
-                             bool screen_only) {
-    const int4 *ra = A.r, *rb = B.r;
-    const int32_t *ea = A.e, *eb = B.e;
-    EdgeOut o{};
-    const int na = ea[ES_N], nb = eb[ES_N];
-    if (na == 0 && nb == 0) {
-        o.empty = true;
-        o.pass = true;
-        o.verified = true;
-        return o;
-    }
-    if (na == 0 || nb == 0) {
-        o.gate = PCL_GATE_E1_MATCH;
-        return o;
-    }
-    const int lxa = ea[ES_LOX], uxa = ea[ES_HIX], lya = ea[ES_LOY], uya = ea[ES_HIY];
-    const int lxb = eb[ES_LOX], uxb = eb[ES_HIX], lyb = eb[ES_LOY], uyb = eb[ES_HIY];
-    if (gates && na == nb && !ea[ES_BORDER] && !eb[ES_BORDER]) {
-        // E2: with a bijection and no border edges every displacement lies in
-        // [T - tol, T + tol], so the bbox sizes differ by at most 2 tol
-        if (abs((uxa - lxa) - (uxb - lxb)) > 2 * tol || abs((uya - lya) - (uyb - lyb)) > 2 * tol) {
-            o.gate = PCL_GATE_E2_BBOX;
-            return o;
-        }
-    }
-    // pre-alignment: difference of the bbox centres (doubled centres halved,
-    // truncated toward zero), clamped to the marker window
-    const int s0x = (ea[ES_HASX] && eb[ES_HASX]) ? clampi(((lxa + uxa) - (lxb + uxb)) / 2, -M, M) : 0;
-    const int s0y = (ea[ES_HASY] && eb[ES_HASY]) ? clampi(((lya + uya) - (lyb + uyb)) / 2, -M, M) : 0;
-    const bool small_is_a = na <= nb;
-    const int4 *rs = small_is_a ? ra : rb;
-    const int4 *rl = small_is_a ? rb : ra;
-    const int ns = small_is_a ? na : nb, nl = small_is_a ? nb : na;
-    o.tx = s0x;
-    o.ty = s0y;
-    // occupancy pre-check of E1, smallest polygons first (most likely to meet
-    // nothing): a small polygon over empty cells of the other clip has no partner
-    {
-        const uint16_t *ro = small_is_a ? A.ro : B.ro;
-        const uint64_t *occ_l = small_is_a ? B.occ : A.occ;
-        const int csz = W / 64;
-        const int csh = (csz & (csz - 1)) == 0 ? __ffs(csz) - 1 : -1;
-        // small polygon in the large clip's frame: a - t (small is A) or b + t
-        const int sx = small_is_a ? -s0x : s0x, sy = small_is_a ? -s0y : s0y;
-        for (int k = 0; k < ns; ++k) {
-            const int4 q = __ldg(rs + __ldg(ro + k));
-            if (!grid_hit(occ_l, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz, csh)) {
-                o.gate = PCL_GATE_E1_MATCH;
-                return o;
-            }
-        }
-    }
-    if (!correspond(rs, ns, rl, nl, small_is_a, s0x, s0y)) {
-        o.gate = PCL_GATE_E1_MATCH;
-        return o;
-    }
-    if (screen_only) return o;
-    // displacements d = e_A - e_B of matched edges off the window border
-    int cx = 0, cy = 0, dminx = INT_MAX, dmaxx = INT_MIN, dminy = INT_MAX, dmaxy = INT_MIN;
-    for (int k = 0; k < ns; ++k) {
-        const int m = partner(rs, rl, nl, small_is_a, k, s0x, s0y);
-        const int4 pa = __ldg(small_is_a ? ra + k : ra + m);
-        const int4 pb = __ldg(small_is_a ? rb + m : rb + k);
-        if (pa.x != 0 && pb.x != 0) { const int d = pa.x - pb.x; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
-        if (pa.z != W && pb.z != W) { const int d = pa.z - pb.z; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
-        if (pa.y != 0 && pb.y != 0) { const int d = pa.y - pb.y; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
-        if (pa.w != W && pb.w != W) { const int d = pa.w - pb.w; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
-    }
-    // Eq. 6 per separable axis: midpoint (trunc toward zero), clamped
-    const int Tx = cx ? clampi((dminx + dmaxx) / 2, -M, M) : s0x;
-    const int Ty = cy ? clampi((dminy + dmaxy) / 2, -M, M) : s0y;
-    const int Ex = cx ? max(Tx - dminx, dmaxx - Tx) : 0;
-    const int Ey = cy ? max(Ty - dminy, dmaxy - Ty) : 0;
-    // the correspondence must hold at T with the same partners
-    bool ok = true;
-    for (int k = 0; k < ns && ok; ++k) {
-        const int m0 = partner(rs, rl, nl, small_is_a, k, s0x, s0y);
-        const int m1 = partner(rs, rl, nl, small_is_a, k, Tx, Ty);
-        ok = (m0 == m1);
-    }
-    o.tx = Tx;
-    o.ty = Ty;
-    o.E = max(Ex, Ey);
-    o.verified = ok;
-    o.pass = ok && Ex <= tol && Ey <= tol;
-    return o;
-}
+using namespace edge_dev;
 
 __device__ __forceinline__ void emit_pair(pcl_pair *out, uint64_t cap, unsigned long long *count,
                                           bool keep, uint32_t a, uint32_t b) {
@@ -354,41 +183,7 @@ __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_cli
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d_n && *d_n < n) n = *d_n;
     if (t >= n) return;
-    const pcl_pair pr = pairs[t];
-    pcl_record r{};
-    r.a = pr.a;
-    r.b = pr.b;
-    r.mode = PCL_MODE_EDGE;
-    if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
-        r.flags = PCL_GATE_BAD_INDEX;
-        out[t] = r;
-        return;
-    }
-    int32_t ea[8], eb[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        ea[k] = __ldg(A.esig + (size_t)pr.a * 8 + k);
-        eb[k] = __ldg(B.esig + (size_t)pr.b * 8 + k);
-    }
-    const uint32_t oa = __ldg(A.rect_off + pr.a), ob = __ldg(B.rect_off + pr.b);
-    const ClipView va{reinterpret_cast<const int4 *>(A.rects) + oa, ea, A.rorder + oa, A.occ + (size_t)pr.a * 64};
-    const ClipView vb{reinterpret_cast<const int4 *>(B.rects) + ob, eb, B.rorder + ob, B.occ + (size_t)pr.b * 64};
-    const bool gates = !(prm.flags & PCL_P_NO_GATES);
-    const EdgeOut o = edge_eval(va, vb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu, gates, false);
-    r.dx_dbu = o.tx;
-    r.dy_dbu = o.ty;
-    if (o.empty) {
-        r.flags = PCL_F_EMPTY;
-        r.pass = 1;
-    } else if (o.gate) {
-        r.flags = (uint16_t)o.gate;
-    } else {
-        r.flags = PCL_F_ALIGNED | (o.verified ? 0 : PCL_F_EDGE_VERIFY_FAIL);
-        r.score = (uint32_t)o.E;
-        r.sim = (float)o.E;
-        r.pass = o.pass ? 1 : 0;
-    }
-    out[t] = r;
+    out[t] = edge_record(prm, A, B, pairs[t]);
 }
 
 }  // namespace

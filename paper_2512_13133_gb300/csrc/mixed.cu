@@ -1,0 +1,172 @@
+// a9: one persistent launch over a mixed batch -- pairs of several raster
+// size classes, cosine (FFT phase correlation) and edge (Min-Max) modes
+// together, with uneven candidate lists.
+//
+// The work list holds the cosine items first, then the edge items.  Each CTA
+// (320 threads, shared memory sized for the largest FFT) repeatedly claims a
+// group of one cosine item per warp; every warp checks its item's indices,
+// emptiness and lossless gates in parallel, and the survivors are then
+// aligned one after the other by the whole CTA with the FFT body of their
+// size class.  When the cosine items are exhausted, every thread takes edge
+// items with a grid stride.  The register DFT radix (2 or 4) and the number
+// of CTAs per SM are tuning parameters (chosen by the autotuner).
+#include "edge_dev.cuh"
+#include "fft_dev.cuh"
+
+namespace pcl {
+
+namespace {
+
+using namespace fft_dev;
+using namespace edge_dev;
+
+constexpr int kMaxClasses = 4;
+constexpr int kThreads = 320;  // ten warps: the pass-1 tasks of P = 32
+constexpr int kWarps = kThreads / 32;
+
+struct MixedArgs {
+    pcl_params prm[kMaxClasses];
+    pcl_clipset cs[kMaxClasses];
+    uint32_t n_classes;
+};
+
+__global__ void mark_mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t n_cos) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_cos;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const pcl_work w = work[t];
+        if (w.cls >= args.n_classes) continue;
+        const pcl_clipset &c = args.cs[w.cls];
+        if (w.a < c.n_clips && c.spec_state[w.a] == 0) c.spec_state[w.a] = 2;
+        if (w.b < c.n_clips && c.spec_state[w.b] == 0) c.spec_state[w.b] = 2;
+    }
+}
+
+template <int RADIX>
+__global__ void __launch_bounds__(kThreads, 1)
+    mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t n_cos, uint64_t n, pcl_record *out,
+                 unsigned int *cursor) {
+    __shared__ uint64_t grp_base;
+    __shared__ uint64_t surv[kWarps];
+    __shared__ int n_surv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // ---- cosine items: gate a group in parallel, align the survivors
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            grp_base = atomicAdd(cursor, (unsigned)kWarps);
+            n_surv = 0;
+        }
+        __syncthreads();
+        const uint64_t base = grp_base;
+        if (base >= n_cos) break;
+        const uint64_t t = base + warp;
+        if (t < n_cos) {
+            const pcl_work w = work[t];
+            pcl_record rec{};
+            rec.a = w.a;
+            rec.b = w.b;
+            rec.mode = PCL_MODE_COSINE;
+            bool done = true;
+            if (w.cls >= args.n_classes || w.a >= args.cs[w.cls].n_clips || w.b >= args.cs[w.cls].n_clips) {
+                rec.flags = PCL_GATE_BAD_INDEX;
+            } else {
+                const pcl_params &prm = args.prm[w.cls];
+                const pcl_clipset &cs = args.cs[w.cls];
+                const Geo g = make_geo(prm);
+                const uint64_t pa = cs.pop[w.a], pb = cs.pop[w.b];
+                if (g.P > 32 || g.S > g.N / 16) {
+                    rec.flags = PCL_GATE_UNSUPPORTED;
+                } else if (pa == 0 && pb == 0) {
+                    rec.flags = PCL_F_EMPTY;
+                    rec.sim = 1.0f;
+                    rec.pass = 1;
+                } else {
+                    int gate = 0;
+                    if (!(prm.flags & PCL_P_NO_GATES))
+                        gate = warp_cosine_gate(cs, w.a, cs, w.b, g, prm.cos_num, prm.cos_den, lane);
+                    if (gate) rec.flags = (uint16_t)gate;
+                    else done = false;
+                }
+            }
+            if (lane == 0) {
+                if (done) out[t] = rec;
+                else surv[atomicAdd(&n_surv, 1)] = t;
+            }
+        }
+        __syncthreads();
+        const int ns = n_surv;
+        for (int k = 0; k < ns; ++k) {
+            const uint64_t ti = surv[k];
+            const pcl_work w = work[ti];
+            const pcl_params &prm = args.prm[w.cls];
+            const pcl_clipset &cs = args.cs[w.cls];
+            switch (make_geo(prm).P) {
+                case 8: pair_body<8, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
+                case 16: pair_body<16, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
+                default: pair_body<32, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- edge items, one per thread
+    for (uint64_t t = n_cos + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const pcl_work w = work[t];
+        if (w.cls >= args.n_classes) {
+            pcl_record r{};
+            r.a = w.a;
+            r.b = w.b;
+            r.mode = PCL_MODE_EDGE;
+            r.flags = PCL_GATE_BAD_INDEX;
+            out[t] = r;
+            continue;
+        }
+        out[t] = edge_record(args.prm[w.cls], args.cs[w.cls], args.cs[w.cls], pcl_pair{w.a, w.b});
+    }
+}
+
+size_t mixed_smem() { return PairSmem<32>::bytes; }
+
+}  // namespace
+
+cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool, cudaStream_t);
+
+cudaError_t launch_mixed(const pcl_params *prm, const pcl_clipset *sets, uint32_t n_classes, const pcl_work *work,
+                         uint64_t n_cos, uint64_t n, pcl_record *out, unsigned int *cursor, uint32_t radix,
+                         uint32_t ctas_per_sm, int num_sms, cudaStream_t st) {
+    if (n_classes == 0 || n_classes > kMaxClasses) return cudaErrorInvalidValue;
+    MixedArgs args{};
+    args.n_classes = n_classes;
+    for (uint32_t c = 0; c < n_classes; ++c) {
+        args.prm[c] = prm[c];
+        args.cs[c] = sets[c];
+    }
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    if (n_cos) {
+        mark_mixed_kernel<<<1024, 256, 0, st>>>(args, work, n_cos);
+        for (uint32_t c = 0; c < n_classes; ++c) {
+            if (!sets[c].spec_state || make_geo(prm[c]).P > 32) continue;
+            if ((e = launch_spectra(prm[c], sets[c], nullptr, 0, true, st)) != cudaSuccess) return e;
+        }
+    }
+    const size_t sm = mixed_smem();
+    int per_sm = 0;
+    if (radix == 4) {
+        e = cudaFuncSetAttribute(mixed_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel<4>, kThreads, sm);
+    } else {
+        e = cudaFuncSetAttribute(mixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel<2>, kThreads, sm);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ctas = (ctas_per_sm == 0 || (int)ctas_per_sm > per_sm) ? per_sm : (int)ctas_per_sm;
+    const unsigned grid = (unsigned)(num_sms * ctas);
+    if (n == 0) return cudaSuccess;
+    if (radix == 4) mixed_kernel<4><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor);
+    else mixed_kernel<2><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor);
+    return cudaGetLastError();
+}
+
+}  // namespace pcl

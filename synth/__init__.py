@@ -153,3 +153,49 @@ def from_lists(clips, window_dbu: int, pitch_dbu: int = 4, marker_dbu: int = 0,
     rects = np.array(flat, dtype=np.int32).reshape(-1, 4)
     return Workload(name, window_dbu, pitch_dbu, marker_dbu, off, rects,
                     np.full(len(clips), -1, np.int32))
+
+
+def batched(seed: int = 1, clips_per_class: int = 1000, sizes=(64, 128, 256, 512), pitch_dbu: int = 4,
+            zipf_s: float = 1.1, max_list: int = 5000, same_seed_frac: float = 0.5, min_rects: int = 5,
+            max_rects: int = 40):
+    """Mixed-size batch: one clip set per raster size (W = N * pitch, marker
+    half-width W/16, 70 % perturbed copies), and per clip a candidate list of
+    Zipf(zipf_s) length truncated to [1, max_list]; a partner is drawn from the
+    clip's seed group with probability same_seed_frac (when it has one), else
+    uniformly from its size class.  Each pair gets a mode, cosine or edge,
+    with probability 1/2.  Returns (workloads, pairs[m, 3] = (class, a, b),
+    modes[m])."""
+    rng = np.random.default_rng(seed)
+    wls = []
+    for k, N in enumerate(sizes):
+        W = N * pitch_dbu
+        M = W // 16
+        n_seeds = max(1, clips_per_class // 20)
+        wls.append(generate(seed * 101 + k, n_clips=clips_per_class, n_seeds=n_seeds,
+                            n_copies=int(0.7 * clips_per_class), window_dbu=W, margin_dbu=M,
+                            min_rects=min_rects, max_rects=max_rects, pitch_dbu=pitch_dbu, name=f"batched{N}"))
+    # truncated Zipf: P(k) proportional to k^-s on [1, max_list] (inverse CDF)
+    ks = np.arange(1, max_list + 1, dtype=np.float64)
+    cdf = np.cumsum(ks ** -zipf_s)
+    cdf /= cdf[-1]
+    out = []
+    for k, wl in enumerate(wls):
+        n = wl.n
+        lab = wl.label.astype(np.int64)
+        lens = 1 + np.searchsorted(cdf, rng.random(n), side="right")
+        lens = np.minimum(lens, max_list)
+        a = np.repeat(np.arange(n), lens)
+        b = rng.integers(0, n, size=a.shape[0])
+        # same-seed partners: members of each seed group, grouped by label
+        order = np.argsort(lab, kind="stable")
+        ls = lab[order]
+        first = np.searchsorted(ls, lab, side="left")
+        size = np.searchsorted(ls, lab, side="right") - first
+        same = (rng.random(a.shape[0]) < same_seed_frac) & (lab[a] >= 0) & (size[a] > 1)
+        pick = first[a[same]] + (rng.random(int(same.sum())) * size[a[same]]).astype(np.int64)
+        b[same] = order[pick]
+        keep = a != b
+        out.append(np.stack([np.full(int(keep.sum()), k), a[keep], b[keep]], 1))
+    pairs = np.concatenate(out).astype(np.int64)
+    modes = np.where(rng.random(len(pairs)) < 0.5, 1, 2).astype(np.int64)
+    return wls, pairs, modes

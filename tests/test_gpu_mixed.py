@@ -1,0 +1,101 @@
+"""One persistent launch over a mixed batch (a9): four raster sizes, cosine
+and edge pairs interleaved in one list, Zipf-length candidate lists.  The
+records equal those of the per-class entry points and the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def batch(torch_cuda):
+    import paper_2512_13133_gb300 as pcl
+    wls, pairs, modes = synth.batched(3, clips_per_class=240)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(pairs), min(len(pairs), 60000), replace=False))
+    pairs, modes = pairs[pick], modes[pick]
+    order = np.lexsort((pairs[:, 1], pairs[:, 0], modes))  # cosine first, then by class and a
+    pairs, modes = pairs[order], modes[order]
+    ctx = pcl.Context(0)
+    Ps, sets = [], []
+    for wl in wls:
+        P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu)
+        cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=wl.raster_n <= 256)
+        if cs.spec is None:  # the 512 class holds no spectra; give it a stub so the API accepts it
+            cs.spec = torch_cuda.empty(16, dtype=torch_cuda.uint8, device="cuda")
+            cs.spec_state = torch_cuda.ones(max(wl.n, 16), dtype=torch_cuda.uint8, device="cuda")
+        pcl.pcl_rasterize(ctx, P, cs)
+        if wl.raster_n > 256:
+            cs.spec_state.fill_(1)  # no spectra to compute for this class
+        Ps.append(P)
+        sets.append(cs)
+    work = np.zeros(len(pairs), dtype=pcl.WORK_DTYPE)
+    work["cls"], work["a"], work["b"], work["mode"] = pairs[:, 0], pairs[:, 1], pairs[:, 2], modes
+    n_cos = int((modes == 1).sum())
+    tw = torch_cuda.from_numpy(work.view(np.uint8).reshape(-1, 12)).cuda()
+    return dict(pcl=pcl, wls=wls, pairs=pairs, modes=modes, ctx=ctx, Ps=Ps, sets=sets, tw=tw, n_cos=n_cos)
+
+
+def _run_mixed(b, radix, torch):
+    pcl = b["pcl"]
+    out = torch.empty((b["tw"].shape[0], 40), dtype=torch.uint8, device="cuda")
+    pcl.pcl_match_mixed(b["ctx"], b["Ps"], b["sets"], b["tw"], b["n_cos"], out, pcl.Tuning(radix, 0))
+    return pcl.records_to_numpy(out)
+
+
+EXACT = ["a", "b", "dx_dbu", "dy_dbu", "score", "pass_", "mode"]
+
+
+@pytest.mark.parametrize("radix", [2, 4])
+def test_mixed_equals_per_class_entry_points(batch, torch_cuda, radix):
+    pcl = batch["pcl"]
+    g = _run_mixed(batch, radix, torch_cuda)
+    pairs, modes = batch["pairs"], batch["modes"]
+    for k, wl in enumerate(batch["wls"]):
+        for mode in (1, 2):
+            sel = np.flatnonzero((pairs[:, 0] == k) & (modes == mode))
+            if len(sel) == 0:
+                continue
+            if mode == 1 and wl.raster_n > 256:
+                assert ((g["flags"][sel] & 15) == pcl.GATE_UNSUPPORTED).all()
+                continue
+            tp = torch_cuda.from_numpy(pairs[sel, 1:].astype(np.int32)).cuda()
+            r = pcl.records_to_numpy(pcl.match(batch["ctx"], batch["Ps"][k], mode, batch["sets"][k],
+                                               batch["sets"][k], tp))
+            for f in EXACT:
+                np.testing.assert_array_equal(g[f][sel], r[f], err_msg=f"class {k} mode {mode} field {f}")
+            np.testing.assert_array_equal(g["flags"][sel] & 0x39F, r["flags"] & 0x39F)
+            assert np.abs(g["sim"][sel] - r["sim"]).max(initial=0) <= 1e-6
+
+
+def test_mixed_matches_oracle_sample(batch, torch_cuda):
+    g = _run_mixed(batch, 4, torch_cuda)
+    pairs, modes = batch["pairs"], batch["modes"]
+    rng = np.random.default_rng(1)
+    for k, wl in enumerate(batch["wls"]):
+        orc = oracle.ClipSet(wl)
+        for mode in (1, 2):
+            if mode == 1 and wl.raster_n > 256:
+                continue
+            sel = np.flatnonzero((pairs[:, 0] == k) & (modes == mode))
+            # every aligned pair plus a random sample of the rest
+            al = sel[(g["flags"][sel] & (1 << 9)) > 0]
+            sel = np.unique(np.concatenate([al[:400], rng.choice(sel, min(400, len(sel)), replace=False)]))
+            o = orc.match(pairs[sel, 1:], mode)
+            for f in ["dx_dbu", "dy_dbu", "pass_"]:
+                m = (o["flags"] & oracle.F_ALIGNED) > 0 if f != "pass_" else np.ones(len(sel), bool)
+                np.testing.assert_array_equal(g[f][sel][m], o[f][m], err_msg=f"class {k} mode {mode} {f}")
+            np.testing.assert_array_equal(g["flags"][sel] & 15, o["flags"] & 15)
+            m = (o["flags"] & oracle.F_ALIGNED) > 0
+            np.testing.assert_array_equal(g["score"][sel][m].astype(np.int64), o["score"][m])
