@@ -40,6 +40,7 @@ GATE_G2_PROFILE = 2
 GATE_G3_DENSITY = 3
 GATE_E1_MATCH = 4
 GATE_E2_BBOX = 5
+GATE_UNSUPPORTED = 14
 GATE_BAD_INDEX = 15
 F_NEAR_BAND = 1 << 4
 F_FFT_GUARD = 1 << 5
