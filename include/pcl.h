@@ -297,7 +297,7 @@ typedef struct pcl_tuning {
    persistent kernel gates the cosine items a warp at a time, aligns the
    survivors with the FFT engine of their class, and evaluates the edge items
    one per thread.  Cosine items of a class with N > 256 or S > N/16 get
-   flags = PCL_GATE_UNSUPPORTED.  Uses 4 bytes of the context workspace.
+   flags = PCL_GATE_UNSUPPORTED (such a class needs no spec buffers).  Uses 4 bytes of the context workspace.
    Errors: PCL_ERR_INVALID, PCL_ERR_OOM, PCL_ERR_CUDA. */
 pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *sets, uint32_t n_classes,
                            const pcl_work *d_work, uint64_t n_cosine, uint64_t n, pcl_record *d_out,

@@ -260,7 +260,8 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
     for (uint32_t c = 0; c < n_classes; ++c) {
         if (pcl_params_validate(&params[c])) return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: class %s%lld params", "", c);
         if ((s = check_clipset(ctx, &sets[c], true))) return s;
-        if (n_cosine && (!sets[c].spec || !sets[c].spec_state))
+        const Geo gc = make_geo(params[c]);
+        if (n_cosine && gc.N <= 256 && (!sets[c].spec || !sets[c].spec_state))
             return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: class %s%lld lacks spectra buffers", "", c);
     }
     const uint32_t radix = tune && tune->fft_radix == 4 ? 4 : 2;

@@ -36,6 +36,7 @@ __global__ void mark_mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t
         const pcl_work w = work[t];
         if (w.cls >= args.n_classes) continue;
         const pcl_clipset &c = args.cs[w.cls];
+        if (!c.spec_state || make_geo(args.prm[w.cls]).P > 32) continue;
         if (w.a < c.n_clips && c.spec_state[w.a] == 0) c.spec_state[w.a] = 2;
         if (w.b < c.n_clips && c.spec_state[w.b] == 0) c.spec_state[w.b] = 2;
     }
