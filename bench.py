@@ -398,6 +398,18 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- GPU arm
 
+def reduce_over_ranks(aligned: int, ms_step: float, e2e_ms: float, world: int, device):
+    """Whole-job figures: aligned pairs summed over ranks, step and end-to-end
+    times maxed over ranks (each rank works on its own clip set)."""
+    if world <= 1:
+        return aligned, ms_step, e2e_ms
+    import torch
+    a = torch.tensor([float(aligned)], dtype=torch.float64, device=device)
+    t = torch.tensor([ms_step, e2e_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(a)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return int(a[0].item()), float(t[0].item()), float(t[1].item())
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -570,15 +582,8 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": float(np.mean(e2e_ms))}
 
     # ---- reduce over ranks
-    tot_aligned = aligned
-    ms_max = ms_step
-    e2e_max = e2e["ms_per_step"] if e2e else 0.0
-    if world > 1:
-        t = torch.tensor([float(aligned), ms_step, e2e_max], dtype=torch.float64, device=dev)
-        a = t.clone()
-        torch.distributed.all_reduce(a[0:1])
-        torch.distributed.all_reduce(t[1:3], op=torch.distributed.ReduceOp.MAX)
-        tot_aligned, ms_max, e2e_max = int(a[0].item()), float(t[1].item()), float(t[2].item())
+    tot_aligned, ms_max, e2e_max = reduce_over_ranks(aligned, ms_step, e2e["ms_per_step"] if e2e else 0.0,
+                                                     world, dev)
     if rank != 0:
         return
     value = tot_aligned / (ms_max / 1e3)
