@@ -255,6 +255,12 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    with the tie order (-c, |dx|+|dy|, dy, dx); c_best verified by popcount;
    decision den^2 c_best^2 > num^2 |A||B|.  Spectra of referenced clips are
    computed first when missing (spec_state == 0).
+   With cos_engine = PCL_ENGINE_TC_DIRECT the overlaps of every shift come
+   from the tensor cores instead (a direct windowed correlation, exact for 0/1
+   pixels): pairs are grouped by representative (list sorted by a runs
+   fastest), no phase-correlation surface is formed (pcm fields 0), and the
+   engine covers N <= 256, S <= N/16 with shift_rule = EXACT_ARGMAX.  A
+   device-side wait that runs out is reported by pcl_device_error.
    EDGE (Sec. 2.2.2 + Eq. 6): pre-alignment, correspondence, per-axis
    d_min/d_max of matched non-border edges, T = trunc((d_min+d_max)/2)
    clamped to +/-M, E = max(T - d_min, d_max - T), re-check at T,
@@ -266,6 +272,11 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
 pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl_clipset *a,
                            pcl_clipset *b, const pcl_pair *d_pairs, uint64_t n, const uint64_t *d_n,
                            pcl_record *d_out, pcl_stream stream);
+
+/* Synchronises the device and reports (then clears) the context's device
+   error word: PCL_ERR_TIMEOUT if a kernel's bounded wait ran out (its records
+   are then incomplete), PCL_OK otherwise; *flag (may be NULL) gets the word. */
+pcl_status pcl_device_error(pcl_ctx *ctx, int *flag);
 
 /* Passing pairs of d_rec[0..min(n, *d_n)) as (a, b), order unspecified
    (d_n as in pcl_match_pairs, may be NULL); *d_count (u64, device) receives

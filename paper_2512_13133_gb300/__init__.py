@@ -153,6 +153,7 @@ def load(build_if_missing: bool = True):
                                            _VP, _VP, _VP], st),
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
+        "pcl_device_error": ([_VP, ctypes.POINTER(ctypes.c_int)], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
         "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
@@ -347,6 +348,14 @@ def pcl_match_mixed(ctx: Context, params_list, sets, work, n_cosine: int, out_re
     ctx.check(ctx.lib.pcl_match_mixed(ctx.h, ctypes.cast(P_arr, _VP), ctypes.cast(S_arr, _VP), k, _ptr(work),
                                       n_cosine, n, _ptr(out_rec), ctypes.byref(tune) if tune else None,
                                       _stream_ptr(stream)), "pcl_match_mixed")
+
+
+def pcl_device_error(ctx: Context) -> int:
+    """Synchronise and return the device error word (0: none); raises
+    PclError(PCL_ERR_TIMEOUT) when a bounded device wait ran out."""
+    f = ctypes.c_int()
+    ctx.check(ctx.lib.pcl_device_error(ctx.h, ctypes.byref(f)), "pcl_device_error")
+    return int(f.value)
 
 
 def pcl_compact_pass(ctx: Context, rec, out_pairs, d_count, d_n=None, stream=None) -> None:

@@ -25,6 +25,10 @@ cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_c
                             uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
                            unsigned long long *, cudaStream_t);
+int tc_batch(const Geo &);
+size_t tc_workspace(uint64_t);
+cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
 cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
                          pcl_record *, unsigned int *, uint32_t, uint32_t, int, cudaStream_t);
 }  // namespace pcl
@@ -114,7 +118,8 @@ pcl_status pcl_create(pcl_ctx **out, int device) {
     if (!c) return PCL_ERR_OOM;
     c->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->d_err, 256) != cudaSuccess || cudaMemset(c->d_err, 0, 256) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return PCL_ERR_CUDA;
@@ -125,10 +130,9 @@ pcl_status pcl_create(pcl_ctx **out, int device) {
 
 void pcl_destroy(pcl_ctx *ctx) {
     if (!ctx) return;
-    if (ctx->ws) {
-        cudaSetDevice(ctx->device);
-        cudaFree(ctx->ws);
-    }
+    cudaSetDevice(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
 }
 
@@ -235,6 +239,14 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     }
     if (mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
     const Geo g = make_geo(*P);
+    if (P->cos_engine == PCL_ENGINE_TC_DIRECT) {
+        if (tc_batch(g) < 16 || g.N > 256 || g.S > g.N / 16 || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+            return fail(ctx, PCL_ERR_UNSUPPORTED, "tensor-core engine covers N <= 256, S <= N/16, exact argmax%s%lld");
+        if (n == 0) return PCL_OK;
+        if ((s = ensure_ws(ctx, tc_workspace(n)))) return s;
+        e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "tensor-core correlation");
+    }
     if (P->cos_engine != PCL_ENGINE_FFT_PCM)
         return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine engine %s%lld not built", "", P->cos_engine);
     if (g.N > 256 || g.S > g.N / 16)
@@ -271,6 +283,17 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
                                        static_cast<unsigned int *>(ctx->ws), radix, ctas, ctx->num_sms,
                                        (cudaStream_t)stream);
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "mixed batch");
+}
+
+pcl_status pcl_device_error(pcl_ctx *ctx, int *flag) {
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pcl_device_error");
+    if (flag) *flag = h;
+    return h ? fail(ctx, PCL_ERR_TIMEOUT, "a device-side wait ran out%s%lld") : PCL_OK;
 }
 
 pcl_status pcl_compact_pass(pcl_ctx *ctx, const pcl_record *d_rec, uint64_t n, const uint64_t *d_n,

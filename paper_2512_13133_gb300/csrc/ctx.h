@@ -9,4 +9,5 @@ struct pcl_ctx {
     std::string err;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    int *d_err = nullptr;  // device error word set by kernels whose bounded waits ran out
 };
