@@ -46,16 +46,18 @@ def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates):
     rng = np.random.default_rng(11)
     pairs = _pairs(wl, rng, 1200)
     flags = 0 if gates else pcl.P_NO_GATES
+    num = 80 if gates else 95  # with gates, a looser threshold lets pairs through to the engine
     ctx = pcl.Context(0)
-    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_engine=pcl.ENGINE_TC_DIRECT, flags=flags)
-    Pf = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, flags=flags)
+    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, cos_engine=pcl.ENGINE_TC_DIRECT,
+                    flags=flags)
+    Pf = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, flags=flags)
     cs = pcl.alloc_clipset(Pf, wl.rect_off, wl.rects)
     pcl.pcl_rasterize(ctx, Pf, cs)
     tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
     gt = pcl.records_to_numpy(pcl.match(ctx, Pt, pcl.MODE_COSINE, cs, cs, tp))
     assert pcl.pcl_device_error(ctx) == 0
     gf = pcl.records_to_numpy(pcl.match(ctx, Pf, pcl.MODE_COSINE, cs, cs, tp))
-    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=gates)
+    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=gates, cos_num=num)
     al = (o["flags"] & oracle.F_ALIGNED) > 0
     assert al.sum() > 0
     np.testing.assert_array_equal(gt["flags"] & 15, o["flags"] & 15)
