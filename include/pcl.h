@@ -56,7 +56,10 @@ typedef enum pcl_status {
 } pcl_status;
 
 enum { PCL_MODE_COSINE = 1, PCL_MODE_EDGE = 2 };
-enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1 };
+/* cosine engines: FFT phase correlation (Sec. 3.2.1), or the direct windowed
+   correlation on tensor cores with FP16 (TC_DIRECT) or E4M3 (TC_DIRECT_FP8)
+   0/1 operands and FP32 accumulation -- both exact for 0/1 pixels */
+enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1, PCL_ENGINE_TC_DIRECT_FP8 = 2 };
 enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
 
 /* pcl_params.flags */
@@ -255,11 +258,14 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    with the tie order (-c, |dx|+|dy|, dy, dx); c_best verified by popcount;
    decision den^2 c_best^2 > num^2 |A||B|.  Spectra of referenced clips are
    computed first when missing (spec_state == 0).
-   With cos_engine = PCL_ENGINE_TC_DIRECT the overlaps of every shift come
+   With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands) or
+   PCL_ENGINE_TC_DIRECT_FP8 (E4M3 operands) the overlaps of every shift come
    from the tensor cores instead (a direct windowed correlation, exact for 0/1
-   pixels): pairs are grouped by representative (list sorted by a runs
-   fastest), no phase-correlation surface is formed (pcm fields 0), and the
-   engine covers N <= 256, S <= N/16 with shift_rule = EXACT_ARGMAX.  A
+   pixels; the L-shaped edge of the window, the row dy = S and the column
+   dx = S, is counted with popcounts): pairs are grouped by representative
+   (a list sorted by a, b runs fastest), no phase-correlation surface is formed
+   (pcm fields 0), and the engine covers (N, S) = (64, 4), (128, 8) and
+   (256, 16) with shift_rule = EXACT_ARGMAX (else PCL_ERR_UNSUPPORTED).  A
    device-side wait that runs out is reported by pcl_device_error.
    EDGE (Sec. 2.2.2 + Eq. 6): pre-alignment, correspondence, per-axis
    d_min/d_max of matched non-border edges, T = trunc((d_min+d_max)/2)

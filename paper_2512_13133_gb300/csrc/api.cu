@@ -25,7 +25,7 @@ cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_c
                             uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
                            unsigned long long *, cudaStream_t);
-int tc_batch(const Geo &);
+bool tc_supported(const Geo &);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
@@ -147,7 +147,7 @@ pcl_status pcl_params_validate(const pcl_params *P) {
     if (P->cos_den == 0 || P->cos_den > 65535 || P->cos_num == 0 || P->cos_num >= P->cos_den)
         return PCL_ERR_INVALID;
     if (P->edge_tol_dbu < 0) return PCL_ERR_INVALID;
-    if (P->cos_engine > PCL_ENGINE_TC_DIRECT || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
+    if (P->cos_engine > PCL_ENGINE_TC_DIRECT_FP8 || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
     if (!(P->near_band >= 0.0f)) return PCL_ERR_INVALID;
     return PCL_OK;
 }
@@ -239,9 +239,10 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     }
     if (mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
     const Geo g = make_geo(*P);
-    if (P->cos_engine == PCL_ENGINE_TC_DIRECT) {
-        if (tc_batch(g) < 16 || g.N > 256 || g.S > g.N / 16 || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
-            return fail(ctx, PCL_ERR_UNSUPPORTED, "tensor-core engine covers N <= 256, S <= N/16, exact argmax%s%lld");
+    if (P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8) {
+        if (!tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+            return fail(ctx, PCL_ERR_UNSUPPORTED,
+                        "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax%s%lld");
         if (n == 0) return PCL_OK;
         if ((s = ensure_ws(ctx, tc_workspace(n)))) return s;
         e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err, st);

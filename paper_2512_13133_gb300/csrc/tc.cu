@@ -1,28 +1,48 @@
 // a8: direct windowed correlation on the 5th-generation tensor cores.
 //
-// For one representative A and a batch of NB members B_n sharing it,
-//   D[t, n] = sum_u A(u + s_t) B_n(u)  =  c_n(s_t)      (c(s) = sum_x A(x) B(x - s))
-// over every shift s_t of the marker window, as a GEMM with M = shifts (tiles
-// of 128), N = members, K = pixels.  0/1 operands are exact in FP16 and the
-// FP32 sums stay below 2^24, so the tensor cores return the exact integer
-// overlaps (no rounding guard is needed).
+// For one representative A and the members B_n listed with it,
+//   c_n(dy, dx) = sum_{y,x} A(y + dy, x + dx) B_n(y, x)     (c(s) = sum_x A(x) B(x - s))
+// over the marker window |dx|, |dy| <= S is computed as a GEMM
+//   D[m, col] = sum_k Aop[m, k] Bop[k, col]
+// with K = pixels, M = 128 shifts and N = (member copy, member) columns.  0/1
+// operands are exact in FP16 (1.0 = 0x3C00) or E4M3 (1.0 = 0x38), and the FP32
+// sums stay below 2^24, so the tensor cores return the exact integer overlaps
+// (no rounding guard is needed).
 //
-// Per K stage (64 pixels of one image row) the CTA writes, in shared memory
-// and in the canonical K-major no-swizzle layout (8-row x 16-byte core
-// matrices, K-adjacent core matrices 128 B apart, 8-row groups 1024 B apart):
-//   - the shifted-representative tile: row t holds A's row y + dy from column
-//     x0 + dx (a 64-bit window of A's bit row), expanded bit -> FP16 by a
-//     256-entry table;
-//   - the member tile: row n holds member n's 64 pixels.
-// One thread issues tcgen05.mma (kind::f16, M = 128, N = NB, K = 16) four
-// times per (shift tile, stage) unit, accumulating in tensor memory; every
-// shift tile of the representative has its own accumulator columns (tiles x NB
-// <= 512), so all of them stay resident until the epilogue.  Two unit buffers alternate;
-// tcgen05.commit arrives on the buffer's mbarrier, and a buffer is rewritten
-// only after that barrier completes (waits are bounded; on time-out the CTA
-// records an error and stops).  The epilogue reads the accumulators with
-// tcgen05.ld (warp w sees rows 32w..32w+31) and reduces the exact argmax with
-// the tie order (-c, |dx|+|dy|, dy, dx).
+// M side, no per-stage generation: for each column phase (CH pixels = one
+// 16-byte core-matrix row) the CTA keeps 16 copies of A's column strip, copy g
+// shifted by dx_a = g - S, every image row (zero padded) at a 16-byte pitch.
+// An M tile is 16 groups of 8 rows: group g = copy g, row r = image row
+// Y + r - S, i.e. 8 consecutive dy.  The next image row is the descriptor start
+// plus 16 bytes, so the second K core matrix of an MMA is the next image row
+// (leading-dimension offset 16 bytes) and no operand is rewritten per stage.
+// N side, written per stage: member n appears NBX x NBY times, copy (i, j)
+// shifted by (16 i, 8 j) pixels, so that with D's (g, r)
+//   dx = -S + g + 16 i,   dy = -S + r + 8 j,
+// covering [-S, -S + 16 NBX) x [-S, -S + 8 NBY).  The K loop runs over every
+// row and column the member copies reach, so each product of the window is
+// summed.  The rest of the window -- the row dy = -S + 8 NBY (= S) and, when
+// -S + 16 NBX <= S, the column dx = -S + 16 NBX: an L of at most 4S + 1
+// shifts -- is counted exactly with AND + popcount on the CUDA cores while
+// the tensor cores run.
+//
+// Warp roles (one CTA per SM, 11 warps):
+//   warp 0      one thread issues tcgen05.mma (kind::f16, K = 16, or
+//               kind::f8f6f4, K = 32) and tcgen05.commit;
+//   warps 1-2   write the 16 shifted copies of the next column phase (two
+//               buffers);
+//   warps 3-6   stage member rows (a ring of 32-bit strips, loads issued one
+//               stage ahead) and write each stage's member tile (a ring of
+//               stage buffers);
+//   warps 7-10  the rest of the window, then the accumulators (tcgen05.ld;
+//               warp w reads TMEM lanes 32 (w % 4) ..) and the exact argmax
+//               with the tie order (-c, |dx|+|dy|, dy, dx).
+// Buffers change hands through mbarriers (producers arrive; the MMA thread's
+// tcgen05.commit releases), and the accumulators are double buffered in TMEM
+// (2 x 256 columns), so the epilogue of one item overlaps the MMAs of the
+// next.  Every wait is bounded (one second): on time-out the CTA records an
+// error, each role leaves its loop together (barrier reductions), and the MMAs
+// still in flight are waited for before the tensor memory is released.
 #include <climits>
 
 #include "gates.cuh"
@@ -31,12 +51,64 @@ namespace pcl {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kStageK = 64;             // pixels per stage
-constexpr int kTileBytesA = 128 * 128;  // 128 rows x 64 fp16
-constexpr int kMaxNB = 256;
+constexpr int kWarps = 11;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kAProd = 64;               // warps 1-2
+constexpr int kBProd = 128;              // warps 3-6
+constexpr int kEpi = 128;                // warps 7-10
+constexpr int kKS = 2;                   // MMAs per stage
+constexpr int kCores = 2 * kKS;          // image rows (K core matrices) per stage
+constexpr int kCopies = 16;              // shifted copies of the representative
+constexpr int kMaxCols = 256;            // N of one MMA / one accumulator buffer
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitLimit = 1ll << 24;
+constexpr uint32_t kSmemMax = 227 * 1024;
+constexpr unsigned long long kWaitNs = 1000000000ull;
+enum { kBarB = 1, kBarEpi = 2 };
+// mbarrier indices: a_full[2], a_empty[2], acc_full[2], acc_empty[2], fin, b_full[R], b_empty[R]
+enum { kAFull = 0, kAEmpty = 2, kAccFull = 4, kAccEmpty = 6, kFin = 8, kBFull = 9 };
+
+template <int S, int NW, bool FP8>
+struct Tc {
+    static constexpr int N = 64 * NW;
+    static constexpr int NBX = (2 * S) / 16 > 0 ? (2 * S) / 16 : 1;  // x copies of a member (16 px apart)
+    static constexpr int NBY = (2 * S) / 8 > 0 ? (2 * S) / 8 : 1;    // 8-row dy blocks of the core
+    static constexpr int JB = NBY >= 2 ? 2 : 1;                       // dy blocks on the member side
+    static constexpr int JA = NBY / JB;                               // dy blocks on A's side (MMAs per K step)
+    static constexpr int NCOPY = NBX * JB;                            // member copies per MMA
+    static constexpr int NB = kMaxCols / (JA * NCOPY);                // members per item
+    static constexpr int NMAX = NCOPY * NB;                           // N of one MMA at most
+    static constexpr int RND = 16 / NCOPY;                            // member rounding (N % 16 == 0)
+    static constexpr int DYL = -S + 8 * NBY;                          // rest row
+    static constexpr int DXL = -S + 16 * NBX;                         // rest column, if <= S
+    static constexpr bool COL = DXL <= S;
+    static constexpr int CH = FP8 ? 16 : 8;                           // pixels per 16-byte row
+    static constexpr int YHI = (N + 8 * (JB - 1) + kCores - 1) / kCores * kCores;  // K image rows
+    static constexpr int NST = YHI / kCores;                          // stages per phase
+    static constexpr int NPH = (N + 16 * (NBX - 1)) / CH;             // column phases
+    static constexpr int ROWS = YHI + 8 + 8 * JB * (JA - 1);          // rows of one copy
+    static constexpr uint32_t ABYTES = (uint32_t)kCopies * ROWS * 16;
+    static constexpr int STRIP = 16 * (NBX - 1);                      // strip start left of the phase
+    static constexpr int WPT = STRIP > 0 ? 2 : 1;                     // 64-bit words per staged strip
+    static constexpr int TASKS = NB * kCores;                         // (member, row) tasks per stage
+    static constexpr int TPT = TASKS / kBProd;                        // tasks per producer thread
+    static constexpr uint32_t SLOT = (uint32_t)kCores * NMAX * 16;    // member tile of one stage
+    static constexpr uint32_t STG = (uint32_t)WPT * TASKS * 8;        // staged words of one stage
+    static constexpr int R = 4;                                       // member tile buffers
+    static constexpr uint32_t FIXED =
+        2 * ABYTES + (uint32_t)R * SLOT + (uint32_t)NB * 8 + (uint32_t)(kBFull + 2 * R) * 8 + 16;
+    static constexpr int DFIT = (int)((kSmemMax - FIXED) / STG);
+    static constexpr int D = DFIT > 16 ? 16 : DFIT;                   // prefetch depth (stages)
+    static constexpr uint32_t OFF_SLOTS = 2 * ABYTES;
+    static constexpr uint32_t OFF_STG = OFF_SLOTS + (uint32_t)R * SLOT;
+    static constexpr uint32_t OFF_KEYS = OFF_STG + (uint32_t)D * STG;
+    static constexpr uint32_t OFF_BARS = OFF_KEYS + (uint32_t)NB * 8;
+    static constexpr uint32_t BYTES = OFF_BARS + (uint32_t)(kBFull + 2 * R) * 8 + 16;
+    static_assert(CH + STRIP <= 32, "member strip exceeds 32 bits");
+    static_assert(NPH * CH == N + 16 * (NBX - 1), "column phases do not cover the member copies");
+    static_assert(TASKS % kBProd == 0 && NB % RND == 0 && JA * JB == NBY, "task split");
+    static_assert(D >= 4 && BYTES <= kSmemMax, "shared memory plan");
+    static_assert(kCores * 2 == 8, "the member-side dy copy is two stages back");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -50,22 +122,56 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+// instruction descriptor: D = F32 (bit 4), A = B = F16 for kind::f16 or E4M3
+// for kind::f8f6f4 (format 0 in bits 7-9 and 10-12), both K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_of(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
 }
+
+// the low CH pixels (bits) of b as one 16-byte core-matrix row of 0 / 1.0
+template <bool FP8>
+__device__ __forceinline__ uint4 expand(uint32_t b) {
+    if constexpr (FP8) {
+        // a nibble times 0x00204081 puts bit k at bit 8k (no carries), masked to 0/1 bytes
+        auto q = [](uint32_t nib) { return ((nib * 0x00204081u) & 0x01010101u) * 0x38u; };
+        return make_uint4(q(b & 15u), q((b >> 4) & 15u), q((b >> 8) & 15u), q((b >> 12) & 15u));
+    } else {
+        auto h = [](uint32_t v) { return ((v & 1u) | ((v & 2u) << 15)) * 0x3C00u; };
+        return make_uint4(h(b & 3u), h((b >> 2) & 3u), h((b >> 4) & 3u), h((b >> 6) & 3u));
+    }
+}
+
+__device__ __forceinline__ void st16(unsigned char *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
@@ -80,11 +186,53 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(mbar, parity)) return true;
-    return false;
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase of the given parity; false on time-out or when
+// another role has aborted (abort_flag may be null: wait regardless)
+__device__ __noinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        for (int i = 0; i < 16; ++i)
+            if (mbar_try_wait(mbar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+}
+
+// barrier over `count` threads of one role that also ORs a flag
+__device__ __forceinline__ bool bar_any(int id, int count, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// 8-byte asynchronous copy global -> shared; bytes past src_bytes are zero
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)),
+                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -100,75 +248,168 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 64-bit window of a bit row starting at pixel `base` (zeros outside)
-__device__ __forceinline__ uint64_t bit_window(const uint64_t *row, int nw, int base) {
+// 64 bits of a bit row starting at pixel `base` (zeros outside the row)
+template <int NW>
+__device__ __forceinline__ uint64_t bit_window(const uint64_t *row, int base) {
     const int wi = base >= 0 ? base >> 6 : -((-base + 63) >> 6);
     const int off = base - 64 * wi;
-    const uint64_t lo = (wi >= 0 && wi < nw) ? row[wi] : 0ull;
-    const uint64_t hi = (wi + 1 >= 0 && wi + 1 < nw) ? row[wi + 1] : 0ull;
+    const uint64_t lo = (wi >= 0 && wi < NW) ? __ldg(row + wi) : 0ull;
+    const uint64_t hi = (wi + 1 >= 0 && wi + 1 < NW) ? __ldg(row + wi + 1) : 0ull;
     return off ? ((lo >> off) | (hi << (64 - off))) : lo;
 }
 
-// shared-memory plan (dynamic): LUT 4 KB | A raster (N*N/8) | 2 x (A tile 16 KB +
-// member tile NB*128 B) | keys | misc; padded to force one CTA per SM
-struct TcSmem {
-    uint32_t lut, araster, tiles, keys, misc, bytes;
-};
-
-__host__ __device__ inline TcSmem tc_smem(int N, int NB, int tiles) {
-    TcSmem s;
-    s.lut = 0;
-    s.araster = 4096;
-    const uint32_t ar = (uint32_t)N * N / 8;
-    s.tiles = (s.araster + ar + 1023) & ~1023u;
-    const uint32_t stage = kTileBytesA + (((uint32_t)NB * 128 + 1023) & ~1023u);
-    s.keys = s.tiles + 2 * stage;
-    s.misc = s.keys + (uint32_t)NB * 8;
-    s.bytes = s.misc + 64;
-    if (s.bytes < 120u * 1024) s.bytes = 120u * 1024;  // one CTA per SM: TMEM is taken whole
-    (void)tiles;
-    return s;
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long k) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, k, o);
+        k = w > k ? w : k;
+    }
+    return k;
 }
 
-// work item: representative a, members pairs[first .. first+count) (all with pair.a == a)
+// Row ya of A shifted left by SH pixels (pixels x + SH), zero outside the raster.
+template <int NW, int SH>
+__device__ __forceinline__ void shifted_row(const uint64_t *__restrict__ A, int ya, uint64_t (&o)[NW]) {
+    uint64_t a[NW + 1];
+    const bool in = ya >= 0 && ya < 64 * NW;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) a[w] = in ? __ldg(A + (size_t)ya * NW + w) : 0ull;
+    a[NW] = 0ull;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) o[w] = (a[w] >> SH) | (a[w + 1] << (64 - SH));
+}
+
+// The rest of the window for one pair, counted exactly by one warp: the row
+// dy = DYL for every dx in [-S, S] and, when COL, the column dx = DXL for dy
+// in [-S, S).  Lanes take 32 consecutive rows y of B at a time.  The row part
+// shifts A's row y + DYL in registers; the column part needs A's rows y + dy
+// shifted by DXL, which the warp holds as two blocks of 32 rows (y0 - S + l
+// and y0 - S + 32 + l) and passes around with one shuffle per word.  Returns
+// the largest shift key among these shifts (the same in every lane).
+template <int S, int NW, int DYL, int DXL, bool COL>
+__device__ __forceinline__ unsigned long long rest_key(const uint64_t *__restrict__ A,
+                                                       const uint64_t *__restrict__ B, int lane) {
+    constexpr int N = 64 * NW;
+    static_assert(!COL || 2 * S <= 32, "column rest spans more than two row blocks");
+    uint32_t cr[2 * S + 1];
+    uint32_t cc[COL ? 2 * S : 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * S; ++d) cr[d] = 0;
+#pragma unroll
+    for (int e = 0; e < (COL ? 2 * S : 1); ++e) cc[e] = 0;
+    for (int y0 = 0; y0 < N; y0 += 32) {
+        const int y = y0 + lane;
+        uint64_t b[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) b[w] = __ldg(B + (size_t)y * NW + w);
+        // a[w + 1] = word w of A's row y + DYL, zero words on both sides
+        uint64_t a[NW + 2];
+        a[0] = 0ull;
+        a[NW + 1] = 0ull;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) a[w + 1] = y + DYL < N ? __ldg(A + (size_t)(y + DYL) * NW + w) : 0ull;
+        uint64_t s0[NW], s1[NW];
+        if constexpr (COL) {
+            shifted_row<NW, DXL>(A, y0 - S + lane, s0);
+            shifted_row<NW, DXL>(A, y0 - S + 32 + lane, s1);
+        }
+#pragma unroll
+        for (int d = 0; d <= 2 * S; ++d) {
+            const int dx = d - S;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                uint64_t sh;  // A's pixels x + dx for the x of word w
+                if (dx > 0) sh = (a[w + 1] >> dx) | (a[w + 2] << (64 - dx));
+                else if (dx < 0) sh = (a[w + 1] << (-dx)) | (a[w] >> (64 + dx));
+                else sh = a[w + 1];
+                sum += (uint32_t)__popcll(sh & b[w]);
+            }
+            cr[d] += sum;
+        }
+        if constexpr (COL) {
+            // lane l needs shifted row y0 + l + dy = block row m = l + dy + S: lane
+            // (m & 31) of block m >> 5; a source lane j serves block 0 when
+            // j >= e (= dy + S), else block 1
+#pragma unroll
+            for (int e = 0; e < 2 * S; ++e) {
+                uint32_t sum = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint64_t v = __shfl_sync(0xffffffffu, lane >= e ? s0[w] : s1[w], (lane + e) & 31);
+                    sum += (uint32_t)__popcll(v & b[w]);
+                }
+                cc[e] += sum;
+            }
+        }
+    }
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int d = 0; d <= 2 * S; ++d) {
+        const uint32_t c = __reduce_add_sync(0xffffffffu, cr[d]);
+        const unsigned long long k = shift_key(c, d - S, DYL, S);
+        best = k > best ? k : best;
+    }
+    if constexpr (COL) {
+#pragma unroll
+        for (int e = 0; e < 2 * S; ++e) {
+            const uint32_t c = __reduce_add_sync(0xffffffffu, cc[e]);
+            const unsigned long long k = shift_key(c, DXL, e - S, S);
+            best = k > best ? k : best;
+        }
+    }
+    return best;
+}
+
+// work item: representative a, members pairs[surv[first .. first+count)] (all with pair.a == a)
 struct TcItem {
     uint32_t first, count;
 };
 
+template <int RND>
+__device__ __forceinline__ int round_members(uint32_t count) {
+    return (int)((count + RND - 1) / RND * RND);
+}
+
+template <int S, int NW, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_corr_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, const uint32_t *surv,
-                   const TcItem *items, const unsigned int *n_items, pcl_record *out, int NB, int *err) {
-    const Geo g = make_geo(prm);
-    const int N = g.N, nw = g.nw, S = g.S, K2 = 2 * S + 1, nshift = K2 * K2;
-    const int tiles = (nshift + 127) / 128;
-    const int nstage = N * N / kStageK;
-    const TcSmem plan = tc_smem(N, NB, tiles);
+                   const TcItem *items, const unsigned int *n_items, pcl_record *out, int *err) {
+    using C = Tc<S, NW, FP8>;
+    constexpr int N = C::N, R = C::R, D = C::D;
     extern __shared__ __align__(1024) unsigned char sm[];
-    uint4 *lut = reinterpret_cast<uint4 *>(sm + plan.lut);
-    uint64_t *araster = reinterpret_cast<uint64_t *>(sm + plan.araster);
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sm + plan.keys);
-    uint32_t *misc = reinterpret_cast<uint32_t *>(sm + plan.misc);  // [0] tmem base, [2..5] mbarriers
-    const uint32_t stage_bytes = kTileBytesA + ((NB * 128 + 1023) & ~1023);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sm + C::OFF_KEYS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::OFF_BARS);
+    volatile uint32_t *misc = reinterpret_cast<volatile uint32_t *>(bars + kBFull + 2 * R);  // [0] tmem, [1] abort
+    const volatile uint32_t *abortf = misc + 1;
+    const uint32_t sbase = smem_u32(sm);
+    const uint32_t bar0 = smem_u32(bars);
+    auto bar = [&](int k) { return bar0 + 8u * (uint32_t)k; };
+    auto raise_abort = [&]() {
+        misc[1] = 1u;
+        atomicExch(err, 1);
+    };
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t mbar0 = smem_u32(misc + 2), mbar1 = smem_u32(misc + 4);
 
-    // bit -> FP16 table: entry v holds 8 halves, element k = bit k of v
-    for (int v = tid; v < 256; v += kThreads) {
-        uint32_t w[4];
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t lo = ((v >> (2 * q)) & 1) ? 0x3C00u : 0u;
-            const uint32_t hi = ((v >> (2 * q + 1)) & 1) ? 0x3C00u : 0u;
-            w[q] = lo | (hi << 16);
-        }
-        lut[v] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    for (int n = tid; n < C::NB; n += kThreads) keys[n] = 0ull;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar1));
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(bar(kAFull + k), kAProd);
+            mbar_init(bar(kAEmpty + k), 1);
+            mbar_init(bar(kAccFull + k), 1);
+            mbar_init(bar(kAccEmpty + k), kEpi);
+        }
+        mbar_init(bar(kFin), 1);
+        for (int k = 0; k < R; ++k) {
+            mbar_init(bar(kBFull + k), kBProd);
+            mbar_init(bar(kBFull + R + k), 1);
+        }
+        misc[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(misc)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(
+                         (const void *)misc)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -176,141 +417,261 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = misc[0];
-    const uint32_t idesc = idesc_f16(128, NB);
-    bool failed = false;
-
     const unsigned int nit = *n_items;
-    uint32_t u = 0;  // units (shift tile, stage) issued by this CTA, for the mbarrier phases
-    for (unsigned int it = blockIdx.x; it < nit && !failed; it += gridDim.x) {
-        const TcItem item = items[it];
-        const uint32_t a = pairs[surv[item.first]].a;
-        const uint64_t *abits = A.bits + (size_t)a * N * nw;
-        for (int t = tid; t < N * nw; t += kThreads) araster[t] = abits[t];
-        __syncthreads();
-        // ---- main loop: shift tiles m (each with its own accumulator columns)
-        //      x stages s (64 pixels of one image row)
-        for (int m = 0; m < tiles && !failed; ++m) {
-            for (int s = 0; s < nstage; ++s) {
-                const int buf = u & 1;
-                const uint32_t mb = buf ? mbar1 : mbar0;
-                // this buffer was last read by the MMAs of unit u - 2
-                if (u >= 2 && !mbar_wait(mb, ((u - 2) >> 1) & 1)) failed = true;
-                failed = __syncthreads_or(failed);
-                if (failed) break;
-                unsigned char *tileA = sm + plan.tiles + buf * stage_bytes;
-                unsigned char *tileB = tileA + kTileBytesA;
-                const int y = s / nw, w0 = s % nw, x0 = 64 * w0;
-                // member tile: row n = member n's 64 pixels of this stage
-                for (int q = tid; q < NB * 8; q += kThreads) {
-                    const int n = q >> 3, j = q & 7;
-                    uint64_t bits = 0;
-                    if (n < (int)item.count) {
-                        const uint32_t b = pairs[surv[item.first + n]].b;
-                        bits = B.bits[((size_t)b * N + y) * nw + w0];
-                    }
-                    const uint32_t byte = (uint32_t)(bits >> (8 * j)) & 0xFFu;
-                    *reinterpret_cast<uint4 *>(tileB + (n >> 3) * 1024 + j * 128 + (n & 7) * 16) = lut[byte];
-                }
-                // shifted-representative tile: thread = row of the tile
-                {
-                    const int t = m * 128 + tid;
-                    uint64_t bits = 0;
-                    if (t < nshift) {
-                        const int dy = t / K2 - S, dx = t % K2 - S;
-                        const int yy = y + dy;
-                        if (yy >= 0 && yy < N) bits = bit_window(araster + (size_t)yy * nw, nw, x0 + dx);
-                    }
-                    unsigned char *row = tileA + (tid >> 3) * 1024 + (tid & 7) * 16;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            bool ok = true;
+            uint32_t pc = 0, sc = 0, li = 0;
+            for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x, ++li) {
+                const TcItem item = items[it];
+                const int ncols = C::NCOPY * round_members<C::RND>(item.count);  // N of each MMA
+                const uint32_t idesc = idesc_of(128, ncols);
+                const uint32_t ab = li & 1;
+                if (li >= 2 && !(ok = wait_phase(bar(kAccEmpty + ab), ((li >> 1) - 1) & 1, abortf))) break;
+                fence_after();
+                const uint32_t dcol = tmem + ab * (uint32_t)kMaxCols;
+                for (int ph = 0; ph < C::NPH && ok; ++ph, ++pc) {
+                    const uint32_t abf = pc & 1;
+                    if (!(ok = wait_phase(bar(kAFull + abf), (pc >> 1) & 1, abortf))) break;
+                    const uint32_t abase = sbase + abf * C::ABYTES;
+                    for (int st = 0; st < C::NST; ++st, ++sc) {
+                        const uint32_t slot = sc % (uint32_t)R;
+                        if (!(ok = wait_phase(bar(kBFull + slot), (sc / R) & 1, abortf))) break;
+                        fence_after();
+                        const uint32_t bbase = sbase + C::OFF_SLOTS + slot * C::SLOT;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        *reinterpret_cast<uint4 *>(row + j * 128) = lut[(uint32_t)(bits >> (8 * j)) & 0xFFu];
+                        for (int t = 0; t < kKS; ++t) {
+                            const int Y = st * kCores + 2 * t;
+                            const uint64_t bd = smem_desc(bbase + (uint32_t)(2 * t * ncols * 16), ncols * 16, 128);
+#pragma unroll
+                            for (int ja = 0; ja < C::JA; ++ja) {
+                                // A rows Y + r - S + 8 JB ja: the dy block ja of A's side
+                                const uint64_t ad =
+                                    smem_desc(abase + (uint32_t)(Y + 8 * C::JB * ja) * 16, 16, C::ROWS * 16);
+                                mma<FP8>(dcol + (uint32_t)(ja * ncols), ad, bd, idesc, (ph | st | t) ? 1u : 0u);
+                            }
+                        }
+                        mma_commit(bar(kBFull + R + slot));
+                    }
+                    if (ok) mma_commit(bar(kAEmpty + abf));
+                }
+                if (ok) mma_commit(bar(kAccFull + ab));
+            }
+            if (!ok) raise_abort();
+            // every MMA issued so far has completed before the tensor memory is released
+            mma_commit(bar(kFin));
+            if (!wait_phase(bar(kFin), 0, nullptr)) raise_abort();
+        }
+        __syncwarp();
+    } else if (warp <= 2) {
+        // ---------------------------------------------------------------- shifted copies of A
+        const int pt = tid - 32;
+        bool ok = true;
+        uint32_t pc = 0;
+        for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x) {
+            const TcItem item = items[it];
+            const uint64_t *abits = A.bits + (size_t)pairs[surv[item.first]].a * N * NW;
+            for (int ph = 0; ph < C::NPH; ++ph, ++pc) {
+                const uint32_t abf = pc & 1;
+                if (pc >= 2 && !(ok = wait_phase(bar(kAEmpty + abf), ((pc >> 1) - 1) & 1, abortf))) break;
+                unsigned char *buf = sm + abf * C::ABYTES;
+                const int base = ph * C::CH - S;  // copy g, pixel k = A column base + g + k
+                for (int ridx = pt; ridx < C::ROWS; ridx += kAProd) {
+                    const int yy = ridx - S;
+                    uint64_t win = 0ull;
+                    if (yy >= 0 && yy < N) win = bit_window<NW>(abits + (size_t)yy * NW, base);
+#pragma unroll
+                    for (int g = 0; g < kCopies; ++g)
+                        st16(buf + ((uint32_t)g * C::ROWS + ridx) * 16, expand<FP8>((uint32_t)(win >> g)));
                 }
                 fence_proxy_async();
-                fence_before();
-                __syncthreads();
-                fence_after();
-                if (tid == 0) {
-                    const uint32_t aaddr = smem_u32(tileA), baddr = smem_u32(tileB);
-                    const uint32_t dcol = tmem + (uint32_t)(m * NB);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = smem_desc(aaddr + kk * 256, 128, 1024);
-                        const uint64_t bd = smem_desc(baddr + kk * 256, 128, 1024);
-                        mma_f16(dcol, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    mma_commit(mb);
-                }
-                ++u;
+                mbar_arrive(bar(kAFull + abf));
             }
         }
-        // ---- drain: the commits of the last two units
-        if (!failed) {
-            for (uint32_t k = (u >= 2 ? u - 2 : 0); k < u; ++k)
-                if (!mbar_wait((k & 1) ? mbar1 : mbar0, (k >> 1) & 1)) failed = true;
+        if (!ok) raise_abort();
+    } else if (warp <= 6) {
+        // ---------------------------------------------------------------- member tiles
+        // Task k = (member n = k % NB, row q = k / NB of each stage); each
+        // thread stages its own strip words D stages ahead with cp.async
+        // (zero-filled outside the raster) and keeps the strips of the two
+        // previous stages, so the member-side dy copy (8 rows = two stages
+        // back) needs no second load.  No barrier among the producers.
+        const int bt = tid - 96;
+        bool ok = true;
+        uint32_t sc = 0;
+        unsigned char *stg = sm + C::OFF_STG;
+        for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x) {
+            const TcItem item = items[it];
+            const int nbp = round_members<C::RND>(item.count);
+            const int ncols = C::NCOPY * nbp;
+            const uint64_t *mb[C::TPT];
+#pragma unroll
+            for (int u = 0; u < C::TPT; ++u) {
+                const int n = (bt + kBProd * u) % C::NB;
+                mb[u] = n < (int)item.count ? B.bits + (size_t)pairs[surv[item.first + n]].b * N * NW : nullptr;
+            }
+            const int total = C::NPH * C::NST;
+            // stage s of this item: copy the strip words of rows st * kCores + q
+            auto issue = [&](int s) {
+                const int ph = s / C::NST, st = s - ph * C::NST;
+                const int sb = ph * C::CH - C::STRIP;
+                const int w0 = sb >= 0 ? sb >> 6 : -((-sb + 63) >> 6);
+                unsigned char *dst = stg + (uint32_t)(s % D) * C::STG;
+#pragma unroll
+                for (int u = 0; u < C::TPT; ++u) {
+                    const int k = bt + kBProd * u;
+                    const int row = st * kCores + k / C::NB;
+#pragma unroll
+                    for (int e = 0; e < C::WPT; ++e) {
+                        const int w = w0 + e;
+                        const bool v = mb[u] && row < N && w >= 0 && w < NW;
+                        const uint64_t *src = v ? mb[u] + (size_t)row * NW + w : B.bits;
+                        cp_async8(dst + ((uint32_t)e * C::TASKS + k) * 8, src, v ? 8u : 0u);
+                    }
+                }
+                cp_async_commit();
+            };
+            for (int s = 0; s < D - 1; ++s) {
+                if (s < total) issue(s);
+                else cp_async_commit();
+            }
+            uint32_t h1[C::TPT], h2[C::TPT];  // strips of stages s - 1 and s - 2
+#pragma unroll
+            for (int u = 0; u < C::TPT; ++u) h1[u] = h2[u] = 0u;
+            for (int s = 0; s < total; ++s, ++sc) {
+                // one group per stage keeps the group count uniform
+                if (s + D - 1 < total) issue(s + D - 1);
+                else cp_async_commit();
+                cp_async_wait<D - 1>();
+                const int ph = s / C::NST, st = s - ph * C::NST;
+                const int sb = ph * C::CH - C::STRIP;
+                const int w0 = sb >= 0 ? sb >> 6 : -((-sb + 63) >> 6);
+                const int off = sb - 64 * w0;
+                const uint64_t *src = reinterpret_cast<const uint64_t *>(stg + (uint32_t)(s % D) * C::STG);
+                uint32_t cur[C::TPT];
+#pragma unroll
+                for (int u = 0; u < C::TPT; ++u) {
+                    const int k = bt + kBProd * u;
+                    const uint64_t lo = src[k];
+                    const uint64_t hi = C::WPT == 2 ? src[C::TASKS + k] : 0ull;
+                    cur[u] = (uint32_t)(off ? (lo >> off) | (hi << (64 - off)) : lo);
+                }
+                const uint32_t slot = sc % (uint32_t)R, ru = sc / (uint32_t)R;
+                if (ru >= 1 && !wait_phase(bar(kBFull + R + slot), (ru - 1) & 1, abortf)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *tile = sm + C::OFF_SLOTS + slot * C::SLOT;
+                const int Ys = st * kCores;
+#pragma unroll
+                for (int u = 0; u < C::TPT; ++u) {
+                    const int k = bt + kBProd * u, n = k % C::NB, q = k / C::NB;
+                    if (n >= nbp) continue;
+                    unsigned char *dst = tile + (uint32_t)(q * ncols * 16);
+#pragma unroll
+                    for (int jb = 0; jb < C::JB; ++jb) {
+                        const int row = Ys + q - 8 * jb;
+                        const bool v = n < (int)item.count && row >= 0 && row < N;
+                        const uint32_t strip = v ? (jb == 0 ? cur[u] : h2[u]) : 0u;
+#pragma unroll
+                        for (int i = 0; i < C::NBX; ++i) {
+                            const int col = (jb * C::NBX + i) * nbp + n;
+                            st16(dst + (col >> 3) * 128 + (col & 7) * 16,
+                                 expand<FP8>(strip >> (16 * (C::NBX - 1 - i))));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < C::TPT; ++u) {
+                    h2[u] = h1[u];
+                    h1[u] = cur[u];
+                }
+                fence_proxy_async();
+                mbar_arrive(bar(kBFull + slot));
+            }
+            cp_async_wait<0>();
         }
-        failed = __syncthreads_or(failed);
-        if (failed) break;
-        fence_after();
-        // ---- epilogue: exact argmax per member over all shift tiles
-        for (int n = tid; n < NB; n += kThreads) keys[n] = 0ull;
-        __syncthreads();
-        for (int m = 0; m < tiles; ++m) {
-            for (int c0 = 0; c0 < NB; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * NB + c0), r);
+        cp_async_wait<0>();
+        if (!ok) raise_abort();
+    } else {
+        // ---------------------------------------------------------------- rest of the window + epilogue
+        const int et = tid - 224, ew = warp - 7, quarter = warp & 3;
+        const Geo g = make_geo(prm);
+        bool ok = true;
+        uint32_t li = 0;
+        for (unsigned int it = blockIdx.x; it < nit; it += gridDim.x, ++li) {
+            const TcItem item = items[it];
+            const uint32_t a = pairs[surv[item.first]].a;
+            const uint64_t *abits = A.bits + (size_t)a * N * NW;
+            for (int n = ew; n < (int)item.count; n += 4) {
+                const uint64_t *bb = B.bits + (size_t)pairs[surv[item.first + n]].b * N * NW;
+                const unsigned long long k = rest_key<S, NW, C::DYL, C::DXL, C::COL>(abits, bb, lane);
+                if (lane == 0) atomicMax(keys + n, k);
+            }
+            const uint32_t ab = li & 1;
+            const bool w = wait_phase(bar(kAccFull + ab), (li >> 1) & 1, abortf);
+            if (bar_any(kBarEpi, kEpi, !w)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const int nbp = round_members<C::RND>(item.count);
+            const int ncols = C::NCOPY * nbp;
+            const int m = 32 * quarter + lane, gg = m >> 3, rr = m & 7;
+            // column ja * ncols + (jb * NBX + i) * nbp + n holds member n at
+            // dx = -S + g + 16 i, dy = -S + r + 8 (jb + JB ja)
+            for (int c0 = 0; c0 < C::JA * ncols; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + ab * (uint32_t)kMaxCols + (uint32_t)c0, v);
                 tmem_wait_ld();
-                const int t = m * 128 + warp * 32 + lane;
-                const bool valid = t < nshift;
-                const int dy = t / K2 - S, dx = t % K2 - S;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float f = __uint_as_float(r[q]);
-                    const uint32_t c = valid ? (uint32_t)f : 0u;
-                    unsigned long long k = valid ? shift_key(c, dx, dy, S) : 0ull;
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) {
-                        const unsigned long long w = __shfl_xor_sync(0xffffffffu, k, o);
-                        k = w > k ? w : k;
-                    }
-                    if (lane == 0 && c0 + q < NB) atomicMax(keys + c0 + q, k);
+                    const int col = c0 + q;
+                    const int ja = col / ncols, cb = col - ja * ncols;
+                    const int b = cb / nbp, n = cb - b * nbp;
+                    const int dx = -S + gg + 16 * (b % C::NBX);
+                    const int dy = -S + rr + 8 * (b / C::NBX + C::JB * ja);
+                    const bool valid = dx <= S;
+                    const unsigned long long k =
+                        warp_max64(valid ? shift_key((uint32_t)__uint_as_float(v[q]), dx, dy, S) : 0ull);
+                    if (lane == 0 && n < (int)item.count) atomicMax(keys + n, k);
                 }
             }
-        }
-        fence_before();
-        __syncthreads();
-        fence_after();
-        for (int n = tid; n < (int)item.count; n += kThreads) {
-            const uint32_t pi = surv[item.first + n];
-            const pcl_pair pr = pairs[pi];
-            const unsigned long long k = keys[n];
-            const int dx = S - (int)(k & 0xffu), dy = S - (int)((k >> 8) & 0xffu);
-            const uint32_t cb = (uint32_t)(k >> 32);
-            const uint64_t pa = A.pop[pr.a], pb = B.pop[pr.b];
-            pcl_record rec{};
-            rec.a = pr.a;
-            rec.b = pr.b;
-            rec.mode = PCL_MODE_COSINE;
-            rec.dx_dbu = dx * g.p;
-            rec.dy_dbu = dy * g.p;
-            rec.score = cb;
-            float sim = (pa && pb) ? (float)cb / sqrtf((float)pa * (float)pb) : 0.0f;
-            uint16_t fl = PCL_F_ALIGNED;
-            const float T = (float)prm.cos_num / (float)prm.cos_den;
-            if (pa && pb && fabsf(sim - T) < prm.near_band) {
-                fl |= PCL_F_NEAR_BAND;
-                sim = (float)((double)cb / sqrt((double)pa * (double)pb));
+            fence_before();
+            mbar_arrive(bar(kAccEmpty + ab));
+            bar_sync(kBarEpi, kEpi);
+            for (int n = et; n < (int)item.count; n += kEpi) {
+                const uint32_t pi = surv[item.first + n];
+                const pcl_pair pr = pairs[pi];
+                const unsigned long long k = keys[n];
+                keys[n] = 0ull;
+                const int dx = S - (int)(k & 0xffu), dy = S - (int)((k >> 8) & 0xffu);
+                const uint32_t cb = (uint32_t)(k >> 32);
+                const uint64_t pa = A.pop[pr.a], pb = B.pop[pr.b];
+                pcl_record rec{};
+                rec.a = pr.a;
+                rec.b = pr.b;
+                rec.mode = PCL_MODE_COSINE;
+                rec.dx_dbu = dx * g.p;
+                rec.dy_dbu = dy * g.p;
+                rec.score = cb;
+                float sim = (pa && pb) ? (float)cb / sqrtf((float)pa * (float)pb) : 0.0f;
+                uint16_t fl = PCL_F_ALIGNED;
+                const float T = (float)prm.cos_num / (float)prm.cos_den;
+                if (pa && pb && fabsf(sim - T) < prm.near_band) {
+                    fl |= PCL_F_NEAR_BAND;
+                    sim = (float)((double)cb / sqrt((double)pa * (double)pb));
+                }
+                rec.sim = sim;
+                rec.flags = fl;
+                rec.pass = cos_exceeds(cb, pa, pb, prm.cos_num, prm.cos_den) ? 1 : 0;
+                out[pi] = rec;
             }
-            rec.sim = sim;
-            rec.flags = fl;
-            rec.pass = cos_exceeds(cb, pa, pb, prm.cos_num, prm.cos_den) ? 1 : 0;
-            out[pi] = rec;
+            bar_sync(kBarEpi, kEpi);
         }
-        __syncthreads();
-    }
-    if (failed) {
-        // let every MMA still in flight finish before the memory is released
-        for (uint32_t k = (u >= 2 ? u - 2 : 0); k < u; ++k) (void)mbar_wait((k & 1) ? mbar1 : mbar0, (k >> 1) & 1);
-        if (tid == 0) atomicExch(err, 1);
+        if (!ok) raise_abort();
     }
     fence_before();
     __syncthreads();
@@ -422,22 +783,42 @@ __global__ void tc_items_kernel(const uint32_t *head, const uint32_t *hpos, cons
 
 }  // namespace
 
-int tc_batch(const Geo &g) {
-    const int tiles = ((2 * g.S + 1) * (2 * g.S + 1) + 127) / 128;
-    int nb = (int)(kTmemCols / (uint32_t)tiles) / 16 * 16;
-    if (nb > kMaxNB) nb = kMaxNB;
-    return nb;
+bool tc_supported(const Geo &g) {
+    return (g.N == 64 && g.S == 4) || (g.N == 128 && g.S == 8) || (g.N == 256 && g.S == 16);
 }
 
 size_t tc_workspace(uint64_t n) { return 4 * (3 * (size_t)n + 8) + sizeof(TcItem) * (size_t)(n + 1) + 256; }
+
+namespace {
+
+template <int S, int NW, bool FP8>
+cudaError_t launch_corr(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
+                        const uint32_t *surv, const TcItem *items, const unsigned int *n_items, pcl_record *out,
+                        int num_sms, int *d_err, cudaStream_t st) {
+    using C = Tc<S, NW, FP8>;
+    cudaError_t e = cudaFuncSetAttribute(tc_corr_kernel<S, NW, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    tc_corr_kernel<S, NW, FP8><<<num_sms, kThreads, C::BYTES, st>>>(prm, a, b, pairs, surv, items, n_items, out, d_err);
+    return cudaGetLastError();
+}
+
+template <int S, int NW>
+int members_of() {
+    return Tc<S, NW, false>::NB;
+}
+
+}  // namespace
 
 cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
                       uint64_t n, const unsigned long long *d_n, pcl_record *out, void *ws, size_t ws_bytes,
                       int num_sms, int *d_err, cudaStream_t st) {
     const Geo g = make_geo(prm);
-    const int NB = tc_batch(g);
-    if (NB < 16 || n == 0) return n == 0 ? cudaSuccess : cudaErrorNotSupported;
+    if (!tc_supported(g)) return cudaErrorNotSupported;
+    if (n == 0) return cudaSuccess;
     if (ws_bytes < tc_workspace(n) || n > 0xffffffffull) return cudaErrorInvalidValue;
+    const bool fp8 = prm.cos_engine == PCL_ENGINE_TC_DIRECT_FP8;
+    const int NB = g.S == 4 ? members_of<4, 1>() : g.S == 8 ? members_of<8, 2>() : members_of<16, 4>();
     char *w = static_cast<char *>(ws);
     uint32_t *keep = reinterpret_cast<uint32_t *>(w);
     uint32_t *pos = keep + n;           // n + 1
@@ -454,12 +835,18 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     // segment heads over the survivors (keep reused as head flags)
     tc_seg_kernel<<<num_sms * 4, 256, 0, st>>>(pairs, surv, pos + n, keep);
     tc_items_kernel<<<num_sms * 4, 256, 0, st>>>(keep, nullptr, pos + n, NB, items, n_items, (uint32_t)n + 1);
-    const int tiles = ((2 * g.S + 1) * (2 * g.S + 1) + 127) / 128;
-    const TcSmem plan = tc_smem(g.N, NB, tiles);
-    e = cudaFuncSetAttribute(tc_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.bytes);
-    if (e != cudaSuccess) return e;
-    tc_corr_kernel<<<num_sms, kThreads, plan.bytes, st>>>(prm, a, b, pairs, surv, items, n_items, out, NB, d_err);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (g.S) {
+        case 4:
+            return fp8 ? launch_corr<4, 1, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
+                       : launch_corr<4, 1, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case 8:
+            return fp8 ? launch_corr<8, 2, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
+                       : launch_corr<8, 2, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        default:
+            return fp8 ? launch_corr<16, 4, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
+                       : launch_corr<16, 4, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+    }
 }
 
 }  // namespace pcl

@@ -1,6 +1,8 @@
 """Tensor-core direct correlation (a8) against the oracle and the FFT engine:
-exact shifts, overlaps and decisions, |sim diff| <= 1e-5, on raster sizes that
-need one, three and nine 128-shift tiles."""
+exact shifts, overlaps and decisions, |sim diff| <= 1e-5, for the three
+(N, S) geometries the engine covers -- (64, 4), (128, 8), (256, 16) -- with
+FP16 and E4M3 operands, member batches from one pair to a full item, and the
+error for a geometry it does not cover."""
 import numpy as np
 import pytest
 
@@ -40,7 +42,8 @@ def _pairs(wl, rng, k):
 
 @pytest.mark.parametrize("kind", ["n64", "n128", "n256"])
 @pytest.mark.parametrize("gates", [False, True])
-def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates):
+@pytest.mark.parametrize("engine", ["f16", "e4m3"])
+def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates, engine):
     import paper_2512_13133_gb300 as pcl
     wl = _workload(kind)
     rng = np.random.default_rng(11)
@@ -48,8 +51,8 @@ def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates):
     flags = 0 if gates else pcl.P_NO_GATES
     num = 80 if gates else 95  # with gates, a looser threshold lets pairs through to the engine
     ctx = pcl.Context(0)
-    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, cos_engine=pcl.ENGINE_TC_DIRECT,
-                    flags=flags)
+    eng = pcl.ENGINE_TC_DIRECT if engine == "f16" else pcl.ENGINE_TC_DIRECT_FP8
+    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, cos_engine=eng, flags=flags)
     Pf = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, flags=flags)
     cs = pcl.alloc_clipset(Pf, wl.rect_off, wl.rects)
     pcl.pcl_rasterize(ctx, Pf, cs)
@@ -68,4 +71,50 @@ def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates):
     assert np.abs(gt["sim"][al].astype(np.float64) - o["sim"][al]).max() <= 1e-5
     for f in ("dx_dbu", "dy_dbu", "score", "pass_"):
         np.testing.assert_array_equal(gt[f], gf[f])
+    ctx.close()
+
+
+def _dense_pairs(wl, rng, reps, per_rep):
+    """reps representatives, each listed with per_rep distinct members (b != a)."""
+    out = []
+    for a in rng.choice(wl.n, reps, replace=False):
+        bs = rng.choice(np.delete(np.arange(wl.n), a), per_rep, replace=False)
+        out += [(int(a), int(b)) for b in sorted(bs)]
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("engine", ["f16", "e4m3"])
+def test_tc_full_items_and_split_segments(torch_cuda, engine):
+    """Representatives with 1, 31, 32, 33 and 70 members: full items of 32
+    members, a segment split over three items, and ragged last items."""
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.preset("scale", seed=8, n_clips=300, n_seeds=30, n_copies=200)
+    rng = np.random.default_rng(5)
+    pairs = np.concatenate([_dense_pairs(wl, rng, 1, k) for k in (1, 31, 32, 33, 70)])
+    eng = pcl.ENGINE_TC_DIRECT if engine == "f16" else pcl.ENGINE_TC_DIRECT_FP8
+    ctx = pcl.Context(0)
+    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_engine=eng, flags=pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(Pt, wl.rect_off, wl.rects)
+    pcl.pcl_rasterize(ctx, Pt, cs)
+    tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
+    gt = pcl.records_to_numpy(pcl.match(ctx, Pt, pcl.MODE_COSINE, cs, cs, tp))
+    assert pcl.pcl_device_error(ctx) == 0
+    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=False)
+    for f in ("dx_dbu", "dy_dbu", "pass_"):
+        np.testing.assert_array_equal(gt[f], o[f])
+    np.testing.assert_array_equal(gt["score"].astype(np.int64), o["score"])
+    ctx.close()
+
+
+def test_tc_rejects_uncovered_geometry(torch_cuda):
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.preset("scale", seed=9, n_clips=20, n_seeds=4, n_copies=10)
+    ctx = pcl.Context(0)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, 32, cos_engine=pcl.ENGINE_TC_DIRECT)  # N = 256, S = 8
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects)
+    pcl.pcl_rasterize(ctx, P, cs)
+    tp = torch_cuda.from_numpy(np.array([[0, 1]], dtype=np.int32)).cuda()
+    with pytest.raises(pcl.PclError) as ei:
+        pcl.match(ctx, P, pcl.MODE_COSINE, cs, cs, tp)
+    assert ei.value.status == pcl.PCL_ERR_UNSUPPORTED
     ctx.close()
