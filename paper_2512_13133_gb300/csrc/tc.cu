@@ -51,12 +51,13 @@ namespace pcl {
 
 namespace {
 
-constexpr int kWarps = 11;
+constexpr int kWarps = 12;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kAProd = 64;               // warps 1-2
-constexpr int kBProd = 128;              // warps 3-6
-constexpr int kEpi = 128;                // warps 7-10
-constexpr int kKS = 2;                   // MMAs per stage
+constexpr int kIssuers = 2;              // warps 0-1: one MMA-issuing thread each
+constexpr int kAProd = 64;               // warps 2-3
+constexpr int kBProd = 128;              // warps 4-7
+constexpr int kEpi = 128;                // warps 8-11
+constexpr int kKS = 4;                   // K steps (MMA K) per stage
 constexpr int kCores = 2 * kKS;          // image rows (K core matrices) per stage
 constexpr int kCopies = 16;              // shifted copies of the representative
 constexpr int kMaxCols = 256;            // N of one MMA / one accumulator buffer
@@ -72,18 +73,22 @@ struct Tc {
     static constexpr int N = 64 * NW;
     static constexpr int NBX = (2 * S) / 16 > 0 ? (2 * S) / 16 : 1;  // x copies of a member (16 px apart)
     static constexpr int NBY = (2 * S) / 8 > 0 ? (2 * S) / 8 : 1;    // 8-row dy blocks of the core
-    static constexpr int JB = NBY >= 2 ? 2 : 1;                       // dy blocks on the member side
-    static constexpr int JA = NBY / JB;                               // dy blocks on A's side (MMAs per K step)
+    static constexpr int JB = NBY;                                    // dy blocks, all on the member side
+    static constexpr int JA = 1;                                      // MMAs per K step
     static constexpr int NCOPY = NBX * JB;                            // member copies per MMA
-    static constexpr int NB = kMaxCols / (JA * NCOPY);                // members per item
+    // members per item: each issuer accumulates into its own copy of the
+    // N columns, and both copies fit one 256-column accumulator buffer
+    static constexpr int NB = kMaxCols / kIssuers / (JA * NCOPY);
     static constexpr int NMAX = NCOPY * NB;                           // N of one MMA at most
-    static constexpr int RND = 16 / NCOPY;                            // member rounding (N % 16 == 0)
+    // member rounding: N % 16 == 0, and each ring entry (NBX * nbp columns) ends on an 8-column group
+    static constexpr int RND = 16 / NCOPY > 8 / NBX ? 16 / NCOPY : 8 / NBX;
     static constexpr int DYL = -S + 8 * NBY;                          // rest row
     static constexpr int DXL = -S + 16 * NBX;                         // rest column, if <= S
     static constexpr bool COL = DXL <= S;
     static constexpr int CH = FP8 ? 16 : 8;                           // pixels per 16-byte row
     static constexpr int YHI = (N + 8 * (JB - 1) + kCores - 1) / kCores * kCores;  // K image rows
     static constexpr int NST = YHI / kCores;                          // stages per phase
+    static constexpr int ZE = JB - 1;                                 // zero entries per phase
     static constexpr int NPH = (N + 16 * (NBX - 1)) / CH;             // column phases
     static constexpr int ROWS = YHI + 8 + 8 * JB * (JA - 1);          // rows of one copy
     static constexpr uint32_t ABYTES = (uint32_t)kCopies * ROWS * 16;
@@ -91,23 +96,28 @@ struct Tc {
     static constexpr int WPT = STRIP > 0 ? 2 : 1;                     // 64-bit words per staged strip
     static constexpr int TASKS = NB * kCores;                         // (member, row) tasks per stage
     static constexpr int TPT = TASKS / kBProd;                        // tasks per producer thread
-    static constexpr uint32_t SLOT = (uint32_t)kCores * NMAX * 16;    // member tile of one stage
-    static constexpr uint32_t STG = (uint32_t)WPT * TASKS * 8;        // staged words of one stage
-    static constexpr int R = 4;                                       // member tile buffers
-    static constexpr uint32_t FIXED =
-        2 * ABYTES + (uint32_t)R * SLOT + (uint32_t)NB * 8 + (uint32_t)(kBFull + 2 * R) * 8 + 16;
-    static constexpr int DFIT = (int)((kSmemMax - FIXED) / STG);
-    static constexpr int D = DFIT > 16 ? 16 : DFIT;                   // prefetch depth (stages)
-    static constexpr uint32_t OFF_SLOTS = 2 * ABYTES;
-    static constexpr uint32_t OFF_STG = OFF_SLOTS + (uint32_t)R * SLOT;
-    static constexpr uint32_t OFF_KEYS = OFF_STG + (uint32_t)D * STG;
+    static constexpr uint32_t HBMAX = (uint32_t)(NMAX / JB) * 16;     // one entry, one K core, at most
+    // ring residues: as many as shared memory holds (even, at most 18), so
+    // that up to RR - JB entries are in flight between producers and MMAs
+    static constexpr uint32_t OTHER = 2 * ABYTES + (uint32_t)NB * 8 + (uint32_t)(kBFull + 2 * 18) * 8 + 16;
+    static constexpr int RFIT = (int)((kSmemMax - OTHER) / (kCores * HBMAX)) - (JB - 1);
+    static constexpr int RR = (RFIT > 18 ? 18 : RFIT) & ~1;
+    static constexpr int POS = RR + JB - 1;                           // ring positions (JB - 1 mirrors)
+    static constexpr uint32_t RING = (uint32_t)POS * kCores * HBMAX;
+    static constexpr int PD = TPT * WPT >= 16 ? 1 : 16 / (TPT * WPT);  // register prefetch depth (stages)
+    static constexpr uint32_t OFF_RING = 2 * ABYTES;
+    static constexpr uint32_t OFF_KEYS = OFF_RING + RING;
     static constexpr uint32_t OFF_BARS = OFF_KEYS + (uint32_t)NB * 8;
-    static constexpr uint32_t BYTES = OFF_BARS + (uint32_t)(kBFull + 2 * R) * 8 + 16;
+    static constexpr uint32_t BYTES = OFF_BARS + (uint32_t)(kBFull + 2 * RR) * 8 + 16;
     static_assert(CH + STRIP <= 32, "member strip exceeds 32 bits");
     static_assert(NPH * CH == N + 16 * (NBX - 1), "column phases do not cover the member copies");
+    static_assert(kThreads == 32 * kIssuers + kAProd + kBProd + kEpi && kEpi == 128, "warp roles");
+    static_assert(JA == 1 && (NST + ZE) % 2 == 0 && RR % kIssuers == 0, "issuers alternate entries, producers pair them");
     static_assert(TASKS % kBProd == 0 && NB % RND == 0 && JA * JB == NBY, "task split");
-    static_assert(D >= 4 && BYTES <= kSmemMax, "shared memory plan");
-    static_assert(kCores * 2 == 8, "the member-side dy copy is two stages back");
+    static_assert((NBX * RND) % 8 == 0 || JB == 1, "an entry must end on an 8-column group");
+    static_assert(RR - JB + 1 >= 3, "producers run at least three entries ahead");
+    static_assert(kCores == 8, "the member-side dy copy (8 rows up) is the previous stage");
+    static_assert(PD >= 2 && BYTES <= kSmemMax, "shared memory plan");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -194,8 +204,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 // bounded wait for the phase of the given parity; false on time-out or when
 // another role has aborted (abort_flag may be null: wait regardless)
-__device__ __noinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
-    if (mbar_try_wait(mbar, parity)) return true;
+__device__ __forceinline__ bool wait_phase_slow(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
     const uint64_t t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 16; ++i)
@@ -203,6 +212,9 @@ __device__ __noinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const vo
         if (abort_flag && *abort_flag) return false;
         if (gtimer() - t0 > kWaitNs) return false;
     }
+}
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
+    return mbar_try_wait(mbar, parity) || wait_phase_slow(mbar, parity, abort_flag);
 }
 
 // barrier over `count` threads of one role that also ORs a flag
@@ -221,18 +233,6 @@ __device__ __forceinline__ bool bar_any(int id, int count, bool v) {
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
     asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-// 8-byte asynchronous copy global -> shared; bytes past src_bytes are zero
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)),
-                 "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -279,39 +279,27 @@ __device__ __forceinline__ void shifted_row(const uint64_t *__restrict__ A, int 
     for (int w = 0; w < NW; ++w) o[w] = (a[w] >> SH) | (a[w + 1] << (64 - SH));
 }
 
-// The rest of the window for one pair, counted exactly by one warp: the row
-// dy = DYL for every dx in [-S, S] and, when COL, the column dx = DXL for dy
-// in [-S, S).  Lanes take 32 consecutive rows y of B at a time.  The row part
-// shifts A's row y + DYL in registers; the column part needs A's rows y + dy
-// shifted by DXL, which the warp holds as two blocks of 32 rows (y0 - S + l
-// and y0 - S + 32 + l) and passes around with one shuffle per word.  Returns
-// the largest shift key among these shifts (the same in every lane).
-template <int S, int NW, int DYL, int DXL, bool COL>
-__device__ __forceinline__ unsigned long long rest_key(const uint64_t *__restrict__ A,
-                                                       const uint64_t *__restrict__ B, int lane) {
+// The rest of the window for one pair is counted exactly by one warp, lanes
+// taking 32 consecutive rows y of B at a time.  Row part: dy = DYL for every
+// dx in [-S, S], shifting A's row y + DYL in registers.  Returns the largest
+// shift key among these shifts (the same in every lane).
+template <int S, int NW, int DYL>
+__device__ __forceinline__ unsigned long long rest_row_key(const uint64_t *__restrict__ A,
+                                                           const uint64_t *__restrict__ B, int lane) {
     constexpr int N = 64 * NW;
-    static_assert(!COL || 2 * S <= 32, "column rest spans more than two row blocks");
     uint32_t cr[2 * S + 1];
-    uint32_t cc[COL ? 2 * S : 1];
 #pragma unroll
     for (int d = 0; d <= 2 * S; ++d) cr[d] = 0;
-#pragma unroll
-    for (int e = 0; e < (COL ? 2 * S : 1); ++e) cc[e] = 0;
-    for (int y0 = 0; y0 < N; y0 += 32) {
-        const int y = y0 + lane;
+    for (int y = lane; y + DYL < N; y += 32) {
         uint64_t b[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) b[w] = __ldg(B + (size_t)y * NW + w);
         // a[w + 1] = word w of A's row y + DYL, zero words on both sides
         uint64_t a[NW + 2];
         a[0] = 0ull;
         a[NW + 1] = 0ull;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) a[w + 1] = y + DYL < N ? __ldg(A + (size_t)(y + DYL) * NW + w) : 0ull;
-        uint64_t s0[NW], s1[NW];
-        if constexpr (COL) {
-            shifted_row<NW, DXL>(A, y0 - S + lane, s0);
-            shifted_row<NW, DXL>(A, y0 - S + 32 + lane, s1);
+        for (int w = 0; w < NW; ++w) {
+            b[w] = __ldg(B + (size_t)y * NW + w);
+            a[w + 1] = __ldg(A + (size_t)(y + DYL) * NW + w);
         }
 #pragma unroll
         for (int d = 0; d <= 2 * S; ++d) {
@@ -327,36 +315,52 @@ __device__ __forceinline__ unsigned long long rest_key(const uint64_t *__restric
             }
             cr[d] += sum;
         }
-        if constexpr (COL) {
-            // lane l needs shifted row y0 + l + dy = block row m = l + dy + S: lane
-            // (m & 31) of block m >> 5; a source lane j serves block 0 when
-            // j >= e (= dy + S), else block 1
-#pragma unroll
-            for (int e = 0; e < 2 * S; ++e) {
-                uint32_t sum = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint64_t v = __shfl_sync(0xffffffffu, lane >= e ? s0[w] : s1[w], (lane + e) & 31);
-                    sum += (uint32_t)__popcll(v & b[w]);
-                }
-                cc[e] += sum;
-            }
-        }
     }
     unsigned long long best = 0ull;
 #pragma unroll
     for (int d = 0; d <= 2 * S; ++d) {
-        const uint32_t c = __reduce_add_sync(0xffffffffu, cr[d]);
-        const unsigned long long k = shift_key(c, d - S, DYL, S);
+        const unsigned long long k = shift_key(__reduce_add_sync(0xffffffffu, cr[d]), d - S, DYL, S);
         best = k > best ? k : best;
     }
-    if constexpr (COL) {
+    return best;
+}
+
+// Column part: dx = DXL for dy in [-S, S).  Lane l needs A's row y0 + l + dy
+// shifted by DXL; the warp holds two blocks of 32 shifted rows (y0 - S + l
+// and y0 - S + 32 + l), and the row for dy is block row m = l + dy + S, i.e.
+// lane (m & 31) of block m >> 5: a source lane j serves block 0 when
+// j >= e (= dy + S), else block 1, so one shuffle per word suffices.
+template <int S, int NW, int DXL>
+__device__ __forceinline__ unsigned long long rest_col_key(const uint64_t *__restrict__ A,
+                                                           const uint64_t *__restrict__ B, int lane) {
+    constexpr int N = 64 * NW;
+    static_assert(2 * S <= 32, "column rest spans more than two row blocks");
+    uint32_t cc[2 * S];
+#pragma unroll
+    for (int e = 0; e < 2 * S; ++e) cc[e] = 0;
+    for (int y0 = 0; y0 < N; y0 += 32) {
+        const int y = y0 + lane;
+        uint64_t b[NW], s0[NW], s1[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) b[w] = __ldg(B + (size_t)y * NW + w);
+        shifted_row<NW, DXL>(A, y0 - S + lane, s0);
+        shifted_row<NW, DXL>(A, y0 - S + 32 + lane, s1);
 #pragma unroll
         for (int e = 0; e < 2 * S; ++e) {
-            const uint32_t c = __reduce_add_sync(0xffffffffu, cc[e]);
-            const unsigned long long k = shift_key(c, DXL, e - S, S);
-            best = k > best ? k : best;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint64_t v = __shfl_sync(0xffffffffu, lane >= e ? s0[w] : s1[w], (lane + e) & 31);
+                sum += (uint32_t)__popcll(v & b[w]);
+            }
+            cc[e] += sum;
         }
+    }
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int e = 0; e < 2 * S; ++e) {
+        const unsigned long long k = shift_key(__reduce_add_sync(0xffffffffu, cc[e]), DXL, e - S, S);
+        best = k > best ? k : best;
     }
     return best;
 }
@@ -371,16 +375,37 @@ __device__ __forceinline__ int round_members(uint32_t count) {
     return (int)((count + RND - 1) / RND * RND);
 }
 
+// The strip words of one stage (phase ph, stage st) for one member-tile
+// producer thread: rows st * kCores + q of its tasks' members, words w0 and
+// w0 + 1 around the strip (zero outside the raster).  Plain read-only loads
+// into registers, issued stages ahead of their use.
+template <typename C>
+__device__ __forceinline__ void stage_load(uint64_t (&o)[C::TPT][C::WPT], const uint64_t *const (&mb)[C::TPT], int bt,
+                                           int ph, int st) {
+    const int sb = ph * C::CH - C::STRIP;
+    const int w0 = sb >= 0 ? sb >> 6 : -((-sb + 63) >> 6);
+#pragma unroll
+    for (int u = 0; u < C::TPT; ++u) {
+        const int row = st * kCores + (bt + kBProd * u) / C::NB;
+#pragma unroll
+        for (int e = 0; e < C::WPT; ++e) {
+            const int w = w0 + e;
+            o[u][e] = (mb[u] && row < C::N && w >= 0 && w < C::N / 64) ? __ldg(mb[u] + (size_t)row * (C::N / 64) + w)
+                                                                       : 0ull;
+        }
+    }
+}
+
 template <int S, int NW, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_corr_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, const uint32_t *surv,
                    const TcItem *items, const unsigned int *n_items, pcl_record *out, int *err) {
     using C = Tc<S, NW, FP8>;
-    constexpr int N = C::N, R = C::R, D = C::D;
+    constexpr int N = C::N, RR = C::RR;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(sm + C::OFF_KEYS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::OFF_BARS);
-    volatile uint32_t *misc = reinterpret_cast<volatile uint32_t *>(bars + kBFull + 2 * R);  // [0] tmem, [1] abort
+    volatile uint32_t *misc = reinterpret_cast<volatile uint32_t *>(bars + kBFull + 2 * RR);  // [0] tmem, [1] abort
     const volatile uint32_t *abortf = misc + 1;
     const uint32_t sbase = smem_u32(sm);
     const uint32_t bar0 = smem_u32(bars);
@@ -395,14 +420,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
             mbar_init(bar(kAFull + k), kAProd);
-            mbar_init(bar(kAEmpty + k), 1);
-            mbar_init(bar(kAccFull + k), 1);
+            mbar_init(bar(kAEmpty + k), kIssuers);
+            mbar_init(bar(kAccFull + k), kIssuers);
             mbar_init(bar(kAccEmpty + k), kEpi);
         }
-        mbar_init(bar(kFin), 1);
-        for (int k = 0; k < R; ++k) {
+        mbar_init(bar(kFin), kIssuers);
+        for (int k = 0; k < RR; ++k) {
             mbar_init(bar(kBFull + k), kBProd);
-            mbar_init(bar(kBFull + R + k), 1);
+            mbar_init(bar(kBFull + RR + k), 1);
         }
         misc[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -419,42 +444,68 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = misc[0];
     const unsigned int nit = *n_items;
 
-    if (warp == 0) {
+    if (warp < kIssuers) {
         // ---------------------------------------------------------------- MMA issue
+        // Member tiles arrive as ring entries e (per phase: JB - 1 zero
+        // entries, then one entry per stage).  Entry e sits at position
+        // RR - 1 - e % RR, so entries e - 1, e - 2, .. follow it in memory
+        // (positions RR .. RR + JB - 2 mirror 0 .. JB - 2): one descriptor
+        // reads "this stage's rows | the rows 8 above | 16 above | .." as the
+        // JB blocks of N.  An issuing thread can start one tcgen05 instruction
+        // (MMA or commit) about every 150 cycles whatever N is, so two warps
+        // issue: warp w takes the entries e = w (mod 2) into its own
+        // accumulator copy (columns w * ncols of the buffer) and commits them;
+        // the epilogue adds the copies.
         if (lane == 0) {
+            const int iw = warp;
             bool ok = true;
-            uint32_t pc = 0, sc = 0, li = 0;
+            uint32_t pc = 0, e = 0, li = 0;
             for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x, ++li) {
                 const TcItem item = items[it];
                 const int ncols = C::NCOPY * round_members<C::RND>(item.count);  // N of each MMA
+                const uint32_t hb = (uint32_t)(ncols / C::JB) * 16, lbo = (uint32_t)C::POS * hb;
                 const uint32_t idesc = idesc_of(128, ncols);
+                uint32_t accum = 0;  // the first MMA of the item into this copy overwrites
                 const uint32_t ab = li & 1;
                 if (li >= 2 && !(ok = wait_phase(bar(kAccEmpty + ab), ((li >> 1) - 1) & 1, abortf))) break;
                 fence_after();
-                const uint32_t dcol = tmem + ab * (uint32_t)kMaxCols;
+                const uint32_t dcol = tmem + ab * (uint32_t)kMaxCols + (uint32_t)(iw * ncols);
+                // descriptors: only the start field (16-byte units) moves below
+                const uint64_t bd_item = smem_desc(sbase + C::OFF_RING, lbo, 128);
                 for (int ph = 0; ph < C::NPH && ok; ++ph, ++pc) {
                     const uint32_t abf = pc & 1;
                     if (!(ok = wait_phase(bar(kAFull + abf), (pc >> 1) & 1, abortf))) break;
-                    const uint32_t abase = sbase + abf * C::ABYTES;
-                    for (int st = 0; st < C::NST; ++st, ++sc) {
-                        const uint32_t slot = sc % (uint32_t)R;
-                        if (!(ok = wait_phase(bar(kBFull + slot), (sc / R) & 1, abortf))) break;
-                        fence_after();
-                        const uint32_t bbase = sbase + C::OFF_SLOTS + slot * C::SLOT;
+                    // A copies interleaved per image row ([row][copy][16 B]): a core
+                    // matrix is 8 copies of one row (128-byte aligned), the next K
+                    // core matrix the next row (256 bytes), the next group of 8 M
+                    // rows the other 8 copies, then the next row (128 bytes)
+                    const uint64_t ad_ph = smem_desc(sbase + abf * C::ABYTES, 256, 128);
+                    // entries of this phase: e0 + (st + ZE); a phase (and an item) has an
+                    // even number of entries, so issuer iw takes st = -ZE + iw, -ZE + iw + 2, ..
+                    const uint32_t e0 = e;
+                    for (int st = -C::ZE + iw; st < C::NST; st += kIssuers) {
+                        const uint32_t e = e0 + (uint32_t)(st + C::ZE);
+                        if (!(ok = wait_phase(bar(kBFull + e % RR), (e / RR) & 1, abortf))) break;
+                        if (st >= 0) {
+                            // the operands were published by the producers' proxy fence
+                            // and arrival; no tcgen05 fence is needed on this path
+                            const uint32_t pos = RR - 1 - e % RR;
+                            const uint64_t bd_e = bd_item + (uint64_t)((pos * hb) >> 4);
+                            const uint64_t ad_st = ad_ph + (uint64_t)(st * kCores * 16);
 #pragma unroll
-                        for (int t = 0; t < kKS; ++t) {
-                            const int Y = st * kCores + 2 * t;
-                            const uint64_t bd = smem_desc(bbase + (uint32_t)(2 * t * ncols * 16), ncols * 16, 128);
-#pragma unroll
-                            for (int ja = 0; ja < C::JA; ++ja) {
-                                // A rows Y + r - S + 8 JB ja: the dy block ja of A's side
-                                const uint64_t ad =
-                                    smem_desc(abase + (uint32_t)(Y + 8 * C::JB * ja) * 16, 16, C::ROWS * 16);
-                                mma<FP8>(dcol + (uint32_t)(ja * ncols), ad, bd, idesc, (ph | st | t) ? 1u : 0u);
+                            for (int t = 0; t < kKS; ++t) {
+                                // K step t: image rows Y, Y + 1 with Y = st * kCores + 2 t;
+                                // M row m = (dy offset m >> 4, copy m & 15) reads A's row
+                                // Y + (m >> 4) - S
+                                const uint64_t bd = bd_e + (uint64_t)((2 * t * lbo) >> 4);
+                                const uint64_t ad = ad_st + (uint64_t)(2 * t * 16);
+                                mma<FP8>(dcol, ad, bd, idesc, accum);
+                                accum = 1u;
                             }
                         }
-                        mma_commit(bar(kBFull + R + slot));
+                        mma_commit(bar(kBFull + RR + e % RR));
                     }
+                    e = e0 + (uint32_t)(C::NST + C::ZE);
                     if (ok) mma_commit(bar(kAEmpty + abf));
                 }
                 if (ok) mma_commit(bar(kAccFull + ab));
@@ -465,9 +516,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!wait_phase(bar(kFin), 0, nullptr)) raise_abort();
         }
         __syncwarp();
-    } else if (warp <= 2) {
+    } else if (warp < kIssuers + kAProd / 32) {
         // ---------------------------------------------------------------- shifted copies of A
-        const int pt = tid - 32;
+        const int pt = tid - 32 * kIssuers;
         bool ok = true;
         uint32_t pc = 0;
         for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x) {
@@ -478,138 +529,157 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (pc >= 2 && !(ok = wait_phase(bar(kAEmpty + abf), ((pc >> 1) - 1) & 1, abortf))) break;
                 unsigned char *buf = sm + abf * C::ABYTES;
                 const int base = ph * C::CH - S;  // copy g, pixel k = A column base + g + k
+                // (row ridx, copy g) at 16 (16 ridx + g); a thread writes the 16
+                // copies of its row, starting at copy (lane & 15) so that a warp's
+                // stores spread over the banks
                 for (int ridx = pt; ridx < C::ROWS; ridx += kAProd) {
                     const int yy = ridx - S;
                     uint64_t win = 0ull;
                     if (yy >= 0 && yy < N) win = bit_window<NW>(abits + (size_t)yy * NW, base);
 #pragma unroll
-                    for (int g = 0; g < kCopies; ++g)
-                        st16(buf + ((uint32_t)g * C::ROWS + ridx) * 16, expand<FP8>((uint32_t)(win >> g)));
+                    for (int j = 0; j < kCopies; ++j) {
+                        const int g = (j + lane) & 15;
+                        st16(buf + (uint32_t)(ridx * kCopies + g) * 16, expand<FP8>((uint32_t)(win >> g)));
+                    }
                 }
                 fence_proxy_async();
                 mbar_arrive(bar(kAFull + abf));
             }
         }
         if (!ok) raise_abort();
-    } else if (warp <= 6) {
+    } else if (warp < kIssuers + (kAProd + kBProd) / 32) {
         // ---------------------------------------------------------------- member tiles
         // Task k = (member n = k % NB, row q = k / NB of each stage); each
         // thread stages its own strip words D stages ahead with cp.async
-        // (zero-filled outside the raster) and keeps the strips of the two
-        // previous stages, so the member-side dy copy (8 rows = two stages
-        // back) needs no second load.  No barrier among the producers.
-        const int bt = tid - 96;
+        // (zero-filled outside the raster) and writes the NBX x copies of its
+        // row into the ring entry of the stage.  No barrier among producers.
+        const int bt = tid - (32 * kIssuers + kAProd);
         bool ok = true;
-        uint32_t sc = 0;
-        unsigned char *stg = sm + C::OFF_STG;
+        uint32_t e = 0;
+        unsigned char *ring = sm + C::OFF_RING;
         for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x) {
             const TcItem item = items[it];
             const int nbp = round_members<C::RND>(item.count);
-            const int ncols = C::NCOPY * nbp;
+            const uint32_t hb = (uint32_t)(C::NBX * nbp) * 16, lbo = (uint32_t)C::POS * hb;
             const uint64_t *mb[C::TPT];
 #pragma unroll
             for (int u = 0; u < C::TPT; ++u) {
                 const int n = (bt + kBProd * u) % C::NB;
                 mb[u] = n < (int)item.count ? B.bits + (size_t)pairs[surv[item.first + n]].b * N * NW : nullptr;
             }
-            const int total = C::NPH * C::NST;
-            // stage s of this item: copy the strip words of rows st * kCores + q
-            auto issue = [&](int s) {
-                const int ph = s / C::NST, st = s - ph * C::NST;
-                const int sb = ph * C::CH - C::STRIP;
-                const int w0 = sb >= 0 ? sb >> 6 : -((-sb + 63) >> 6);
-                unsigned char *dst = stg + (uint32_t)(s % D) * C::STG;
+            // Register ping-pong: the words of pair g + 1 are loaded into one
+            // buffer while pair g is written from the other, so a load has a
+            // whole pair of entries to arrive and no register in flight is moved.
+            constexpr int PPP = (C::NST + C::ZE) / 2;  // pairs per phase
+            uint64_t bufA[2][C::TPT][C::WPT], bufB[2][C::TPT][C::WPT];
+            int nph = 0, nj = 0;  // next pair to load
+            auto pair_load = [&](uint64_t(&b)[2][C::TPT][C::WPT]) {
 #pragma unroll
-                for (int u = 0; u < C::TPT; ++u) {
-                    const int k = bt + kBProd * u;
-                    const int row = st * kCores + k / C::NB;
+                for (int h = 0; h < 2; ++h) {
+                    const int st = -C::ZE + 2 * nj + h;
+                    if (nph < C::NPH && st >= 0) {
+                        stage_load<C>(b[h], mb, bt, nph, st);
+                    } else {
 #pragma unroll
-                    for (int e = 0; e < C::WPT; ++e) {
-                        const int w = w0 + e;
-                        const bool v = mb[u] && row < N && w >= 0 && w < NW;
-                        const uint64_t *src = v ? mb[u] + (size_t)row * NW + w : B.bits;
-                        cp_async8(dst + ((uint32_t)e * C::TASKS + k) * 8, src, v ? 8u : 0u);
+                        for (int u = 0; u < C::TPT; ++u)
+#pragma unroll
+                            for (int w = 0; w < C::WPT; ++w) b[h][u][w] = 0ull;
                     }
                 }
-                cp_async_commit();
+                if (++nj == PPP) {
+                    nj = 0;
+                    ++nph;
+                }
             };
-            for (int s = 0; s < D - 1; ++s) {
-                if (s < total) issue(s);
-                else cp_async_commit();
-            }
-            uint32_t h1[C::TPT], h2[C::TPT];  // strips of stages s - 1 and s - 2
-#pragma unroll
-            for (int u = 0; u < C::TPT; ++u) h1[u] = h2[u] = 0u;
-            for (int s = 0; s < total; ++s, ++sc) {
-                // one group per stage keeps the group count uniform
-                if (s + D - 1 < total) issue(s + D - 1);
-                else cp_async_commit();
-                cp_async_wait<D - 1>();
-                const int ph = s / C::NST, st = s - ph * C::NST;
+            bool first = true;  // the layout changes with the item: wait for the previous item's MMAs
+            // done(x): the MMAs of entry x (by issuer x % 2) have completed
+            auto done = [&](uint32_t x) { return wait_phase(bar(kBFull + RR + x % RR), (x / RR) & 1, abortf); };
+            // entries e, e + 1 (stages st0, st0 + 1 of phase ph) from the words in b
+            auto pair_step = [&](const uint64_t(&b)[2][C::TPT][C::WPT], int ph, int st0) -> bool {
                 const int sb = ph * C::CH - C::STRIP;
                 const int w0 = sb >= 0 ? sb >> 6 : -((-sb + 63) >> 6);
                 const int off = sb - 64 * w0;
-                const uint64_t *src = reinterpret_cast<const uint64_t *>(stg + (uint32_t)(s % D) * C::STG);
-                uint32_t cur[C::TPT];
+                uint32_t cur[2][C::TPT];
 #pragma unroll
-                for (int u = 0; u < C::TPT; ++u) {
-                    const int k = bt + kBProd * u;
-                    const uint64_t lo = src[k];
-                    const uint64_t hi = C::WPT == 2 ? src[C::TASKS + k] : 0ull;
-                    cur[u] = (uint32_t)(off ? (lo >> off) | (hi << (64 - off)) : lo);
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int u = 0; u < C::TPT; ++u) {
+                        const uint64_t lo = b[h][u][0];
+                        const uint64_t hi = C::WPT == 2 ? b[h][u][C::WPT - 1] : 0ull;
+                        cur[h][u] = (uint32_t)(off ? (lo >> off) | (hi << (64 - off)) : lo);
+                    }
+                // the position of entry x last held entry x - RR, read by the MMAs of
+                // entries x - RR .. x - RR + JB - 1 = x - lag; with JB >= 2 those
+                // come from both issuers, so the other issuer's last one, x - lag - 1,
+                // is waited for too.  Every entry waited for is at least e - RR:
+                // an older one shares its barrier with an entry already written,
+                // and its phase parity would no longer tell the two apart.
+                constexpr uint32_t lag = (uint32_t)(RR - C::JB + 1);
+                bool okw = true;
+                if (first) {
+                    if (e >= 1) okw = done(e - 1);
+                    if (okw && e >= 2) okw = done(e - 2);
+                } else {
+                    if (C::JB >= 2 && e >= lag + 1) okw = done(e - lag - 1);
+                    if (okw && e >= lag) okw = done(e - lag);
+                    if (okw && e + 1 >= lag) okw = done(e + 1 - lag);
                 }
-                const uint32_t slot = sc % (uint32_t)R, ru = sc / (uint32_t)R;
-                if (ru >= 1 && !wait_phase(bar(kBFull + R + slot), (ru - 1) & 1, abortf)) {
-                    ok = false;
-                    break;
-                }
-                unsigned char *tile = sm + C::OFF_SLOTS + slot * C::SLOT;
-                const int Ys = st * kCores;
+                first = false;
+                if (!okw) return false;
 #pragma unroll
-                for (int u = 0; u < C::TPT; ++u) {
-                    const int k = bt + kBProd * u, n = k % C::NB, q = k / C::NB;
-                    if (n >= nbp) continue;
-                    unsigned char *dst = tile + (uint32_t)(q * ncols * 16);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t pos = RR - 1 - (e + h) % RR;
+                    unsigned char *d0 = ring + pos * hb;
+                    // positions RR .. RR + JB - 2 mirror 0 .. JB - 2
+                    unsigned char *d1 = (C::JB > 1 && pos + 1 < (uint32_t)C::JB) ? ring + (pos + RR) * hb : nullptr;
+                    const int st = st0 + h, Ys = st * kCores;
 #pragma unroll
-                    for (int jb = 0; jb < C::JB; ++jb) {
-                        const int row = Ys + q - 8 * jb;
-                        const bool v = n < (int)item.count && row >= 0 && row < N;
-                        const uint32_t strip = v ? (jb == 0 ? cur[u] : h2[u]) : 0u;
+                    for (int u = 0; u < C::TPT; ++u) {
+                        const int k = bt + kBProd * u, n = k % C::NB, q = k / C::NB;
+                        if (n >= nbp) continue;
+                        const bool v = st >= 0 && n < (int)item.count && Ys + q < N;
+                        const uint32_t strip = v ? cur[h][u] : 0u;
 #pragma unroll
                         for (int i = 0; i < C::NBX; ++i) {
-                            const int col = (jb * C::NBX + i) * nbp + n;
-                            st16(dst + (col >> 3) * 128 + (col & 7) * 16,
-                                 expand<FP8>(strip >> (16 * (C::NBX - 1 - i))));
+                            const int c0 = i * nbp + n;
+                            const uint32_t o = (uint32_t)q * lbo + (uint32_t)(c0 >> 3) * 128 + (uint32_t)(c0 & 7) * 16;
+                            const uint4 x = expand<FP8>(strip >> (16 * (C::NBX - 1 - i)));
+                            st16(d0 + o, x);
+                            if (d1) st16(d1 + o, x);
                         }
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < C::TPT; ++u) {
-                    h2[u] = h1[u];
-                    h1[u] = cur[u];
-                }
                 fence_proxy_async();
-                mbar_arrive(bar(kBFull + slot));
+                mbar_arrive(bar(kBFull + e % RR));
+                mbar_arrive(bar(kBFull + (e + 1) % RR));
+                return true;
+            };
+            pair_load(bufA);
+            uint32_t gp = 0;  // pairs of this item so far
+            for (int ph = 0; ph < C::NPH && ok; ++ph) {
+                for (int j = 0; j < PPP; ++j, ++gp, e += 2) {
+                    const int st0 = -C::ZE + 2 * j;
+                    if (gp & 1) {
+                        pair_load(bufA);
+                        ok = pair_step(bufB, ph, st0);
+                    } else {
+                        pair_load(bufB);
+                        ok = pair_step(bufA, ph, st0);
+                    }
+                    if (!ok) break;
+                }
             }
-            cp_async_wait<0>();
         }
-        cp_async_wait<0>();
         if (!ok) raise_abort();
     } else {
-        // ---------------------------------------------------------------- rest of the window + epilogue
-        const int et = tid - 224, ew = warp - 7, quarter = warp & 3;
+        // ---------------------------------------------------------------- epilogue + rest of the window
+        const int et = tid - (32 * kIssuers + kAProd + kBProd), ew = et >> 5, quarter = warp & 3;
         const Geo g = make_geo(prm);
         bool ok = true;
         uint32_t li = 0;
         for (unsigned int it = blockIdx.x; it < nit; it += gridDim.x, ++li) {
             const TcItem item = items[it];
             const uint32_t a = pairs[surv[item.first]].a;
-            const uint64_t *abits = A.bits + (size_t)a * N * NW;
-            for (int n = ew; n < (int)item.count; n += 4) {
-                const uint64_t *bb = B.bits + (size_t)pairs[surv[item.first + n]].b * N * NW;
-                const unsigned long long k = rest_key<S, NW, C::DYL, C::DXL, C::COL>(abits, bb, lane);
-                if (lane == 0) atomicMax(keys + n, k);
-            }
             const uint32_t ab = li & 1;
             const bool w = wait_phase(bar(kAccFull + ab), (li >> 1) & 1, abortf);
             if (bar_any(kBarEpi, kEpi, !w)) {
@@ -619,28 +689,69 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_after();
             const int nbp = round_members<C::RND>(item.count);
             const int ncols = C::NCOPY * nbp;
-            const int m = 32 * quarter + lane, gg = m >> 3, rr = m & 7;
-            // column ja * ncols + (jb * NBX + i) * nbp + n holds member n at
-            // dx = -S + g + 16 i, dy = -S + r + 8 (jb + JB ja)
-            for (int c0 = 0; c0 < C::JA * ncols; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + ab * (uint32_t)kMaxCols + (uint32_t)c0, v);
+            const int m = 32 * quarter + lane, gg = m & 15, rr = m >> 4;  // copy, dy offset
+            // column (jb * NBX + i) * nbp + n of each accumulator copy holds
+            // member n at dx = -S + g + 16 i, dy = -S + r + 8 jb
+            constexpr int nacc = kIssuers;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + ab * (uint32_t)kMaxCols;
+            for (int c0 = 0; c0 < ncols; c0 += 16) {
+                uint32_t v[16], w[16];
+                tmem_ld16(tbase + (uint32_t)c0, v);
                 tmem_wait_ld();
+                for (int cp = 1; cp < nacc; ++cp) {
+                    tmem_ld16(tbase + (uint32_t)(cp * ncols + c0), w);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+                }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int col = c0 + q;
-                    const int ja = col / ncols, cb = col - ja * ncols;
-                    const int b = cb / nbp, n = cb - b * nbp;
+                    const int b = col / nbp, n = col - b * nbp;
                     const int dx = -S + gg + 16 * (b % C::NBX);
-                    const int dy = -S + rr + 8 * (b / C::NBX + C::JB * ja);
+                    const int dy = -S + rr + 8 * (b / C::NBX);
                     const bool valid = dx <= S;
                     const unsigned long long k =
                         warp_max64(valid ? shift_key((uint32_t)__uint_as_float(v[q]), dx, dy, S) : 0ull);
                     if (lane == 0 && n < (int)item.count) atomicMax(keys + n, k);
                 }
             }
+            // the accumulators are free for item li + 2 as soon as they are read
             fence_before();
             mbar_arrive(bar(kAccEmpty + ab));
+            bar_sync(kBarEpi, kEpi);
+            // The rest of the window (row dy = DYL, column dx = DXL) only
+            // matters where it can reach the best core overlap c*: it is
+            // skipped when the projection-profile bound, which holds for every
+            // shift of that row (column), is below c* -- an exact, lossless test.
+            const uint64_t *abits = A.bits + (size_t)a * N * NW;
+            const uint16_t *pa = A.prof + (size_t)a * 2 * N;
+            for (int n = ew; n < (int)item.count; n += 4) {
+                const uint32_t bi = pairs[surv[item.first + n]].b;
+                const uint16_t *pb = B.prof + (size_t)bi * 2 * N;
+                const unsigned long long kc = keys[n];
+                const uint32_t cstar = (uint32_t)(kc >> 32);
+                uint32_t brow = 0, bcol = 0;
+                for (int y = lane; y < N - C::DYL; y += 32) brow += min((uint32_t)pa[y + C::DYL], (uint32_t)pb[y]);
+                if constexpr (C::COL)
+                    for (int x = lane; x < N - C::DXL; x += 32)
+                        bcol += min((uint32_t)pa[N + x + C::DXL], (uint32_t)pb[N + x]);
+                brow = __reduce_add_sync(0xffffffffu, brow);
+                bcol = __reduce_add_sync(0xffffffffu, bcol);
+                const uint64_t *bbits = B.bits + (size_t)bi * N * NW;
+                unsigned long long k = kc;
+                if (brow >= cstar) {
+                    const unsigned long long r = rest_row_key<S, NW, C::DYL>(abits, bbits, lane);
+                    k = r > k ? r : k;
+                }
+                if constexpr (C::COL) {
+                    if (bcol >= cstar) {
+                        const unsigned long long r = rest_col_key<S, NW, C::DXL>(abits, bbits, lane);
+                        k = r > k ? r : k;
+                    }
+                }
+                if (lane == 0) keys[n] = k;
+            }
             bar_sync(kBarEpi, kEpi);
             for (int n = et; n < (int)item.count; n += kEpi) {
                 const uint32_t pi = surv[item.first + n];
