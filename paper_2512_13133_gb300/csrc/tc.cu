@@ -170,6 +170,10 @@ __device__ __forceinline__ uint4 expand(uint32_t b) {
 }
 
 __device__ __forceinline__ void st16(unsigned char *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+// 16-byte store to a shared-memory address (shared state space, not generic)
+__device__ __forceinline__ void sts16(uint32_t a, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int bt = tid - (32 * kIssuers + kAProd);
         bool ok = true;
         uint32_t e = 0;
-        unsigned char *ring = sm + C::OFF_RING;
+        const uint32_t ring_s = sbase + C::OFF_RING;
         for (unsigned int it = blockIdx.x; it < nit && ok; it += gridDim.x) {
             const TcItem item = items[it];
             const int nbp = round_members<C::RND>(item.count);
@@ -629,9 +633,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t pos = RR - 1 - (e + h) % RR;
-                    unsigned char *d0 = ring + pos * hb;
+                    const uint32_t d0 = ring_s + pos * hb;
                     // positions RR .. RR + JB - 2 mirror 0 .. JB - 2
-                    unsigned char *d1 = (C::JB > 1 && pos + 1 < (uint32_t)C::JB) ? ring + (pos + RR) * hb : nullptr;
+                    const bool mir = C::JB > 1 && pos + 1 < (uint32_t)C::JB;
+                    const uint32_t d1 = ring_s + (pos + RR) * hb;
                     const int st = st0 + h, Ys = st * kCores;
 #pragma unroll
                     for (int u = 0; u < C::TPT; ++u) {
@@ -644,8 +649,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int c0 = i * nbp + n;
                             const uint32_t o = (uint32_t)q * lbo + (uint32_t)(c0 >> 3) * 128 + (uint32_t)(c0 & 7) * 16;
                             const uint4 x = expand<FP8>(strip >> (16 * (C::NBX - 1 - i)));
-                            st16(d0 + o, x);
-                            if (d1) st16(d1 + o, x);
+                            sts16(d0 + o, x);
+                            if (mir) sts16(d1 + o, x);
                         }
                     }
                 }
