@@ -9,40 +9,47 @@
 // sums stay below 2^24, so the tensor cores return the exact integer overlaps
 // (no rounding guard is needed).
 //
-// M side, no per-stage generation: for each column phase (CH pixels = one
-// 16-byte core-matrix row) the CTA keeps 16 copies of A's column strip, copy g
-// shifted by dx_a = g - S, every image row (zero padded) at a 16-byte pitch.
-// An M tile is 16 groups of 8 rows: group g = copy g, row r = image row
-// Y + r - S, i.e. 8 consecutive dy.  The next image row is the descriptor start
-// plus 16 bytes, so the second K core matrix of an MMA is the next image row
-// (leading-dimension offset 16 bytes) and no operand is rewritten per stage.
-// N side, written per stage: member n appears NBX x NBY times, copy (i, j)
-// shifted by (16 i, 8 j) pixels, so that with D's (g, r)
-//   dx = -S + g + 16 i,   dy = -S + r + 8 j,
-// covering [-S, -S + 16 NBX) x [-S, -S + 8 NBY).  The K loop runs over every
-// row and column the member copies reach, so each product of the window is
-// summed.  The rest of the window -- the row dy = -S + 8 NBY (= S) and, when
-// -S + 16 NBX <= S, the column dx = -S + 16 NBX: an L of at most 4S + 1
-// shifts -- is counted exactly with AND + popcount on the CUDA cores while
-// the tensor cores run.
+// M side, no per-stage writes: for each column phase (CH pixels = one 16-byte
+// core-matrix row) the CTA keeps 16 copies of A's column strip, copy g shifted
+// by dx_a = g - S, interleaved by image row ([row][copy][16 B], zero padded).
+// An M tile is 8 consecutive image rows x 16 copies: M row m = (dy offset
+// m >> 4, copy m & 15).  A core matrix is 8 copies of one row (128-byte
+// aligned); the next K core matrix is the next row (256 bytes on) and the next
+// image row of a stage moves the descriptor start by 256 bytes, so no operand
+// is rewritten per stage.
+// N side, a ring of member tiles: member n appears NBX x JB times, copy (i, jb)
+// shifted by (16 i, 8 jb) pixels, so that with D's (copy g, dy offset r)
+//   dx = -S + g + 16 i,   dy = -S + r + 8 jb,
+// covering [-S, -S + 16 NBX) x [-S, -S + 8 JB).  A ring entry holds the jb = 0
+// rows of one stage (8 image rows); the rows 8 jb above are the previous
+// entries, and entry e sits at position RR - 1 - e % RR so that entries e,
+// e - 1, .., e - JB + 1 are adjacent and one descriptor spans them (positions
+// RR .. RR + JB - 2 mirror 0 .. JB - 2; each phase starts with JB - 1 zero
+// entries).  The K loop runs over every row and column the member copies
+// reach, so each product of the window is summed.  The rest of the window --
+// the row dy = -S + 8 JB (= S) and, when -S + 16 NBX <= S, the column
+// dx = -S + 16 NBX: an L of at most 4S + 1 shifts -- is counted exactly with
+// AND + popcount on the CUDA cores, where its projection-profile bound can
+// reach the best overlap of the core.
 //
-// Warp roles (one CTA per SM, 11 warps):
-//   warp 0      one thread issues tcgen05.mma (kind::f16, K = 16, or
-//               kind::f8f6f4, K = 32) and tcgen05.commit;
-//   warps 1-2   write the 16 shifted copies of the next column phase (two
+// Warp roles (one CTA per SM, 12 warps):
+//   warps 0-1   one thread each issues tcgen05.mma (kind::f16, K = 16, or
+//               kind::f8f6f4, K = 32) for alternate ring entries into its own
+//               accumulator copy, and tcgen05.commit;
+//   warps 2-3   write the 16 shifted copies of the next column phase (two
 //               buffers);
-//   warps 3-6   stage member rows (a ring of 32-bit strips, loads issued one
-//               stage ahead) and write each stage's member tile (a ring of
-//               stage buffers);
-//   warps 7-10  the rest of the window, then the accumulators (tcgen05.ld;
-//               warp w reads TMEM lanes 32 (w % 4) ..) and the exact argmax
-//               with the tie order (-c, |dx|+|dy|, dy, dx).
-// Buffers change hands through mbarriers (producers arrive; the MMA thread's
-// tcgen05.commit releases), and the accumulators are double buffered in TMEM
-// (2 x 256 columns), so the epilogue of one item overlaps the MMAs of the
-// next.  Every wait is bounded (one second): on time-out the CTA records an
-// error, each role leaves its loop together (barrier reductions), and the MMAs
-// still in flight are waited for before the tensor memory is released.
+//   warps 4-7   load member rows into registers a pair of entries ahead
+//               (ping-pong buffers) and write the ring entries in pairs;
+//   warps 8-11  the accumulators (tcgen05.ld; warp w reads TMEM lanes
+//               32 (w % 4) ..; the two copies are added), the exact argmax with
+//               the tie order (-c, |dx|+|dy|, dy, dx), the rest of the window,
+//               and the records.
+// Buffers change hands through mbarriers (producers arrive; tcgen05.commit
+// releases), and the accumulators are double buffered in TMEM (2 x 256
+// columns), so the epilogue of one item overlaps the MMAs of the next.  Every
+// wait is bounded (one second): on time-out the CTA records an error, each role
+// leaves its loop, and the MMAs still in flight are waited for before the
+// tensor memory is released.
 #include <climits>
 
 #include "gates.cuh"
@@ -554,9 +561,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp < kIssuers + (kAProd + kBProd) / 32) {
         // ---------------------------------------------------------------- member tiles
         // Task k = (member n = k % NB, row q = k / NB of each stage); each
-        // thread stages its own strip words D stages ahead with cp.async
-        // (zero-filled outside the raster) and writes the NBX x copies of its
-        // row into the ring entry of the stage.  No barrier among producers.
+        // thread loads its own strip words (zero outside the raster) and writes
+        // the NBX x copies of its row into the ring entry of the stage.  No
+        // barrier among producers.
         const int bt = tid - (32 * kIssuers + kAProd);
         bool ok = true;
         uint32_t e = 0;
