@@ -329,7 +329,7 @@ def run_batched(pcl, ctx, dev, clips_per_class: int, steps: int, seed: int = 1):
     unsupported = int(((rec["flags"] & 15) == pcl.GATE_UNSUPPORTED).sum())
     best_ms = min(eager_ms, graph_ms) if isinstance(graph_ms, float) else eager_ms
     return {"clips": int(sum(w.n for w in wls)), "sizes": [w.raster_n for w in wls], "pairs": int(len(pairs)),
-            "cosine_pairs": n_cos, "aligned": aligned, "unsupported_512_cosine": unsupported,
+            "cosine_pairs": n_cos, "aligned": aligned, "unsupported": unsupported,
             "ms_eager": eager_ms, "ms_graph": graph_ms, "pairs_per_s": len(pairs) / (best_ms / 1e3),
             "aligned_per_s": aligned / (best_ms / 1e3),
             "tuning": {"fft_radix": int(tune.fft_radix), "ctas_per_sm": int(tune.ctas_per_sm),

@@ -257,7 +257,11 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    correlation surface (Eq. 5) and the correlation c(s); exact integer argmax
    with the tie order (-c, |dx|+|dy|, dy, dx); c_best verified by popcount;
    decision den^2 c_best^2 > num^2 |A||B|.  Spectra of referenced clips are
-   computed first when missing (spec_state == 0).
+   computed first when missing (spec_state == 0).  512^2 rasters (S <= 32)
+   hold no spectra: after the gates their pairs take an exact window scan of
+   every shift with popcounts in shared memory (pcm fields 0, spectra not
+   read), which requires shift_rule = EXACT_ARGMAX (else
+   PCL_ERR_UNSUPPORTED).
    With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands) or
    PCL_ENGINE_TC_DIRECT_FP8 (E4M3 operands) the overlaps of every shift come
    from the tensor cores instead (a direct windowed correlation, exact for 0/1
@@ -313,8 +317,11 @@ typedef struct pcl_tuning {
    Spectra of referenced clips are computed first when missing; then a single
    persistent kernel gates the cosine items a warp at a time, aligns the
    survivors with the FFT engine of their class, and evaluates the edge items
-   one per thread.  Cosine items of a class with N > 256 or S > N/16 get
-   flags = PCL_GATE_UNSUPPORTED (such a class needs no spec buffers).  Uses 4 bytes of the context workspace.
+   one per thread.  Cosine items of a 512^2 class (S <= 32) take the exact
+   window scan of pcl_match_pairs instead of the FFT, so such a class needs
+   no spec buffers (spec and spec_state may be NULL); with a shift_rule other
+   than EXACT_ARGMAX, and in any other class with N > 256 or S > N/16, cosine
+   items get flags = PCL_GATE_UNSUPPORTED.  Uses 4 bytes of the context workspace.
    Errors: PCL_ERR_INVALID, PCL_ERR_OOM, PCL_ERR_CUDA. */
 pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *sets, uint32_t n_classes,
                            const pcl_work *d_work, uint64_t n_cosine, uint64_t n, pcl_record *d_out,

@@ -26,6 +26,8 @@ cudaError_t launch_pair_fft(const pcl_params &, const pcl_clipset &, const pcl_c
 cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long long *, pcl_pair *, uint64_t,
                            unsigned long long *, cudaStream_t);
 bool tc_supported(const Geo &);
+cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
+                               uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
@@ -250,8 +252,15 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     }
     if (P->cos_engine != PCL_ENGINE_FFT_PCM)
         return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine engine %s%lld not built", "", P->cos_engine);
+    if (g.N == 512 && g.S <= 32) {
+        // 512²: gates, then the exact window scan (no phase-correlation surface)
+        if (P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+            return fail(ctx, PCL_ERR_UNSUPPORTED, "512² rasters take the exact argmax only%s%lld");
+        e = launch_exact_pairs(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "exact window scan");
+    }
     if (g.N > 256 || g.S > g.N / 16)
-        return fail(ctx, PCL_ERR_UNSUPPORTED, "FFT engine covers N <= 256 and S <= N/16%s%lld");
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "FFT engine covers N <= 256 (512 by exact scan) and S <= N/16%s%lld");
     if (!a->spec || !a->spec_state || !b->spec || !b->spec_state)
         return fail(ctx, PCL_ERR_INVALID, "spec / spec_state buffers missing%s%lld");
     if ((e = launch_mark(d_pairs, n, dn, *a, *b, st)) != cudaSuccess) return cuda_fail(ctx, e, "mark");

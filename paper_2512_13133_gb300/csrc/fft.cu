@@ -155,6 +155,52 @@ __global__ void __launch_bounds__(32 * 2 * ((9 * P / 2 + 1 + 31) / 32), 1)
     }
 }
 
+// 512² rasters: the FFT body's buffers exceed shared memory at this size, so
+// a pair passes the indices, emptiness and lossless gates as in pair_body and
+// the survivors take the exact window scan (exact_body).  One pair per CTA
+// iteration, persistent grid.
+constexpr int kExactThreads = 320;
+
+__global__ void __launch_bounds__(kExactThreads, 1)
+    exact_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, uint64_t npairs,
+                      const unsigned long long *d_n, pcl_record *out) {
+    if (d_n && *d_n < npairs) npairs = *d_n;
+    __shared__ int gate_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Geo g = make_geo(prm);
+    for (uint64_t pid = blockIdx.x; pid < npairs; pid += gridDim.x) {
+        const pcl_pair pr = pairs[pid];
+        pcl_record rec{};
+        rec.a = pr.a;
+        rec.b = pr.b;
+        rec.mode = PCL_MODE_COSINE;
+        bool done = true;  // the same in every thread
+        if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
+            rec.flags = PCL_GATE_BAD_INDEX;
+        } else if (A.pop[pr.a] == 0 && B.pop[pr.b] == 0) {
+            rec.flags = PCL_F_EMPTY;
+            rec.sim = 1.0f;
+            rec.pass = 1;
+        } else if (!(prm.flags & PCL_P_NO_GATES)) {
+            __syncthreads();
+            if (warp == 0) {
+                const int gt = warp_cosine_gate(A, pr.a, B, pr.b, g, prm.cos_num, prm.cos_den, lane);
+                if (lane == 0) gate_s = gt;
+            }
+            __syncthreads();
+            rec.flags = (uint16_t)gate_s;
+            done = gate_s != 0;
+        } else {
+            done = false;
+        }
+        if (done) {
+            if (threadIdx.x == 0) out[pid] = rec;
+            continue;
+        }
+        exact_body<8, 32>(prm, A, B, pr, out + pid);
+    }
+}
+
 template <int P>
 size_t spectra_smem() {
     constexpr int L = 9 * P, N = 8 * P;
@@ -209,6 +255,23 @@ cudaError_t launch_mark(const pcl_pair *pairs, uint64_t n, const unsigned long l
                         pcl_clipset &b, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     mark_kernel<<<1024, 256, 0, st>>>(pairs, n, d_n, a.spec_state, b.spec_state, a.n_clips, b.n_clips);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_pairs(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
+                               const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
+                               int num_sms, cudaStream_t st) {
+    const Geo g = make_geo(prm);
+    if (g.N != 512 || g.S > 32) return cudaErrorNotSupported;
+    const size_t sm = exact_smem<8>();
+    cudaError_t e = cudaFuncSetAttribute(exact_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess || n == 0) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_pair_kernel, kExactThreads, sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(n < cap ? n : cap);
+    exact_pair_kernel<<<grid, kExactThreads, sm, st>>>(prm, a, b, pairs, n, d_n, out);
     return cudaGetLastError();
 }
 

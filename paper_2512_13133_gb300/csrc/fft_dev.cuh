@@ -307,5 +307,110 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
 }
 
 
+// Exact window scan for rasters the FFT body does not cover (N = 64 NW, here
+// 512²): c(s) = sum_x A(x) B(x - s) counted with AND + popcount for every shift
+// |dx|, |dy| <= S (S <= SMAX) -- the definition itself, so the record is the
+// oracle's.  Both rasters are staged in shared memory (2 N²/8 bytes); warps take
+// (dy, 8 consecutive dx), lanes take row pairs (A row y, B row y - dy) and
+// count the 8 shifts of a row pair from registers.  No phase-correlation surface is formed (pcm fields 0).  Meant
+// for the few pairs that pass the lossless gates.  The caller has checked the
+// indices, emptiness and gates.
+template <int NW, int SMAX>
+__device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
+                                           const pcl_pair pr, pcl_record *dst) {
+    constexpr int N = 64 * NW;
+    const Geo g = make_geo(prm);
+    const int S = g.S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sa = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *sb = sa + N * NW;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * NW);  // [32]
+    const uint64_t *ga = A.bits + (size_t)pr.a * N * NW, *gb = B.bits + (size_t)pr.b * N * NW;
+    __syncthreads();  // the shared memory may still be read by the previous item
+    for (int t = threadIdx.x; t < N * NW; t += blockDim.x) {
+        sa[t] = __ldg(ga + t);
+        sb[t] = __ldg(gb + t);
+    }
+    __syncthreads();
+    unsigned long long best = 0ull;
+    // (dy, chunk of 8 dx) per warp task; lanes take the row pairs and count the
+    // chunk's 8 shifts from registers
+    constexpr int DXC = 8;
+    const int K = 2 * S + 1, nch = (K + DXC - 1) / DXC;
+    for (int task = warp; task < K * nch; task += nwarps) {
+        const int dy = task / nch - S, dx0 = (task % nch) * DXC - S;
+        uint32_t cnt[DXC];
+#pragma unroll
+        for (int u = 0; u < DXC; ++u) cnt[u] = 0;
+        const int j0 = dy > 0 ? dy : 0, j1 = dy < 0 ? N + dy : N;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            uint64_t a[NW], b[NW + 2];  // b[w + 1] = word w of B's row j - dy
+            b[0] = 0ull;
+            b[NW + 1] = 0ull;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                a[w] = sa[j * NW + w];
+                b[w + 1] = sb[(j - dy) * NW + w];
+            }
+#pragma unroll
+            for (int u = 0; u < DXC; ++u) {
+                const int dx = dx0 + u;  // B's pixel x - dx lands on A's pixel x (|dx| <= S < 64)
+                uint32_t sum = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    uint64_t sh;
+                    if (dx > 0) sh = (b[w + 1] << dx) | (b[w] >> (64 - dx));
+                    else if (dx < 0) sh = (b[w + 1] >> (-dx)) | (b[w + 2] << (64 + dx));
+                    else sh = b[w + 1];
+                    sum += (uint32_t)__popcll(a[w] & sh);
+                }
+                cnt[u] += sum;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < DXC; ++u) {
+            const int dx = dx0 + u;
+            const uint32_t c = __reduce_add_sync(0xffffffffu, cnt[u]);
+            if (dx <= S) {
+                const unsigned long long k = shift_key(c, dx, dy, S);
+                best = k > best ? k : best;
+            }
+        }
+    }
+    if (lane == 0) keys[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bk = 0ull;
+        for (int w = 0; w < nwarps; ++w) bk = keys[w] > bk ? keys[w] : bk;
+        const int dx = S - (int)(bk & 0xffu), dy = S - (int)((bk >> 8) & 0xffu);
+        const uint32_t cb = (uint32_t)(bk >> 32);
+        const uint64_t pa = A.pop[pr.a], pb = B.pop[pr.b];
+        pcl_record rec{};
+        rec.a = pr.a;
+        rec.b = pr.b;
+        rec.mode = PCL_MODE_COSINE;
+        rec.dx_dbu = dx * g.p;
+        rec.dy_dbu = dy * g.p;
+        rec.score = cb;
+        float sim = (pa && pb) ? (float)cb / sqrtf((float)pa * (float)pb) : 0.0f;
+        uint16_t fl = PCL_F_ALIGNED;
+        const float T = (float)prm.cos_num / (float)prm.cos_den;
+        if (pa && pb && fabsf(sim - T) < prm.near_band) {
+            fl |= PCL_F_NEAR_BAND;
+            sim = (float)((double)cb / sqrt((double)pa * (double)pb));
+        }
+        rec.sim = sim;
+        rec.flags = fl;
+        rec.pass = cos_exceeds(cb, pa, pb, prm.cos_num, prm.cos_den) ? 1 : 0;
+        *dst = rec;
+    }
+    __syncthreads();
+}
+
+// shared memory of exact_body
+template <int NW>
+constexpr size_t exact_smem() { return 2 * sizeof(uint64_t) * 64 * NW * NW + 32 * 8; }
+
 }  // namespace fft_dev
 }  // namespace pcl

@@ -7,7 +7,8 @@
 // group of one cosine item per warp; every warp checks its item's indices,
 // emptiness and lossless gates in parallel, and the survivors are then
 // aligned one after the other by the whole CTA with the FFT body of their
-// size class.  When the cosine items are exhausted, every thread takes edge
+// size class (512² rasters, beyond the FFT body's shared memory, take the exact
+// window scan of exact_body instead).  When the cosine items are exhausted, every thread takes edge
 // items with a grid stride.  The register DFT radix (2 or 4) and the number
 // of CTAs per SM are tuning parameters (chosen by the autotuner).
 #include "edge_dev.cuh"
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const pcl_clipset &cs = args.cs[w.cls];
                 const Geo g = make_geo(prm);
                 const uint64_t pa = cs.pop[w.a], pb = cs.pop[w.b];
-                if (g.P > 32 || g.S > g.N / 16) {
+                if ((g.P > 32 && (g.P != 64 || prm.shift_rule != PCL_SHIFT_EXACT_ARGMAX)) || g.S > g.N / 16) {
                     rec.flags = PCL_GATE_UNSUPPORTED;
                 } else if (pa == 0 && pb == 0) {
                     rec.flags = PCL_F_EMPTY;
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             switch (make_geo(prm).P) {
                 case 8: pair_body<8, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
                 case 16: pair_body<16, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
+                case 64: exact_body<8, 32>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti); break;  // 512²
                 default: pair_body<32, RADIX>(prm, cs, cs, pcl_pair{w.a, w.b}, out + ti, true); break;
             }
             __syncthreads();
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-size_t mixed_smem() { return PairSmem<32>::bytes; }
+size_t mixed_smem() { return PairSmem<32>::bytes > exact_smem<8>() ? PairSmem<32>::bytes : exact_smem<8>(); }
 
 }  // namespace
 

@@ -259,7 +259,8 @@ def test_full_size_sampled_parity(ctx, torch_cuda):
 
 def test_unsupported_and_invalid(ctx, torch_cuda):
     import paper_2512_13133_gb300 as pcl
-    wl = synth.from_lists([[[0, 0, 100, 100]], [[10, 10, 90, 90]]], 2048, 4, 64)
+    # 512² with a marker of 40 px: beyond S <= N/16 for the cosine engines
+    wl = synth.from_lists([[[0, 0, 100, 100]], [[10, 10, 90, 90]]], 2048, 4, 160)
     P = _P(wl)
     cs = _gpu_set(ctx, wl, P)
     tp = torch_cuda.tensor([[0, 1]], dtype=torch_cuda.int32, device="cuda")
@@ -269,3 +270,33 @@ def test_unsupported_and_invalid(ctx, torch_cuda):
     # edge mode covers N = 512
     r = pcl.records_to_numpy(pcl.match(ctx, P, pcl.MODE_EDGE, cs, cs, tp))
     assert r["flags"][0] & pcl.F_ALIGNED
+
+
+@pytest.mark.parametrize("gates", [True, False])
+def test_cosine_512_exact_scan_matches_oracle(ctx, torch_cuda, gates):
+    """512² rasters (S = 32): gates, then the exact window scan; records equal
+    the oracle's (shift, overlap, decision; |sim diff| <= 1e-5)."""
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.generate(12, n_clips=60, n_seeds=8, n_copies=40, window_dbu=2048, margin_dbu=128,
+                        min_rects=5, max_rects=40)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80 if gates else 95,
+                   flags=0 if gates else pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    rng = np.random.default_rng(4)
+    lab = wl.label
+    same = np.array([(i, j) for i in range(wl.n) for j in range(wl.n) if i != j and lab[i] >= 0 and lab[i] == lab[j]])
+    k = 40 if gates else 12
+    pairs = np.concatenate([same[rng.choice(len(same), min(k, len(same)), replace=False)],
+                            rng.integers(0, wl.n, size=(k // 2, 2)), [[3, 3], [0, 5]]]).astype(np.int64)
+    tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
+    g = pcl.records_to_numpy(pcl.match(ctx, P, pcl.MODE_COSINE, cs, cs, tp))
+    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=gates, cos_num=80 if gates else 95)
+    al = (o["flags"] & oracle.F_ALIGNED) > 0
+    assert al.sum() > 0
+    np.testing.assert_array_equal(g["flags"] & 15, o["flags"] & 15)
+    np.testing.assert_array_equal(g["pass_"], o["pass_"])
+    for f in ("dx_dbu", "dy_dbu"):
+        np.testing.assert_array_equal(g[f][al], o[f][al])
+    np.testing.assert_array_equal(g["score"][al].astype(np.int64), o["score"][al])
+    assert np.abs(g["sim"][al].astype(np.float64) - o["sim"][al]).max() <= 1e-5
