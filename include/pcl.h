@@ -139,6 +139,9 @@ typedef struct pcl_record {
 /*
  * A clip set: the caller allocates every buffer (device memory, sizes from
  * pcl_clipset_sizes) and fills rect_off/rects; the library fills the rest.
+ * rects, bits, esig and occ must start on 16-byte boundaries (cudaMalloc and
+ * PyTorch allocations do); calls taking a clip set return PCL_ERR_INVALID
+ * otherwise.
  *   rect_off [n+1] u32   clip i owns rects[4*rect_off[i] .. 4*rect_off[i+1])
  *   rects    [4R]  i32   x0, y0, x1, y1 (window-relative dbu)
  *   bits     [n][N][N/64] u64   raster rows; bit t of word w = pixel 64w+t

@@ -88,6 +88,10 @@ pcl_status check_clipset(pcl_ctx *ctx, const pcl_clipset *cs, bool need_edge_or_
     if (cs->n_clips && (!cs->rect_off || !cs->rects || !cs->bits || !cs->pop || !cs->prof || !cs->blk ||
                         (need_edge_or_raster && (!cs->esig || !cs->occ || !cs->rorder))))
         return fail(ctx, PCL_ERR_INVALID, "clip set has a NULL buffer%s%lld");
+    // kernels read rects and esig (and the 8-byte arrays) with 16-byte vector loads
+    const uintptr_t mis = (uintptr_t)cs->rects | (uintptr_t)cs->bits | (uintptr_t)cs->esig | (uintptr_t)cs->occ;
+    if (cs->n_clips && (mis & 15u))
+        return fail(ctx, PCL_ERR_INVALID, "clip set buffer not 16-byte aligned%s%lld");
     return PCL_OK;
 }
 

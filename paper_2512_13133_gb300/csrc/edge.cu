@@ -29,143 +29,312 @@ __device__ __forceinline__ void emit_pair(pcl_pair *out, uint64_t cap, unsigned 
     }
 }
 
-constexpr int kTileI = 16;
-constexpr int kQueue = 64;  // per-warp queue of pairs awaiting the full E1 check
+// cell_of with the cell side known to be a power of two (P2) or not
+template <bool P2>
+__device__ __forceinline__ int cell_at(int v, int csz, int csh) {
+    if constexpr (P2) return min(max(v >> csh, 0), 63);
+    else return cell_of(v, csz, -1);
+}
 
-// Self-join screen: block (bx, by) covers rows i in [kTileI bx, kTileI bx +
-// kTileI) and columns j in [256 by, 256 by + 256); pairs with i < j only.
+// grid_hit for a grid that may sit in shared or global memory (generic loads)
+template <bool P2>
+__device__ __forceinline__ bool grid_hit_any(const uint64_t *occ, int x0, int y0, int x1, int y1, int csz,
+                                             int csh) {
+    if (x1 <= x0 || y1 <= y0) return true;  // degenerate input: no pruning
+    const int cx0 = cell_at<P2>(x0, csz, csh), cx1 = cell_at<P2>(x1 - 1, csz, csh);
+    const int cy0 = cell_at<P2>(y0, csz, csh), cy1 = cell_at<P2>(y1 - 1, csz, csh);
+    const uint64_t m = (~0ull >> (63 - (cx1 - cx0))) << cx0;
+    uint64_t acc = 0ull;  // independent loads, no branch between them
+    for (int cy = cy0; cy <= cy1; ++cy) acc |= occ[cy];
+    return (acc & m) != 0ull;
+}
+
+constexpr int kColsB = 256;  // column clips per block (32 row clips: one per lane)
+constexpr int kQueue = 64;   // per-warp queue capacity (grid tests, full checks)
+constexpr int kGS = 65;      // stride of a staged grid in shared memory (u64, padded against bank conflicts)
+
+// Warp-cooperative correspondence (Sec. 2.2.2 condition 1) of small list rs
+// against large list rl at shift t: every small polygon has exactly one
+// partner and no large polygon overlaps two small polygons.  Lanes take the
+// large polygons; the result is warp-uniform and equals correspond().
+// The small polygons are visited smallest first (ro: the small clip's area
+// order); the result does not depend on the order.
+__device__ __forceinline__ bool warp_correspond(const int4 *__restrict__ rs, const uint16_t *__restrict__ ro,
+                                                int ns, const int4 *__restrict__ rl, int nl, bool small_is_a,
+                                                int tx, int ty, int lane) {
+    if (ns <= 64 && nl <= 64) {
+        // both lists in registers, two polygons per lane at most; the large
+        // list is moved by the shift once: A's polygon first and B's moved by
+        // t is (s, l + t) with the small clip on side A, else (l, s + t), and
+        // both overlap tests equal the plain test of s against l + t or l - t
+        const bool v0 = lane < nl, v1 = lane + 32 < nl;
+        const int ux = small_is_a ? tx : -tx, uy = small_is_a ? ty : -ty;
+        int4 l0 = v0 ? __ldg(rl + lane) : make_int4(0, 0, 0, 0);
+        int4 l1 = v1 ? __ldg(rl + lane + 32) : make_int4(0, 0, 0, 0);
+        l0 = make_int4(l0.x + ux, l0.y + uy, l0.z + ux, l0.w + uy);
+        l1 = make_int4(l1.x + ux, l1.y + uy, l1.z + ux, l1.w + uy);
+        // small polygons in ascending area, where a missing partner is most likely
+        const int4 sv0 = lane < ns ? __ldg(rs + __ldg(ro + lane)) : make_int4(0, 0, 0, 0);
+        const int4 sv1 = lane + 32 < ns ? __ldg(rs + __ldg(ro + lane + 32)) : make_int4(0, 0, 0, 0);
+        int c0 = 0, c1 = 0;
+        if (nl <= 32) {
+            for (int k = 0; k < ns; ++k) {
+                const int4 sk = k < 32 ? sv0 : sv1;
+                const int src = k & 31;
+                const int sx0 = __shfl_sync(0xffffffffu, sk.x, src), sy0 = __shfl_sync(0xffffffffu, sk.y, src);
+                const int sx1 = __shfl_sync(0xffffffffu, sk.z, src), sy1 = __shfl_sync(0xffffffffu, sk.w, src);
+                const bool h0 = v0 && sx0 < l0.z && l0.x < sx1 && sy0 < l0.w && l0.y < sy1;
+                const unsigned b0 = __ballot_sync(0xffffffffu, h0);
+                if (b0 == 0u || (b0 & (b0 - 1u))) return false;  // not exactly one partner
+                c0 += h0 ? 1 : 0;
+            }
+        } else {
+            for (int k = 0; k < ns; ++k) {
+                const int4 sk = k < 32 ? sv0 : sv1;
+                const int src = k & 31;
+                const int sx0 = __shfl_sync(0xffffffffu, sk.x, src), sy0 = __shfl_sync(0xffffffffu, sk.y, src);
+                const int sx1 = __shfl_sync(0xffffffffu, sk.z, src), sy1 = __shfl_sync(0xffffffffu, sk.w, src);
+                const bool h0 = v0 && sx0 < l0.z && l0.x < sx1 && sy0 < l0.w && l0.y < sy1;
+                const bool h1 = v1 && sx0 < l1.z && l1.x < sx1 && sy0 < l1.w && l1.y < sy1;
+                const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+                if (__popc(b0) + __popc(b1) != 1) return false;
+                c0 += h0 ? 1 : 0;
+                c1 += h1 ? 1 : 0;
+            }
+        }
+        return !__any_sync(0xffffffffu, c0 > 1 || c1 > 1);
+    }
+    for (int k = 0; k < ns; ++k) {
+        const int4 s = __ldg(rs + k);
+        int cnt = 0;
+        for (int m0 = 0; m0 < nl && cnt < 2; m0 += 32) {
+            const int m = m0 + lane;
+            const bool h = m < nl && (small_is_a ? ovl(s, __ldg(rl + m), tx, ty) : ovl(__ldg(rl + m), s, tx, ty));
+            cnt += __popc(__ballot_sync(0xffffffffu, h));
+        }
+        if (cnt != 1) return false;
+    }
+    for (int m0 = 0; m0 < nl; m0 += 32) {
+        const int m = m0 + lane;
+        int c = 0;
+        if (m < nl) {
+            const int4 l = __ldg(rl + m);
+            for (int k = 0; k < ns && c < 2; ++k) {
+                const int4 s = __ldg(rs + k);
+                c += (small_is_a ? ovl(s, l, tx, ty) : ovl(l, s, tx, ty)) ? 1 : 0;
+            }
+        }
+        if (__any_sync(0xffffffffu, c > 1)) return false;
+    }
+    return true;
+}
+
+// Self-join screen: block (bx, by) covers row clips i = 32 bx + lane and
+// column clips j in [kColsB by, kColsB by + kColsB); warp w takes the columns
+// w, w + 8, ...  Pairs with i < j only.  The row clips' signatures live in
+// registers and their occupancy grids in shared memory; the column clips'
+// signatures are staged per block and each column's grid per warp, so every
+// grid read of the first test is a shared-memory load.
 //
-// Each lane owns column j and walks its rows as a small state machine: every
-// iteration it may set up one new pair (empty / E2 / pre-alignment) and runs
-// one occupancy-grid test of one small-side polygon.  Lanes therefore advance
-// through their pairs independently instead of waiting for the slowest lane
-// of every pair.  Pairs whose polygons all pass the grid test (about 0.3 % of
-// random pairs) go to a per-warp queue; once 32 are queued the warp runs the
-// full correspondence check on them, one pair per lane.
-__global__ void __launch_bounds__(256) edge_screen_kernel(pcl_params prm, pcl_clipset cs,
+// Phase 1 takes one column at a time for all 32 rows: empty clips, E2 and the
+// pre-alignment of every pair, then the grid test of the smaller clip's
+// smallest polygon, which alone rejects about three quarters of random pairs.
+// Survivors with more polygons go to a per-warp queue of grid tests (polygons
+// in ascending area), which runs only while it holds work for every lane, so
+// lanes advance through their pairs independently without idling.  Pairs
+// whose polygons all meet occupied cells (a few per thousand) go to a second
+// queue, where the whole warp checks one pair at a time with ballots.
+// P2: the grid's cell side W/64 is a power of two (cells by shifts)
+template <bool P2>
+__global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl_clipset cs,
                                                           pcl_pair *out, uint64_t cap,
                                                           unsigned long long *count,
                                                           unsigned long long *gates) {
     const uint32_t n = cs.n_clips;
-    const uint32_t j = blockIdx.y * 256u + threadIdx.x;
-    const uint32_t i0 = blockIdx.x * kTileI;
-    if (i0 >= n || i0 > blockIdx.y * 256u + 255u) return;  // whole block below the diagonal
+    const uint32_t i0 = blockIdx.x * 32u;
+    const uint32_t jblk = blockIdx.y * (uint32_t)kColsB;
+    if (jblk >= n || i0 + 1u >= min(jblk + (uint32_t)kColsB, n)) return;  // no pair i < j in the block
     const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int32_t es_i[kTileI][8];
-    __shared__ uint32_t off_i[kTileI];
-    __shared__ uint2 queue[8][kQueue];
-    for (int t = threadIdx.x; t < kTileI * 8; t += blockDim.x) {
-        const uint32_t i = i0 + t / 8;
-        es_i[t / 8][t % 8] = i < n ? __ldg(cs.esig + (size_t)i * 8 + t % 8) : 0;
-    }
-    for (int t = threadIdx.x; t < kTileI; t += blockDim.x) off_i[t] = i0 + t < n ? __ldg(cs.rect_off + i0 + t) : 0;
-    __syncthreads();
-    const bool jv = j < n;
-    int32_t eb[8];
-    uint32_t ob = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) eb[k] = jv ? __ldg(cs.esig + (size_t)j * 8 + k) : 0;
-    if (jv) ob = __ldg(cs.rect_off + j);
+    __shared__ uint64_t grids[(32 + 8) * kGS];  // row clips' grids, then each warp's current column grid
+    __shared__ int4 csig[kColsB][2];  // {n, flags, lox+hix, loy+hiy}, {hix-lox, hiy-loy, rect offset, 0}
+    __shared__ int4 cp0[kColsB];      // smallest polygon of each column clip
+    __shared__ int4 tq[8][kQueue];    // grid tests: {row | col << 8 | small_is_a << 16, sx, sy, 0}
+    __shared__ int4 fq[8][kQueue];    // full checks: {row | col << 8 | small_is_a << 16, s0x, s0y, 0}
     const int4 *rects4 = reinterpret_cast<const int4 *>(cs.rects);
+    // flags: bit 0 has x edges, bit 1 has y edges, bit 2 touches the border
+    auto load_sig = [&](uint32_t c, int4 &s0, int4 &s1, int4 &p0) {
+        const int4 *e4 = reinterpret_cast<const int4 *>(cs.esig + (size_t)c * 8);
+        const int4 lo = __ldg(e4), hi = __ldg(e4 + 1);  // {n, hasx, lox, hix}, {hasy, loy, hiy, border}
+        const uint32_t off = __ldg(cs.rect_off + c);
+        s0 = make_int4(lo.x, (lo.y ? 1 : 0) | (hi.x ? 2 : 0) | (hi.w ? 4 : 0), lo.z + lo.w, hi.y + hi.z);
+        s1 = make_int4(lo.w - lo.z, hi.z - hi.y, (int)off, 0);
+        p0 = lo.x > 0 ? __ldg(rects4 + off + __ldg(cs.rorder + off)) : make_int4(0, 0, 0, 0);
+    };
+    for (int c = threadIdx.x; c < kColsB; c += blockDim.x) {
+        int4 s0 = make_int4(0, 0, 0, 0), s1 = s0, p0 = s0;
+        if (jblk + c < n) load_sig(jblk + c, s0, s1, p0);
+        csig[c][0] = s0;
+        csig[c][1] = s1;
+        cp0[c] = p0;
+    }
+    for (int w = threadIdx.x; w < 32 * 64; w += blockDim.x)
+        grids[(w >> 6) * kGS + (w & 63)] = i0 + (w >> 6) < n ? __ldg(cs.occ + (size_t)i0 * 64 + w) : 0ull;
+    // this lane's row clip
+    const uint32_t i = i0 + lane;
+    int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, pa = a0;
+    if (i < n) load_sig(i, a0, a1, pa);
+    const int na = a0.x;
+    __syncthreads();
     const int csz = W / 64;
     const int csh = (csz & (csz - 1)) == 0 ? __ffs(csz) - 1 : -1;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t *gcol = grids + (32 + warp) * kGS;  // this warp's current column grid
 
     uint32_t g_e1 = 0, g_e2 = 0, kept = 0;
-    int t = 0;          // next tile row to set up
-    bool have = false;  // a pair is in its grid phase
-    int k = 0, ns = 0, sx = 0, sy = 0;
-    uint32_t cur_i = 0;
-    const int4 *rs = nullptr;
-    const uint16_t *ro = nullptr;
-    const uint64_t *occl = nullptr;
-    int qn = 0;  // queue length (warp-uniform)
+    int qn = 0, fn = 0;  // queue lengths (warp-uniform)
+    // grid-test state of this lane
+    bool h2 = false;
+    int k2 = 0, ns2 = 0, sx2 = 0, sy2 = 0, e2x = 0;
+    const int4 *rs2 = nullptr;
+    const uint16_t *ro2 = nullptr;
+    const uint64_t *g2 = nullptr;
 
-    auto full_check = [&](uint2 pr, bool valid) {
-        bool keep = false;
-        if (valid) {
-            int32_t ea[8], ebb[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                ea[q] = __ldg(cs.esig + (size_t)pr.x * 8 + q);
-                ebb[q] = __ldg(cs.esig + (size_t)pr.y * 8 + q);
+    auto run_full = [&]() {  // warp-uniform: check and emit every queued pair
+        unsigned ok0 = 0u, ok1 = 0u;
+        for (int q = 0; q < fn; ++q) {
+            const int4 e = fq[warp][q];
+            const int r = e.x & 0xff, c = (e.x >> 8) & 0xff;
+            const bool sa = (e.x >> 16) & 1;
+            const int offa = __shfl_sync(0xffffffffu, a1.z, r), nar = __shfl_sync(0xffffffffu, na, r);
+            const int offb = csig[c][1].z, nbc = csig[c][0].x;
+            const int offs = sa ? offa : offb;
+            const bool ok = warp_correspond(rects4 + offs, cs.rorder + offs, sa ? nar : nbc,
+                                            rects4 + (sa ? offb : offa), sa ? nbc : nar, sa, e.y, e.z, lane);
+            if (ok) {
+                if (q < 32) ok0 |= 1u << q;
+                else ok1 |= 1u << (q - 32);
             }
-            const uint32_t oa = __ldg(cs.rect_off + pr.x), obb = __ldg(cs.rect_off + pr.y);
-            const ClipView A{rects4 + oa, ea, cs.rorder + oa, cs.occ + (size_t)pr.x * 64};
-            const ClipView B{rects4 + obb, ebb, cs.rorder + obb, cs.occ + (size_t)pr.y * 64};
-            const EdgeOut o = edge_eval(A, B, W, M, tol, true, true);
-            if (o.gate == PCL_GATE_E1_MATCH) ++g_e1;
-            else if (o.gate == PCL_GATE_E2_BBOX) ++g_e2;
-            else { keep = true; ++kept; }
         }
-        emit_pair(out, cap, count, keep, pr.x, pr.y);
+        if (lane == 0) {
+            const uint32_t nk = (uint32_t)(__popc(ok0) + __popc(ok1));
+            kept += nk;
+            g_e1 += (uint32_t)fn - nk;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = h * 32 + lane;
+            const bool mine = q < fn;
+            const int4 e = mine ? fq[warp][q] : make_int4(0, 0, 0, 0);
+            const bool keep = mine && (((h ? ok1 : ok0) >> lane) & 1u);
+            emit_pair(out, cap, count, keep, i0 + (e.x & 0xff), jblk + ((e.x >> 8) & 0xff));
+        }
+        __syncwarp();
+        fn = 0;
+    };
+    // tag: row | col << 8 | small_is_a << 16 of the pair
+    auto push_full = [&](bool p, int tag, int s0x, int s0y) {
+        const unsigned m = __ballot_sync(0xffffffffu, p);
+        if (p) fq[warp][fn + __popc(m & lt)] = make_int4(tag, s0x, s0y, 0);
+        fn += __popc(m);
+        __syncwarp();
+        if (fn >= 32) run_full();  // keeps fn below 32 between pushes
+    };
+    // one round of the grid-test queue: idle lanes take entries (pushed by any
+    // lane of the warp), every lane holding a pair tests its next polygon
+    auto step2 = [&]() {
+        const unsigned idle = __ballot_sync(0xffffffffu, !h2);
+        const int rk = __popc(idle & lt);
+        const bool take = !h2 && rk < qn;
+        const int4 e = take ? tq[warp][qn - 1 - rk] : make_int4(0, 0, 0, 0);
+        const int r = e.x & 0xff;
+        const int offa = __shfl_sync(0xffffffffu, a1.z, r), nar = __shfl_sync(0xffffffffu, na, r);
+        if (take) {
+            const int c = (e.x >> 8) & 0xff;
+            const bool sa = (e.x >> 16) & 1;
+            const int off = sa ? offa : csig[c][1].z;
+            ns2 = sa ? nar : csig[c][0].x;
+            rs2 = rects4 + off;
+            ro2 = cs.rorder + off;
+            g2 = sa ? cs.occ + (size_t)(jblk + c) * 64 : grids + r * kGS;
+            sx2 = e.y;
+            sy2 = e.z;
+            e2x = e.x;
+            k2 = 1;
+            h2 = true;
+        }
+        qn = qn > __popc(idle) ? qn - __popc(idle) : 0;
+        __syncwarp();
+        bool done = false;
+        if (h2) {
+            const int4 q = __ldg(rs2 + __ldg(ro2 + k2));
+            if (!grid_hit_any<P2>(g2, q.x + sx2, q.y + sy2, q.z + sx2, q.w + sy2, csz, csh)) {
+                ++g_e1;
+                h2 = false;
+            } else if (++k2 == ns2) {
+                done = true;
+                h2 = false;
+            }
+        }
+        const bool sa = (e2x >> 16) & 1;
+        push_full(done, e2x, sa ? -sx2 : sx2, sa ? -sy2 : sy2);
     };
 
-    for (;;) {
-        bool push = false;
-        if (!have && t < kTileI) {
-            const uint32_t i = i0 + t;
-            const int32_t *ea = es_i[t];
-            ++t;
-            if (jv && i < n && i < j) {
-                const int na = ea[ES_N], nb = eb[ES_N];
-                if (na == 0 || nb == 0) {
-                    if (na == 0 && nb == 0) { push = true; cur_i = i; }  // kept by the full check
-                    else ++g_e1;
-                } else if (na == nb && !ea[ES_BORDER] && !eb[ES_BORDER] &&
-                           (abs((ea[ES_HIX] - ea[ES_LOX]) - (eb[ES_HIX] - eb[ES_LOX])) > 2 * tol ||
-                            abs((ea[ES_HIY] - ea[ES_LOY]) - (eb[ES_HIY] - eb[ES_LOY])) > 2 * tol)) {
+    // columns of this warp: c = warp + 8 m; the next column's grid is fetched
+    // into registers while the current one is processed
+    const uint32_t jlast = min(jblk + (uint32_t)kColsB, n);  // one past the last column
+    uint32_t c = warp;
+    while (c < (uint32_t)kColsB && jblk + c <= i0) c += 8;  // columns with no row below them
+    ulonglong2 gnext = make_ulonglong2(0ull, 0ull);
+    if (jblk + c < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(cs.occ + (size_t)(jblk + c) * 64) + lane);
+    for (; jblk + c < jlast; c += 8) {
+        const uint32_t j = jblk + c;
+        __syncwarp();  // the previous column's grid is no longer read
+        gcol[2 * lane] = gnext.x;
+        gcol[2 * lane + 1] = gnext.y;
+        if (j + 8 < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(cs.occ + (size_t)(j + 8) * 64) + lane);
+        __syncwarp();
+        const int4 b0 = csig[c][0];
+        const int nb = b0.x;
+        bool push_t = false, push_f = false, both_empty = false;
+        bool sa = false;
+        int s0x = 0, s0y = 0;
+        if (i < j) {
+            if (na == 0 || nb == 0) {
+                if (na == 0 && nb == 0) both_empty = true;
+                else ++g_e1;
+            } else {
+                const int4 b1 = csig[c][1];
+                if (na == nb && !((a0.y | b0.y) & 4) &&
+                    (abs(a1.x - b1.x) > 2 * tol || abs(a1.y - b1.y) > 2 * tol)) {
                     ++g_e2;
                 } else {
-                    const int s0x = (ea[ES_HASX] && eb[ES_HASX])
-                                        ? clampi(((ea[ES_LOX] + ea[ES_HIX]) - (eb[ES_LOX] + eb[ES_HIX])) / 2, -M, M)
-                                        : 0;
-                    const int s0y = (ea[ES_HASY] && eb[ES_HASY])
-                                        ? clampi(((ea[ES_LOY] + ea[ES_HIY]) - (eb[ES_LOY] + eb[ES_HIY])) / 2, -M, M)
-                                        : 0;
-                    const bool small_is_a = na <= nb;
-                    const uint32_t oa = off_i[t - 1];
-                    rs = rects4 + (small_is_a ? oa : ob);
-                    ro = cs.rorder + (small_is_a ? oa : ob);
-                    occl = cs.occ + (size_t)(small_is_a ? j : i) * 64;
-                    ns = small_is_a ? na : nb;
-                    sx = small_is_a ? -s0x : s0x;
-                    sy = small_is_a ? -s0y : s0y;
-                    k = 0;
-                    cur_i = i;
-                    have = true;
+                    s0x = (a0.y & b0.y & 1) ? clampi((a0.z - b0.z) / 2, -M, M) : 0;
+                    s0y = (a0.y & b0.y & 2) ? clampi((a0.w - b0.w) / 2, -M, M) : 0;
+                    sa = na <= nb;
+                    // the smaller clip's smallest polygon in the other clip's frame
+                    const int4 q = sa ? pa : cp0[c];
+                    const int sx = sa ? -s0x : s0x, sy = sa ? -s0y : s0y;
+                    const uint64_t *grid = sa ? gcol : grids + lane * kGS;
+                    if (!grid_hit_any<P2>(grid, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz, csh)) ++g_e1;
+                    else if ((sa ? na : nb) == 1) push_f = true;
+                    else push_t = true;
                 }
             }
         }
-        if (have) {
-            const int4 q = __ldg(rs + __ldg(ro + k));
-            if (!grid_hit(occl, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz, csh)) {
-                ++g_e1;
-                have = false;
-            } else if (++k == ns) {
-                push = true;
-                have = false;
-            }
+        const int tag = lane | (int)(c << 8) | (sa ? 1 << 16 : 0);
+        const unsigned mt = __ballot_sync(0xffffffffu, push_t);
+        if (push_t) tq[warp][qn + __popc(mt & lt)] = make_int4(tag, sa ? -s0x : s0x, sa ? -s0y : s0y, 0);
+        qn += __popc(mt);
+        push_full(push_f, tag, s0x, s0y);
+        if (__any_sync(0xffffffffu, both_empty)) {  // similar by definition
+            kept += both_empty ? 1u : 0u;
+            emit_pair(out, cap, count, both_empty, i, j);
         }
-        const unsigned pm = __ballot_sync(0xffffffffu, push);
-        if (pm) {
-            if (push) queue[warp][qn + __popc(pm & ((1u << lane) - 1u))] = make_uint2(cur_i, j);
-            qn += __popc(pm);
-            __syncwarp();
-            if (qn >= 32) {
-                qn -= 32;
-                const uint2 pr = queue[warp][qn + lane];
-                __syncwarp();
-                full_check(pr, true);
-            }
-        }
-        if (!__any_sync(0xffffffffu, have || t < kTileI)) break;
+        while (qn + __popc(__ballot_sync(0xffffffffu, h2)) >= 32) step2();
     }
-    if (qn > 0) {
-        const uint2 pr = lane < qn ? queue[warp][lane] : make_uint2(0u, 0u);
-        __syncwarp();
-        full_check(pr, lane < qn);
-    }
+    while (qn > 0 || __any_sync(0xffffffffu, h2)) step2();
+    if (fn > 0) run_full();
     // gate counters: one atomic per warp and counter
     g_e1 = __reduce_add_sync(0xffffffffu, g_e1);
     g_e2 = __reduce_add_sync(0xffffffffu, g_e2);
@@ -177,13 +346,15 @@ __global__ void __launch_bounds__(256) edge_screen_kernel(pcl_params prm, pcl_cl
     }
 }
 
+// one pair per warp (warp_edge_record), lane 0 writes the record
 __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
                                                          const pcl_pair *pairs, uint64_t n,
                                                          const unsigned long long *d_n, pcl_record *out) {
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (d_n && *d_n < n) n = *d_n;
-    if (t >= n) return;
-    out[t] = edge_record(prm, A, B, pairs[t]);
+    if (t >= n) return;  // warp-uniform
+    const pcl_record r = warp_edge_record(prm, A, B, pairs[t], threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) out[t] = r;
 }
 
 }  // namespace
@@ -193,9 +364,11 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
                                cudaStream_t st) {
     const uint32_t n = cs.n_clips;
     if (n < 2) return cudaSuccess;
-    dim3 grid((n + kTileI - 1) / kTileI, (n + 255) / 256);
+    dim3 grid((n + 31) / 32, (n + kColsB - 1) / kColsB);
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    edge_screen_kernel<<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
+    const int csz = prm.window_dbu / 64;
+    if ((csz & (csz - 1)) == 0) edge_screen_kernel<true><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
+    else edge_screen_kernel<false><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
     return cudaGetLastError();
 }
 
@@ -203,7 +376,7 @@ cudaError_t launch_edge_match(const pcl_params &prm, const pcl_clipset &a, const
                               const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
                               cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const uint64_t blocks = (n + 255) / 256;
+    const uint64_t blocks = (n + 7) / 8;  // 8 warps per block, one pair per warp
     if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     edge_match_kernel<<<(unsigned)blocks, 256, 0, st>>>(prm, a, b, pairs, n, d_n, out);
     return cudaGetLastError();

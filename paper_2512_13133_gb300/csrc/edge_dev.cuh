@@ -181,6 +181,147 @@ __device__ inline EdgeOut edge_eval(const ClipView &A, const ClipView &B, int W,
 }
 
 
+// edge_eval for one pair per warp (the result is the same, in every lane):
+// lanes hold the polygons of both clips (at most 64 per clip, otherwise every
+// lane runs edge_eval); the small clip's polygons are broadcast one at a time
+// and ballots over the large clip's give each one's partner.  Partners,
+// displacement extremes and the re-check at T do not depend on the order in
+// which the small polygons are visited.
+__device__ inline EdgeOut warp_edge_eval(const ClipView &A, const ClipView &B, int W, int M, int tol, bool gates,
+                                         int lane) {
+    const int32_t *ea = A.e, *eb = B.e;
+    const int na = ea[ES_N], nb = eb[ES_N];
+    if (na > 64 || nb > 64) return edge_eval(A, B, W, M, tol, gates, false);
+    EdgeOut o{};
+    if (na == 0 && nb == 0) {
+        o.empty = true;
+        o.pass = true;
+        o.verified = true;
+        return o;
+    }
+    if (na == 0 || nb == 0) {
+        o.gate = PCL_GATE_E1_MATCH;
+        return o;
+    }
+    const int lxa = ea[ES_LOX], uxa = ea[ES_HIX], lya = ea[ES_LOY], uya = ea[ES_HIY];
+    const int lxb = eb[ES_LOX], uxb = eb[ES_HIX], lyb = eb[ES_LOY], uyb = eb[ES_HIY];
+    if (gates && na == nb && !ea[ES_BORDER] && !eb[ES_BORDER]) {
+        if (abs((uxa - lxa) - (uxb - lxb)) > 2 * tol || abs((uya - lya) - (uyb - lyb)) > 2 * tol) {
+            o.gate = PCL_GATE_E2_BBOX;
+            return o;
+        }
+    }
+    const int s0x = (ea[ES_HASX] && eb[ES_HASX]) ? clampi(((lxa + uxa) - (lxb + uxb)) / 2, -M, M) : 0;
+    const int s0y = (ea[ES_HASY] && eb[ES_HASY]) ? clampi(((lya + uya) - (lyb + uyb)) / 2, -M, M) : 0;
+    const bool small_is_a = na <= nb;
+    const int4 *rs = small_is_a ? A.r : B.r;
+    const int4 *rl = small_is_a ? B.r : A.r;
+    const int ns = small_is_a ? na : nb, nl = small_is_a ? nb : na;
+    o.tx = s0x;
+    o.ty = s0y;
+    const unsigned full = 0xffffffffu;
+    // the small polygons, lane k holding k and k + 32
+    const bool w0 = lane < ns, w1 = lane + 32 < ns;
+    const int4 sv0 = w0 ? __ldg(rs + lane) : make_int4(0, 0, 0, 0);
+    const int4 sv1 = w1 ? __ldg(rs + lane + 32) : make_int4(0, 0, 0, 0);
+    if (gates) {  // occupancy pre-check of E1
+        const uint64_t *occ_l = small_is_a ? B.occ : A.occ;
+        const int csz = W / 64;
+        const int csh = (csz & (csz - 1)) == 0 ? __ffs(csz) - 1 : -1;
+        const int sx = small_is_a ? -s0x : s0x, sy = small_is_a ? -s0y : s0y;
+        bool miss = w0 && !grid_hit(occ_l, sv0.x + sx, sv0.y + sy, sv0.z + sx, sv0.w + sy, csz, csh);
+        miss = miss || (w1 && !grid_hit(occ_l, sv1.x + sx, sv1.y + sy, sv1.z + sx, sv1.w + sy, csz, csh));
+        if (__any_sync(full, miss)) {
+            o.gate = PCL_GATE_E1_MATCH;
+            return o;
+        }
+    }
+    // the large polygons, lane m holding m and m + 32; an overlap of A's
+    // polygon with B's moved by t is the plain overlap of the small polygon
+    // with the large one moved by u = t (small on side A) or -t
+    const bool v0 = lane < nl, v1 = lane + 32 < nl;
+    const int4 lv0 = v0 ? __ldg(rl + lane) : make_int4(0, 0, 0, 0);
+    const int4 lv1 = v1 ? __ldg(rl + lane + 32) : make_int4(0, 0, 0, 0);
+    // partner of small polygon k with the large list moved by (ux, uy): its
+    // index, -1 if none, -2 if several
+    auto partner_at = [&](int k, int ux, int uy) {
+        const int4 sk = k < 32 ? sv0 : sv1;
+        const int src = k & 31;
+        const int x0 = __shfl_sync(full, sk.x, src), y0 = __shfl_sync(full, sk.y, src);
+        const int x1 = __shfl_sync(full, sk.z, src), y1 = __shfl_sync(full, sk.w, src);
+        const bool h0 = v0 && x0 < lv0.z + ux && lv0.x + ux < x1 && y0 < lv0.w + uy && lv0.y + uy < y1;
+        const bool h1 = v1 && x0 < lv1.z + ux && lv1.x + ux < x1 && y0 < lv1.w + uy && lv1.y + uy < y1;
+        const unsigned b0 = __ballot_sync(full, h0), b1 = __ballot_sync(full, h1);
+        const int c = __popc(b0) + __popc(b1);
+        return c == 0 ? -1 : (c > 1 ? -2 : (b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1));
+    };
+    // correspondence at s0 (Sec. 2.2.2 condition 1), with injectivity
+    const int u0x = small_is_a ? s0x : -s0x, u0y = small_is_a ? s0y : -s0y;
+    int mk0 = -1, mk1 = -1;  // partners of this lane's small polygons
+    for (int k = 0; k < ns; ++k) {
+        const int m = partner_at(k, u0x, u0y);
+        if (m < 0) {
+            o.gate = PCL_GATE_E1_MATCH;
+            return o;
+        }
+        if (lane == (k & 31)) {
+            if (k < 32) mk0 = m;
+            else mk1 = m;
+        }
+    }
+    // injectivity: no large polygon is the partner of two small polygons
+    {
+        int cnt0 = 0, cnt1 = 0;  // small polygons partnered with large polygons lane, lane + 32
+        for (int k = 0; k < ns; ++k) {
+            const int m = __shfl_sync(full, k < 32 ? mk0 : mk1, k & 31);
+            cnt0 += (m == lane) ? 1 : 0;
+            cnt1 += (m == lane + 32) ? 1 : 0;
+        }
+        if (__any_sync(full, cnt0 > 1 || cnt1 > 1)) {
+            o.gate = PCL_GATE_E1_MATCH;
+            return o;
+        }
+    }
+    // displacements d = e_A - e_B of matched edges off the window border
+    int cx = 0, cy = 0, dminx = INT_MAX, dmaxx = INT_MIN, dminy = INT_MAX, dmaxy = INT_MIN;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (h ? w1 : w0) {
+            const int4 sp = h ? sv1 : sv0;
+            const int4 lp = __ldg(rl + (h ? mk1 : mk0));
+            const int4 pa = small_is_a ? sp : lp, pb = small_is_a ? lp : sp;
+            if (pa.x != 0 && pb.x != 0) { const int d = pa.x - pb.x; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
+            if (pa.z != W && pb.z != W) { const int d = pa.z - pb.z; dminx = min(dminx, d); dmaxx = max(dmaxx, d); cx = 1; }
+            if (pa.y != 0 && pb.y != 0) { const int d = pa.y - pb.y; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
+            if (pa.w != W && pb.w != W) { const int d = pa.w - pb.w; dminy = min(dminy, d); dmaxy = max(dmaxy, d); cy = 1; }
+        }
+    }
+    cx = __reduce_or_sync(full, (unsigned)cx);
+    cy = __reduce_or_sync(full, (unsigned)cy);
+    dminx = __reduce_min_sync(full, dminx);
+    dmaxx = __reduce_max_sync(full, dmaxx);
+    dminy = __reduce_min_sync(full, dminy);
+    dmaxy = __reduce_max_sync(full, dmaxy);
+    // Eq. 6 per separable axis: midpoint (trunc toward zero), clamped
+    const int Tx = cx ? clampi((dminx + dmaxx) / 2, -M, M) : s0x;
+    const int Ty = cy ? clampi((dminy + dmaxy) / 2, -M, M) : s0y;
+    const int Ex = cx ? max(Tx - dminx, dmaxx - Tx) : 0;
+    const int Ey = cy ? max(Ty - dminy, dmaxy - Ty) : 0;
+    // the correspondence must hold at T with the same partners
+    const int uTx = small_is_a ? Tx : -Tx, uTy = small_is_a ? Ty : -Ty;
+    bool ok = true;
+    for (int k = 0; k < ns && ok; ++k) {
+        const int m0 = __shfl_sync(full, k < 32 ? mk0 : mk1, k & 31);
+        ok = partner_at(k, uTx, uTy) == m0;
+    }
+    o.tx = Tx;
+    o.ty = Ty;
+    o.E = max(Ex, Ey);
+    o.verified = ok;
+    o.pass = ok && Ex <= tol && Ey <= tol;
+    return o;
+}
+
 // one edge-mode record for pair pr (bounds-checked), as written by the match kernels
 __device__ __forceinline__ pcl_record edge_record(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
                                                   pcl_pair pr) {
@@ -203,6 +344,44 @@ __device__ __forceinline__ pcl_record edge_record(const pcl_params &prm, const p
     const ClipView vb{reinterpret_cast<const int4 *>(B.rects) + ob, eb, B.rorder + ob, B.occ + (size_t)pr.b * 64};
     const bool gates = !(prm.flags & PCL_P_NO_GATES);
     const EdgeOut o = edge_eval(va, vb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu, gates, false);
+    r.dx_dbu = o.tx;
+    r.dy_dbu = o.ty;
+    if (o.empty) {
+        r.flags = PCL_F_EMPTY;
+        r.pass = 1;
+    } else if (o.gate) {
+        r.flags = (uint16_t)o.gate;
+    } else {
+        r.flags = PCL_F_ALIGNED | (o.verified ? 0 : PCL_F_EDGE_VERIFY_FAIL);
+        r.score = (uint32_t)o.E;
+        r.sim = (float)o.E;
+        r.pass = o.pass ? 1 : 0;
+    }
+    return r;
+}
+
+// edge_record computed by a whole warp (every lane gets the record)
+__device__ __forceinline__ pcl_record warp_edge_record(const pcl_params &prm, const pcl_clipset &A,
+                                                       const pcl_clipset &B, pcl_pair pr, int lane) {
+    pcl_record r{};
+    r.a = pr.a;
+    r.b = pr.b;
+    r.mode = PCL_MODE_EDGE;
+    if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
+        r.flags = PCL_GATE_BAD_INDEX;
+        return r;
+    }
+    int32_t ea[8], eb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        ea[k] = __ldg(A.esig + (size_t)pr.a * 8 + k);
+        eb[k] = __ldg(B.esig + (size_t)pr.b * 8 + k);
+    }
+    const uint32_t oa = __ldg(A.rect_off + pr.a), ob = __ldg(B.rect_off + pr.b);
+    const ClipView va{reinterpret_cast<const int4 *>(A.rects) + oa, ea, A.rorder + oa, A.occ + (size_t)pr.a * 64};
+    const ClipView vb{reinterpret_cast<const int4 *>(B.rects) + ob, eb, B.rorder + ob, B.occ + (size_t)pr.b * 64};
+    const bool gates = !(prm.flags & PCL_P_NO_GATES);
+    const EdgeOut o = warp_edge_eval(va, vb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu, gates, lane);
     r.dx_dbu = o.tx;
     r.dy_dbu = o.ty;
     if (o.empty) {
