@@ -19,6 +19,8 @@
 // (p, end_p) with end_p = #{clips with area <= floor((den^2 a_p - 1)/num^2)}.
 // Warps take positions p from a global counter and test G3 and G2 on every
 // band member with the whole warp.
+#include <climits>
+
 #include "gates.cuh"
 
 namespace pcl {
@@ -75,28 +77,50 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
     }
 }
 
-// G3 for one band member b of representative a with a's block words held in
-// registers (WPL u32 words per lane = two 16-bit blocks each); deficits are
-// accumulated as packed 16-bit halves (min <= value, so no borrow crosses
-// halves) and checked after every 32-lane chunk.
+// Largest overlap u that does NOT pass the integer rule of Eq. 2 for areas
+// pa, pb (cos_exceeds(u) is false exactly for u <= result): a float estimate
+// of num sqrt(pa pb) / den corrected by the exact rule (the estimate is off by
+// at most one or two).
+__device__ __forceinline__ int64_t cos_umax(uint64_t pa, uint64_t pb, uint32_t num, uint32_t den) {
+    uint64_t u = (uint64_t)(sqrtf((float)pa * (float)pb) * ((float)num / (float)den));
+    while (u > 0 && cos_exceeds(u, pa, pb, num, den)) --u;
+    while (!cos_exceeds(u + 1, pa, pb, num, den)) ++u;
+    return (int64_t)u;
+}
+
+// G3 for one band member with the representative's block words in registers
+// (WPL u32 words per lane = two 16-bit blocks each).  Deficits accumulate as
+// packed 16-bit halves (min <= value, so no borrow crosses halves; a chunk's
+// 32-lane sum of one half is at most 32 * 256); after every 32-lane chunk the
+// bound min(pa - DA, pb - DB) is compared with the pair's thresholds: it
+// fails Eq. 2 exactly when DA >= tA or DB >= tB (tX = pX - cos_umax).  In the
+// first chunk A's deficit is summed and tested before B's: on its own it
+// rejects most pairs of a band.
 template <int WPL>
-__device__ __forceinline__ bool g3_rejects_reg(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+__device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
                                                const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
-                                               int words, uint64_t pa, uint64_t pb, uint32_t num, uint32_t den,
-                                               int lane) {
-    uint32_t pda = 0, pdb = 0;
+                                               int words, int tA, int tB, int lane) {
+    const bool v = lane < words;  // lanes past the words hold zero block counts
+    const uint32_t d0 = v ? __ldg(db + lane) : 0u, b0 = v ? __ldg(cb + lane) : 0u;
+    uint32_t sr = __reduce_add_sync(0xffffffffu, ca[0] - __vminu2(ca[0], d0));
+    int DA = (int)((sr & 0xffffu) + (sr >> 16));
+    if (DA >= tA) return true;
+    sr = __reduce_add_sync(0xffffffffu, b0 - __vminu2(b0, da[0]));
+    int DB = (int)((sr & 0xffffu) + (sr >> 16));
+    if (DB >= tB) return true;
 #pragma unroll
-    for (int c = 0; c < WPL; ++c) {
+    for (int c = 1; c < WPL; ++c) {
         const int t = c * 32 + lane;
+        uint32_t pda = 0u, pdb = 0u;
         if (t < words) {
             const uint32_t b = __ldg(cb + t);
-            pda += ca[c] - __vminu2(ca[c], __ldg(db + t));
-            pdb += b - __vminu2(b, da[c]);
+            pda = ca[c] - __vminu2(ca[c], __ldg(db + t));
+            pdb = b - __vminu2(b, da[c]);
         }
-        const uint64_t DA = __reduce_add_sync(0xffffffffu, (pda & 0xffffu) + (pda >> 16));
-        const uint64_t DB = __reduce_add_sync(0xffffffffu, (pdb & 0xffffu) + (pdb >> 16));
-        const uint64_t ua = pa - DA, ub = pb - DB;
-        if (!cos_exceeds(ua < ub ? ua : ub, pa, pb, num, den)) return true;
+        const uint32_t sa = __reduce_add_sync(0xffffffffu, pda), sb = __reduce_add_sync(0xffffffffu, pdb);
+        DA += (int)((sa & 0xffffu) + (sa >> 16));
+        DB += (int)((sb & 0xffffu) + (sb >> 16));
+        if (DA >= tA || DB >= tB) return true;
     }
     return false;
 }
@@ -132,27 +156,54 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
             ca[c] = t < words ? cwa[t] : 0u;
             da[c] = t < words ? cwa[words + t] : 0u;
         }
-        for (uint32_t q = p + 1; q < end; ++q) {
-            const uint32_t b = order[q];
-            const uint64_t pb = spop[q];
-            if (!(pa == 0 && pb == 0)) {
-                const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)b * 2 * nb2);
-                if (g3_rejects_reg<WPL>(ca, da, cwb, cwb + words, words, pa, pb, prm.cos_num, prm.cos_den,
-                                        lane)) {
+        if (pa == 0) {  // the band holds the other empty clips only: similar by definition
+            for (uint32_t q0 = p + 1; q0 < end; q0 += 32) {
+                const bool v = q0 + lane < end;
+                const uint32_t bq = v ? order[q0 + lane] : 0u;
+                const unsigned m = __ballot_sync(0xffffffffu, v);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (v && base + lane < cap) out[base + lane] = pcl_pair{min(a, bq), max(a, bq)};
+                kept += __popc(m);
+            }
+            continue;
+        }
+        // band members 32 at a time: lane l sets up member q0 + l (index,
+        // thresholds; members of a non-empty representative are non-empty),
+        // then the warp tests them one after the other
+        for (uint32_t q0 = p + 1; q0 < end; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            uint32_t b = 0;
+            int tA = 0, tB = 0;  // areas are below 2^31, so are the thresholds (clamped below)
+            if (q < end) {
+                b = order[q];
+                const uint64_t pb = spop[q];
+                const int64_t um = cos_umax(pa, pb, prm.cos_num, prm.cos_den);
+                tA = (int)max((int64_t)pa - um, (int64_t)INT_MIN);
+                tB = (int)max((int64_t)pb - um, (int64_t)INT_MIN);
+            }
+            const int cnt = (int)min(32u, end - q0);
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+                const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)bk * 2 * nb2);
+                if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
                     ++g3;
                     continue;
                 }
-                const uint32_t u2 = warp_g2(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)b * 2 * g.N,
+                const uint64_t pbk = spop[q0 + k];
+                const uint32_t u2 = warp_g2(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N,
                                             g.N, g.S, lane);
-                if (!cos_exceeds(u2, pa, pb, prm.cos_num, prm.cos_den)) {
+                if (!cos_exceeds(u2, pa, pbk, prm.cos_num, prm.cos_den)) {
                     ++g2;
                     continue;
                 }
-            }
-            ++kept;
-            if (lane == 0) {
-                const unsigned long long idx = atomicAdd(count, 1ull);
-                if (idx < cap) out[idx] = pcl_pair{min(a, b), max(a, b)};
+                ++kept;
+                if (lane == 0) {
+                    const unsigned long long idx = atomicAdd(count, 1ull);
+                    if (idx < cap) out[idx] = pcl_pair{min(a, bk), max(a, bk)};
+                }
             }
         }
     }
