@@ -324,7 +324,7 @@ typedef struct pcl_tuning {
    window scan of pcl_match_pairs instead of the FFT, so such a class needs
    no spec buffers (spec and spec_state may be NULL); with a shift_rule other
    than EXACT_ARGMAX, and in any other class with N > 256 or S > N/16, cosine
-   items get flags = PCL_GATE_UNSUPPORTED.  Uses 4 bytes of the context workspace.
+   items get flags = PCL_GATE_UNSUPPORTED.  Uses 8 bytes of the context workspace.
    Errors: PCL_ERR_INVALID, PCL_ERR_OOM, PCL_ERR_CUDA. */
 pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *sets, uint32_t n_classes,
                            const pcl_work *d_work, uint64_t n_cosine, uint64_t n, pcl_record *d_out,

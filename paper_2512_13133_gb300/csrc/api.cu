@@ -32,7 +32,7 @@ size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
 cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
-                         pcl_record *, unsigned int *, uint32_t, uint32_t, int, cudaStream_t);
+                         pcl_record *, unsigned long long *, uint32_t, uint32_t, int, cudaStream_t);
 }  // namespace pcl
 
 #include "ctx.h"
@@ -294,7 +294,7 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
     const uint32_t ctas = tune ? tune->ctas_per_sm : 0;
     if ((s = ensure_ws(ctx, 256))) return s;
     const cudaError_t e = launch_mixed(params, sets, n_classes, d_work, n_cosine, n, d_out,
-                                       static_cast<unsigned int *>(ctx->ws), radix, ctas, ctx->num_sms,
+                                       static_cast<unsigned long long *>(ctx->ws), radix, ctas, ctx->num_sms,
                                        (cudaStream_t)stream);
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "mixed batch");
 }

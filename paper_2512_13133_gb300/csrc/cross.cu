@@ -107,14 +107,13 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
             const uint32_t b = lib_order[pos];
             const uint64_t pb = lib_spop[pos];
             if (!(pa == 0 && pb == 0)) {
-                if (warp_g3_rejects(Q.blk + (size_t)q * 2 * nb2, L.blk + (size_t)b * 2 * nb2, nb2, pa, pb, prm.cos_num,
-                                    prm.cos_den, lane)) {
+                const int64_t um = cos_umax(pa, pb, prm.cos_num, prm.cos_den);
+                if (warp_g3_rejects(Q.blk + (size_t)q * 2 * nb2, L.blk + (size_t)b * 2 * nb2, nb2, pa, pb, um, lane)) {
                     ++g3;
                     continue;
                 }
-                const uint32_t u2 =
-                    warp_g2(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)b * 2 * g.N, g.N, g.S, lane);
-                if (!cos_exceeds(u2, pa, pb, prm.cos_num, prm.cos_den)) {
+                if (warp_g2_rejects_n(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)b * 2 * g.N, g.N, g.S, um,
+                                      lane)) {
                     ++g2;
                     continue;
                 }

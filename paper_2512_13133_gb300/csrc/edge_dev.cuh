@@ -360,6 +360,69 @@ __device__ __forceinline__ pcl_record edge_record(const pcl_params &prm, const p
     return r;
 }
 
+// The gates of edge_record for one pair in one thread (empty clips, E2, the
+// occupancy pre-check of E1): true when the pair passes them and needs the
+// rest of the procedure (then *rec is not set); otherwise *rec is the record
+// edge_record would write.
+__device__ inline bool edge_gate_record(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
+                                        pcl_pair pr, pcl_record *rec) {
+    pcl_record r{};
+    r.a = pr.a;
+    r.b = pr.b;
+    r.mode = PCL_MODE_EDGE;
+    if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
+        r.flags = PCL_GATE_BAD_INDEX;
+        *rec = r;
+        return false;
+    }
+    const int4 *e4a = reinterpret_cast<const int4 *>(A.esig + (size_t)pr.a * 8);
+    const int4 *e4b = reinterpret_cast<const int4 *>(B.esig + (size_t)pr.b * 8);
+    const int4 alo = __ldg(e4a), ahi = __ldg(e4a + 1), blo = __ldg(e4b), bhi = __ldg(e4b + 1);
+    // {n, hasx, lox, hix}, {hasy, loy, hiy, border}
+    const int na = alo.x, nb = blo.x;
+    if (na == 0 && nb == 0) {
+        r.flags = PCL_F_EMPTY;
+        r.pass = 1;
+        *rec = r;
+        return false;
+    }
+    if (na == 0 || nb == 0) {
+        r.flags = PCL_GATE_E1_MATCH;
+        *rec = r;
+        return false;
+    }
+    if (prm.flags & PCL_P_NO_GATES) return true;
+    const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
+    if (na == nb && !ahi.w && !bhi.w &&
+        (abs((alo.w - alo.z) - (blo.w - blo.z)) > 2 * tol || abs((ahi.z - ahi.y) - (bhi.z - bhi.y)) > 2 * tol)) {
+        r.flags = PCL_GATE_E2_BBOX;
+        *rec = r;
+        return false;
+    }
+    const int s0x = (alo.y && blo.y) ? clampi(((alo.z + alo.w) - (blo.z + blo.w)) / 2, -M, M) : 0;
+    const int s0y = (ahi.x && bhi.x) ? clampi(((ahi.y + ahi.z) - (bhi.y + bhi.z)) / 2, -M, M) : 0;
+    const bool small_is_a = na <= nb;
+    const uint32_t oa = __ldg(A.rect_off + pr.a), ob = __ldg(B.rect_off + pr.b);
+    const int4 *rs = reinterpret_cast<const int4 *>(small_is_a ? A.rects : B.rects) + (small_is_a ? oa : ob);
+    const uint16_t *ro = (small_is_a ? A.rorder : B.rorder) + (small_is_a ? oa : ob);
+    const uint64_t *occ_l = small_is_a ? B.occ + (size_t)pr.b * 64 : A.occ + (size_t)pr.a * 64;
+    const int ns = small_is_a ? na : nb;
+    const int csz = W / 64;
+    const int csh = (csz & (csz - 1)) == 0 ? __ffs(csz) - 1 : -1;
+    const int sx = small_is_a ? -s0x : s0x, sy = small_is_a ? -s0y : s0y;
+    for (int k = 0; k < ns; ++k) {
+        const int4 q = __ldg(rs + __ldg(ro + k));
+        if (!grid_hit(occ_l, q.x + sx, q.y + sy, q.z + sx, q.w + sy, csz, csh)) {
+            r.flags = PCL_GATE_E1_MATCH;
+            r.dx_dbu = s0x;
+            r.dy_dbu = s0y;
+            *rec = r;
+            return false;
+        }
+    }
+    return true;
+}
+
 // edge_record computed by a whole warp (every lane gets the record)
 __device__ __forceinline__ pcl_record warp_edge_record(const pcl_params &prm, const pcl_clipset &A,
                                                        const pcl_clipset &B, pcl_pair pr, int lane) {

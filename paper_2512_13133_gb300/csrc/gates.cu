@@ -77,17 +77,6 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
     }
 }
 
-// Largest overlap u that does NOT pass the integer rule of Eq. 2 for areas
-// pa, pb (cos_exceeds(u) is false exactly for u <= result): a float estimate
-// of num sqrt(pa pb) / den corrected by the exact rule (the estimate is off by
-// at most one or two).
-__device__ __forceinline__ int64_t cos_umax(uint64_t pa, uint64_t pb, uint32_t num, uint32_t den) {
-    uint64_t u = (uint64_t)(sqrtf((float)pa * (float)pb) * ((float)num / (float)den));
-    while (u > 0 && cos_exceeds(u, pa, pb, num, den)) --u;
-    while (!cos_exceeds(u + 1, pa, pb, num, den)) ++u;
-    return (int64_t)u;
-}
-
 // G3 for one band member with the representative's block words in registers
 // (WPL u32 words per lane = two 16-bit blocks each).  Deficits accumulate as
 // packed 16-bit halves (min <= value, so no borrow crosses halves; a chunk's
@@ -192,10 +181,9 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
                     ++g3;
                     continue;
                 }
-                const uint64_t pbk = spop[q0 + k];
-                const uint32_t u2 = warp_g2(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N,
-                                            g.N, g.S, lane);
-                if (!cos_exceeds(u2, pa, pbk, prm.cos_num, prm.cos_den)) {
+                // G2 with the same threshold (tA = pa - um; never clamped in a band)
+                if (warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N, g.S,
+                                         (int64_t)pa - tAk, lane)) {
                     ++g2;
                     continue;
                 }

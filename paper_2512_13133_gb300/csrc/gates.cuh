@@ -6,43 +6,146 @@
 
 namespace pcl {
 
+// Largest overlap u that does NOT pass the integer rule of Eq. 2 for areas
+// pa, pb (cos_exceeds(u) is false exactly for u <= result): a float estimate
+// of num sqrt(pa pb) / den corrected by the exact rule (the estimate is off by
+// at most one or two).  A gate bound u rejects a pair exactly when u <= this.
+__device__ __forceinline__ int64_t cos_umax(uint64_t pa, uint64_t pb, uint32_t num, uint32_t den) {
+    uint64_t u = (uint64_t)(sqrtf((float)pa * (float)pb) * ((float)num / (float)den));
+    while (u > 0 && cos_exceeds(u, pa, pb, num, den)) --u;
+    while (!cos_exceeds(u + 1, pa, pb, num, den)) ++u;
+    return (int64_t)u;
+}
+
 // warp-cooperative G3 test: true if the density bound (both directions,
-// minimum kept) cannot reach the threshold.  Blocks are visited 64 at a time;
-// after each chunk the deficits seen so far, sum_k (cnt_A(k) - min(cnt_A(k),
-// nbr_B(k))) and the same the other way, already bound c from above by
-// min(|A| - def_A, |B| - def_B), so most pairs are rejected before all blocks
+// minimum kept) cannot pass Eq. 2, i.e. min(|A| - def_A, |B| - def_B) <= um.
+// Blocks are visited 64 at a time; after each chunk the deficits seen so far,
+// sum_k (cnt_A(k) - min(cnt_A(k), nbr_B(k))) and the same the other way,
+// already bound c from above, so most pairs are rejected before all blocks
 // are read.  The last chunk gives exactly the full bound, so the decision is
-// the same as evaluating the bound at once.
+// the same as evaluating the bound at once.  Deficits accumulate as packed
+// 16-bit halves (a chunk's 32-lane sum of one half is at most 32 * 256).
 __device__ __forceinline__ bool warp_g3_rejects(const uint16_t *__restrict__ ba, const uint16_t *__restrict__ bb,
-                                                int nb2, uint64_t pa, uint64_t pb, uint32_t num, uint32_t den,
-                                                int lane) {
+                                                int nb2, uint64_t pa, uint64_t pb, int64_t um, int lane) {
     const uint32_t *ca = reinterpret_cast<const uint32_t *>(ba);
     const uint32_t *da = reinterpret_cast<const uint32_t *>(ba + nb2);
     const uint32_t *cb = reinterpret_cast<const uint32_t *>(bb);
     const uint32_t *db = reinterpret_cast<const uint32_t *>(bb + nb2);
     const int words = nb2 / 2;
-    uint32_t defa = 0, defb = 0;
+    const int64_t tA = (int64_t)pa - um, tB = (int64_t)pb - um;  // reject once DA >= tA or DB >= tB
+    int64_t DA = 0, DB = 0;
+    // the next chunk's words are loaded while the current one is reduced
+    uint32_t a = 0u, b = 0u, na = 0u, nb = 0u;
+    if (lane < words) {
+        a = __ldg(ca + lane);
+        b = __ldg(cb + lane);
+        na = __ldg(db + lane);
+        nb = __ldg(da + lane);
+    }
     for (int t0 = 0; t0 < words; t0 += 32) {
-        const int t = t0 + lane;
+        const uint32_t pda = a - __vminu2(a, na), pdb = b - __vminu2(b, nb);
+        const int t = t0 + 32 + lane;
+        a = b = na = nb = 0u;
         if (t < words) {
-            const uint32_t a = __ldg(ca + t), b = __ldg(cb + t);
-            const uint32_t m1 = __vminu2(a, __ldg(db + t));
-            const uint32_t m2 = __vminu2(b, __ldg(da + t));
-            defa += ((a & 0xffffu) + (a >> 16)) - ((m1 & 0xffffu) + (m1 >> 16));
-            defb += ((b & 0xffffu) + (b >> 16)) - ((m2 & 0xffffu) + (m2 >> 16));
+            a = __ldg(ca + t);
+            b = __ldg(cb + t);
+            na = __ldg(db + t);
+            nb = __ldg(da + t);
         }
-        const uint64_t DA = __reduce_add_sync(0xffffffffu, defa);
-        const uint64_t DB = __reduce_add_sync(0xffffffffu, defb);
-        const uint64_t ua = pa - DA, ub = pb - DB;
-        if (!cos_exceeds(ua < ub ? ua : ub, pa, pb, num, den)) return true;
+        const uint32_t sa = __reduce_add_sync(0xffffffffu, pda), sb = __reduce_add_sync(0xffffffffu, pdb);
+        DA += (sa & 0xffffu) + (sa >> 16);
+        DB += (sb & 0xffffu) + (sb >> 16);
+        if (DA >= tA || DB >= tB) return true;
     }
     return false;
 }
 
-// warp-cooperative G2 bound: min over (rows, columns) of the max over
-// |d| <= S of sum_j min(prof_A(j), prof_B(j - d))
-__device__ __forceinline__ uint32_t warp_g2(const uint16_t *__restrict__ pa, const uint16_t *__restrict__ pb,
-                                            int N, int S, int lane) {
+// G2 as a decision (kept out of line: it is rare in the hot loops that call it,
+// and inlining it would cost them registers): true if the bound min(max_d R(d), max_d Q(d)) <= um,
+// i.e. one axis keeps every shift's profile sum at or below um.  The rows are
+// tried first (the columns are skipped when the rows already reject); an axis
+// stops at its first shift above um, visiting d = 0, 1, -1, 2, -2, ...  A's
+// profile is held in registers (NPL = N / 32 values per lane).
+template <int NPL>
+__device__ __forceinline__ bool warp_g2_rejects(const uint16_t *__restrict__ pa, const uint16_t *__restrict__ pb,
+                                                int S, int64_t um, int lane) {
+    constexpr int N = 32 * NPL;
+#pragma unroll 1
+    for (int ax = 0; ax < 2; ++ax) {
+        const uint16_t *A = pa + ax * N, *B = pb + ax * N;
+        uint32_t av[NPL];
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) av[u] = __ldg(A + lane + 32 * u);
+        bool above = false;
+        for (int i = 0; i <= 2 * S && !above; ++i) {
+            const int d = (i & 1) ? (i + 1) >> 1 : -(i >> 1);
+            uint32_t t = 0;
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) {
+                const int k = lane + 32 * u - d;
+                if (k >= 0 && k < N) t += min(av[u], (uint32_t)__ldg(B + k));
+            }
+            above = (int64_t)__reduce_add_sync(0xffffffffu, t) > um;
+        }
+        if (!above) return true;
+    }
+    return false;
+}
+
+static __device__ __noinline__ bool warp_g2_rejects_n(const uint16_t *pa, const uint16_t *pb, int N, int S, int64_t um,
+                                                  int lane) {
+    switch (N) {
+        case 64: return warp_g2_rejects<2>(pa, pb, S, um, lane);
+        case 128: return warp_g2_rejects<4>(pa, pb, S, um, lane);
+        case 256: return warp_g2_rejects<8>(pa, pb, S, um, lane);
+        default: return warp_g2_rejects<16>(pa, pb, S, um, lane);
+    }
+}
+
+// G2 as a decision with B's two profiles staged by the warp in shared memory
+// (scratch: 2 (N + 2S) u16, zero padded by S on both sides, so no bounds
+// checks), A's profile in registers; otherwise as warp_g2_rejects.
+template <int NPL>
+__device__ __forceinline__ bool warp_g2_rejects_smem(const uint16_t *__restrict__ pa,
+                                                     const uint16_t *__restrict__ pb, int S, int64_t um, int lane,
+                                                     uint16_t *scratch) {
+    constexpr int N = 32 * NPL;
+    const int L = N + 2 * S;
+    __syncwarp();  // the previous pair's reads of scratch are done
+    for (int k = lane; k < 2 * L; k += 32) {
+        const int ax = k >= L, i = k - ax * L - S;
+        scratch[k] = (i >= 0 && i < N) ? __ldg(pb + ax * N + i) : (uint16_t)0;
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int ax = 0; ax < 2; ++ax) {
+        const uint16_t *A = pa + ax * N;
+        const uint16_t *Bs = scratch + ax * L + S;  // Bs[k] = prof_B(k) for -S <= k < N + S
+        uint32_t av[NPL];
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) av[u] = __ldg(A + lane + 32 * u);
+        bool above = false;
+        for (int i = 0; i <= 2 * S && !above; ++i) {
+            const int d = (i & 1) ? (i + 1) >> 1 : -(i >> 1);
+            uint32_t t = 0;
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) t += min(av[u], (uint32_t)Bs[lane + 32 * u - d]);
+            above = (int64_t)__reduce_add_sync(0xffffffffu, t) > um;
+        }
+        if (!above) return true;
+    }
+    return false;
+}
+
+// shared-memory G2 scratch per warp (u16 elements) for rasters up to N = 512
+constexpr int kG2Scratch = 2 * (512 + 2 * 64);
+
+// The same decision with every profile value loaded where it is used and no
+// early exit: fewer registers, for callers where G2 is rare and register
+// pressure matters more than its speed.
+__device__ __forceinline__ bool warp_g2_rejects_lite(const uint16_t *__restrict__ pa,
+                                                     const uint16_t *__restrict__ pb, int N, int S, int64_t um,
+                                                     int lane) {
     uint32_t ur = 0, uc = 0;
     for (int d = -S; d <= S; ++d) {
         uint32_t tr = 0, tc = 0;
@@ -53,25 +156,37 @@ __device__ __forceinline__ uint32_t warp_g2(const uint16_t *__restrict__ pa, con
                 tc += min((uint32_t)__ldg(pa + N + j), (uint32_t)__ldg(pb + N + k));
             }
         }
-        tr = __reduce_add_sync(0xffffffffu, tr);
-        tc = __reduce_add_sync(0xffffffffu, tc);
-        ur = max(ur, tr);
-        uc = max(uc, tc);
+        ur = max(ur, __reduce_add_sync(0xffffffffu, tr));
+        uc = max(uc, __reduce_add_sync(0xffffffffu, tc));
     }
-    return ur < uc ? ur : uc;
+    return (int64_t)(ur < uc ? ur : uc) <= um;
 }
 
-// cosine gates of one pair (warp-uniform result): PCL_GATE_* or 0
+// cosine gates of one pair (warp-uniform result): PCL_GATE_* or 0.  scratch
+// (kG2Scratch u16 of shared memory owned by the warp, may be null) speeds up G2.
 __device__ __forceinline__ int warp_cosine_gate(const pcl_clipset &A, uint32_t a, const pcl_clipset &B, uint32_t b,
-                                const Geo &g, uint32_t num, uint32_t den, int lane) {
+                                const Geo &g, uint32_t num, uint32_t den, int lane,
+                                uint16_t *scratch = nullptr) {
     const uint64_t pa = A.pop[a], pb = B.pop[b];
     const uint64_t mn = pa < pb ? pa : pb, mx = pa < pb ? pb : pa;
     if (!((uint64_t)den * den * mn > (uint64_t)num * num * mx)) return PCL_GATE_G1_AREA;
+    const int64_t um = cos_umax(pa, pb, num, den);
     const int nb2 = g.nb * g.nb;
-    if (warp_g3_rejects(A.blk + (size_t)a * 2 * nb2, B.blk + (size_t)b * 2 * nb2, nb2, pa, pb, num, den, lane))
+    if (warp_g3_rejects(A.blk + (size_t)a * 2 * nb2, B.blk + (size_t)b * 2 * nb2, nb2, pa, pb, um, lane))
         return PCL_GATE_G3_DENSITY;
-    const uint32_t u2 = warp_g2(A.prof + (size_t)a * 2 * g.N, B.prof + (size_t)b * 2 * g.N, g.N, g.S, lane);
-    if (!cos_exceeds(u2, pa, pb, num, den)) return PCL_GATE_G2_PROFILE;
+    const uint16_t *pra = A.prof + (size_t)a * 2 * g.N, *prb = B.prof + (size_t)b * 2 * g.N;
+    bool g2;
+    if (scratch) {
+        switch (g.N) {
+            case 64: g2 = warp_g2_rejects_smem<2>(pra, prb, g.S, um, lane, scratch); break;
+            case 128: g2 = warp_g2_rejects_smem<4>(pra, prb, g.S, um, lane, scratch); break;
+            case 256: g2 = warp_g2_rejects_smem<8>(pra, prb, g.S, um, lane, scratch); break;
+            default: g2 = warp_g2_rejects_smem<16>(pra, prb, g.S, um, lane, scratch); break;
+        }
+    } else {
+        g2 = warp_g2_rejects_n(pra, prb, g.N, g.S, um, lane);
+    }
+    if (g2) return PCL_GATE_G2_PROFILE;
     return PCL_GATE_NONE;
 }
 

@@ -3,13 +3,14 @@
 // together, with uneven candidate lists.
 //
 // The work list holds the cosine items first, then the edge items.  Each CTA
-// (320 threads, shared memory sized for the largest FFT) repeatedly claims a
-// group of one cosine item per warp; every warp checks its item's indices,
-// emptiness and lossless gates in parallel, and the survivors are then
-// aligned one after the other by the whole CTA with the FFT body of their
-// size class (512² rasters, beyond the FFT body's shared memory, take the exact
-// window scan of exact_body instead).  When the cosine items are exhausted, every thread takes edge
-// items with a grid stride.  The register DFT radix (2 or 4) and the number
+// (320 threads, shared memory sized for the largest FFT) works in rounds:
+// every warp claims a run of consecutive cosine items and checks their
+// indices, emptiness and lossless gates one after the other; the round's
+// survivors are then aligned one after the other by the whole CTA with the
+// FFT body of their size class (512² rasters, beyond the FFT body's shared
+// memory, take the exact window scan of exact_body instead).  When the cosine
+// items are exhausted, every warp takes edge items 32 at a time: the lanes
+// run their items' gates, and the whole warp evaluates the survivors.  The register DFT radix (2 or 4) and the number
 // of CTAs per SM are tuning parameters (chosen by the autotuner).
 #include "edge_dev.cuh"
 #include "fft_dev.cuh"
@@ -24,6 +25,7 @@ using namespace edge_dev;
 constexpr int kMaxClasses = 4;
 constexpr int kThreads = 320;  // ten warps: the pass-1 tasks of P = 32
 constexpr int kWarps = kThreads / 32;
+constexpr int kClaim = 16;     // cosine items a warp claims per round
 
 struct MixedArgs {
     pcl_params prm[kMaxClasses];
@@ -46,23 +48,29 @@ __global__ void mark_mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t
 template <int RADIX>
 __global__ void __launch_bounds__(kThreads, 1)
     mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t n_cos, uint64_t n, pcl_record *out,
-                 unsigned int *cursor) {
-    __shared__ uint64_t grp_base;
-    __shared__ uint64_t surv[kWarps];
-    __shared__ int n_surv;
+                 unsigned long long *cursor) {
+    __shared__ uint64_t surv[kWarps * kClaim];
+    __shared__ int n_surv, exhausted;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // ---- cosine items: gate a group in parallel, align the survivors
+    // while gating, the alignment bodies' shared memory is free: each warp
+    // takes a slice of it for the G2 profiles
+    extern __shared__ __align__(16) unsigned char mixed_sm[];
+    uint16_t *g2_scratch = reinterpret_cast<uint16_t *>(mixed_sm);
+    // ---- cosine items, in rounds: every warp claims kClaim consecutive items
+    // and gates them one after the other (the gate cost varies a lot between
+    // items, so a round evens it out over kClaim items); the survivors of the
+    // round are then aligned one after the other by the whole CTA
     for (;;) {
-        __syncthreads();
         if (threadIdx.x == 0) {
-            grp_base = atomicAdd(cursor, (unsigned)kWarps);
             n_surv = 0;
+            exhausted = 0;
         }
         __syncthreads();
-        const uint64_t base = grp_base;
-        if (base >= n_cos) break;
-        const uint64_t t = base + warp;
-        if (t < n_cos) {
+        uint64_t t0 = 0;
+        if (lane == 0) t0 = atomicAdd(cursor, (unsigned long long)kClaim);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= n_cos && lane == 0) exhausted = 1;
+        for (uint64_t t = t0; t < t0 + kClaim && t < n_cos; ++t) {
             const pcl_work w = work[t];
             pcl_record rec{};
             rec.a = w.a;
@@ -85,7 +93,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                     int gate = 0;
                     if (!(prm.flags & PCL_P_NO_GATES))
-                        gate = warp_cosine_gate(cs, w.a, cs, w.b, g, prm.cos_num, prm.cos_den, lane);
+                        gate = warp_cosine_gate(cs, w.a, cs, w.b, g, prm.cos_num, prm.cos_den, lane,
+                                                g2_scratch + warp * kG2Scratch);
                     if (gate) rec.flags = (uint16_t)gate;
                     else done = false;
                 }
@@ -110,32 +119,55 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncthreads();
         }
+        if (exhausted) break;  // some warp found no items left: this round was the last
+        __syncthreads();       // exhausted and n_surv are reset only after every warp read them
     }
-    // ---- edge items, one per thread
-    for (uint64_t t = n_cos + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const pcl_work w = work[t];
-        if (w.cls >= args.n_classes) {
+    // ---- edge items: each lane takes one item and runs its gates (most items
+    // end there); the whole warp then evaluates the survivors one at a time
+    // (warp_edge_record).  Warps stride the list 32 items at a time.
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = n_cos + 32 * gw; base < n; base += 32 * nw) {
+        const uint64_t t = base + lane;
+        bool surv_e = false;
+        pcl_work w{};
+        if (t < n) {
+            w = work[t];
             pcl_record r{};
-            r.a = w.a;
-            r.b = w.b;
-            r.mode = PCL_MODE_EDGE;
-            r.flags = PCL_GATE_BAD_INDEX;
-            out[t] = r;
-            continue;
+            if (w.cls >= args.n_classes) {
+                r.a = w.a;
+                r.b = w.b;
+                r.mode = PCL_MODE_EDGE;
+                r.flags = PCL_GATE_BAD_INDEX;
+            } else {
+                surv_e = edge_gate_record(args.prm[w.cls], args.cs[w.cls], args.cs[w.cls], pcl_pair{w.a, w.b}, &r);
+            }
+            if (!surv_e) out[t] = r;
         }
-        out[t] = edge_record(args.prm[w.cls], args.cs[w.cls], args.cs[w.cls], pcl_pair{w.a, w.b});
+        unsigned m = __ballot_sync(0xffffffffu, surv_e);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t cls = __shfl_sync(0xffffffffu, (uint32_t)w.cls, src);
+            const uint32_t a = __shfl_sync(0xffffffffu, w.a, src), b = __shfl_sync(0xffffffffu, w.b, src);
+            const pcl_record r = warp_edge_record(args.prm[cls], args.cs[cls], args.cs[cls], pcl_pair{a, b}, lane);
+            if (lane == 0) out[base + src] = r;
+        }
     }
 }
 
-size_t mixed_smem() { return PairSmem<32>::bytes > exact_smem<8>() ? PairSmem<32>::bytes : exact_smem<8>(); }
+size_t mixed_smem() {
+    size_t b = PairSmem<32>::bytes > exact_smem<8>() ? PairSmem<32>::bytes : exact_smem<8>();
+    const size_t g2 = sizeof(uint16_t) * kWarps * kG2Scratch;  // gating scratch, same memory
+    return b > g2 ? b : g2;
+}
 
 }  // namespace
 
 cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool, cudaStream_t);
 
 cudaError_t launch_mixed(const pcl_params *prm, const pcl_clipset *sets, uint32_t n_classes, const pcl_work *work,
-                         uint64_t n_cos, uint64_t n, pcl_record *out, unsigned int *cursor, uint32_t radix,
+                         uint64_t n_cos, uint64_t n, pcl_record *out, unsigned long long *cursor, uint32_t radix,
                          uint32_t ctas_per_sm, int num_sms, cudaStream_t st) {
     if (n_classes == 0 || n_classes > kMaxClasses) return cudaErrorInvalidValue;
     MixedArgs args{};
@@ -144,7 +176,7 @@ cudaError_t launch_mixed(const pcl_params *prm, const pcl_clipset *sets, uint32_
         args.prm[c] = prm[c];
         args.cs[c] = sets[c];
     }
-    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     if (n_cos) {
         mark_mixed_kernel<<<1024, 256, 0, st>>>(args, work, n_cos);
