@@ -115,7 +115,7 @@ __device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const 
 }
 
 template <int WPL>
-__global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
+__global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
                                                         const uint32_t *spop, const uint32_t *cum,
                                                         uint32_t vmax_all, pcl_pair *out, uint64_t cap,
                                                         unsigned long long *count,
@@ -173,26 +173,50 @@ __global__ void __launch_bounds__(256) band_join_kernel(pcl_params prm, pcl_clip
                 tB = (int)max((int64_t)pb - um, (int64_t)INT_MIN);
             }
             const int cnt = (int)min(32u, end - q0);
-            for (int k = 0; k < cnt; ++k) {
-                const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
-                const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+            // the rest of the gates for member k after the pre-screen
+            auto finish = [&](int k, uint32_t bk, int tAk, int tBk) {
                 const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)bk * 2 * nb2);
                 if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
                     ++g3;
-                    continue;
+                    return;
                 }
                 // G2 with the same threshold (tA = pa - um; never clamped in a band)
                 if (warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N, g.S,
                                          (int64_t)pa - tAk, lane)) {
                     ++g2;
-                    continue;
+                    return;
                 }
                 ++kept;
                 if (lane == 0) {
                     const unsigned long long idx = atomicAdd(count, 1ull);
                     if (idx < cap) out[idx] = pcl_pair{min(a, bk), max(a, bk)};
                 }
+            };
+            // Pre-screen two members at a time: the representative's deficit
+            // over the first 64 blocks against each member (the test that
+            // alone rejects most band pairs), both sums in one reduction (each
+            // lane's share of one sum is at most 2 * 256, a 32-lane sum at
+            // most 16384, so the two fit in 16-bit halves).  Members the
+            // pre-screen keeps get the full gates, which repeat this test.
+            const bool v0 = lane < words;
+            int k = 0;
+            for (; k + 1 < cnt; k += 2) {
+                const uint32_t b0 = __shfl_sync(0xffffffffu, b, k), b1 = __shfl_sync(0xffffffffu, b, k + 1);
+                const int tA0 = __shfl_sync(0xffffffffu, tA, k), tA1 = __shfl_sync(0xffffffffu, tA, k + 1);
+                const uint32_t *d0p = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)b0 * 2 * nb2) + words;
+                const uint32_t *d1p = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)b1 * 2 * nb2) + words;
+                const uint32_t n0 = v0 ? __ldg(d0p + lane) : 0u, n1 = v0 ? __ldg(d1p + lane) : 0u;
+                const uint32_t x0 = ca[0] - __vminu2(ca[0], n0), x1 = ca[0] - __vminu2(ca[0], n1);
+                const uint32_t both = ((x0 & 0xffffu) + (x0 >> 16)) | (((x1 & 0xffffu) + (x1 >> 16)) << 16);
+                const uint32_t sr = __reduce_add_sync(0xffffffffu, both);
+                const bool r0 = (int)(sr & 0xffffu) >= tA0, r1 = (int)(sr >> 16) >= tA1;
+                g3 += (r0 ? 1 : 0) + (r1 ? 1 : 0);
+                if (!r0) finish(k, b0, tA0, __shfl_sync(0xffffffffu, tB, k));
+                if (!r1) finish(k + 1, b1, tA1, __shfl_sync(0xffffffffu, tB, k + 1));
             }
+            if (k < cnt)
+                finish(k, __shfl_sync(0xffffffffu, b, k), __shfl_sync(0xffffffffu, tA, k),
+                       __shfl_sync(0xffffffffu, tB, k));
         }
     }
     if (lane == 0) {
