@@ -81,13 +81,8 @@ TRAFFIC = {
     "cand_edge": {"sources": {"paper_2512_13133_gb300/csrc/edge.cu":
                               "3557236a676c7089c289ff46a1a8f0304646ccd222e9c11395ff37832c6702dc",
                               "paper_2512_13133_gb300/csrc/edge_dev.cuh":
-                              "84f86ca59107549d7632373f5b70900b0b91d26c4975c187990a723a5096d202"},
-                  "bytes": 1.91e9 + 22.75e6},
-    "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
-                             "8e529c9008c144caafb4a43e928af62544ca1b01c0fabd995fc5e74576392bce",
-                             "paper_2512_13133_gb300/csrc/gates.cuh":
-                             "cb4a592902f30f5adbe8402a1027c0dd33e9d01ca9f654bc0d73ea9719b253a4"},
-                 "bytes": 183.12e6 + 3.62e6},
+                              "3da6799f1bb5ecc170f4da51af6f5d5012aa45d1ad8811bac26a01766c3bcf0a"},
+                  "bytes": 1.92e9 + 22.86e6},
 }
 
 

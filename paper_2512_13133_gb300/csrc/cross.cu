@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(1024) scan_items_kernel(const uint32_t *v, uin
     if (threadIdx.x == 1023) out[m] = run;
 }
 
+// WPL: u32 words of block counts per lane (the query's are held in registers)
+template <int WPL>
 __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
                                                          const uint32_t *lib_order, const uint32_t *lib_spop,
                                                          const uint32_t *beg, const uint32_t *item_off,
@@ -84,8 +86,17 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
     const int lane = threadIdx.x & 31;
     const uint32_t nq = Q.n_clips;
     const uint32_t total = item_off[nq];
-    const int nb2 = g.nb * g.nb;
+    const int nb2 = g.nb * g.nb, words = nb2 / 2;
     unsigned long long kept = 0, g2 = 0, g3 = 0;
+    auto emit = [&](bool keep, uint32_t q, uint32_t b) {  // warp-aggregated
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+        if (keep && idx < cap) out[idx] = pcl_pair{q, b};
+    };
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(next_item, 1u);
@@ -103,25 +114,54 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
         const uint32_t p0 = beg[q] + (t - item_off[q]) * kChunk;
         const uint32_t p1 = min(p0 + kChunk, bend);
         const uint64_t pa = Q.pop[q];
-        for (uint32_t pos = p0; pos < p1; ++pos) {
-            const uint32_t b = lib_order[pos];
-            const uint64_t pb = lib_spop[pos];
-            if (!(pa == 0 && pb == 0)) {
+        if (pa == 0) {  // the band holds the empty library clips only: similar by definition
+            for (uint32_t q0 = p0; q0 < p1; q0 += 32) {
+                const bool v = q0 + lane < p1;
+                emit(v, q, v ? lib_order[q0 + lane] : 0u);
+                kept += __popc(__ballot_sync(0xffffffffu, v));
+            }
+            continue;
+        }
+        const uint32_t *cwa = reinterpret_cast<const uint32_t *>(Q.blk + (size_t)q * 2 * nb2);
+        uint32_t ca[WPL], da[WPL];
+#pragma unroll
+        for (int c = 0; c < WPL; ++c) {
+            const int w = c * 32 + lane;
+            ca[c] = w < words ? cwa[w] : 0u;
+            da[c] = w < words ? cwa[words + w] : 0u;
+        }
+        // members 32 at a time: lane l sets up member q0 + l (index, the
+        // thresholds of the exact rule; G1 passes, so neither is clamped),
+        // then the warp tests them one after the other
+        for (uint32_t q0 = p0; q0 < p1; q0 += 32) {
+            uint32_t b = 0;
+            int tA = 0, tB = 0;
+            if (q0 + lane < p1) {
+                b = lib_order[q0 + lane];
+                const uint64_t pb = lib_spop[q0 + lane];
                 const int64_t um = cos_umax(pa, pb, prm.cos_num, prm.cos_den);
-                if (warp_g3_rejects(Q.blk + (size_t)q * 2 * nb2, L.blk + (size_t)b * 2 * nb2, nb2, pa, pb, um, lane)) {
+                tA = (int)((int64_t)pa - um);
+                tB = (int)((int64_t)pb - um);
+            }
+            const int cnt = (int)min(32u, p1 - q0);
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+                const uint32_t *cwb = reinterpret_cast<const uint32_t *>(L.blk + (size_t)bk * 2 * nb2);
+                if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
                     ++g3;
                     continue;
                 }
-                if (warp_g2_rejects_n(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)b * 2 * g.N, g.N, g.S, um,
-                                      lane)) {
+                if (warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N, g.S,
+                                         (int64_t)pa - tAk, lane)) {
                     ++g2;
                     continue;
                 }
-            }
-            ++kept;
-            if (lane == 0) {
-                const unsigned long long idx = atomicAdd(count, 1ull);
-                if (idx < cap) out[idx] = pcl_pair{q, b};
+                ++kept;
+                if (lane == 0) {
+                    const unsigned long long idx = atomicAdd(count, 1ull);
+                    if (idx < cap) out[idx] = pcl_pair{q, bk};
+                }
             }
         }
     }
@@ -170,8 +210,16 @@ cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const
         cross_prep_kernel<<<(nq + 255) / 256, 256, 0, st>>>(Q.pop, nq, lib_cum, (uint32_t)g.N * g.N, prm.cos_num,
                                                              prm.cos_den, beg, endp, nch);
         scan_items_kernel<<<1, 1024, 0, st>>>(nch, nq, item_off);
-        cross_join_kernel<<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off, out, cap,
-                                                       count, local, next_item);
+        switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
+            case 1: cross_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off,
+                                                                      out, cap, count, local, next_item); break;
+            case 4: cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off,
+                                                                      out, cap, count, local, next_item); break;
+            case 16: cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg,
+                                                                        item_off, out, cap, count, local,
+                                                                        next_item); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
     cross_finish_kernel<<<1, 32, 0, st>>>(local, gates, (unsigned long long)nq * L.n_clips);
     return cudaGetLastError();

@@ -162,6 +162,43 @@ __device__ __forceinline__ bool warp_g2_rejects_lite(const uint16_t *__restrict_
     return (int64_t)(ur < uc ? ur : uc) <= um;
 }
 
+// G3 for one band member with the representative's block words in registers
+// (WPL u32 words per lane = two 16-bit blocks each).  Deficits accumulate as
+// packed 16-bit halves (min <= value, so no borrow crosses halves; a chunk's
+// 32-lane sum of one half is at most 32 * 256); after every 32-lane chunk the
+// bound min(pa - DA, pb - DB) is compared with the pair's thresholds: it
+// fails Eq. 2 exactly when DA >= tA or DB >= tB (tX = pX - cos_umax).  In the
+// first chunk A's deficit is summed and tested before B's: on its own it
+// rejects most pairs of a band.
+template <int WPL>
+__device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+                                               const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
+                                               int words, int tA, int tB, int lane) {
+    const bool v = lane < words;  // lanes past the words hold zero block counts
+    const uint32_t d0 = v ? __ldg(db + lane) : 0u, b0 = v ? __ldg(cb + lane) : 0u;
+    uint32_t sr = __reduce_add_sync(0xffffffffu, ca[0] - __vminu2(ca[0], d0));
+    int DA = (int)((sr & 0xffffu) + (sr >> 16));
+    if (DA >= tA) return true;
+    sr = __reduce_add_sync(0xffffffffu, b0 - __vminu2(b0, da[0]));
+    int DB = (int)((sr & 0xffffu) + (sr >> 16));
+    if (DB >= tB) return true;
+#pragma unroll
+    for (int c = 1; c < WPL; ++c) {
+        const int t = c * 32 + lane;
+        uint32_t pda = 0u, pdb = 0u;
+        if (t < words) {
+            const uint32_t b = __ldg(cb + t);
+            pda = ca[c] - __vminu2(ca[c], __ldg(db + t));
+            pdb = b - __vminu2(b, da[c]);
+        }
+        const uint32_t sa = __reduce_add_sync(0xffffffffu, pda), sb = __reduce_add_sync(0xffffffffu, pdb);
+        DA += (int)((sa & 0xffffu) + (sa >> 16));
+        DB += (int)((sb & 0xffffu) + (sb >> 16));
+        if (DA >= tA || DB >= tB) return true;
+    }
+    return false;
+}
+
 // cosine gates of one pair (warp-uniform result): PCL_GATE_* or 0.  scratch
 // (kG2Scratch u16 of shared memory owned by the warp, may be null) speeds up G2.
 __device__ __forceinline__ int warp_cosine_gate(const pcl_clipset &A, uint32_t a, const pcl_clipset &B, uint32_t b,
