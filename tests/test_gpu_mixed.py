@@ -91,3 +91,49 @@ def test_mixed_matches_oracle_sample(batch, torch_cuda):
             np.testing.assert_array_equal(g["flags"][sel] & 15, o["flags"] & 15)
             m = (o["flags"] & oracle.F_ALIGNED) > 0
             np.testing.assert_array_equal(g["score"][sel][m].astype(np.int64), o["score"][m])
+
+
+def test_mixed_without_gates_and_pcm_rule(torch_cuda):
+    """Gates off: every non-empty item reaches its alignment engine (edge
+    items the whole-warp Min-Max, cosine items the FFT body or, at 512², the
+    exact window scan) and the records still equal the per-class entry
+    points'.  With shift_rule = PCM_PEAK the 512² class has no engine: its
+    cosine items are reported unsupported, the other classes are unaffected."""
+    import paper_2512_13133_gb300 as pcl
+    wls, pairs, modes = synth.batched(5, clips_per_class=48)
+    rng = np.random.default_rng(2)
+    pick = np.sort(rng.choice(len(pairs), min(len(pairs), 1500), replace=False))
+    pairs, modes = pairs[pick], modes[pick]
+    order = np.lexsort((pairs[:, 1], pairs[:, 0], modes))
+    pairs, modes = pairs[order], modes[order]
+    ctx = pcl.Context(0)
+    work = np.zeros(len(pairs), dtype=pcl.WORK_DTYPE)
+    work["cls"], work["a"], work["b"], work["mode"] = pairs[:, 0], pairs[:, 1], pairs[:, 2], modes
+    n_cos = int((modes == 1).sum())
+    tw = torch_cuda.from_numpy(work.view(np.uint8).reshape(-1, 12)).cuda()
+    for flags, rule in ((pcl.P_NO_GATES, pcl.SHIFT_EXACT_ARGMAX), (0, pcl.SHIFT_PCM_PEAK)):
+        Ps, sets = [], []
+        for wl in wls:
+            P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, flags=flags, shift_rule=rule)
+            cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=wl.raster_n <= 256)
+            pcl.pcl_rasterize(ctx, P, cs)
+            Ps.append(P)
+            sets.append(cs)
+        out = torch_cuda.empty((len(pairs), 40), dtype=torch_cuda.uint8, device="cuda")
+        pcl.pcl_match_mixed(ctx, Ps, sets, tw, n_cos, out, pcl.Tuning(2, 0))
+        g = pcl.records_to_numpy(out)
+        for k, wl in enumerate(wls):
+            for mode in (1, 2):
+                sel = np.flatnonzero((pairs[:, 0] == k) & (modes == mode))
+                if len(sel) == 0:
+                    continue
+                if mode == 1 and wl.raster_n == 512 and rule == pcl.SHIFT_PCM_PEAK:
+                    assert np.all((g["flags"][sel] & 15) == pcl.GATE_UNSUPPORTED)
+                    continue
+                tp = torch_cuda.from_numpy(pairs[sel, 1:].astype(np.int32)).cuda()
+                r = pcl.records_to_numpy(pcl.match(ctx, Ps[k], mode, sets[k], sets[k], tp))
+                for f in EXACT:
+                    np.testing.assert_array_equal(g[f][sel], r[f], err_msg=f"class {k} mode {mode} field {f}")
+                np.testing.assert_array_equal(g["flags"][sel] & 0x39F, r["flags"] & 0x39F)
+        if flags:
+            assert ((g["flags"] & pcl.F_ALIGNED) > 0).sum() > len(pairs) // 2
