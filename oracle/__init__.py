@@ -34,6 +34,7 @@ _SRC = os.path.join(_HERE, "pcl_oracle.c")
 
 MODE_COSINE = 1
 MODE_EDGE = 2
+MODE_COSINE_XYSEP = 3  # cosine mode, shift by XY-separation interval competition (Sec. 3.2.1 (2))
 
 GATE_NONE = 0
 GATE_G1_AREA = 1
@@ -96,6 +97,7 @@ def _load():
     lib.orc_corr_window.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
     lib.orc_cosine_pair.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.orc_edge_pair.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.orc_xysep_pair.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.orc_minmax_scan.restype = ctypes.c_int
     lib.orc_minmax_scan.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.orc_minmax_closed.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
@@ -237,7 +239,8 @@ class ClipSet:
     def pair(self, a: int, b: int, mode: int = MODE_COSINE, **kw) -> np.void:
         rec = np.zeros(1, dtype=REC_DTYPE)
         p = self.params(**kw)
-        fn = self._lib.orc_cosine_pair if mode == MODE_COSINE else self._lib.orc_edge_pair
+        fn = {MODE_COSINE: self._lib.orc_cosine_pair, MODE_EDGE: self._lib.orc_edge_pair,
+              MODE_COSINE_XYSEP: self._lib.orc_xysep_pair}[mode]
         fn(self._h, a, b, ctypes.byref(p), rec.ctypes.data)
         return rec[0]
 

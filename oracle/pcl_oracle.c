@@ -30,6 +30,7 @@
 enum {
     ORC_MODE_COSINE = 1,
     ORC_MODE_EDGE = 2,
+    ORC_MODE_COSINE_XYSEP = 3,  /* cosine mode, shift by interval competition */
 };
 
 /* gate / outcome codes (low 4 bits of flags) */
@@ -561,6 +562,100 @@ void orc_minmax_closed(const int32_t *d, int n, int M, int *T, int *E) {
     *E = (*T - dmin) > (dmax - *T) ? (*T - dmin) : (dmax - *T);
 }
 
+/*
+ * Cosine mode with the shift of the XY-separation interval competition
+ * (Sec. 3.2.1 (2), the geometric alternative to phase correlation), written
+ * from its four steps with the readings below (the paper states only the
+ * steps):
+ *  0. both clips empty -> pass (sim 1); the cosine gates first when enabled.
+ *  1. polygon pairs: pre-alignment s0 as in edge mode (doubled centres of the
+ *     non-border-edge bboxes, truncated, clamped to +/-M; 0 on an axis that
+ *     lacks such edges in either clip); each polygon k of the clip with fewer
+ *     polygons (A on a tie) pairs with its partner m when exactly one polygon
+ *     of the other clip overlaps it at s0 (no pair otherwise).
+ *     Allowable interval of a pair on an axis: [d_min, d_max] over the
+ *     displacements d = e_A - e_B of its two edges on that axis, edges on the
+ *     window border in either clip excluded (no interval if both are).
+ *  2. interval quality Q = d_max - d_min.
+ *  3. axis winner: the pair with the smallest Q; ties go to the smaller k.
+ *  4. T = trunc((d_min + d_max) / 2) of the winner, clamped to +/-M; an axis
+ *     without any interval keeps T = s0.
+ * The dbu shift becomes the raster shift s = T / p rounded half away from
+ * zero and clamped to +/-S; the record holds c(s) (exact overlap), sim and
+ * the integer decision of Eq. 2 at that shift.  Since c(s) <= c(s*), this
+ * engine can only lose passes of the exact argmax, never add any.
+ */
+static int round_div_away(int v, int p) { return v >= 0 ? (v + p / 2) / p : -((-v + p / 2) / p); }
+
+void orc_xysep_pair(const orc_set *s, int a, int b, const orc_params *P, orc_rec *out) {
+    memset(out, 0, sizeof(*out));
+    out->a = (uint32_t)a; out->b = (uint32_t)b; out->mode = ORC_MODE_COSINE;
+    int64_t pa = s->pop[a], pb = s->pop[b];
+    if (pa == 0 && pb == 0) {
+        out->sim = 1.0; out->pass = 1; out->flags = ORC_F_EMPTY;
+        return;
+    }
+    if (P->use_gates) {
+        int g = cosine_gate(s, a, b, P);
+        if (g != ORC_GATE_NONE) { out->flags = (uint32_t)g; return; }
+    }
+    int na, nb;
+    const orc_rect *ra = clip_rects(s, a, &na), *rb = clip_rects(s, b, &nb);
+    int W = s->W, M = P->marker_dbu;
+    int hxa, lxa, uxa, hya, lya, uya, hxb, lxb, uxb, hyb, lyb, uyb;
+    edge_bbox(ra, na, W, &hxa, &lxa, &uxa, &hya, &lya, &uya);
+    edge_bbox(rb, nb, W, &hxb, &lxb, &uxb, &hyb, &lyb, &uyb);
+    int s0x = (hxa && hxb) ? clampi(((lxa + uxa) - (lxb + uxb)) / 2, -M, M) : 0;
+    int s0y = (hya && hyb) ? clampi(((lya + uya) - (lyb + uyb)) / 2, -M, M) : 0;
+    int small_is_a = na <= nb;
+    int ns = small_is_a ? na : nb, nl = small_is_a ? nb : na;
+    /* best interval per axis: quality, d_min + d_max */
+    int qx = -1, sx = 0, qy = -1, sy = 0;
+    for (int k = 0; k < ns; ++k) {
+        int cnt = 0, m = -1;
+        for (int j = 0; j < nl; ++j) {
+            int hit = small_is_a ? overlaps(&ra[k], &rb[j], s0x, s0y) : overlaps(&ra[j], &rb[k], s0x, s0y);
+            if (hit) { ++cnt; m = j; }
+        }
+        if (cnt != 1) continue;
+        const orc_rect *p_a = small_is_a ? &ra[k] : &ra[m];
+        const orc_rect *p_b = small_is_a ? &rb[m] : &rb[k];
+        int dx[2] = {p_a->x0 - p_b->x0, p_a->x1 - p_b->x1};
+        int okx[2] = {p_a->x0 != 0 && p_b->x0 != 0, p_a->x1 != W && p_b->x1 != W};
+        int dy[2] = {p_a->y0 - p_b->y0, p_a->y1 - p_b->y1};
+        int oky[2] = {p_a->y0 != 0 && p_b->y0 != 0, p_a->y1 != W && p_b->y1 != W};
+        int has = 0, lo = 0, hi = 0;
+        for (int e = 0; e < 2; ++e)
+            if (okx[e]) {
+                if (!has || dx[e] < lo) lo = dx[e];
+                if (!has || dx[e] > hi) hi = dx[e];
+                has = 1;
+            }
+        if (has && (qx < 0 || hi - lo < qx)) { qx = hi - lo; sx = lo + hi; }
+        has = 0;
+        for (int e = 0; e < 2; ++e)
+            if (oky[e]) {
+                if (!has || dy[e] < lo) lo = dy[e];
+                if (!has || dy[e] > hi) hi = dy[e];
+                has = 1;
+            }
+        if (has && (qy < 0 || hi - lo < qy)) { qy = hi - lo; sy = lo + hi; }
+    }
+    int Tx = qx >= 0 ? clampi(sx / 2, -M, M) : s0x;
+    int Ty = qy >= 0 ? clampi(sy / 2, -M, M) : s0y;
+    int S = s->S, p = s->p;
+    int dxp = clampi(round_div_away(Tx, p), -S, S), dyp = clampi(round_div_away(Ty, p), -S, S);
+    int N = s->N, nw = s->nw;
+    const uint64_t *A = s->wd + (size_t)a * N * nw, *B = s->wd + (size_t)b * N * nw;
+    int64_t c = corr_words(A, B, N, nw, dxp, dyp);
+    out->dx_dbu = dxp * p;
+    out->dy_dbu = dyp * p;
+    out->score = c;
+    out->sim = (pa > 0 && pb > 0) ? (double)c / sqrt((double)pa * (double)pb) : 0.0;
+    out->pass = cos_exceeds(c, pa, pb, P->cos_num, P->cos_den);
+    out->flags = ORC_F_ALIGNED;
+}
+
 /* edge gates alone (E2 then E1 correspondence at s0); returns rejecting gate */
 static int edge_gate(const orc_set *s, int a, int b, const orc_params *P) {
     orc_rec r;
@@ -596,6 +691,7 @@ static void *match_worker(void *arg) {
         for (size_t i = lo; i < hi; ++i) {
             int a = (int)j->pairs[2 * i], b = (int)j->pairs[2 * i + 1];
             if (j->mode == ORC_MODE_COSINE) orc_cosine_pair(j->s, a, b, j->P, &j->out[i]);
+            else if (j->mode == ORC_MODE_COSINE_XYSEP) orc_xysep_pair(j->s, a, b, j->P, &j->out[i]);
             else orc_edge_pair(j->s, a, b, j->P, &j->out[i]);
         }
     }

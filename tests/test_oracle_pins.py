@@ -449,3 +449,90 @@ def test_cluster_loop_invariants(small_set):
         if k != r:
             assert (min(k, r), max(k, r)) in ok
     assert rounds >= 1
+
+
+# ---- XY-separation interval competition (Sec. 3.2.1 (2)) --------------------
+
+def _xysep(a_rects, b_rects, W=512, M=32, **kw):
+    wl = synth.from_lists([a_rects, b_rects], W, 4, M)
+    cs = oracle.ClipSet(wl)
+    return cs, cs.pair(0, 1, mode=oracle.MODE_COSINE_XYSEP, use_gates=False, **kw)
+
+
+def test_xysep_worked_example_narrowest_interval_wins():
+    # Worked by hand from the four steps.  Pre-alignment: A's non-border edge
+    # bbox is x 100..332, y 100..400, B's x 108..344, y 100..404, so s0 =
+    # (trunc(-20/2), trunc(-4/2)) = (-10, -2); at s0 each polygon of A meets
+    # exactly its counterpart.  Displacements d = e_A - e_B:
+    #   pair 1: x {100-108, 200-220} = {-8, -20} (Q 12), y {0, 0}   (Q 0)
+    #   pair 2: x {300-312, 332-344} = {-12, -12} (Q 0), y {-4, -4} (Q 0)
+    # x: pair 2 wins (Q 0 < 12), T_x = -12 -> -3 px (pair 1 would give -14 ->
+    # -4 px); y: tie at Q 0, the first polygon (pair 1) wins, T_y = 0 (pair 2
+    # would give -1 px).  Reported shift (-12, 0) dbu.
+    a = [[100, 100, 200, 148], [300, 300, 332, 400]]
+    b = [[108, 100, 220, 148], [312, 304, 344, 404]]
+    cs, r = _xysep(a, b)
+    assert (r["dx_dbu"], r["dy_dbu"]) == (-12, 0)
+    A, B = cs.image(0), cs.image(1)
+    assert r["score"] == oracle.corr_pixel(A, B, -3, 0)
+    # the exact argmax is at least as good and here strictly better (it also
+    # aligns pair 2 in y), so the interval shift loses overlap on this pair
+    e = cs.pair(0, 1, use_gates=False)
+    assert e["score"] >= r["score"]
+
+
+def test_xysep_pure_translate_matches_exact_argmax():
+    base = [[100, 120, 160, 180], [220, 300, 300, 330], [330, 90, 380, 250]]
+    for tx, ty in [(8, -12), (-32, 32), (4, 0), (0, -28)]:
+        cs, r = _xysep(base, _translate(base, tx, ty))
+        assert (r["dx_dbu"], r["dy_dbu"]) == (-tx, -ty)
+        assert r["score"] == cs.pop(0) and abs(r["sim"] - 1.0) < 1e-15 and r["pass_"] == 1
+
+
+def test_xysep_swap_negates_shift_without_ties():
+    # distinct qualities on both axes, so no tie rule is involved
+    a = [[100, 100, 200, 148], [300, 300, 332, 400]]
+    b = [[108, 102, 212, 148], [312, 304, 344, 404]]
+    _, r1 = _xysep(a, b)
+    _, r2 = _xysep(b, a)
+    assert (r2["dx_dbu"], r2["dy_dbu"]) == (-r1["dx_dbu"], -r1["dy_dbu"])
+    assert r1["score"] == r2["score"]
+
+
+def test_xysep_shift_clamped_to_marker():
+    # a translate of 100 dbu lies outside M = 32: the pre-alignment clamps, the
+    # interval midpoint clamps, and the raster shift stays at -S
+    base = [[100, 120, 160, 180], [220, 300, 300, 330]]
+    _, r = _xysep(base, _translate(base, 100, 0))
+    assert r["dx_dbu"] == -32
+
+
+def test_xysep_never_beats_exact(small_wl):
+    cs = oracle.ClipSet(small_wl)
+    rng = np.random.default_rng(9)
+    lab = small_wl.label
+    idx = np.flatnonzero(lab >= 0)
+    pairs = []
+    for s in np.unique(lab[idx])[:40]:
+        m = idx[lab[idx] == s]
+        pairs += [(i, j) for i in m for j in m if i != j]
+    pairs = np.array(pairs + [tuple(x) for x in rng.integers(0, small_wl.n, size=(300, 2))], dtype=np.int64)
+    x = cs.match(pairs, oracle.MODE_COSINE_XYSEP, use_gates=False)
+    e = cs.match(pairs, oracle.MODE_COSINE, use_gates=False)
+    assert np.all(x["score"] <= e["score"])
+    assert np.all(x["pass_"] <= e["pass_"])
+    # where the interval shift lands on the exact optimum, the records agree
+    hit = x["score"] == e["score"]
+    assert hit.any()
+    np.testing.assert_array_equal(x["pass_"][hit], e["pass_"][hit])
+
+
+def test_xysep_dbu_shift_rounds_half_away_from_zero():
+    # a translate by a non-multiple of the 4-dbu pitch: T = -t exactly, then
+    # the raster shift T / 4 is rounded half away from zero:
+    #   t = (6, -6):  T = (-6, 6)  -> (-1.5, 1.5)  -> (-2, 2) px = (-8, 8) dbu
+    #   t = (5, -7):  T = (-5, 7)  -> (-1.25, 1.75) -> (-1, 2) px = (-4, 8) dbu
+    base = [[100, 120, 160, 180], [220, 300, 300, 330], [330, 90, 380, 250]]
+    for (tx, ty), want in [((6, -6), (-8, 8)), ((5, -7), (-4, 8))]:
+        _, r = _xysep(base, _translate(base, tx, ty))
+        assert (r["dx_dbu"], r["dy_dbu"]) == want
