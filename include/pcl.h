@@ -59,7 +59,7 @@ enum { PCL_MODE_COSINE = 1, PCL_MODE_EDGE = 2 };
 /* cosine engines: FFT phase correlation (Sec. 3.2.1), or the direct windowed
    correlation on tensor cores with FP16 (TC_DIRECT) or E4M3 (TC_DIRECT_FP8)
    0/1 operands and FP32 accumulation -- both exact for 0/1 pixels */
-enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1, PCL_ENGINE_TC_DIRECT_FP8 = 2 };
+enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1, PCL_ENGINE_TC_DIRECT_FP8 = 2, PCL_ENGINE_XYSEP = 3 };
 enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
 
 /* pcl_params.flags */
@@ -274,6 +274,16 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    (pcm fields 0), and the engine covers (N, S) = (64, 4), (128, 8) and
    (256, 16) with shift_rule = EXACT_ARGMAX (else PCL_ERR_UNSUPPORTED).  A
    device-side wait that runs out is reported by pcl_device_error.
+   With cos_engine = PCL_ENGINE_XYSEP the shift is not searched but
+   synthesised by the XY-separation interval competition of Sec. 3.2.1 (2):
+   polygon pairs from the pre-alignment of EDGE mode (each polygon of the
+   clip with fewer polygons with its unique overlapping partner), per axis the
+   pair whose edge displacements span the narrowest interval, T = its
+   truncated midpoint clamped to +/-M, rounded half away from zero to the
+   pixel grid; the record holds the exact overlap at that shift and the
+   decision of Eq. 2 there (so it can only miss passes of the exact argmax;
+   pcm fields 0; shift_rule is ignored).  Any N and S; needs esig, occ and
+   rorder like EDGE mode, no spectra.  One warp per pair.
    EDGE (Sec. 2.2.2 + Eq. 6): pre-alignment, correspondence, per-axis
    d_min/d_max of matched non-border edges, T = trunc((d_min+d_max)/2)
    clamped to +/-M, E = max(T - d_min, d_max - T), re-check at T,

@@ -31,6 +31,8 @@ cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pc
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
+cudaError_t launch_xysep(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                         const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
                          pcl_record *, unsigned long long *, uint32_t, uint32_t, int, cudaStream_t);
 }  // namespace pcl
@@ -153,7 +155,7 @@ pcl_status pcl_params_validate(const pcl_params *P) {
     if (P->cos_den == 0 || P->cos_den > 65535 || P->cos_num == 0 || P->cos_num >= P->cos_den)
         return PCL_ERR_INVALID;
     if (P->edge_tol_dbu < 0) return PCL_ERR_INVALID;
-    if (P->cos_engine > PCL_ENGINE_TC_DIRECT_FP8 || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
+    if (P->cos_engine > PCL_ENGINE_XYSEP || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
     if (!(P->near_band >= 0.0f)) return PCL_ERR_INVALID;
     return PCL_OK;
 }
@@ -234,8 +236,8 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     pcl_status s = enter(ctx);
     if (s) return s;
     if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
-    if ((s = check_clipset(ctx, a, mode == PCL_MODE_EDGE)) || (s = check_clipset(ctx, b, mode == PCL_MODE_EDGE)))
-        return s;
+    const bool geo = mode == PCL_MODE_EDGE || P->cos_engine == PCL_ENGINE_XYSEP;  // needs the polygons
+    if ((s = check_clipset(ctx, a, geo)) || (s = check_clipset(ctx, b, geo))) return s;
     if (n && (!d_pairs || !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL pair list or output%s%lld");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
@@ -253,6 +255,10 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
         if ((s = ensure_ws(ctx, tc_workspace(n)))) return s;
         e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "tensor-core correlation");
+    }
+    if (P->cos_engine == PCL_ENGINE_XYSEP) {
+        e = launch_xysep(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "interval-competition shift");
     }
     if (P->cos_engine != PCL_ENGINE_FFT_PCM)
         return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine engine %s%lld not built", "", P->cos_engine);
