@@ -607,6 +607,36 @@ def run_ours(args, rank, world, local_rank):
                                                       (rt["pass_"] == recs["pass_"]).all())
         tc["device_error"] = pcl.pcl_device_error(ctx)
         fft["tc_engine"] = tc
+        # the interval-competition shift (Sec. 3.2.1 (2)) on the same list:
+        # speed, and what it loses against the exact argmax of the FFT engine
+        Px = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
+                        cos_engine=pcl.ENGINE_XYSEP, flags=pcl.P_NO_GATES)
+        rx = torch.empty((len(fp), 40), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            pcl.pcl_match_pairs(ctx, Px, pcl.MODE_COSINE, cs, cs, tfp, rx)
+        torch.cuda.synchronize()
+        x_ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            pcl.pcl_match_pairs(ctx, Px, pcl.MODE_COSINE, cs, cs, tfp, rx)
+            a1.record()
+            torch.cuda.synchronize()
+            x_ms.append(a0.elapsed_time(a1))
+        xr = pcl.records_to_numpy(rx)
+        xms = float(np.mean(x_ms))
+        same_shift = (xr["dx_dbu"] == recs["dx_dbu"]) & (xr["dy_dbu"] == recs["dy_dbu"])
+        fft["xysep_engine"] = {
+            "pairs": int(len(fp)), "ms": xms, "pairs_per_s": len(fp) / (xms / 1e3),
+            "speedup_vs_fft": fms / xms,
+            "same_shift_as_exact": float(same_shift.mean()),
+            "same_overlap_as_exact": float((xr["score"] == recs["score"]).mean()),
+            "passes": int(xr["pass_"].sum()), "passes_exact": int(recs["pass_"].sum()),
+            "passes_lost": int(((recs["pass_"] == 1) & (xr["pass_"] == 0)).sum()),
+            "mean_sim_loss": float((recs["sim"].astype(np.float64) - xr["sim"].astype(np.float64)).mean()),
+            "never_above_exact": bool((xr["score"] <= recs["score"]).all())}
         # spectra are per-step work of the main path again
         pcl.pcl_rasterize(ctx, P, cs)
         torch.cuda.synchronize()
