@@ -81,7 +81,7 @@ TRAFFIC = {
     "cand_edge": {"sources": {"paper_2512_13133_gb300/csrc/edge.cu":
                               "3557236a676c7089c289ff46a1a8f0304646ccd222e9c11395ff37832c6702dc",
                               "paper_2512_13133_gb300/csrc/edge_dev.cuh":
-                              "3da6799f1bb5ecc170f4da51af6f5d5012aa45d1ad8811bac26a01766c3bcf0a"},
+                              "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
                   "bytes": 1.91e9 + 22.89e6},
 }
 

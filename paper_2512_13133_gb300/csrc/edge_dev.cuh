@@ -322,48 +322,10 @@ __device__ inline EdgeOut warp_edge_eval(const ClipView &A, const ClipView &B, i
     return o;
 }
 
-// one edge-mode record for pair pr (bounds-checked), as written by the match kernels
-__device__ __forceinline__ pcl_record edge_record(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
-                                                  pcl_pair pr) {
-    pcl_record r{};
-    r.a = pr.a;
-    r.b = pr.b;
-    r.mode = PCL_MODE_EDGE;
-    if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
-        r.flags = PCL_GATE_BAD_INDEX;
-        return r;
-    }
-    int32_t ea[8], eb[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        ea[k] = __ldg(A.esig + (size_t)pr.a * 8 + k);
-        eb[k] = __ldg(B.esig + (size_t)pr.b * 8 + k);
-    }
-    const uint32_t oa = __ldg(A.rect_off + pr.a), ob = __ldg(B.rect_off + pr.b);
-    const ClipView va{reinterpret_cast<const int4 *>(A.rects) + oa, ea, A.rorder + oa, A.occ + (size_t)pr.a * 64};
-    const ClipView vb{reinterpret_cast<const int4 *>(B.rects) + ob, eb, B.rorder + ob, B.occ + (size_t)pr.b * 64};
-    const bool gates = !(prm.flags & PCL_P_NO_GATES);
-    const EdgeOut o = edge_eval(va, vb, prm.window_dbu, prm.marker_dbu, prm.edge_tol_dbu, gates, false);
-    r.dx_dbu = o.tx;
-    r.dy_dbu = o.ty;
-    if (o.empty) {
-        r.flags = PCL_F_EMPTY;
-        r.pass = 1;
-    } else if (o.gate) {
-        r.flags = (uint16_t)o.gate;
-    } else {
-        r.flags = PCL_F_ALIGNED | (o.verified ? 0 : PCL_F_EDGE_VERIFY_FAIL);
-        r.score = (uint32_t)o.E;
-        r.sim = (float)o.E;
-        r.pass = o.pass ? 1 : 0;
-    }
-    return r;
-}
-
-// The gates of edge_record for one pair in one thread (empty clips, E2, the
-// occupancy pre-check of E1): true when the pair passes them and needs the
-// rest of the procedure (then *rec is not set); otherwise *rec is the record
-// edge_record would write.
+// The gates of the edge-mode record for one pair in one thread (empty clips,
+// E2, the occupancy pre-check of E1): true when the pair passes them and needs
+// the rest of the procedure (then *rec is not set); otherwise *rec is the
+// record warp_edge_record would write.
 __device__ inline bool edge_gate_record(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
                                         pcl_pair pr, pcl_record *rec) {
     pcl_record r{};
@@ -423,7 +385,8 @@ __device__ inline bool edge_gate_record(const pcl_params &prm, const pcl_clipset
     return true;
 }
 
-// edge_record computed by a whole warp (every lane gets the record)
+// One edge-mode record for pair pr (bounds-checked), computed by a whole warp
+// (every lane gets the record)
 __device__ __forceinline__ pcl_record warp_edge_record(const pcl_params &prm, const pcl_clipset &A,
                                                        const pcl_clipset &B, pcl_pair pr, int lane) {
     pcl_record r{};
