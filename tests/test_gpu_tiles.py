@@ -1,0 +1,54 @@
+"""Self-join candidates at clip counts around the tile sizes of the screens
+(the edge screen takes 32 row clips and 256 column clips per block; the band
+join walks bands of the area order): 2, 3, 31, 33, 257 and 300 clips, with
+empty clips and identical copies mixed in.  Candidate sets and gate counts
+must equal the oracle's exhaustive screen exactly, in both modes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    import paper_2512_13133_gb300 as pcl
+    return pcl.Context(0)
+
+
+def _workload(n):
+    base = synth.preset("small", seed=3, n_clips=max(n, 4), n_seeds=max(1, n // 6), n_copies=int(0.6 * max(n, 4)))
+    clips = [base.clip(i).tolist() for i in range(n)]
+    # empty clips and exact duplicates at tile edges
+    for k in (0, n // 2, n - 1):
+        if 0 <= k < n and k % 3 == 0:
+            clips[k] = []
+    if n > 32:
+        clips[32] = list(clips[31])
+    return synth.from_lists(clips, base.window_dbu, base.pitch_dbu, base.marker_dbu)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 257, 300])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_candidates_at_tile_edges(ctx, n, mode):
+    import paper_2512_13133_gb300 as pcl
+    wl = _workload(n)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    gp, gcounts = pcl.candidates(ctx, P, mode, cs)
+    op, ocounts = oracle.ClipSet(wl).candidates(mode, cos_num=80)
+    got = set(map(tuple, gp.cpu().numpy().astype(np.int64).tolist()))
+    assert got == set(map(tuple, op.astype(np.int64).tolist()))
+    np.testing.assert_array_equal(gcounts[:6], ocounts[:6].astype(np.int64))
+    assert gcounts[:6].sum() == n * (n - 1) // 2
