@@ -15,8 +15,8 @@ cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, si
                              unsigned long long *, unsigned long long *, int, cudaStream_t);
 cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
                                unsigned long long *, unsigned long long *, cudaStream_t);
-cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
-                              uint64_t, const unsigned long long *, pcl_record *, cudaStream_t);
+cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                              const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool,
                            cudaStream_t);
 cudaError_t launch_mark(const pcl_pair *, uint64_t, const unsigned long long *, pcl_clipset &, pcl_clipset &,
@@ -242,7 +242,7 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (mode == PCL_MODE_EDGE) {
-        e = launch_edge_match(*P, *a, *b, d_pairs, n, dn, d_out, st);
+        e = launch_edge_match(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge match");
     }
     if (mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);

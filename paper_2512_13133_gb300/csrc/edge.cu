@@ -346,15 +346,20 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     }
 }
 
-// one pair per warp (warp_edge_record), lane 0 writes the record
+// one pair per warp (warp_edge_record), lane 0 writes the record; warps stride
+// the list (the grid is sized to the GPU, not to the list, whose length may
+// only be known on the device)
 __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
                                                          const pcl_pair *pairs, uint64_t n,
                                                          const unsigned long long *d_n, pcl_record *out) {
-    const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (d_n && *d_n < n) n = *d_n;
-    if (t >= n) return;  // warp-uniform
-    const pcl_record r = warp_edge_record(prm, A, B, pairs[t], threadIdx.x & 31);
-    if ((threadIdx.x & 31) == 0) out[t] = r;
+    const int lane = threadIdx.x & 31;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t t = w0; t < n; t += nw) {  // warp-uniform
+        const pcl_record r = warp_edge_record(prm, A, B, pairs[t], lane);
+        if (lane == 0) out[t] = r;
+    }
 }
 
 }  // namespace
@@ -374,11 +379,14 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
 
 cudaError_t launch_edge_match(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
                               const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
-                              cudaStream_t st) {
+                              int num_sms, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const uint64_t blocks = (n + 7) / 8;  // 8 warps per block, one pair per warp
-    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    edge_match_kernel<<<(unsigned)blocks, 256, 0, st>>>(prm, a, b, pairs, n, d_n, out);
+    const uint64_t need = (n + 7) / 8;  // 8 warps per block, one pair per warp
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_match_kernel, 256, 0);
+    if (e != cudaSuccess) return e;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);  // resident blocks
+    edge_match_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, st>>>(prm, a, b, pairs, n, d_n, out);
     return cudaGetLastError();
 }
 
