@@ -129,6 +129,31 @@ __device__ __forceinline__ bool warp_correspond(const int4 *__restrict__ rs, con
     return true;
 }
 
+// Tiles (bx, by) of 32 row clips x kColsB column clips with any pair i < j,
+// column block by holding the row tiles bx < min(8 by + 8, nbx) (kColsB = 256
+// = 8 row tiles), are numbered column block after column block: tile idx lies
+// in column block by with cum(by) <= idx < cum(by + 1), where cum(y) =
+// 4 y (y + 1) while 8 y <= nbx and grows by nbx per block after that.
+static_assert(kColsB == 256, "eight row tiles per column block");
+__host__ __device__ inline uint64_t screen_tiles_before(uint32_t y, uint32_t nbx) {
+    const uint64_t y0 = nbx / 8;
+    return y <= y0 ? 4ull * y * (y + 1) : 4ull * y0 * (y0 + 1) + (uint64_t)(y - y0) * nbx;
+}
+__device__ inline void screen_tile(uint32_t idx, uint32_t nbx, uint32_t &bx, uint32_t &by) {
+    const uint32_t y0 = nbx / 8;
+    const uint64_t c0 = 4ull * y0 * (y0 + 1);
+    uint32_t y;
+    if (idx < c0) {  // 4 y (y + 1) <= idx: float estimate, corrected exactly
+        y = (uint32_t)((sqrtf(1.0f + (float)idx) - 1.0f) * 0.5f);
+        while (4ull * (y + 1) * (y + 2) <= idx) ++y;
+        while (y > 0 && 4ull * y * (y + 1) > idx) --y;
+    } else {
+        y = y0 + (uint32_t)((idx - c0) / nbx);
+    }
+    by = y;
+    bx = (uint32_t)(idx - screen_tiles_before(y, nbx));
+}
+
 // Self-join screen: block (bx, by) covers row clips i = 32 bx + lane and
 // column clips j in [kColsB by, kColsB by + kColsB); warp w takes the columns
 // w, w + 8, ...  Pairs with i < j only.  The row clips' signatures live in
@@ -151,8 +176,10 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
                                                           unsigned long long *count,
                                                           unsigned long long *gates) {
     const uint32_t n = cs.n_clips;
-    const uint32_t i0 = blockIdx.x * 32u;
-    const uint32_t jblk = blockIdx.y * (uint32_t)kColsB;
+    uint32_t bx, by;
+    screen_tile(blockIdx.x, (n + 31) / 32, bx, by);
+    const uint32_t i0 = bx * 32u;
+    const uint32_t jblk = by * (uint32_t)kColsB;
     if (jblk >= n || i0 + 1u >= min(jblk + (uint32_t)kColsB, n)) return;  // no pair i < j in the block
     const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -369,8 +396,11 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
                                cudaStream_t st) {
     const uint32_t n = cs.n_clips;
     if (n < 2) return cudaSuccess;
-    dim3 grid((n + 31) / 32, (n + kColsB - 1) / kColsB);
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    // only the tiles that hold pairs i < j (about half of them)
+    const uint32_t nbx = (n + 31) / 32, nby = (n + kColsB - 1) / kColsB;
+    const uint64_t tiles = screen_tiles_before(nby, nbx);
+    if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)tiles;
     const int csz = prm.window_dbu / 64;
     if ((csz & (csz - 1)) == 0) edge_screen_kernel<true><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
     else edge_screen_kernel<false><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
