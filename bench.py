@@ -518,6 +518,33 @@ def run_ours(args, rank, world, local_rank):
     ms_step = float(st_ms.sum(axis=1).mean())
     per_stage = {s: float(st_ms[:, i].mean()) for i, s in enumerate(stages)}
 
+    # ---- a11: the host set cover and coarse-to-fine loop on the last step's
+    # records (outside the timed region).  Strict decisions are the records'
+    # own; the relaxed ones use the loop's defaults: cosine threshold
+    # (num - 2) / den by the integer rule, edge tolerance + 2 dbu.
+    host_loop = None
+    if rank == 0:
+        pops = cs.pop.cpu().numpy().astype(np.int64)
+        host_loop = {}
+        for name, rec_t, m_k in (("edge", re_, int(c[1])), ("cosine", rc, int(c[0]))):
+            r = pcl.records_to_numpy(rec_t[:m_k])
+            al = (r["flags"] & pcl.F_ALIGNED) > 0
+            if name == "edge":
+                relaxed = al & ((r["flags"] & pcl.F_EDGE_VERIFY_FAIL) == 0) & (r["score"].astype(np.int64) <= TOL + 2)
+            else:
+                cc = r["score"].astype(np.int64)
+                pp = pops[r["a"].astype(np.int64)] * pops[r["b"].astype(np.int64)]
+                relaxed = al & (COS_DEN ** 2 * cc * cc > (COS_NUM - 2) ** 2 * pp)
+            prs = np.stack([r["a"], r["b"]], 1).astype(np.uint32)
+            t0 = time.perf_counter()
+            _, ncl, nrd = pcl.pcl_cluster_loop(prs, r["pass_"].astype(np.uint8), relaxed.astype(np.uint8), n)
+            t1 = time.perf_counter()
+            order, _ = pcl.pcl_setcover(prs[relaxed], n)
+            t2 = time.perf_counter()
+            host_loop[name] = {"pairs": m_k, "relaxed": int(relaxed.sum()), "strict": int(r["pass_"].sum()),
+                               "clusters": ncl, "rounds": nrd, "loop_ms": (t1 - t0) * 1e3,
+                               "setcover_ms": (t2 - t1) * 1e3, "setcover_selected": int(len(order))}
+
     # ---- FFT phase-correlation engine on a fixed pair list: the same-seed
     # pairs of the workload (the pairs a looser coarse threshold would send
     # to alignment), gates off, spectra cached beforehand
@@ -739,6 +766,7 @@ def run_ours(args, rank, world, local_rank):
                    "stage_ms": per_stage, "screened_pairs_per_s": 2 * total_pairs * world / (ms_max / 1e3),
                    "wall_s_timed": wall},
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
+        "host_loop": host_loop,
         "serving": serving,
         "batched": batched,
     }
