@@ -148,7 +148,9 @@ typedef struct pcl_record {
  *   pop      [n] u32     |A| (ones of the raster)
  *   prof     [n][2N] u16 row counts r(j), then column counts q(i)
  *   blk      [n][2*nb*nb] u16  16x16 block counts, then their neighbourhood
- *                        sums over (2*ceil(S/16)+1)^2 blocks (nb = N/16)
+ *                        sums over (2*ceil(S/16)+1)^2 blocks (nb = N/16);
+ *                        block (by, bx) at position ((by%4)*4 + bx%4) * q*q
+ *                        + (by/4)*q + bx/4, q = nb/4 (spread blocks first)
  *   esig     [n][8] i32  edge signature: n_rects, has_x, lo_x, hi_x, has_y,
  *                        lo_y, hi_y, touches_border (non-border edges only)
  *   occ      [n][64] u64 64 x 64 occupancy grid of the rectangles (cell side

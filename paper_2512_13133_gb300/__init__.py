@@ -413,13 +413,22 @@ def unpack_bits(cs: ClipSet) -> np.ndarray:
     return b.reshape(cs.n, cs.N, cs.N)
 
 
+def blk_positions(nb: int) -> np.ndarray:
+    """[nb, nb] storage positions of the 16x16 blocks (by, bx) in a clip set's
+    blk buffer (the layout documented at pcl_clipset in pcl.h)"""
+    by, bx = np.meshgrid(np.arange(nb), np.arange(nb), indexing="ij")
+    q = nb // 4
+    return ((by % 4) * 4 + bx % 4) * q * q + (by // 4) * q + bx // 4
+
+
 def signatures(cs: ClipSet):
     """pop, profiles, block counts, edge signatures as numpy (for tests)"""
     n, N = cs.n, cs.N
     nb = N // 16
     pop = cs.pop[: 4 * n].cpu().numpy().view(np.uint32)
     prof = cs.prof[: 4 * n * N].cpu().numpy().view(np.uint16).reshape(n, 2, N)
-    blk = cs.blk[: 4 * n * nb * nb].cpu().numpy().view(np.uint16).reshape(n, 2, nb, nb)
+    stored = cs.blk[: 4 * n * nb * nb].cpu().numpy().view(np.uint16).reshape(n, 2, nb * nb)
+    blk = stored[:, :, blk_positions(nb)]  # back to row-major (by, bx)
     esig = cs.esig[: 32 * n].cpu().numpy().view(np.int32).reshape(n, 8)
     return dict(pop=pop, rows=prof[:, 0], cols=prof[:, 1], blk=blk[:, 0], dil=blk[:, 1], esig=esig)
 

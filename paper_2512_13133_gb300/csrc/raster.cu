@@ -15,6 +15,15 @@ namespace {
 
 constexpr int kRectChunk = 256;
 
+// Storage position of 16x16 block (by, bx) among the nb x nb blocks (nb a
+// multiple of 4): blocks are grouped by (by mod 4, bx mod 4), groups in
+// row-major order of that pair, blocks within a group row-major; at nb = 16
+// the first 64 positions are the block rows 0, 4, 8 and 12.
+__device__ __forceinline__ int blk_pos(int by, int bx, int nb) {
+    const int q = nb >> 2;
+    return (((by & 3) << 2) | (bx & 3)) * q * q + (by >> 2) * q + (bx >> 2);
+}
+
 // grid cell of coordinate v (floor division, clamped to the 64 cells)
 __device__ __forceinline__ int cell_of(int v, int csz) {
     const int q = v >= 0 ? v / csz : -((-v + csz - 1) / csz);
@@ -100,7 +109,9 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
         for (int jj = 0; jj < N; ++jj) q += (uint32_t)((rows[jj * NW + k] >> b) & 1ull);
         cs.prof[(size_t)c * 2 * N + N + i] = (uint16_t)q;
     }
-    // 16x16 block counts, then neighbourhood sums
+    // 16x16 block counts, then neighbourhood sums, each stored in the order of
+    // blk_pos: blocks spread over the whole clip come first, so the gates'
+    // chunked density bound sees every part of the clip in its first chunk
     const int nb = g.nb, nb2 = nb * nb;
     uint16_t *blk = cs.blk + (size_t)c * 2 * nb2;
     __shared__ uint16_t cnt_s[32 * 32];
@@ -110,7 +121,7 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
         uint32_t s = 0;
         for (int jj = 0; jj < 16; ++jj) s += (uint32_t)__popcll((rows[(by * 16 + jj) * NW + k] >> sh) & 0xffffull);
         cnt_s[t] = (uint16_t)s;
-        blk[t] = (uint16_t)s;
+        blk[blk_pos(by, bx, nb)] = (uint16_t)s;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
                 const int yy = by + oy, xx = bx + ox;
                 if (yy >= 0 && yy < nb && xx >= 0 && xx < nb) s += cnt_s[yy * nb + xx];
             }
-        blk[nb2 + t] = (uint16_t)min(s, 65535u);
+        blk[nb2 + blk_pos(by, bx, nb)] = (uint16_t)min(s, 65535u);
     }
     // edge signature (warp 0): bbox over edges that are not on the window border
     if (threadIdx.x < 32) {
