@@ -344,9 +344,11 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
 
 /* ---- a10: serving loop ----------------------------------------------------
    A resident representative library and continuously batched query requests
-   (cosine mode, FFT phase-correlation engine).  pcl_server_create computes
-   the library's spectra (all clips; the library must be rasterised and own
-   spec/spec_state buffers) and sorts it by area, then allocates max_inflight
+   (cfg mode COSINE: FFT phase-correlation engine; EDGE: Min-Max procedure).
+   For COSINE, pcl_server_create computes the library's spectra (all clips;
+   the library must be rasterised and own spec/spec_state buffers) and sorts
+   it by area; an EDGE library needs its rasters and edge signatures only
+   (esig, occ, rorder).  It then allocates max_inflight
    request slots (one stream each, pinned staging) and one device arena of
    mem_budget bytes.  pcl_server_submit admits a request of n_clips query
    clips (host rectangles, copied before return) when a slot is free and its
@@ -355,15 +357,18 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
    (resubmit after a poll/release); the request then runs asynchronously:
    rasterisation, query x library band join with the G1/G3/G2 gates,
    spectra of the referenced query clips, phase-correlation matching with
-   the exact decision, pass compaction and the copy of the pass list back.
+   the exact decision, pass compaction and the copy of the pass list back
+   (EDGE: every query x library pair through E2 and E1 one pair per lane, the
+   Min-Max record of each survivor by a whole warp, pass compaction, copy).
    pcl_server_poll returns finished requests (pass pairs are
    (query index, library index), in server-owned host memory valid until
    pcl_server_release frees the request's slot and arena region); a request
    whose candidates exceeded its capacity completes with PCL_ERR_BUSY.
    Timestamps are steady-clock nanoseconds: submit, and device completion as
    stamped by a host callback on the request's stream.  One host thread at a
-   time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (N > 256 or
-   S > N/16), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not admitted). */
+   time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with
+   N > 256 or S > N/16), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not
+   admitted). */
 typedef struct pcl_server pcl_server;
 
 typedef struct pcl_server_cfg {
@@ -373,6 +378,8 @@ typedef struct pcl_server_cfg {
     uint32_t cand_per_query;   /* candidate capacity per query clip */
     uint32_t pass_copy;        /* pass pairs copied back without a second copy */
     uint64_t mem_budget;       /* device bytes for in-flight requests */
+    uint32_t mode;             /* PCL_MODE_COSINE (or 0) or PCL_MODE_EDGE */
+    uint32_t reserved;
 } pcl_server_cfg;
 
 typedef struct pcl_completion {

@@ -110,7 +110,8 @@ assert WORK_DTYPE.itemsize == 12
 class _ServerCfg(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_uint32), ("max_query_clips", ctypes.c_uint32),
                 ("max_query_rects", ctypes.c_uint64), ("cand_per_query", ctypes.c_uint32),
-                ("pass_copy", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64)]
+                ("pass_copy", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class _Completion(ctypes.Structure):
@@ -464,12 +465,13 @@ class Server:
 
     def __init__(self, ctx: Context, P: Params, library: ClipSet, max_inflight: int = 8,
                  max_query_clips: int = 4096, max_query_rects: int = 4096 * 48, cand_per_query: int = 256,
-                 pass_copy: int = 1 << 16, mem_budget: int = 8 << 30):
+                 pass_copy: int = 1 << 16, mem_budget: int = 8 << 30, mode: int = MODE_COSINE):
         self.ctx = ctx
         self.lib = ctx.lib
         self.library = library  # keeps the library buffers alive
         self._cl = library.cstruct()
-        cfg = _ServerCfg(max_inflight, max_query_clips, max_query_rects, cand_per_query, pass_copy, mem_budget)
+        cfg = _ServerCfg(max_inflight, max_query_clips, max_query_rects, cand_per_query, pass_copy, mem_budget,
+                         mode, 0)
         h = _VP()
         ctx.check(self.lib.pcl_server_create(ctx.h, ctypes.byref(P), ctypes.byref(self._cl), ctypes.byref(cfg),
                                              ctypes.byref(h)), "pcl_server_create")

@@ -1,5 +1,6 @@
 // a10: serving loop -- a resident representative library and continuously
-// batched query requests (cosine mode, FFT phase-correlation engine).
+// batched query requests (cosine mode with the FFT phase-correlation engine,
+// or edge mode with the Min-Max procedure).
 //
 // The library's rasters, signatures and spectra stay in device memory, with
 // its clips sorted by area once.  Each admitted request gets a slot: its own
@@ -34,6 +35,8 @@ cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long lon
 cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                              int, cudaStream_t);
 size_t cross_join_workspace(uint32_t);
+cudaError_t launch_edge_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *, pcl_record *,
+                              uint64_t, unsigned long long *, int, cudaStream_t);
 cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
                               const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
                               unsigned long long *, unsigned long long *, int, cudaStream_t);
@@ -135,7 +138,7 @@ struct pcl_server {
 namespace {
 
 // device bytes of one request of nq clips and R rectangles with candidate capacity cap
-size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap) {
+size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap, bool edge) {
     size_t b = 0;
     b += align256(4ull * (nq + 1));                 // rect_off
     b += align256(16ull * (R ? R : 1));             // rects
@@ -146,16 +149,16 @@ size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap) {
     b += align256(32ull * nq);                      // esig
     b += align256(512ull * nq);                     // occ
     b += align256(2ull * (R ? R : 1));              // rorder
-    b += align256(8ull * nq * g.L * g.Ls);          // spec
+    b += edge ? 0 : align256(8ull * nq * g.L * g.Ls);  // spec (cosine only)
     b += align256(nq);                              // spec_state
     b += align256(8ull * cap) * 2;                  // cand, pass
     b += align256(40ull * cap);                     // records
     b += align256(64);                              // counts
-    b += align256(pcl::cross_join_workspace(nq));   // join workspace
+    b += edge ? 0 : align256(pcl::cross_join_workspace(nq));  // band-join workspace (cosine only)
     return b;
 }
 
-void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint64_t cap) {
+void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint64_t cap, bool edge) {
     char *p = base;
     auto take = [&](size_t n) {
         char *r = p;
@@ -172,14 +175,14 @@ void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint
     s.q.esig = reinterpret_cast<int32_t *>(take(32ull * nq));
     s.q.occ = reinterpret_cast<uint64_t *>(take(512ull * nq));
     s.q.rorder = reinterpret_cast<uint16_t *>(take(2ull * (R ? R : 1)));
-    s.q.spec = take(8ull * nq * g.L * g.Ls);
+    s.q.spec = edge ? nullptr : take(8ull * nq * g.L * g.Ls);
     s.q.spec_state = reinterpret_cast<uint8_t *>(take(nq));
     s.cand = reinterpret_cast<pcl_pair *>(take(8ull * cap));
     s.pass = reinterpret_cast<pcl_pair *>(take(8ull * cap));
     s.rec = reinterpret_cast<pcl_record *>(take(40ull * cap));
     s.counts = reinterpret_cast<unsigned long long *>(take(64));
-    s.ws_bytes = pcl::cross_join_workspace(nq);
-    s.ws = take(s.ws_bytes);
+    s.ws_bytes = edge ? 0 : pcl::cross_join_workspace(nq);
+    s.ws = edge ? nullptr : take(s.ws_bytes);
 }
 
 pcl_status fail(pcl_ctx *ctx, pcl_status s, const std::string &m) {
@@ -200,12 +203,21 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
     if (!cfg || !library || cfg->max_inflight == 0 || cfg->max_inflight > 64 || cfg->max_query_clips == 0 ||
         cfg->cand_per_query == 0)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: invalid configuration");
-    if (!library->spec || !library->spec_state || !library->pop || !library->blk || !library->prof ||
-        !library->bits)
-        return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters, signatures and spectra");
+    const bool edge = cfg->mode == PCL_MODE_EDGE;
+    if (cfg->mode != 0 && cfg->mode != PCL_MODE_COSINE && !edge)
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: mode must be PCL_MODE_COSINE or PCL_MODE_EDGE");
     const pcl::Geo g = pcl::make_geo(*P);
-    if (g.N > 256 || g.S > g.N / 16)
-        return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+    if (edge) {
+        if (!library->rect_off || !library->rects || !library->bits || !library->esig || !library->occ ||
+            !library->rorder)
+            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: edge library needs rectangles and edge signatures");
+    } else {
+        if (!library->spec || !library->spec_state || !library->pop || !library->blk || !library->prof ||
+            !library->bits)
+            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters, signatures and spectra");
+        if (g.N > 256 || g.S > g.N / 16)
+            return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+    }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail(ctx, PCL_ERR_CUDA, "cudaSetDevice");
     pcl_server *s = new (std::nothrow) pcl_server;
@@ -228,11 +240,13 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
         return cleanup(PCL_ERR_OOM, "pcl_server_create: device allocation failed");
     }
     s->arena.init(s->arena_mem, cfg->mem_budget);
-    // resident library: spectra of every clip and the area order, once
-    e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
-    if (e == cudaSuccess)
-        e = pcl::launch_area_sort(library->pop, nl, V, s->lib_cum, s->lib_fill, s->lib_order, s->lib_spop,
-                                  ctx->num_sms, 0);
+    // resident library (cosine): spectra of every clip and the area order, once
+    if (!edge) {
+        e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
+        if (e == cudaSuccess)
+            e = pcl::launch_area_sort(library->pop, nl, V, s->lib_cum, s->lib_fill, s->lib_order, s->lib_spop,
+                                      ctx->num_sms, 0);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(PCL_ERR_CUDA, std::string("library preparation: ") + cudaGetErrorString(e));
     s->slots.resize(cfg->max_inflight);
@@ -272,7 +286,8 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         }
     if (!sl) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: no free slot");
     const uint64_t cap = (uint64_t)s->cfg.cand_per_query * n_clips + 64;
-    const size_t bytes = footprint(s->g, n_clips, R, cap);
+    const bool edge = s->cfg.mode == PCL_MODE_EDGE;
+    const size_t bytes = footprint(s->g, n_clips, R, cap, edge);
     size_t off = 0;
     if (!s->arena.alloc(bytes, &off)) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: memory budget full");
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -286,7 +301,7 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
     sl->overflow.clear();
     sl->t_done = 0;
     sl->t_submit = now_ns();
-    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap);
+    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap, edge);
     std::memcpy(sl->h_off, h_rect_off, 4ull * (n_clips + 1));
     if (R) std::memcpy(sl->h_rects, h_rects, 16ull * R);
     cudaStream_t st = sl->st;
@@ -299,13 +314,20 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         e = cudaMemcpyAsync((void *)sl->q.rects, sl->h_rects, 16ull * R, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->counts, 0, 64, st);
     if (e == cudaSuccess) e = pcl::launch_raster(s->P, sl->q, st);
-    if (e == cudaSuccess)
-        e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws, sl->ws_bytes,
-                                   sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
-    if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
-    if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
-    if (e == cudaSuccess)
-        e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
+    if (edge) {
+        // every (query, library) pair through the edge gates; the survivors'
+        // records come out of the same pass
+        if (e == cudaSuccess)
+            e = pcl::launch_edge_cross(s->P, sl->q, s->lib, sl->cand, sl->rec, cap, sl->counts + 0, ctx->num_sms, st);
+    } else {
+        if (e == cudaSuccess)
+            e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws,
+                                       sl->ws_bytes, sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
+        if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
+        if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
+        if (e == cudaSuccess)
+            e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
+    }
     if (e == cudaSuccess) e = pcl::launch_compact(sl->rec, cap, sl->counts + 0, sl->pass, cap, sl->counts + 1, st);
     const uint32_t pass_copy = s->cfg.pass_copy ? s->cfg.pass_copy : 1;
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_counts, sl->counts, 16, cudaMemcpyDeviceToHost, st);

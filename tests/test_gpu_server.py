@@ -148,3 +148,36 @@ def test_admission_by_budget_and_slots(served):
         big = synth.from_lists([[[0, 0, 10, 10]]] * 600, lib.window_dbu, lib.pitch_dbu, lib.marker_dbu)
         b.submit(big.rect_off, big.rects, 9)
     b.close()
+
+
+@pytest.mark.parametrize("tol", [4, 12])
+def test_edge_served_results_equal_oracle(served, tol):
+    """Edge-mode server: every (query, library) pair through the edge gates and
+    the Min-Max procedure; candidates and pass pairs equal the oracle's, alone
+    and for several requests in flight."""
+    pcl = served["pcl"]
+    lib, ctx, reqs = served["lib"], served["ctx"], served["reqs"]
+    P = pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, edge_tol_dbu=tol)
+    cs = pcl.alloc_clipset(P, lib.rect_off, lib.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    srv = pcl.Server(ctx, P, cs, max_inflight=4, max_query_clips=512, cand_per_query=2048,
+                     mem_budget=1 << 30, mode=pcl.MODE_EDGE)
+    for k, q in enumerate(reqs[:4]):  # 1, 7, 64 and 200 queries
+        assert srv.submit(q.rect_off, q.rects, 10 + k)
+    got = _wait_all(srv, [10 + k for k in range(4)])
+    total_pass = 0
+    for k, q in enumerate(reqs[:4]):
+        res = got[10 + k]
+        assert res["status"] == 0
+        both = synth.from_lists([q.clip(i).tolist() for i in range(q.n)] +
+                                [lib.clip(i).tolist() for i in range(lib.n)], lib.window_dbu, lib.pitch_dbu,
+                                lib.marker_dbu)
+        pairs = np.array([(a, q.n + b) for a in range(q.n) for b in range(lib.n)], dtype=np.int64)
+        o = oracle.ClipSet(both).match(pairs, oracle.MODE_EDGE, edge_tol_dbu=tol)
+        cand = ((o["flags"] & 15) == 0)
+        assert res["n_candidates"] == int(cand.sum())
+        opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
+        assert _pairset(res["pass_pairs"]) == opass
+        total_pass += len(opass)
+    assert total_pass > 0
+    srv.close()
