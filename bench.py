@@ -218,12 +218,14 @@ def serving_requests(wl, n_req: int, seed: int = 7, max_clips: int = 4096):
     return reqs
 
 
-def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0):
+def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
     """Continuous batching against the resident library: a closed-loop burst
     gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it
-    give p50/p99 latency (arrival to device completion)."""
+    give p50/p99 latency (arrival to device completion).  mode: cosine (the
+    FFT engine behind the area band join) or edge (every query x library
+    pair through the edge gates and Min-Max)."""
     srv = pcl.Server(ctx, P, cs, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
-                     cand_per_query=64, mem_budget=24 << 30)
+                     cand_per_query=64 if mode == pcl.MODE_COSINE else 256, mem_budget=24 << 30, mode=mode)
     reqs = serving_requests(wl, 256)
 
     def drive(arrivals):
@@ -272,7 +274,8 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0):
     sat = drive(None)
     rps_sat = sat["requests"] / sat["wall_s"]
     rng = np.random.default_rng(3)
-    out = {"library_clips": wl.n, "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
+    out = {"mode": "cosine" if mode == pcl.MODE_COSINE else "edge", "library_clips": wl.n,
+           "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
     for frac in (0.5, 0.9):
         lam = frac * rps_sat
         n = max(8, int(lam * seconds))
@@ -670,10 +673,11 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- serving: continuous batching of query requests against the clip set
     # as a resident library (p50/p99 latency beside throughput)
-    serving = None
+    serving = serving_edge = None
     if not args.no_serving and world == 1:
         pcl.pcl_rasterize(ctx, P, cs)
         serving = run_serving(pcl, ctx, P, cs, wl)
+        serving_edge = run_serving(pcl, ctx, P, cs, wl, mode=pcl.MODE_EDGE)
         pcl.pcl_rasterize(ctx, P, cs)
         torch.cuda.synchronize()
 
@@ -768,6 +772,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
         "host_loop": host_loop,
         "serving": serving,
+        "serving_edge": serving_edge,
         "batched": batched,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
