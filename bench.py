@@ -58,6 +58,8 @@ def parse():
                     help="override the clip count (seeds and copies scale with it; profiling runs)")
     ap.add_argument("--no-fft-engine", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--library-clips", type=int, default=2_000_000,
+                    help="clips of the large serving library (tensor-core cosine and edge; 0: skip)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-clips", type=int, default=25000, help="clips per size class of the mixed batch")
     return ap.parse_args()
@@ -218,14 +220,17 @@ def serving_requests(wl, n_req: int, seed: int = 7, max_clips: int = 4096):
     return reqs
 
 
-def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
+def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_per_query: int = 0):
     """Continuous batching against the resident library: a closed-loop burst
     gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it
     give p50/p99 latency (arrival to device completion).  mode: cosine (the
-    FFT engine behind the area band join) or edge (every query x library
-    pair through the edge gates and Min-Max)."""
+    engine P names behind the area band join: FFT or tensor-core direct
+    correlation) or edge (every query x library pair through the edge gates
+    and Min-Max)."""
+    if not cand_per_query:
+        cand_per_query = 64 if mode == pcl.MODE_COSINE else 1024
     srv = pcl.Server(ctx, P, cs, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
-                     cand_per_query=64 if mode == pcl.MODE_COSINE else 256, mem_budget=24 << 30, mode=mode)
+                     cand_per_query=cand_per_query, mem_budget=24 << 30, mode=mode)
     reqs = serving_requests(wl, 256)
 
     def drive(arrivals):
@@ -233,7 +238,7 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
         t0 = time.monotonic_ns()
         queue, done, nxt = [], {}, 0
         arr = {}
-        lat, pairs, clips = [], 0, 0
+        lat, pairs, clips, bad = [], 0, 0, 0
         n_total = len(arrivals) if arrivals is not None else None
         deadline = t0 + int(seconds * 1e9)
         rid = 0
@@ -258,6 +263,7 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
                 lat.append((c["t_done_ns"] - arr[c["id"]]) / 1e6)
                 pairs += c["n_candidates"]
                 clips += c["n_queries"]
+                bad += c["status"] != 0  # candidate capacity exceeded (or a device wait ran out)
                 done[c["id"]] = c
             if arrivals is None:
                 if now >= deadline and not queue and len(done) == rid:
@@ -266,7 +272,7 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
                 break
             time.sleep(0.0002)
         wall = (time.monotonic_ns() - t0) / 1e9
-        return dict(requests=len(done), wall_s=wall, pairs_per_s=pairs / wall, query_clips_per_s=clips / wall,
+        return dict(requests=len(done), not_ok=bad, wall_s=wall, pairs_per_s=pairs / wall, query_clips_per_s=clips / wall,
                     p50_ms=float(np.percentile(lat, 50)) if lat else None,
                     p99_ms=float(np.percentile(lat, 99)) if lat else None)
 
@@ -274,7 +280,9 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1):
     sat = drive(None)
     rps_sat = sat["requests"] / sat["wall_s"]
     rng = np.random.default_rng(3)
+    eng = {pcl.ENGINE_FFT_PCM: "fft", pcl.ENGINE_TC_DIRECT: "tc_f16", pcl.ENGINE_TC_DIRECT_FP8: "tc_e4m3"}
     out = {"mode": "cosine" if mode == pcl.MODE_COSINE else "edge", "library_clips": wl.n,
+           "engine": eng.get(P.cos_engine, "?") if mode == pcl.MODE_COSINE else "min-max",
            "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
     for frac in (0.5, 0.9):
         lam = frac * rps_sat
@@ -673,11 +681,35 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- serving: continuous batching of query requests against the clip set
     # as a resident library (p50/p99 latency beside throughput)
-    serving = serving_edge = None
+    serving = serving_edge = serving_tc = serving_large = None
     if not args.no_serving and world == 1:
         pcl.pcl_rasterize(ctx, P, cs)
         serving = run_serving(pcl, ctx, P, cs, wl)
         serving_edge = run_serving(pcl, ctx, P, cs, wl, mode=pcl.MODE_EDGE)
+        # the same library and requests on the tensor-core engine (no spectra)
+        Ptc = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
+                         cos_engine=pcl.ENGINE_TC_DIRECT)
+        serving_tc = run_serving(pcl, ctx, Ptc, cs, wl)
+        if args.library_clips and args.config == "scale":
+            # a resident library of the serving form's size: rasters and
+            # signatures only (the tensor-core engine needs no spectra)
+            import synth
+            t0 = time.time()
+            k = args.library_clips
+            lib = synth.preset("scale", seed=args.seed + 100, n_clips=k, n_seeds=k // 20, n_copies=7 * k // 10)
+            cs_lib = pcl.alloc_clipset(Ptc, lib.rect_off, lib.rects, with_spec=False)
+            pcl.pcl_rasterize(ctx, Ptc, cs_lib)
+            torch.cuda.synchronize()
+            serving_large = {"library_clips": k, "library_device_gb": sum(
+                t.numel() * t.element_size() for t in (cs_lib.rect_off, cs_lib.rects, cs_lib.bits, cs_lib.pop,
+                                                       cs_lib.prof, cs_lib.blk, cs_lib.esig, cs_lib.occ,
+                                                       cs_lib.rorder)) / 1e9,
+                             "setup_s": time.time() - t0,
+                             "cosine": run_serving(pcl, ctx, Ptc, cs_lib, lib, cand_per_query=256),
+                             "edge": run_serving(pcl, ctx, P, cs_lib, lib, mode=pcl.MODE_EDGE,
+                                                 cand_per_query=8192)}
+            del cs_lib, lib
+            torch.cuda.empty_cache()
         pcl.pcl_rasterize(ctx, P, cs)
         torch.cuda.synchronize()
 
@@ -773,6 +805,8 @@ def run_ours(args, rank, world, local_rank):
         "host_loop": host_loop,
         "serving": serving,
         "serving_edge": serving_edge,
+        "serving_tc": serving_tc,
+        "serving_large_library": serving_large,
         "batched": batched,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4

@@ -344,11 +344,14 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
 
 /* ---- a10: serving loop ----------------------------------------------------
    A resident representative library and continuously batched query requests
-   (cfg mode COSINE: FFT phase-correlation engine; EDGE: Min-Max procedure).
-   For COSINE, pcl_server_create computes the library's spectra (all clips;
-   the library must be rasterised and own spec/spec_state buffers) and sorts
-   it by area; an EDGE library needs its rasters and edge signatures only
-   (esig, occ, rorder).  It then allocates max_inflight
+   (cfg mode COSINE: the engine P->cos_engine names, PCL_ENGINE_FFT_PCM or
+   PCL_ENGINE_TC_DIRECT(_FP8); EDGE: Min-Max procedure).  For COSINE the
+   library must be rasterised (bits, pop, prof, blk) and pcl_server_create
+   sorts it by area; with the FFT engine it also computes the spectra of all
+   library clips (spec/spec_state buffers required), while the tensor-core
+   engine reads the rasters only (spec may be NULL: ~10.6 KB per 256^2 clip
+   instead of ~350 KB, so 2,000,000 library clips fit in ~21 GB).  An EDGE
+   library needs its rasters and edge signatures only (esig, occ, rorder).  It then allocates max_inflight
    request slots (one stream each, pinned staging) and one device arena of
    mem_budget bytes.  pcl_server_submit admits a request of n_clips query
    clips (host rectangles, copied before return) when a slot is free and its
@@ -357,17 +360,23 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
    (resubmit after a poll/release); the request then runs asynchronously:
    rasterisation, query x library band join with the G1/G3/G2 gates,
    spectra of the referenced query clips, phase-correlation matching with
-   the exact decision, pass compaction and the copy of the pass list back
+   the exact decision (tensor-core engine: the candidates grouped by query
+   clip through the direct correlation, exact argmax; its workspace of
+   20 bytes per candidate slot shares the band join's), pass compaction and
+   the copy of the pass list back
    (EDGE: every query x library pair through E2 and E1 one pair per lane, the
    Min-Max record of each survivor by a whole warp, pass compaction, copy).
    pcl_server_poll returns finished requests (pass pairs are
    (query index, library index), in server-owned host memory valid until
    pcl_server_release frees the request's slot and arena region); a request
-   whose candidates exceeded its capacity completes with PCL_ERR_BUSY.
+   whose candidates exceeded its capacity completes with PCL_ERR_BUSY, and one
+   whose tensor-core wait ran out (records not valid) with PCL_ERR_TIMEOUT.
    Timestamps are steady-clock nanoseconds: submit, and device completion as
    stamped by a host callback on the request's stream.  One host thread at a
    time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with
-   N > 256 or S > N/16), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not
+   the FFT engine and N > 256 or S > N/16; the tensor-core engine outside
+   (N, S) = (64, 4), (128, 8), (256, 16) or with a shift rule other than
+   EXACT_ARGMAX; any other cosine engine), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not
    admitted). */
 typedef struct pcl_server pcl_server;
 
@@ -384,7 +393,7 @@ typedef struct pcl_server_cfg {
 
 typedef struct pcl_completion {
     uint64_t request_id;
-    int32_t status;        /* PCL_OK or PCL_ERR_BUSY (candidate capacity exceeded) */
+    int32_t status;        /* PCL_OK, PCL_ERR_BUSY (candidate capacity exceeded) or PCL_ERR_TIMEOUT */
     uint32_t n_queries;
     uint64_t n_candidates; /* pairs that reached the alignment engine */
     uint64_t n_pass;

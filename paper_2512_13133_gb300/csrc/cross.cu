@@ -4,23 +4,32 @@
 // The library is sorted by area once (launch_area_sort).  For a query of
 // area a the G1 survivors are exactly the library clips with area in
 // [floor(num^2 a / den^2) + 1, floor((den^2 a - 1) / num^2)], a contiguous range
-// of the sorted order.  Each query's range is cut into chunks of kChunk
-// positions; warps take (query, chunk) items from a global counter and test
-// G3 and G2 on every member with the whole warp, as in the self-join.
+// of the sorted order.  The queries of a request are sorted by area too, so
+// both ends of their bands are monotone and the queries whose band meets a
+// library chunk (kChunk sorted positions) are a contiguous run of them.  Work
+// items are (chunk, query) pairs in chunk-major order: the warps in flight
+// at any moment cover a few neighbouring chunks with all their queries, so
+// each chunk's signatures come from DRAM about once per request and are
+// re-read from L2 by the other queries (a band of a large library is larger
+// than L2, and query-major order re-fetched it from DRAM for every query).
+// Each warp tests G3 and G2 on every member of its item, as in the self-join.
 #include "gates.cuh"
 
 namespace pcl {
+
+cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
+                             int, cudaStream_t);
 
 namespace {
 
 constexpr uint32_t kChunk = 1024;
 
-// per query: first sorted position, end position, chunk count
-__global__ void cross_prep_kernel(const uint32_t *qpop, uint32_t nq, const uint32_t *lib_cum, uint32_t vmax_all,
-                                  uint32_t num, uint32_t den, uint32_t *beg, uint32_t *end, uint32_t *nch) {
+// per query, in area order (position i): first and end position of its band
+__global__ void cross_prep_kernel(const uint32_t *qspop, uint32_t nq, const uint32_t *lib_cum, uint32_t vmax_all,
+                                  uint32_t num, uint32_t den, uint32_t *beg, uint32_t *end) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    const uint64_t a = qpop[q];
+    const uint64_t a = qspop[q];
     const uint64_t n2 = (uint64_t)num * num, d2 = (uint64_t)den * den;
     uint64_t lo, hi;
     if (a == 0) {
@@ -31,14 +40,37 @@ __global__ void cross_prep_kernel(const uint32_t *qpop, uint32_t nq, const uint3
         hi = (d2 * a - 1) / n2;
     }
     if (hi > vmax_all) hi = vmax_all;
-    uint32_t b = 0, e = 0;
-    if (lo <= hi) {
-        b = lib_cum[lo];
-        e = lib_cum[hi + 1];
-    }
+    // lo <= hi whenever num < den; an empty band keeps both ends monotone
+    const uint32_t b = lib_cum[lo <= vmax_all + 1 ? lo : vmax_all + 1];
+    const uint32_t e = lo <= hi ? lib_cum[hi + 1] : b;
     beg[q] = b;
     end[q] = e;
-    nch[q] = (e - b + kChunk - 1) / kChunk;
+}
+
+// per library chunk k: the area-order positions [qlo, qlo + cnt) of the
+// queries whose band meets [k kChunk, (k + 1) kChunk) (beg and end are
+// non-decreasing; a query with an empty band inside the run gets an empty item)
+__global__ void cross_chunks_kernel(const uint32_t *beg, const uint32_t *end, uint32_t nq, uint32_t n_ch,
+                                    uint32_t *qlo, uint32_t *cnt) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_ch) return;
+    const uint32_t c0 = k * kChunk, c1 = c0 + kChunk;
+    uint32_t lo = 0, hi = nq;  // first position with end > c0
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (end[mid] > c0) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint32_t a = lo;
+    lo = a;
+    hi = nq;  // first position with beg >= c1
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (beg[mid] >= c1) hi = mid;
+        else lo = mid + 1;
+    }
+    qlo[k] = a;
+    cnt[k] = lo - a;
 }
 
 // exclusive scan of v[0..m) into out[0..m], out[m] = total (single CTA)
@@ -79,13 +111,15 @@ __global__ void __launch_bounds__(1024) scan_items_kernel(const uint32_t *v, uin
 template <int WPL>
 __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
                                                          const uint32_t *lib_order, const uint32_t *lib_spop,
-                                                         const uint32_t *beg, const uint32_t *item_off,
-                                                         pcl_pair *out, uint64_t cap, unsigned long long *count,
-                                                         unsigned long long *local, unsigned int *next_item) {
+                                                         const uint32_t *qorder, const uint32_t *qspop,
+                                                         const uint32_t *beg, const uint32_t *end,
+                                                         const uint32_t *qlo, const uint32_t *item_off,
+                                                         uint32_t n_ch, pcl_pair *out, uint64_t cap,
+                                                         unsigned long long *count, unsigned long long *local,
+                                                         unsigned int *next_item) {
     const Geo g = make_geo(prm);
     const int lane = threadIdx.x & 31;
-    const uint32_t nq = Q.n_clips;
-    const uint32_t total = item_off[nq];
+    const uint32_t total = item_off[n_ch];
     const int nb2 = g.nb * g.nb, words = nb2 / 2;
     unsigned long long kept = 0, g2 = 0, g3 = 0;
     auto emit = [&](bool keep, uint32_t q, uint32_t b) {  // warp-aggregated
@@ -102,18 +136,20 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
         if (lane == 0) t = atomicAdd(next_item, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total) break;
-        // query of item t: last q with item_off[q] <= t
-        uint32_t lo = 0, hi = nq;
+        // chunk of item t: last k with item_off[k] <= t; then its query
+        uint32_t lo = 0, hi = n_ch;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) / 2;
             if (item_off[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const uint32_t q = lo;
-        const uint32_t bend = item_off[nq + 1 + q];  // end of q's band
-        const uint32_t p0 = beg[q] + (t - item_off[q]) * kChunk;
-        const uint32_t p1 = min(p0 + kChunk, bend);
-        const uint64_t pa = Q.pop[q];
+        const uint32_t k = lo;
+        const uint32_t i = qlo[k] + (t - item_off[k]);  // area-order position of the query
+        const uint32_t q = qorder[i];
+        const uint32_t p0 = max(k * kChunk, beg[i]);
+        const uint32_t p1 = min(k * kChunk + kChunk, end[i]);
+        if (p0 >= p1) continue;
+        const uint64_t pa = qspop[i];
         if (pa == 0) {  // the band holds the empty library clips only: similar by definition
             for (uint32_t q0 = p0; q0 < p1; q0 += 32) {
                 const bool v = q0 + lane < p1;
@@ -185,39 +221,51 @@ __global__ void cross_finish_kernel(const unsigned long long *local, unsigned lo
 
 }  // namespace
 
-// workspace of the cross join for nq queries: 16 u64 counters + next item
-// (64 B) + beg[nq] + nch[nq] + item offsets [nq + 1] + band ends [nq]
-size_t cross_join_workspace(uint32_t nq) { return 8 * 16 + 64 + 4 * (4 * (size_t)nq + 2); }
+// workspace of the cross join for nq queries against n_lib library clips:
+// 16 u64 counters + next item (64 B), the queries' area histogram and fill
+// counters [2 V], their area order and sorted areas, band begins and ends
+// [4 nq], per chunk the first query, the item count and the item offsets
+// [3 n_ch + 1]
+static uint32_t lib_chunks(uint32_t n_lib) { return (n_lib + kChunk - 1) / kChunk; }
+size_t cross_join_workspace(const Geo &g, uint32_t nq, uint32_t n_lib) {
+    const size_t V = (size_t)g.N * g.N + 2;
+    return 8 * 16 + 64 + 4 * (2 * V + 4 * (size_t)nq + 3 * (size_t)lib_chunks(n_lib) + 1);
+}
 
 cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const pcl_clipset &L,
                               const uint32_t *lib_order, const uint32_t *lib_spop, const uint32_t *lib_cum,
                               void *ws, size_t ws_bytes, pcl_pair *out, uint64_t cap, unsigned long long *count,
                               unsigned long long *gates, int num_sms, cudaStream_t st) {
     const Geo g = make_geo(prm);
-    const uint32_t nq = Q.n_clips;
-    if (ws_bytes < cross_join_workspace(nq)) return cudaErrorInvalidValue;
+    const uint32_t nq = Q.n_clips, n_ch = lib_chunks(L.n_clips);
+    if (ws_bytes < cross_join_workspace(g, nq, L.n_clips)) return cudaErrorInvalidValue;
+    const uint32_t V = (uint32_t)g.N * g.N + 2;
     char *w = static_cast<char *>(ws);
     unsigned long long *local = reinterpret_cast<unsigned long long *>(w);
     unsigned int *next_item = reinterpret_cast<unsigned int *>(w + 8 * 16);
-    uint32_t *beg = reinterpret_cast<uint32_t *>(w + 8 * 16 + 64);
-    uint32_t *nch = beg + nq;
-    // item_off[0..nq] then band ends at item_off[nq + 1 + q]
-    uint32_t *item_off = nch + nq;
-    uint32_t *endp = item_off + nq + 1;
+    uint32_t *qcum = reinterpret_cast<uint32_t *>(w + 8 * 16 + 64);
+    uint32_t *qfill = qcum + V;
+    uint32_t *qorder = qfill + V, *qspop = qorder + nq, *beg = qspop + nq, *endp = beg + nq;
+    uint32_t *qlo = endp + nq, *cnt = qlo + n_ch, *item_off = cnt + n_ch;
     cudaError_t e = cudaMemsetAsync(w, 0, 8 * 16 + 64, st);
     if (e != cudaSuccess) return e;
-    if (nq) {
-        cross_prep_kernel<<<(nq + 255) / 256, 256, 0, st>>>(Q.pop, nq, lib_cum, (uint32_t)g.N * g.N, prm.cos_num,
-                                                             prm.cos_den, beg, endp, nch);
-        scan_items_kernel<<<1, 1024, 0, st>>>(nch, nq, item_off);
+    if (nq && n_ch) {
+        e = launch_area_sort(Q.pop, nq, V, qcum, qfill, qorder, qspop, num_sms, st);
+        if (e != cudaSuccess) return e;
+        cross_prep_kernel<<<(nq + 255) / 256, 256, 0, st>>>(qspop, nq, lib_cum, (uint32_t)g.N * g.N, prm.cos_num,
+                                                             prm.cos_den, beg, endp);
+        cross_chunks_kernel<<<(n_ch + 255) / 256, 256, 0, st>>>(beg, endp, nq, n_ch, qlo, cnt);
+        scan_items_kernel<<<1, 1024, 0, st>>>(cnt, n_ch, item_off);
         switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
-            case 1: cross_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off,
-                                                                      out, cap, count, local, next_item); break;
-            case 4: cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg, item_off,
-                                                                      out, cap, count, local, next_item); break;
-            case 16: cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, beg,
-                                                                        item_off, out, cap, count, local,
-                                                                        next_item); break;
+            case 1: cross_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,
+                                                                      beg, endp, qlo, item_off, n_ch, out, cap,
+                                                                      count, local, next_item); break;
+            case 4: cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,
+                                                                      beg, endp, qlo, item_off, n_ch, out, cap,
+                                                                      count, local, next_item); break;
+            case 16: cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder,
+                                                                        qspop, beg, endp, qlo, item_off, n_ch, out,
+                                                                        cap, count, local, next_item); break;
             default: return cudaErrorInvalidValue;
         }
     }

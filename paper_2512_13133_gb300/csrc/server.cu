@@ -1,9 +1,12 @@
 // a10: serving loop -- a resident representative library and continuously
-// batched query requests (cosine mode with the FFT phase-correlation engine,
-// or edge mode with the Min-Max procedure).
+// batched query requests (cosine mode with the FFT phase-correlation engine or
+// the tensor-core direct correlation, or edge mode with the Min-Max procedure).
 //
-// The library's rasters, signatures and spectra stay in device memory, with
-// its clips sorted by area once.  Each admitted request gets a slot: its own
+// The library's rasters and signatures stay in device memory (with the FFT
+// engine also its spectra), with its clips sorted by area once.  The
+// tensor-core engine reads the bit-packed rasters only, so its library costs
+// N^2/8 bytes of rasters plus ~2.6 KB of signatures per clip (2,000,000 clips
+// of 256^2 px: ~21 GB) instead of ~350 KB with spectra.  Each admitted request gets a slot: its own
 // stream and a region of a fixed device arena holding the query clip set,
 // candidates and records.  Admission needs a free slot and room in the arena
 // (the memory budget), so requests that arrive while others run are admitted
@@ -11,7 +14,9 @@
 // request's work: host->device copy of its rectangles, rasterisation,
 // query x library candidate join, spectra of the referenced query clips,
 // phase-correlation matching, pass compaction, device->host copy of the pass
-// list; a host callback on the stream stamps the completion time.
+// list; a host callback on the stream stamps the completion time.  With the
+// tensor-core engine the spectra and phase-correlation steps are replaced by
+// the grouped direct correlation of the candidates (exact argmax).
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -34,7 +39,11 @@ cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long lon
                            unsigned long long *, cudaStream_t);
 cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                              int, cudaStream_t);
-size_t cross_join_workspace(uint32_t);
+size_t cross_join_workspace(const Geo &, uint32_t, uint32_t);
+bool tc_supported(const Geo &);
+size_t tc_workspace(uint64_t);
+cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
 cudaError_t launch_edge_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *, pcl_record *,
                               uint64_t, unsigned long long *, int, cudaStream_t);
 cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
@@ -104,7 +113,7 @@ struct Slot {
     pcl_clipset q{};
     pcl_pair *cand = nullptr, *pass = nullptr;
     pcl_record *rec = nullptr;
-    unsigned long long *counts = nullptr;  // [0] candidates, [1] pass
+    unsigned long long *counts = nullptr;  // [0] candidates, [1] pass, [2] device error word of the request
     void *ws = nullptr;
     size_t ws_bytes = 0;
     // pinned host staging
@@ -128,6 +137,7 @@ struct pcl_server {
     pcl::Geo g{};
     pcl_server_cfg cfg{};
     pcl_clipset lib{};
+    int engine = 0;  // kEdge, kFft or kTc
     uint32_t *lib_cum = nullptr, *lib_fill = nullptr, *lib_order = nullptr, *lib_spop = nullptr;
     char *arena_mem = nullptr;
     Arena arena;
@@ -137,8 +147,21 @@ struct pcl_server {
 
 namespace {
 
+// request pipelines
+constexpr int kEdge = 0, kFft = 1, kTc = 2;
+
+// workspace of a cosine request: the band join's, then (same stream, after
+// it) the tensor-core engine's grouping buffers in the same bytes
+size_t request_ws(const pcl::Geo &g, int engine, uint32_t nq, uint32_t n_lib, uint64_t cap) {
+    if (engine == kEdge) return 0;
+    const size_t cj = pcl::cross_join_workspace(g, nq, n_lib);
+    if (engine == kFft) return cj;
+    const size_t tc = pcl::tc_workspace(cap);
+    return cj > tc ? cj : tc;
+}
+
 // device bytes of one request of nq clips and R rectangles with candidate capacity cap
-size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap, bool edge) {
+size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap, int engine, uint32_t n_lib) {
     size_t b = 0;
     b += align256(4ull * (nq + 1));                 // rect_off
     b += align256(16ull * (R ? R : 1));             // rects
@@ -149,16 +172,17 @@ size_t footprint(const pcl::Geo &g, uint32_t nq, uint64_t R, uint64_t cap, bool 
     b += align256(32ull * nq);                      // esig
     b += align256(512ull * nq);                     // occ
     b += align256(2ull * (R ? R : 1));              // rorder
-    b += edge ? 0 : align256(8ull * nq * g.L * g.Ls);  // spec (cosine only)
+    b += engine == kFft ? align256(8ull * nq * g.L * g.Ls) : 0;  // spec (FFT engine only)
     b += align256(nq);                              // spec_state
     b += align256(8ull * cap) * 2;                  // cand, pass
     b += align256(40ull * cap);                     // records
     b += align256(64);                              // counts
-    b += edge ? 0 : align256(pcl::cross_join_workspace(nq));  // band-join workspace (cosine only)
+    b += align256(request_ws(g, engine, nq, n_lib, cap));     // band join / tensor-core workspace (cosine only)
     return b;
 }
 
-void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint64_t cap, bool edge) {
+void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint64_t cap, int engine,
+           uint32_t n_lib) {
     char *p = base;
     auto take = [&](size_t n) {
         char *r = p;
@@ -175,14 +199,14 @@ void carve(Slot &s, const pcl::Geo &g, char *base, uint32_t nq, uint64_t R, uint
     s.q.esig = reinterpret_cast<int32_t *>(take(32ull * nq));
     s.q.occ = reinterpret_cast<uint64_t *>(take(512ull * nq));
     s.q.rorder = reinterpret_cast<uint16_t *>(take(2ull * (R ? R : 1)));
-    s.q.spec = edge ? nullptr : take(8ull * nq * g.L * g.Ls);
+    s.q.spec = engine == kFft ? take(8ull * nq * g.L * g.Ls) : nullptr;
     s.q.spec_state = reinterpret_cast<uint8_t *>(take(nq));
     s.cand = reinterpret_cast<pcl_pair *>(take(8ull * cap));
     s.pass = reinterpret_cast<pcl_pair *>(take(8ull * cap));
     s.rec = reinterpret_cast<pcl_record *>(take(40ull * cap));
     s.counts = reinterpret_cast<unsigned long long *>(take(64));
-    s.ws_bytes = edge ? 0 : pcl::cross_join_workspace(nq);
-    s.ws = edge ? nullptr : take(s.ws_bytes);
+    s.ws_bytes = request_ws(g, engine, nq, n_lib, cap);
+    s.ws = s.ws_bytes ? take(s.ws_bytes) : nullptr;
 }
 
 pcl_status fail(pcl_ctx *ctx, pcl_status s, const std::string &m) {
@@ -207,16 +231,29 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
     if (cfg->mode != 0 && cfg->mode != PCL_MODE_COSINE && !edge)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: mode must be PCL_MODE_COSINE or PCL_MODE_EDGE");
     const pcl::Geo g = pcl::make_geo(*P);
+    const bool tc = P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8;
+    const int engine = edge ? kEdge : (tc ? kTc : kFft);
     if (edge) {
         if (!library->rect_off || !library->rects || !library->bits || !library->esig || !library->occ ||
             !library->rorder)
             return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: edge library needs rectangles and edge signatures");
     } else {
-        if (!library->spec || !library->spec_state || !library->pop || !library->blk || !library->prof ||
-            !library->bits)
-            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters, signatures and spectra");
-        if (g.N > 256 || g.S > g.N / 16)
-            return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+        if (!library->pop || !library->blk || !library->prof || !library->bits)
+            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters and signatures");
+        if (tc) {
+            if (!pcl::tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+                return fail(ctx, PCL_ERR_UNSUPPORTED,
+                            "pcl_server_create: tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), "
+                            "exact argmax");
+        } else {
+            if (P->cos_engine != PCL_ENGINE_FFT_PCM)
+                return fail(ctx, PCL_ERR_UNSUPPORTED,
+                            "pcl_server_create: cosine serving takes the FFT or the tensor-core engine");
+            if (!library->spec || !library->spec_state)
+                return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: FFT engine needs the library's spectra");
+            if (g.N > 256 || g.S > g.N / 16)
+                return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+        }
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail(ctx, PCL_ERR_CUDA, "cudaSetDevice");
@@ -227,6 +264,7 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
     s->g = g;
     s->cfg = *cfg;
     s->lib = *library;
+    s->engine = engine;
     const uint32_t V = (uint32_t)g.N * g.N + 2;
     const uint32_t nl = library->n_clips;
     auto cleanup = [&](pcl_status st, const std::string &m) {
@@ -240,9 +278,10 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
         return cleanup(PCL_ERR_OOM, "pcl_server_create: device allocation failed");
     }
     s->arena.init(s->arena_mem, cfg->mem_budget);
-    // resident library (cosine): spectra of every clip and the area order, once
+    // resident library (cosine): the area order, and with the FFT engine the
+    // spectra of every clip, once
     if (!edge) {
-        e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
+        if (engine == kFft) e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
         if (e == cudaSuccess)
             e = pcl::launch_area_sort(library->pop, nl, V, s->lib_cum, s->lib_fill, s->lib_order, s->lib_spop,
                                       ctx->num_sms, 0);
@@ -286,8 +325,7 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         }
     if (!sl) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: no free slot");
     const uint64_t cap = (uint64_t)s->cfg.cand_per_query * n_clips + 64;
-    const bool edge = s->cfg.mode == PCL_MODE_EDGE;
-    const size_t bytes = footprint(s->g, n_clips, R, cap, edge);
+    const size_t bytes = footprint(s->g, n_clips, R, cap, s->engine, s->lib.n_clips);
     size_t off = 0;
     if (!s->arena.alloc(bytes, &off)) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: memory budget full");
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -301,7 +339,7 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
     sl->overflow.clear();
     sl->t_done = 0;
     sl->t_submit = now_ns();
-    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap, edge);
+    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap, s->engine, s->lib.n_clips);
     std::memcpy(sl->h_off, h_rect_off, 4ull * (n_clips + 1));
     if (R) std::memcpy(sl->h_rects, h_rects, 16ull * R);
     cudaStream_t st = sl->st;
@@ -314,7 +352,7 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         e = cudaMemcpyAsync((void *)sl->q.rects, sl->h_rects, 16ull * R, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->counts, 0, 64, st);
     if (e == cudaSuccess) e = pcl::launch_raster(s->P, sl->q, st);
-    if (edge) {
+    if (s->engine == kEdge) {
         // every (query, library) pair through the edge gates; the survivors'
         // records come out of the same pass
         if (e == cudaSuccess)
@@ -323,14 +361,23 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         if (e == cudaSuccess)
             e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws,
                                        sl->ws_bytes, sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
-        if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
-        if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
-        if (e == cudaSuccess)
-            e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
+        if (s->engine == kTc) {
+            // candidates grouped by query clip through the direct correlation;
+            // a bounded wait that runs out sets the request's own error word
+            if (e == cudaSuccess)
+                e = pcl::launch_tc(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, sl->ws, sl->ws_bytes,
+                                   ctx->num_sms, reinterpret_cast<int *>(sl->counts + 2), st);
+        } else {
+            if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
+            if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
+            if (e == cudaSuccess)
+                e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms,
+                                         st);
+        }
     }
     if (e == cudaSuccess) e = pcl::launch_compact(sl->rec, cap, sl->counts + 0, sl->pass, cap, sl->counts + 1, st);
     const uint32_t pass_copy = s->cfg.pass_copy ? s->cfg.pass_copy : 1;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_counts, sl->counts, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_counts, sl->counts, 24, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl->h_pass, sl->pass, 8ull * (pass_copy < cap ? pass_copy : cap), cudaMemcpyDeviceToHost,
                             st);
@@ -367,7 +414,7 @@ pcl_status pcl_server_poll(pcl_server *s, pcl_completion *out, uint32_t cap, uin
         } else {
             c.n_candidates = sl.h_counts[0];
             const uint64_t np = sl.h_counts[1];
-            c.status = (c.n_candidates > sl.cap) ? PCL_ERR_BUSY : PCL_OK;
+            c.status = sl.h_counts[2] ? PCL_ERR_TIMEOUT : (c.n_candidates > sl.cap) ? PCL_ERR_BUSY : PCL_OK;
             const uint64_t got = np < sl.cap ? np : sl.cap;
             c.n_pass = got;
             if (got <= pass_copy) {

@@ -181,3 +181,52 @@ def test_edge_served_results_equal_oracle(served, tol):
         total_pass += len(opass)
     assert total_pass > 0
     srv.close()
+
+
+@pytest.mark.parametrize("engine", ["tc_f16", "tc_e4m3"])
+def test_tc_served_results_equal_oracle(served, engine):
+    """Cosine server on the tensor-core engine: a library without spectra (the
+    form that lets a 2,000,000-clip library stay resident); candidates and pass
+    pairs equal the oracle's (exact argmax), alone and with requests in flight
+    together; an engine or rule it does not cover is refused at creation."""
+    pcl = served["pcl"]
+    lib, ctx, reqs = served["lib"], served["ctx"], served["reqs"]
+    eng = pcl.ENGINE_TC_DIRECT if engine == "tc_f16" else pcl.ENGINE_TC_DIRECT_FP8
+    P = pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, cos_num=80, cos_den=100, cos_engine=eng)
+    cs = pcl.alloc_clipset(P, lib.rect_off, lib.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    srv = pcl.Server(ctx, P, cs, max_inflight=4, max_query_clips=512, cand_per_query=2048, mem_budget=1 << 30)
+    got = {}
+    t0 = time.time()
+    for k, q in enumerate(reqs[:5]):  # 1, 7, 64, 200 and 33 queries, up to four in flight
+        while not srv.submit(q.rect_off, q.rects, 10 + k):
+            for c in srv.poll():  # a slot frees when its result is taken
+                got[c["id"]] = c
+            assert time.time() - t0 < 60
+    got.update(_wait_all(srv, [10 + k for k in range(5) if 10 + k not in got]))
+    total_pass = 0
+    for k, q in enumerate(reqs[:5]):
+        res = got[10 + k]
+        assert res["status"] == 0
+        both = synth.from_lists([q.clip(i).tolist() for i in range(q.n)] +
+                                [lib.clip(i).tolist() for i in range(lib.n)], lib.window_dbu, lib.pitch_dbu,
+                                lib.marker_dbu)
+        pairs = np.array([(a, q.n + b) for a in range(q.n) for b in range(lib.n)], dtype=np.int64)
+        o = oracle.ClipSet(both).match(pairs, oracle.MODE_COSINE, cos_num=80, cos_den=100)
+        assert res["n_candidates"] == int(((o["flags"] & 15) == 0).sum())
+        opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
+        assert _pairset(res["pass_pairs"]) == opass
+        total_pass += len(opass)
+    assert total_pass >= sum(q.n for q in reqs[:5])
+    srv.close()
+    # the FFT engine still needs the library's spectra; other engines and rules are refused
+    with pytest.raises(pcl.PclError):
+        pcl.Server(ctx, pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu), cs, max_inflight=1,
+                   max_query_clips=8, mem_budget=1 << 26)
+    with pytest.raises(pcl.PclError):
+        pcl.Server(ctx, pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, cos_engine=pcl.ENGINE_XYSEP),
+                   cs, max_inflight=1, max_query_clips=8, mem_budget=1 << 26)
+    with pytest.raises(pcl.PclError):
+        pcl.Server(ctx, pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, cos_engine=eng,
+                                   shift_rule=pcl.SHIFT_PCM_PEAK), cs, max_inflight=1, max_query_clips=8,
+                   mem_budget=1 << 26)
