@@ -230,3 +230,60 @@ def test_tc_served_results_equal_oracle(served, engine):
         pcl.Server(ctx, pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu, cos_engine=eng,
                                    shift_rule=pcl.SHIFT_PCM_PEAK), cs, max_inflight=1, max_query_clips=8,
                    mem_budget=1 << 26)
+
+
+def _pass_check(q, lib, res_pass, idx, mode, **kw):
+    """the pass pairs the server returned against library clips idx (sorted),
+    and the oracle's pass pairs of every query against those clips"""
+    sub = lib.subset(idx)
+    both = synth.from_lists([q.clip(i).tolist() for i in range(q.n)] + [sub.clip(i).tolist() for i in range(sub.n)],
+                            lib.window_dbu, lib.pitch_dbu, lib.marker_dbu)
+    a, b = np.meshgrid(np.arange(q.n), np.arange(sub.n), indexing="ij")
+    pairs = np.stack([a.ravel(), q.n + b.ravel()], axis=1).astype(np.int64)
+    o = oracle.ClipSet(both).match(pairs, mode, **kw)
+    opass = {(int(x), int(idx[y - q.n])) for x, y in pairs[o["pass_"] == 1]}
+    inset = set(idx.tolist())
+    mine = {(int(x), int(y)) for x, y in np.asarray(res_pass, dtype=np.int64) if int(y) in inset}
+    return mine, opass
+
+
+@pytest.mark.parametrize("mode", ["cosine_tc", "edge"])
+def test_full_size_library_sampled_parity(torch_cuda, mode):
+    """Serving form at full size, in the configuration the benchmark serves
+    with: a resident library of 2,000,000 clips of 256^2 px (the tensor-core
+    cosine engine needs no spectra) and a request of 48 query clips moved
+    from library clips.  Every pass pair the server returns passes in the
+    oracle, and against a sample of 4,000 library clips plus the queries'
+    sources the server returns exactly the oracle's pass pairs."""
+    import paper_2512_13133_gb300 as pcl
+    k = 2_000_000
+    lib = synth.preset("scale", seed=101, n_clips=k, n_seeds=k // 20, n_copies=7 * k // 10)
+    ctx = pcl.Context(0)
+    cosine = mode == "cosine_tc"
+    kw = dict(cos_num=80, cos_den=100) if cosine else dict(edge_tol_dbu=12)
+    P = pcl.params(lib.window_dbu, lib.pitch_dbu, lib.marker_dbu,
+                   cos_engine=pcl.ENGINE_TC_DIRECT if cosine else pcl.ENGINE_FFT_PCM, **kw)
+    cs = pcl.alloc_clipset(P, lib.rect_off, lib.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    srv = pcl.Server(ctx, P, cs, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
+                     cand_per_query=256 if cosine else 8192, mem_budget=24 << 30,
+                     mode=pcl.MODE_COSINE if cosine else pcl.MODE_EDGE)
+    rng = np.random.default_rng(11)
+    src = rng.choice(lib.n, 48, replace=False)
+    q = _translated_queries(lib, src, rng, lib.window_dbu)
+    assert srv.submit(q.rect_off, q.rects, 1)
+    res = _wait_all(srv, [1], timeout=120)[1]
+    srv.close()
+    assert res["status"] == 0
+    got = res["pass_pairs"].astype(np.int64)
+    omode = oracle.MODE_COSINE if cosine else oracle.MODE_EDGE
+    # every returned pass passes in the oracle
+    ids = np.unique(got[:, 1]) if len(got) else np.zeros(0, np.int64)
+    mine, opass = _pass_check(q, lib, got, ids, omode, **kw)
+    assert mine == {(int(x), int(y)) for x, y in got}
+    assert mine <= opass
+    # completeness on the sample
+    sample = np.unique(np.concatenate([rng.choice(lib.n, 4000, replace=False), src]))
+    mine, opass = _pass_check(q, lib, got, sample, omode, **kw)
+    assert mine == opass
+    assert len(opass) >= 24  # most queries pass against their source clip
