@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--library-clips", type=int, default=2_000_000,
                     help="clips of the large serving library (tensor-core cosine and edge; 0: skip)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--precision-sample", type=int, default=100_000,
+                    help="same-seed pairs checked against the FP64 oracle per engine (0: skip)")
     ap.add_argument("--batch-clips", type=int, default=25000, help="clips per size class of the mixed batch")
     return ap.parse_args()
 
@@ -295,6 +297,64 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
         out["poisson"].append(r)
     srv.close()
     return out
+
+
+def _precision_worker(job):
+    """Oracle records (exact argmax, FP64 similarity) of one shard of the
+    precision sample: the shard's clips only, one host thread."""
+    sub, local, cos_num, cos_den = job
+    import oracle
+    o = oracle.ClipSet(sub).match(local, oracle.MODE_COSINE, threads=1, use_gates=False,
+                                  cos_num=cos_num, cos_den=cos_den)
+    return {f: o[f].copy() for f in ("dx_dbu", "dy_dbu", "score", "sim", "pass_")}
+
+
+def precision_report(wl, fp, recs_by_engine, sample: int, near_bit: int, seed: int = 5):
+    """Per-result error against the FP64 oracle on a seeded sample of the
+    same-seed list fp (whole seed groups, so each oracle shard rasterises
+    only its own clips): shift, overlap and decision mismatches and the
+    distribution of |sim - sim_fp64| for every engine's records of fp."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    rng = np.random.default_rng(seed)
+    grp = wl.label[fp[:, 0]].astype(np.int64)
+    labels = rng.permutation(np.unique(grp))
+    cnt = np.bincount(grp, minlength=int(grp.max()) + 1)
+    k = int(np.searchsorted(np.cumsum(cnt[labels]), sample)) + 1
+    chosen = np.isin(grp, labels[:k])
+    rows = np.flatnonzero(chosen)
+    if len(rows) > sample:
+        rows = np.sort(rng.choice(rows, sample, replace=False))
+    workers = max(1, min(16, os.cpu_count() or 1))
+    shards = np.array_split(np.sort(np.unique(grp[rows])), workers)
+    jobs, parts = [], []
+    for sh in shards:
+        r = rows[np.isin(grp[rows], sh)]
+        if not len(r):
+            continue
+        ids = np.unique(fp[r].ravel())
+        loc = np.searchsorted(ids, fp[r])
+        jobs.append((wl.subset(ids), loc.astype(np.int64), COS_NUM, COS_DEN))
+        parts.append(r)
+    t0 = time.time()
+    # spawned workers (no fork after CUDA initialisation); a worker that dies
+    # raises instead of leaving the map waiting
+    with ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as pool:
+        outs = list(pool.map(_precision_worker, jobs))
+    o = {f: np.concatenate([x[f] for x in outs]) for f in outs[0]}
+    r = np.concatenate(parts)
+    rep = {"sample_pairs": int(len(r)), "clips": int(sum(j[0].n for j in jobs)), "oracle_s": time.time() - t0,
+           "oracle_threads": len(jobs)}
+    for name, g in recs_by_engine.items():
+        g = g[r]
+        err = np.abs(g["sim"].astype(np.float64) - o["sim"])
+        rep[name] = {"shift_mismatch": int(((g["dx_dbu"] != o["dx_dbu"]) | (g["dy_dbu"] != o["dy_dbu"])).sum()),
+                     "overlap_mismatch": int((g["score"].astype(np.int64) != o["score"]).sum()),
+                     "decision_mismatch": int((g["pass_"] != o["pass_"]).sum()),
+                     "sim_abs_err_max": float(err.max()), "sim_abs_err_mean": float(err.mean()),
+                     "sim_abs_err_p99": float(np.percentile(err, 99)),
+                     "near_band": int(((g["flags"] & near_bit) > 0).sum())}
+    return rep
 
 
 def run_batched(pcl, ctx, dev, clips_per_class: int, steps: int, seed: int = 1):
@@ -612,6 +672,7 @@ def run_ours(args, rank, world, local_rank):
         dense = np.stack([np.repeat(reps, 32), rngd.integers(0, wl.n, 4096 * 32)], 1)
         dense = dense[dense[:, 0] != dense[:, 1]].astype(np.int32)
         tc = {}
+        same_seed_recs = {"fft": recs}
         for eng_name, eng, peak_mult in (("f16", pcl.ENGINE_TC_DIRECT, 1.0), ("e4m3", pcl.ENGINE_TC_DIRECT_FP8, 2.0)):
             Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
                             cos_engine=eng, flags=pcl.P_NO_GATES)
@@ -639,12 +700,17 @@ def run_ours(args, rank, world, local_rank):
                            "frac_of_peak": flop / (ms / 1e3) / 1e12 / (pk["bf16_tflops"] * peak_mult)}
                 if name == "same_seed":
                     rt = pcl.records_to_numpy(rl)
+                    same_seed_recs[f"tc_{eng_name}"] = rt
                     tc[key]["agrees_with_fft"] = bool((rt["score"] == recs["score"]).all() and
                                                       (rt["dx_dbu"] == recs["dx_dbu"]).all() and
                                                       (rt["dy_dbu"] == recs["dy_dbu"]).all() and
                                                       (rt["pass_"] == recs["pass_"]).all())
         tc["device_error"] = pcl.pcl_device_error(ctx)
         fft["tc_engine"] = tc
+        # per-result error against the FP64 oracle (the precision form's report)
+        if args.precision_sample and rank == 0:
+            fft["precision_vs_fp64_oracle"] = precision_report(wl, fp.astype(np.int64), same_seed_recs,
+                                                               args.precision_sample, pcl.F_NEAR_BAND)
         # the interval-competition shift (Sec. 3.2.1 (2)) on the same list:
         # speed, and what it loses against the exact argmax of the FFT engine
         Px = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
