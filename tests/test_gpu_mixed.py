@@ -137,3 +137,65 @@ def test_mixed_without_gates_and_pcm_rule(torch_cuda):
                 np.testing.assert_array_equal(g["flags"][sel] & 0x39F, r["flags"] & 0x39F)
         if flags:
             assert ((g["flags"] & pcl.F_ALIGNED) > 0).sum() > len(pairs) // 2
+
+
+def test_mixed_full_size_sampled_parity(torch_cuda):
+    """Batched form at full size in the launch configuration the benchmark
+    times (autotuned radix and CTAs per SM): 1,000,000 clips (250,000 per
+    size class, 64² to 512²), ~3.6e8 Zipf-listed items of both modes in one
+    persistent launch.  Per class and mode, up to 300 aligned items and 300
+    random ones equal the oracle's records (gate, shift, overlap, decision)."""
+    import paper_2512_13133_gb300 as pcl
+    from paper_2512_13133_gb300 import autotune
+    wls, pairs, modes = synth.batched(1, clips_per_class=250_000)
+    # cosine first; within a mode the generator's (class, a) order is kept
+    order = np.concatenate([np.flatnonzero(modes == 1), np.flatnonzero(modes == 2)])
+    pairs, modes = pairs[order], modes[order]
+    assert len(pairs) > 3e8
+    ctx = pcl.Context(0)
+    Ps, sets = [], []
+    for wl in wls:
+        P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu)
+        Ps.append(P)
+        sets.append(pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=wl.raster_n <= 256))
+    work = np.zeros(len(pairs), dtype=pcl.WORK_DTYPE)
+    work["cls"], work["a"], work["b"], work["mode"] = pairs[:, 0], pairs[:, 1], pairs[:, 2], modes
+    n_cos = int((modes == 1).sum())
+    tw = torch_cuda.from_numpy(work.view(np.uint8).reshape(-1, 12)).cuda()
+    del work
+    out = torch_cuda.empty((len(pairs), 40), dtype=torch_cuda.uint8, device="cuda")
+
+    def raster_all():
+        for P, cs in zip(Ps, sets):
+            pcl.pcl_rasterize(ctx, P, cs)
+
+    raster_all()
+    tune, _ = autotune.tune_mixed(ctx, Ps, sets, tw, n_cos, out, reset=raster_all)
+    raster_all()
+    pcl.pcl_match_mixed(ctx, Ps, sets, tw, n_cos, out, tune)
+    torch_cuda.cuda.synchronize()
+    rng = np.random.default_rng(2)
+    checked = aligned = 0
+    for k, wl in enumerate(wls):
+        for mode in (1, 2):
+            sel = np.flatnonzero((pairs[:, 0] == k) & (modes == mode))
+            if not len(sel):
+                continue
+            probe = sel[rng.choice(len(sel), min(len(sel), 20000), replace=False)]
+            gp = pcl.records_to_numpy(out[torch_cuda.from_numpy(probe).cuda()])
+            al = probe[(gp["flags"] & (1 << 9)) > 0][:300]
+            pick = np.unique(np.concatenate([al, rng.choice(sel, min(300, len(sel)), replace=False)]))
+            g = pcl.records_to_numpy(out[torch_cuda.from_numpy(pick).cuda()])
+            ids = np.unique(pairs[pick, 1:].ravel())
+            loc = np.searchsorted(ids, pairs[pick, 1:])
+            o = oracle.ClipSet(wl.subset(ids)).match(loc, mode)
+            np.testing.assert_array_equal(g["flags"] & 15, o["flags"] & 15, err_msg=f"class {k} mode {mode}")
+            np.testing.assert_array_equal(g["pass_"], o["pass_"], err_msg=f"class {k} mode {mode}")
+            m = (o["flags"] & oracle.F_ALIGNED) > 0
+            for f in ("dx_dbu", "dy_dbu"):
+                np.testing.assert_array_equal(g[f][m], o[f][m], err_msg=f"class {k} mode {mode} {f}")
+            np.testing.assert_array_equal(g["score"][m].astype(np.int64), o["score"][m])
+            assert np.abs(g["sim"][m].astype(np.float64) - o["sim"][m]).max(initial=0) <= 1e-5
+            checked += len(pick)
+            aligned += int(m.sum())
+    assert checked > 3000 and aligned > 1000
