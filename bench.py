@@ -282,7 +282,8 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
     sat = drive(None)
     rps_sat = sat["requests"] / sat["wall_s"]
     rng = np.random.default_rng(3)
-    eng = {pcl.ENGINE_FFT_PCM: "fft", pcl.ENGINE_TC_DIRECT: "tc_f16", pcl.ENGINE_TC_DIRECT_FP8: "tc_e4m3"}
+    eng = {pcl.ENGINE_FFT_PCM: "fft", pcl.ENGINE_TC_DIRECT: "tc_f16", pcl.ENGINE_TC_DIRECT_BF16: "tc_bf16",
+           pcl.ENGINE_TC_DIRECT_FP8: "tc_e4m3"}
     out = {"mode": "cosine" if mode == pcl.MODE_COSINE else "edge", "library_clips": wl.n,
            "engine": eng.get(P.cos_engine, "?") if mode == pcl.MODE_COSINE else "min-max",
            "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
@@ -665,9 +666,9 @@ def run_ours(args, rank, world, local_rank):
                "pcm_agree_rate": float(((recs["flags"] & pcl.F_PCM_AGREES) > 0).mean()) if len(recs) else 0.0,
                "pass": int(recs["pass_"].sum())}
         # the tensor-core direct correlation on the same list and on a dense
-        # list (32 members per representative: full items), FP16 and E4M3
-        # operands (both exact for 0/1 pixels); the roofline denominator is the
-        # measured bf16 peak, times 2 for E4M3 (the nominal dense ratio)
+        # list (32 members per representative: full items), FP16, BF16 and
+        # E4M3 operands (all exact for 0/1 pixels); the roofline denominator is
+        # the measured bf16 peak, times 2 for E4M3 (the nominal dense ratio)
         pk, _ = peaks()
         rngd = np.random.default_rng(5)
         reps = rngd.choice(wl.n, 4096, replace=False)
@@ -675,7 +676,8 @@ def run_ours(args, rank, world, local_rank):
         dense = dense[dense[:, 0] != dense[:, 1]].astype(np.int32)
         tc = {}
         same_seed_recs = {"fft": recs}
-        for eng_name, eng, peak_mult in (("f16", pcl.ENGINE_TC_DIRECT, 1.0), ("e4m3", pcl.ENGINE_TC_DIRECT_FP8, 2.0)):
+        for eng_name, eng, peak_mult in (("f16", pcl.ENGINE_TC_DIRECT, 1.0), ("bf16", pcl.ENGINE_TC_DIRECT_BF16, 1.0),
+                                         ("e4m3", pcl.ENGINE_TC_DIRECT_FP8, 2.0)):
             Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
                             cos_engine=eng, flags=pcl.P_NO_GATES)
             for name, lst in (("same_seed", fp), ("dense32", dense)):

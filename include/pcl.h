@@ -59,7 +59,13 @@ enum { PCL_MODE_COSINE = 1, PCL_MODE_EDGE = 2 };
 /* cosine engines: FFT phase correlation (Sec. 3.2.1), or the direct windowed
    correlation on tensor cores with FP16 (TC_DIRECT) or E4M3 (TC_DIRECT_FP8)
    0/1 operands and FP32 accumulation -- both exact for 0/1 pixels */
-enum { PCL_ENGINE_FFT_PCM = 0, PCL_ENGINE_TC_DIRECT = 1, PCL_ENGINE_TC_DIRECT_FP8 = 2, PCL_ENGINE_XYSEP = 3 };
+enum {
+    PCL_ENGINE_FFT_PCM = 0,
+    PCL_ENGINE_TC_DIRECT = 1,      /* tensor cores, FP16 operands */
+    PCL_ENGINE_TC_DIRECT_FP8 = 2,  /* tensor cores, E4M3 operands */
+    PCL_ENGINE_XYSEP = 3,
+    PCL_ENGINE_TC_DIRECT_BF16 = 4  /* tensor cores, BF16 operands */
+};
 enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
 
 /* pcl_params.flags */
@@ -267,8 +273,9 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    every shift with popcounts in shared memory (pcm fields 0, spectra not
    read), which requires shift_rule = EXACT_ARGMAX (else
    PCL_ERR_UNSUPPORTED).
-   With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands) or
-   PCL_ENGINE_TC_DIRECT_FP8 (E4M3 operands) the overlaps of every shift come
+   With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands),
+   PCL_ENGINE_TC_DIRECT_BF16 (BF16 operands) or PCL_ENGINE_TC_DIRECT_FP8
+   (E4M3 operands) the overlaps of every shift come
    from the tensor cores instead (a direct windowed correlation, exact for 0/1
    pixels; the L-shaped edge of the window, the row dy = S and the column
    dx = S, is counted with popcounts): pairs are grouped by representative
@@ -345,7 +352,7 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
 /* ---- a10: serving loop ----------------------------------------------------
    A resident representative library and continuously batched query requests
    (cfg mode COSINE: the engine P->cos_engine names, PCL_ENGINE_FFT_PCM or
-   PCL_ENGINE_TC_DIRECT(_FP8); EDGE: Min-Max procedure).  For COSINE the
+   PCL_ENGINE_TC_DIRECT(_BF16, _FP8); EDGE: Min-Max procedure).  For COSINE the
    library must be rasterised (bits, pop, prof, blk) and pcl_server_create
    sorts it by area; with the FFT engine it also computes the spectra of all
    library clips (spec/spec_state buffers required), while the tensor-core

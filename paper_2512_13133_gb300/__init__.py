@@ -31,6 +31,7 @@ ENGINE_FFT_PCM = 0
 ENGINE_TC_DIRECT = 1
 ENGINE_TC_DIRECT_FP8 = 2
 ENGINE_XYSEP = 3  # shift by XY-separation interval competition (Sec. 3.2.1 (2))
+ENGINE_TC_DIRECT_BF16 = 4
 SHIFT_EXACT_ARGMAX = 0
 SHIFT_PCM_PEAK = 1
 P_NO_GATES = 1

@@ -155,7 +155,7 @@ pcl_status pcl_params_validate(const pcl_params *P) {
     if (P->cos_den == 0 || P->cos_den > 65535 || P->cos_num == 0 || P->cos_num >= P->cos_den)
         return PCL_ERR_INVALID;
     if (P->edge_tol_dbu < 0) return PCL_ERR_INVALID;
-    if (P->cos_engine > PCL_ENGINE_XYSEP || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
+    if (P->cos_engine > PCL_ENGINE_TC_DIRECT_BF16 || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
     if (!(P->near_band >= 0.0f)) return PCL_ERR_INVALID;
     return PCL_OK;
 }
@@ -247,7 +247,8 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
     }
     if (mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
     const Geo g = make_geo(*P);
-    if (P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8) {
+    if (P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8 ||
+        P->cos_engine == PCL_ENGINE_TC_DIRECT_BF16) {
         if (!tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
             return fail(ctx, PCL_ERR_UNSUPPORTED,
                         "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax%s%lld");

@@ -231,7 +231,8 @@ pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipse
     if (cfg->mode != 0 && cfg->mode != PCL_MODE_COSINE && !edge)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: mode must be PCL_MODE_COSINE or PCL_MODE_EDGE");
     const pcl::Geo g = pcl::make_geo(*P);
-    const bool tc = P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8;
+    const bool tc = P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8 ||
+                    P->cos_engine == PCL_ENGINE_TC_DIRECT_BF16;
     const int engine = edge ? kEdge : (tc ? kTc : kFft);
     if (edge) {
         if (!library->rect_off || !library->rects || !library->bits || !library->esig || !library->occ ||

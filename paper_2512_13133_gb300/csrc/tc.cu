@@ -5,7 +5,8 @@
 // over the marker window |dx|, |dy| <= S is computed as a GEMM
 //   D[m, col] = sum_k Aop[m, k] Bop[k, col]
 // with K = pixels, M = 128 shifts and N = (member copy, member) columns.  0/1
-// operands are exact in FP16 (1.0 = 0x3C00) or E4M3 (1.0 = 0x38), and the FP32
+// operands are exact in FP16 (1.0 = 0x3C00), BF16 (1.0 = 0x3F80) or E4M3
+// (1.0 = 0x38), and the FP32
 // sums stay below 2^24, so the tensor cores return the exact integer overlaps
 // (no rounding guard is needed).
 //
@@ -75,7 +76,10 @@ enum { kBarB = 1, kBarEpi = 2 };
 // mbarrier indices: a_full[2], a_empty[2], acc_full[2], acc_empty[2], fin, b_full[R], b_empty[R]
 enum { kAFull = 0, kAEmpty = 2, kAccFull = 4, kAccEmpty = 6, kFin = 8, kBFull = 9 };
 
-template <int S, int NW, bool FP8>
+// operand types (both MMA operands always have the same one)
+enum { kOpF16 = 0, kOpBF16 = 1, kOpE4M3 = 2 };
+
+template <int S, int NW, int OP>
 struct Tc {
     static constexpr int N = 64 * NW;
     static constexpr int NBX = (2 * S) / 16 > 0 ? (2 * S) / 16 : 1;  // x copies of a member (16 px apart)
@@ -92,7 +96,7 @@ struct Tc {
     static constexpr int DYL = -S + 8 * NBY;                          // rest row
     static constexpr int DXL = -S + 16 * NBX;                         // rest column, if <= S
     static constexpr bool COL = DXL <= S;
-    static constexpr int CH = FP8 ? 16 : 8;                           // pixels per 16-byte row
+    static constexpr int CH = OP == kOpE4M3 ? 16 : 8;                 // pixels per 16-byte row
     static constexpr int YHI = (N + 8 * (JB - 1) + kCores - 1) / kCores * kCores;  // K image rows
     static constexpr int NST = YHI / kCores;                          // stages per phase
     static constexpr int ZE = JB - 1;                                 // zero entries per phase
@@ -139,11 +143,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// instruction descriptor: D = F32 (bit 4), A = B = F16 for kind::f16 or E4M3
-// for kind::f8f6f4 (format 0 in bits 7-9 and 10-12), both K-major, N >> 3 at
-// bit 17, M >> 4 at bit 24
-__host__ __device__ constexpr uint32_t idesc_of(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor: D = F32 (bit 4), A and B formats in bits 7-9 and
+// 10-12 (kind::f16: 0 = F16, 1 = BF16; kind::f8f6f4: 0 = E4M3), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_of(int M, int N, int op) {
+    const uint32_t ab = op == kOpBF16 ? 1u : 0u;  // the same format for A and B
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 template <bool FP8>
@@ -164,14 +169,15 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
 }
 
 // the low CH pixels (bits) of b as one 16-byte core-matrix row of 0 / 1.0
-template <bool FP8>
+template <int OP>
 __device__ __forceinline__ uint4 expand(uint32_t b) {
-    if constexpr (FP8) {
+    if constexpr (OP == kOpE4M3) {
         // a nibble times 0x00204081 puts bit k at bit 8k (no carries), masked to 0/1 bytes
         auto q = [](uint32_t nib) { return ((nib * 0x00204081u) & 0x01010101u) * 0x38u; };
         return make_uint4(q(b & 15u), q((b >> 4) & 15u), q((b >> 8) & 15u), q((b >> 12) & 15u));
     } else {
-        auto h = [](uint32_t v) { return ((v & 1u) | ((v & 2u) << 15)) * 0x3C00u; };
+        constexpr uint32_t one = OP == kOpBF16 ? 0x3F80u : 0x3C00u;  // 1.0 in the 16-bit format
+        auto h = [](uint32_t v) { return ((v & 1u) | ((v & 2u) << 15)) * one; };
         return make_uint4(h(b & 3u), h((b >> 2) & 3u), h((b >> 4) & 3u), h((b >> 6) & 3u));
     }
 }
@@ -407,11 +413,11 @@ __device__ __forceinline__ void stage_load(uint64_t (&o)[C::TPT][C::WPT], const 
     }
 }
 
-template <int S, int NW, bool FP8>
+template <int S, int NW, int OP>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_corr_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, const uint32_t *surv,
                    const TcItem *items, const unsigned int *n_items, pcl_record *out, int *err) {
-    using C = Tc<S, NW, FP8>;
+    using C = Tc<S, NW, OP>;
     constexpr int N = C::N, RR = C::RR;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(sm + C::OFF_KEYS);
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const TcItem item = items[it];
                 const int ncols = C::NCOPY * round_members<C::RND>(item.count);  // N of each MMA
                 const uint32_t hb = (uint32_t)(ncols / C::JB) * 16, lbo = (uint32_t)C::POS * hb;
-                const uint32_t idesc = idesc_of(128, ncols);
+                const uint32_t idesc = idesc_of(128, ncols, OP);
                 uint32_t accum = 0;  // the first MMA of the item into this copy overwrites
                 const uint32_t ab = li & 1;
                 if (li >= 2 && !(ok = wait_phase(bar(kAccEmpty + ab), ((li >> 1) - 1) & 1, abortf))) break;
@@ -510,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 // Y + (m >> 4) - S
                                 const uint64_t bd = bd_e + (uint64_t)((2 * t * lbo) >> 4);
                                 const uint64_t ad = ad_st + (uint64_t)(2 * t * 16);
-                                mma<FP8>(dcol, ad, bd, idesc, accum);
+                                mma<OP == kOpE4M3>(dcol, ad, bd, idesc, accum);
                                 accum = 1u;
                             }
                         }
@@ -550,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < kCopies; ++j) {
                         const int g = (j + lane) & 15;
-                        st16(buf + (uint32_t)(ridx * kCopies + g) * 16, expand<FP8>((uint32_t)(win >> g)));
+                        st16(buf + (uint32_t)(ridx * kCopies + g) * 16, expand<OP>((uint32_t)(win >> g)));
                     }
                 }
                 fence_proxy_async();
@@ -655,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int i = 0; i < C::NBX; ++i) {
                             const int c0 = i * nbp + n;
                             const uint32_t o = (uint32_t)q * lbo + (uint32_t)(c0 >> 3) * 128 + (uint32_t)(c0 & 7) * 16;
-                            const uint4 x = expand<FP8>(strip >> (16 * (C::NBX - 1 - i)));
+                            const uint4 x = expand<OP>(strip >> (16 * (C::NBX - 1 - i)));
                             sts16(d0 + o, x);
                             if (mir) sts16(d1 + o, x);
                         }
@@ -914,21 +920,32 @@ size_t tc_workspace(uint64_t n) { return 4 * (3 * (size_t)n + 8) + sizeof(TcItem
 
 namespace {
 
-template <int S, int NW, bool FP8>
+template <int S, int NW, int OP>
 cudaError_t launch_corr(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
                         const uint32_t *surv, const TcItem *items, const unsigned int *n_items, pcl_record *out,
                         int num_sms, int *d_err, cudaStream_t st) {
-    using C = Tc<S, NW, FP8>;
-    cudaError_t e = cudaFuncSetAttribute(tc_corr_kernel<S, NW, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using C = Tc<S, NW, OP>;
+    cudaError_t e = cudaFuncSetAttribute(tc_corr_kernel<S, NW, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::BYTES);
     if (e != cudaSuccess) return e;
-    tc_corr_kernel<S, NW, FP8><<<num_sms, kThreads, C::BYTES, st>>>(prm, a, b, pairs, surv, items, n_items, out, d_err);
+    tc_corr_kernel<S, NW, OP><<<num_sms, kThreads, C::BYTES, st>>>(prm, a, b, pairs, surv, items, n_items, out, d_err);
     return cudaGetLastError();
 }
 
 template <int S, int NW>
+cudaError_t launch_corr_op(int op, const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
+                           const pcl_pair *pairs, const uint32_t *surv, const TcItem *items,
+                           const unsigned int *n_items, pcl_record *out, int num_sms, int *d_err, cudaStream_t st) {
+    switch (op) {
+        case kOpE4M3: return launch_corr<S, NW, kOpE4M3>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case kOpBF16: return launch_corr<S, NW, kOpBF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        default: return launch_corr<S, NW, kOpF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+    }
+}
+
+template <int S, int NW>
 int members_of() {
-    return Tc<S, NW, false>::NB;
+    return Tc<S, NW, kOpF16>::NB;  // the same for every operand type
 }
 
 }  // namespace
@@ -940,7 +957,9 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     if (!tc_supported(g)) return cudaErrorNotSupported;
     if (n == 0) return cudaSuccess;
     if (ws_bytes < tc_workspace(n) || n > 0xffffffffull) return cudaErrorInvalidValue;
-    const bool fp8 = prm.cos_engine == PCL_ENGINE_TC_DIRECT_FP8;
+    const int op = prm.cos_engine == PCL_ENGINE_TC_DIRECT_FP8   ? kOpE4M3
+                   : prm.cos_engine == PCL_ENGINE_TC_DIRECT_BF16 ? kOpBF16
+                                                                 : kOpF16;
     const int NB = g.S == 4 ? members_of<4, 1>() : g.S == 8 ? members_of<8, 2>() : members_of<16, 4>();
     char *w = static_cast<char *>(ws);
     uint32_t *keep = reinterpret_cast<uint32_t *>(w);
@@ -960,15 +979,9 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     tc_items_kernel<<<num_sms * 4, 256, 0, st>>>(keep, nullptr, pos + n, NB, items, n_items, (uint32_t)n + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (g.S) {
-        case 4:
-            return fp8 ? launch_corr<4, 1, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
-                       : launch_corr<4, 1, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        case 8:
-            return fp8 ? launch_corr<8, 2, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
-                       : launch_corr<8, 2, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        default:
-            return fp8 ? launch_corr<16, 4, true>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st)
-                       : launch_corr<16, 4, false>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case 4: return launch_corr_op<4, 1>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case 8: return launch_corr_op<8, 2>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        default: return launch_corr_op<16, 4>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
     }
 }
 

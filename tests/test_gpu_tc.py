@@ -1,7 +1,7 @@
 """Tensor-core direct correlation (a8) against the oracle and the FFT engine:
 exact shifts, overlaps and decisions, |sim diff| <= 1e-5, for the three
 (N, S) geometries the engine covers -- (64, 4), (128, 8), (256, 16) -- with
-FP16 and E4M3 operands, member batches from one pair to a full item, and the
+FP16, BF16 and E4M3 operands, member batches from one pair to a full item, and the
 error for a geometry it does not cover."""
 import numpy as np
 import pytest
@@ -42,7 +42,7 @@ def _pairs(wl, rng, k):
 
 @pytest.mark.parametrize("kind", ["n64", "n128", "n256"])
 @pytest.mark.parametrize("gates", [False, True])
-@pytest.mark.parametrize("engine", ["f16", "e4m3"])
+@pytest.mark.parametrize("engine", ["f16", "bf16", "e4m3"])
 def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates, engine):
     import paper_2512_13133_gb300 as pcl
     wl = _workload(kind)
@@ -51,7 +51,7 @@ def test_tc_engine_matches_oracle_and_fft(torch_cuda, kind, gates, engine):
     flags = 0 if gates else pcl.P_NO_GATES
     num = 80 if gates else 95  # with gates, a looser threshold lets pairs through to the engine
     ctx = pcl.Context(0)
-    eng = pcl.ENGINE_TC_DIRECT if engine == "f16" else pcl.ENGINE_TC_DIRECT_FP8
+    eng = {"f16": pcl.ENGINE_TC_DIRECT, "bf16": pcl.ENGINE_TC_DIRECT_BF16, "e4m3": pcl.ENGINE_TC_DIRECT_FP8}[engine]
     Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, cos_engine=eng, flags=flags)
     Pf = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=num, flags=flags)
     cs = pcl.alloc_clipset(Pf, wl.rect_off, wl.rects)
@@ -83,7 +83,7 @@ def _dense_pairs(wl, rng, reps, per_rep):
     return np.array(out, dtype=np.int64)
 
 
-@pytest.mark.parametrize("engine", ["f16", "e4m3"])
+@pytest.mark.parametrize("engine", ["f16", "bf16", "e4m3"])
 def test_tc_full_items_and_split_segments(torch_cuda, engine):
     """Representatives with 1, 31, 32, 33 and 70 members: full items of 32
     members, a segment split over three items, and ragged last items."""
@@ -91,7 +91,7 @@ def test_tc_full_items_and_split_segments(torch_cuda, engine):
     wl = synth.preset("scale", seed=8, n_clips=300, n_seeds=30, n_copies=200)
     rng = np.random.default_rng(5)
     pairs = np.concatenate([_dense_pairs(wl, rng, 1, k) for k in (1, 31, 32, 33, 70)])
-    eng = pcl.ENGINE_TC_DIRECT if engine == "f16" else pcl.ENGINE_TC_DIRECT_FP8
+    eng = {"f16": pcl.ENGINE_TC_DIRECT, "bf16": pcl.ENGINE_TC_DIRECT_BF16, "e4m3": pcl.ENGINE_TC_DIRECT_FP8}[engine]
     ctx = pcl.Context(0)
     Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_engine=eng, flags=pcl.P_NO_GATES)
     cs = pcl.alloc_clipset(Pt, wl.rect_off, wl.rects)
