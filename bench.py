@@ -1,6 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark: aligned pair-similarities per second of the pairwise
-optimal-alignment similarity path on one GB300 (or N of them, weak scaling).
+optimal-alignment similarity path on one GB300 (or N of them: a clip set per
+rank, or with --scaling strong one clip set whose self-join the ranks split).
 
 A step is one pass of the whole path over one clip set resident in HBM:
 rasterisation + signatures, the cosine candidate screen (area band join with
@@ -58,6 +59,9 @@ def parse():
                     help="override the clip count (seeds and copies scale with it; profiling runs)")
     ap.add_argument("--no-fft-engine", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: each rank its own clip set (weak), or one clip set whose self-join the ranks "
+                         "split with pcl_candidates_shard (strong)")
     ap.add_argument("--library-clips", type=int, default=2_000_000,
                     help="clips of the large serving library (tensor-core cosine and edge; 0: skip)")
     ap.add_argument("--no-batched", action="store_true")
@@ -83,10 +87,10 @@ def peaks():
 # was taken; otherwise the bench reports null.
 TRAFFIC = {
     "cand_edge": {"sources": {"paper_2512_13133_gb300/csrc/edge.cu":
-                              "1741d0fe786d2e55c41ac3aae4de556f6ea4dec5f2e092ae4a30117e235b9a1f",
+                              "7cec77773739fabbd01c2243d2f53a312993d387a8ac7c8d0f0382b06f6ae959",
                               "paper_2512_13133_gb300/csrc/edge_dev.cuh":
                               "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
-                  "bytes": 1.92e9 + 22.82e6},
+                  "bytes": 1.914e9 + 22.62e6},
 }
 
 
@@ -504,7 +508,8 @@ def run_reference(args, rank, world):
 
 def reduce_over_ranks(aligned: int, ms_step: float, e2e_ms: float, world: int, device):
     """Whole-job figures: aligned pairs summed over ranks, step and end-to-end
-    times maxed over ranks (each rank works on its own clip set)."""
+    times maxed over ranks (each rank works on its own clip set, or on its
+    shard of one self-join)."""
     if world <= 1:
         return aligned, ms_step, e2e_ms
     import torch
@@ -523,7 +528,8 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = workload(args.config, args.seed + rank, args.clips)
+    strong = args.scaling == "strong" and world > 1
+    wl = workload(args.config, args.seed + (0 if strong else rank), args.clips)
     P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL)
     ctx = pcl.Context(local_rank)
     h_off = torch.from_numpy(wl.rect_off.view(np.int32).copy()).pin_memory()
@@ -543,6 +549,13 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stages = ["raster", "cand_cos", "cand_edge", "match_cos", "match_edge", "compact"]
 
+    def cand(mode, out, c, g):
+        # strong scaling: this rank's shard of the one self-join
+        if strong:
+            pcl.pcl_candidates_shard(ctx, P, mode, cs, rank, world, out, c, g)
+        else:
+            pcl.pcl_candidates(ctx, P, mode, cs, out, c, g)
+
     def step(ev=None):
         def mark(i):
             if ev is not None:
@@ -550,9 +563,9 @@ def run_ours(args, rank, world, local_rank):
         mark(0)
         pcl.pcl_rasterize(ctx, P, cs)
         mark(1)
-        pcl.pcl_candidates(ctx, P, pcl.MODE_COSINE, cs, pc, cnt[0:1], gates[0])
+        cand(pcl.MODE_COSINE, pc, cnt[0:1], gates[0])
         mark(2)
-        pcl.pcl_candidates(ctx, P, pcl.MODE_EDGE, cs, pe, cnt[1:2], gates[1])
+        cand(pcl.MODE_EDGE, pe, cnt[1:2], gates[1])
         mark(3)
         pcl.pcl_match_pairs(ctx, P, pcl.MODE_COSINE, cs, cs, pc, rc, d_n=cnt[0:1])
         mark(4)
@@ -860,7 +873,7 @@ def run_ours(args, rank, world, local_rank):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": args.scaling,
         "vs_baseline": None, "dtype": "u64/i32/f32", "data": "synthetic",
         "config": {"workload": f"{args.config}: {n} clips, {N}x{N} px, W={wl.window_dbu} dbu, "
                                f"M={wl.marker_dbu} dbu, T=0.95, tol=4 dbu, both modes",

@@ -242,6 +242,26 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
                           pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
                           pcl_stream stream);
 
+/* One shard of the self-join of pcl_candidates, for n_shards GPUs (or calls)
+   sharing one clip set: shard s of S (0 <= s < S) screens a fixed subset of
+   the pairs, the S subsets are disjoint and their union is every pair, so
+   the union of the shards' outputs is exactly pcl_candidates' output and the
+   shards' gate counts sum to its counts.  The subsets depend on clip indices
+   only (every caller holds the whole clip set, in the same order):
+     COSINE  pairs (a, b) with (a + b) mod S = s (the band join still walks
+             every band, testing only its shard's members; the G1 count is
+             the shard's pair count minus the pairs it enumerated);
+     EDGE    the tiles s, s + S, s + 2S, ... of the screen's tile numbering
+             (32 row clips i x 256 column clips j with i < j, numbered column
+             block after column block: column block y holds row tiles
+             0 .. min(8y + 8, ceil(n/32)) - 1 and starts at tile 4y(y + 1)
+             while 8y <= ceil(n/32), then grows by ceil(n/32) per block).
+   pcl_candidates is shard 0 of 1.  Errors: those of pcl_candidates, and
+   PCL_ERR_INVALID when s >= S or S = 0. */
+pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
+                                uint32_t shard, uint32_t n_shards, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
+                                uint64_t *d_gate_counts, pcl_stream stream);
+
 /* Cosine candidate generation without any device allocation (the paper has
    no counterpart; this serves callers that cannot allocate device memory,
    e.g. when another allocator owns the device's memory under a fixed budget,

@@ -153,6 +153,8 @@ def load(build_if_missing: bool = True):
         "pcl_spectra": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, ctypes.c_uint32, _VP], st),
         "pcl_candidates": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset), _VP, _U64,
                             _VP, _VP, _VP], st),
+        "pcl_candidates_shard": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
+                                  ctypes.c_uint32, ctypes.c_uint32, _VP, _U64, _VP, _VP, _VP], st),
         "pcl_candidates_cosine_noalloc": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, _U64,
                                            _VP, _VP, _VP], st),
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
@@ -253,6 +255,26 @@ class ClipSet:
     spec: object
     spec_state: object
 
+    def view(self, P: Params, c0: int, c1: int) -> "ClipSet":
+        """Clips [c0, c1) as a clip set of their own, sharing this set's
+        device memory (no copy): per-clip arrays start at clip c0, the
+        rectangle offsets keep indexing this set's rectangle array.  Clip k of
+        the view is clip c0 + k here."""
+        if not 0 <= c0 <= c1 <= self.n:
+            raise ValueError("clip range out of bounds")
+        one, two = clipset_sizes(P, 1), clipset_sizes(P, 2)
+
+        def part(t, field):
+            if t is None:
+                return None
+            per = int(getattr(two, field)) - int(getattr(one, field))
+            return t[c0 * per:c1 * per]
+
+        return ClipSet(c1 - c0, self.N, self.S, self.L, self.Ls, self.rect_off[c0:c1 + 1], self.rects,
+                       part(self.bits, "bits"), part(self.pop, "pop"), part(self.prof, "prof"),
+                       part(self.blk, "blk"), part(self.esig, "esig"), part(self.occ, "occ"), self.rorder,
+                       part(self.spec, "spec"), part(self.spec_state, "spec_state"))
+
     def cstruct(self) -> _Clipset:
         return _Clipset(self.n, 0, _ptr(self.rect_off), _ptr(self.rects), _ptr(self.bits), _ptr(self.pop),
                         _ptr(self.prof), _ptr(self.blk), _ptr(self.esig), _ptr(self.occ), _ptr(self.rorder),
@@ -314,6 +336,16 @@ def pcl_candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, out_pairs, d
     cap = 0 if out_pairs is None else int(out_pairs.shape[0])
     ctx.check(ctx.lib.pcl_candidates(ctx.h, ctypes.byref(P), mode, ctypes.byref(c), _ptr(out_pairs), cap,
                                      _ptr(d_count), _ptr(d_gates), _stream_ptr(stream)), "pcl_candidates")
+
+
+def pcl_candidates_shard(ctx: Context, P: Params, mode: int, cs: ClipSet, shard: int, n_shards: int, out_pairs,
+                         d_count, d_gates=None, stream=None) -> None:
+    """pcl_candidates_shard: the pairs of shard `shard` of `n_shards` only."""
+    c = cs.cstruct()
+    cap = 0 if out_pairs is None else int(out_pairs.shape[0])
+    ctx.check(ctx.lib.pcl_candidates_shard(ctx.h, ctypes.byref(P), mode, ctypes.byref(c), shard, n_shards,
+                                           _ptr(out_pairs), cap, _ptr(d_count), _ptr(d_gates),
+                                           _stream_ptr(stream)), "pcl_candidates_shard")
 
 
 def pcl_candidates_cosine_noalloc(ctx: Context, P: Params, cs: ClipSet, out_pairs, d_count, d_gates=None,
@@ -435,17 +467,21 @@ def signatures(cs: ClipSet):
     return dict(pop=pop, rows=prof[:, 0], cols=prof[:, 1], blk=blk[:, 0], dil=blk[:, 1], esig=esig)
 
 
-def candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, cap: int = 1 << 20, stream=None):
+def candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, cap: int = 1 << 20, stream=None,
+               shard: int = 0, n_shards: int = 1):
     """Self-join candidate pairs of `mode` (re-runs once with the exact capacity
-    if `cap` was too small).  Returns (pairs int32 [m, 2] CUDA, gate counts
-    numpy int64 [16])."""
+    if `cap` was too small), or those of one shard of the pair space.  Returns
+    (pairs int32 [m, 2] CUDA, gate counts numpy int64 [16])."""
     torch = _torch()
     dev = cs.bits.device
     for _ in range(2):
         out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         gates = torch.zeros(16, dtype=torch.int64, device=dev)
-        pcl_candidates(ctx, P, mode, cs, out, cnt, gates, stream)
+        if n_shards == 1:
+            pcl_candidates(ctx, P, mode, cs, out, cnt, gates, stream)
+        else:
+            pcl_candidates_shard(ctx, P, mode, cs, shard, n_shards, out, cnt, gates, stream)
         m = int(cnt.item())
         if m <= cap:
             return out[:m], gates.cpu().numpy()

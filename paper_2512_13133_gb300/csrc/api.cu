@@ -12,9 +12,9 @@ namespace pcl {
 cudaError_t launch_raster(const pcl_params &, const pcl_clipset &, cudaStream_t);
 size_t band_join_workspace(const Geo &, uint32_t);
 cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
-                             unsigned long long *, unsigned long long *, int, cudaStream_t);
+                             unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
 cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
-                               unsigned long long *, unsigned long long *, cudaStream_t);
+                               unsigned long long *, unsigned long long *, cudaStream_t, uint32_t, uint32_t);
 cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                               const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool,
@@ -204,9 +204,16 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
 pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
                           pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
                           pcl_stream stream) {
+    return pcl_candidates_shard(ctx, P, mode, cs, 0, 1, d_out, cap, d_count, d_gate_counts, stream);
+}
+
+pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
+                                uint32_t shard, uint32_t n_shards, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
+                                uint64_t *d_gate_counts, pcl_stream stream) {
     pcl_status s = enter(ctx);
     if (s) return s;
     if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    if (n_shards == 0 || shard >= n_shards) return fail(ctx, PCL_ERR_INVALID, "shard out of range%s%lld");
     if ((s = check_clipset(ctx, cs, mode == PCL_MODE_EDGE))) return s;
     if (!d_count || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL output%s%lld");
     cudaStream_t st = (cudaStream_t)stream;
@@ -219,11 +226,12 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
         if (g.S > g.N / 16) return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine gates need S <= N/16%s%lld");
         const size_t need = band_join_workspace(g, cs->n_clips);
         if ((s = ensure_ws(ctx, need))) return s;
-        e = launch_band_join(*P, *cs, ctx->ws, ctx->ws_bytes, d_out, cap, cnt, gates, ctx->num_sms, st);
+        e = launch_band_join(*P, *cs, ctx->ws, ctx->ws_bytes, d_out, cap, cnt, gates, ctx->num_sms, st, shard,
+                             n_shards);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "band join");
     }
     if (mode == PCL_MODE_EDGE) {
-        e = launch_edge_screen(*P, *cs, d_out, cap, cnt, gates, st);
+        e = launch_edge_screen(*P, *cs, d_out, cap, cnt, gates, st, shard, n_shards);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge screen");
     }
     return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);

@@ -1,12 +1,11 @@
 // a2 (edge gates) and a7: edge-displacement mode (Sec. 2.2.2) with the
-// geometric Min-Max closed form of Sec. 3.2.2 (Eq. 6).
+// geometric Min-Max closed form of Sec. 3.2.2 (Eq. 6), integer dbu throughout.
 //
-// Integer dbu throughout.  One thread evaluates one pair: the polygon lists
-// are short (tens of rectangles) and the procedure is a handful of O(n_A n_B)
-// scans with early exits, so per-thread evaluation keeps every lane busy on
-// its own pair instead of idling lanes on small clips.  Partners are
-// recomputed by scanning rather than stored, so no per-thread arrays are
-// needed for any polygon count.
+// edge_screen_kernel: the self-join screen of all pairs i < j through E2 and
+// E1 (tiles of 32 row clips x 256 column clips; the cheap occupancy-grid
+// tests of E1 run one pair per lane, the exact correspondence of the few
+// survivors one pair per warp).  edge_match_kernel: the Min-Max record of
+// each listed pair, one pair per warp (lanes hold the polygons).
 #include "edge_dev.cuh"
 
 namespace pcl {
@@ -174,10 +173,11 @@ template <bool P2>
 __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl_clipset cs,
                                                           pcl_pair *out, uint64_t cap,
                                                           unsigned long long *count,
-                                                          unsigned long long *gates) {
+                                                          unsigned long long *gates, uint32_t shard,
+                                                          uint32_t n_shards) {
     const uint32_t n = cs.n_clips;
     uint32_t bx, by;
-    screen_tile(blockIdx.x, (n + 31) / 32, bx, by);
+    screen_tile(blockIdx.x * n_shards + shard, (n + 31) / 32, bx, by);  // shard s of S: tiles s, s + S, ...
     const uint32_t i0 = bx * 32u;
     const uint32_t jblk = by * (uint32_t)kColsB;
     if (jblk >= n || i0 + 1u >= min(jblk + (uint32_t)kColsB, n)) return;  // no pair i < j in the block
@@ -391,19 +391,27 @@ __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_cli
 
 }  // namespace
 
+// shard s of S (several GPUs sharing one self-join) screens the tiles
+// s, s + S, s + 2S, ... of the 1-D tile numbering: a partition by clip index
+uint64_t edge_screen_tiles(uint32_t n) {
+    if (n < 2) return 0;
+    return screen_tiles_before((n + kColsB - 1) / kColsB, (n + 31) / 32);
+}
+
 cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl_pair *out,
                                uint64_t cap, unsigned long long *count, unsigned long long *gates,
-                               cudaStream_t st) {
-    const uint32_t n = cs.n_clips;
-    if (n < 2) return cudaSuccess;
+                               cudaStream_t st, uint32_t shard, uint32_t n_shards) {
+    if (n_shards == 0 || shard >= n_shards) return cudaErrorInvalidValue;
     // only the tiles that hold pairs i < j (about half of them)
-    const uint32_t nbx = (n + 31) / 32, nby = (n + kColsB - 1) / kColsB;
-    const uint64_t tiles = screen_tiles_before(nby, nbx);
+    const uint64_t tiles = edge_screen_tiles(cs.n_clips);
     if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    const unsigned grid = (unsigned)tiles;
+    if (tiles <= shard) return cudaSuccess;
+    const unsigned grid = (unsigned)((tiles - shard + n_shards - 1) / n_shards);
     const int csz = prm.window_dbu / 64;
-    if ((csz & (csz - 1)) == 0) edge_screen_kernel<true><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
-    else edge_screen_kernel<false><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates);
+    if ((csz & (csz - 1)) == 0)
+        edge_screen_kernel<true><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates, shard, n_shards);
+    else
+        edge_screen_kernel<false><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates, shard, n_shards);
     return cudaGetLastError();
 }
 

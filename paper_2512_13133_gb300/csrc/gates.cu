@@ -18,7 +18,10 @@
 // area every G1 survivor (i, j) lies in the band of positions
 // (p, end_p) with end_p = #{clips with area <= floor((den^2 a_p - 1)/num^2)}.
 // Warps take positions p from a global counter and test G3 and G2 on every
-// band member with the whole warp.
+// band member with the whole warp.  A shard s of S (several GPUs sharing one
+// self-join) keeps the pairs (a, b) with (a + b) mod S = s: a partition that
+// depends on the clip indices only, not on the order the counting sort gives
+// clips of equal area.
 #include <climits>
 
 #include "gates.cuh"
@@ -26,6 +29,18 @@
 namespace pcl {
 
 namespace {
+
+// position of the (r + 1)-th set bit of m, -1 if m has r set bits or fewer
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
+    if (__popc(m) <= r) return -1;
+    int lo = 0, hi = 31;  // smallest p with popc(m & bits 0..p) > r
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;  // <= 30, so the mask below does not overflow
+        if (__popc(m & ((2u << mid) - 1u)) > r) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
 
 __global__ void hist_kernel(const uint32_t *pop, uint32_t n, uint32_t *hist) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -83,7 +98,8 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                                                         uint32_t vmax_all, pcl_pair *out, uint64_t cap,
                                                         unsigned long long *count,
                                                         unsigned long long *local_gates,
-                                                        unsigned int *next_pos) {
+                                                        unsigned int *next_pos, uint32_t shard,
+                                                        uint32_t n_shards) {
     const Geo g = make_geo(prm);
     const int lane = threadIdx.x & 31;
     const uint32_t n = cs.n_clips;
@@ -110,13 +126,14 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
         }
         if (pa == 0) {  // the band holds the other empty clips only: similar by definition
             for (uint32_t q0 = p + 1; q0 < end; q0 += 32) {
-                const bool v = q0 + lane < end;
-                const uint32_t bq = v ? order[q0 + lane] : 0u;
+                const uint32_t bq = q0 + lane < end ? order[q0 + lane] : 0u;
+                const bool v = q0 + lane < end && ((uint64_t)a + bq) % n_shards == shard;
                 const unsigned m = __ballot_sync(0xffffffffu, v);
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(m));
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (v && base + lane < cap) out[base + lane] = pcl_pair{min(a, bq), max(a, bq)};
+                const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+                if (v && idx < cap) out[idx] = pcl_pair{min(a, bq), max(a, bq)};
                 kept += __popc(m);
             }
             continue;
@@ -135,7 +152,16 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                 tA = (int)max((int64_t)pa - um, (int64_t)INT_MIN);
                 tB = (int)max((int64_t)pb - um, (int64_t)INT_MIN);
             }
-            const int cnt = (int)min(32u, end - q0);
+            int cnt = (int)min(32u, end - q0);
+            if (n_shards > 1) {  // this shard's members only, moved to the low lanes in order
+                const unsigned mem = __ballot_sync(0xffffffffu, q < end && ((uint64_t)a + b) % n_shards == shard);
+                const int src = nth_set_bit(mem, lane);  // lane of this lane's member
+                const int from = src >= 0 ? src : lane;
+                b = __shfl_sync(0xffffffffu, b, from);
+                tA = __shfl_sync(0xffffffffu, tA, from);
+                tB = __shfl_sync(0xffffffffu, tB, from);
+                cnt = __popc(mem);
+            }
             // the rest of the gates for member k after the pre-screen
             auto finish = [&](int k, uint32_t bk, int tAk, int tBk) {
                 const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)bk * 2 * nb2);
@@ -224,9 +250,23 @@ size_t band_join_workspace(const Geo &g, uint32_t n) {
     return 4 * (2 * V + 2 * (size_t)n) + 8 * 16 + 64;
 }
 
+// pairs i < j < n with (i + j) mod S = s: for each i, the j in (i, n) of one residue
+uint64_t shard_pairs(uint64_t n, uint32_t s, uint32_t S) {
+    if (S <= 1) return n * (n ? n - 1 : 0) / 2;
+    auto below = [S](uint64_t x, uint64_t r) { return x > r ? (x - r + S - 1) / S : 0; };  // #{j < x : j % S == r}
+    uint64_t t = 0;
+    for (uint64_t i = 0; i + 1 < n; ++i) {
+        const uint64_t r = (s + S - i % S) % S;
+        t += below(n, r) - below(i + 1, r);
+    }
+    return t;
+}
+
 cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void *ws, size_t ws_bytes,
                              pcl_pair *out, uint64_t cap, unsigned long long *count,
-                             unsigned long long *gates, int num_sms, cudaStream_t st) {
+                             unsigned long long *gates, int num_sms, cudaStream_t st, uint32_t shard,
+                             uint32_t n_shards) {
+    if (n_shards == 0 || shard >= n_shards) return cudaErrorInvalidValue;
     const Geo g = make_geo(prm);
     const uint32_t n = cs.n_clips;
     if (ws_bytes < band_join_workspace(g, n)) return cudaErrorInvalidValue;
@@ -250,14 +290,14 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     const uint32_t vall = (uint32_t)g.N * g.N;
     switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
         case 1: band_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
-                                                                 local, next_pos); break;
+                                                                 local, next_pos, shard, n_shards); break;
         case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
-                                                                 local, next_pos); break;
+                                                                 local, next_pos, shard, n_shards); break;
         case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
-                                                                   local, next_pos); break;
+                                                                   local, next_pos, shard, n_shards); break;
         default: return cudaErrorInvalidValue;
     }
-    const unsigned long long total = (unsigned long long)n * (n - 1) / 2;
+    const unsigned long long total = shard_pairs(n, shard, n_shards);
     finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, total);
     return cudaGetLastError();
 }

@@ -18,7 +18,7 @@
 namespace pcl {
 size_t band_join_workspace(const Geo &, uint32_t);
 cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
-                             unsigned long long *, unsigned long long *, int, cudaStream_t);
+                             unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
 }  // namespace pcl
 
 namespace {
@@ -98,7 +98,7 @@ extern "C" pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_para
     if (e == cudaSuccess)
         e = pcl::launch_band_join(*P, *cs, ws, kScratchBytes, d_out, cap,
                                   reinterpret_cast<unsigned long long *>(d_count),
-                                  reinterpret_cast<unsigned long long *>(d_gate_counts), ctx->num_sms, st);
+                                  reinterpret_cast<unsigned long long *>(d_gate_counts), ctx->num_sms, st, 0, 1);
     if (e != cudaSuccess) {
         ctx->err = std::string("band join: ") + cudaGetErrorString(e);
         return PCL_ERR_CUDA;
