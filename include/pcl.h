@@ -391,7 +391,8 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
    clip through the direct correlation, exact argmax; its workspace of
    20 bytes per candidate slot shares the band join's), pass compaction and
    the copy of the pass list back
-   (EDGE: every query x library pair through E2 and E1 one pair per lane, the
+   (EDGE: every query x library pair through E2 and E1 in the tiled screen of
+   pcl_candidates -- 32 query clips x 256 library clips per tile -- then the
    Min-Max record of each survivor by a whole warp, pass compaction, copy).
    pcl_server_poll returns finished requests (pass pairs are
    (query index, library index), in server-owned host memory valid until

@@ -168,19 +168,33 @@ __device__ inline void screen_tile(uint32_t idx, uint32_t nbx, uint32_t &bx, uin
 // lanes advance through their pairs independently without idling.  Pairs
 // whose polygons all meet occupied cells (a few per thousand) go to a second
 // queue, where the whole warp checks one pair at a time with ballots.
-// P2: the grid's cell side W/64 is a power of two (cells by shifts)
-template <bool P2>
-__global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl_clipset cs,
+// P2: the grid's cell side W/64 is a power of two (cells by shifts).
+// CROSS: rows from clip set RS and columns from CS, every (row, column) pair
+// (the query x library screen of the serving loop; tiles numbered column
+// block after column block, row tile fastest); otherwise RS = CS and the
+// pairs i < j of the triangular tile numbering.
+template <bool P2, bool CROSS>
+__global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl_clipset RS, pcl_clipset CS,
                                                           pcl_pair *out, uint64_t cap,
                                                           unsigned long long *count,
                                                           unsigned long long *gates, uint32_t shard,
                                                           uint32_t n_shards) {
-    const uint32_t n = cs.n_clips;
+    const uint32_t nr = RS.n_clips, n = CS.n_clips;  // rows, columns
     uint32_t bx, by;
-    screen_tile(blockIdx.x * n_shards + shard, (n + 31) / 32, bx, by);  // shard s of S: tiles s, s + S, ...
+    if constexpr (CROSS) {
+        const uint32_t nbx = (nr + 31) / 32;
+        bx = blockIdx.x % nbx;
+        by = blockIdx.x / nbx;
+    } else {
+        screen_tile(blockIdx.x * n_shards + shard, (n + 31) / 32, bx, by);  // shard s of S: tiles s, s + S, ...
+    }
     const uint32_t i0 = bx * 32u;
     const uint32_t jblk = by * (uint32_t)kColsB;
-    if (jblk >= n || i0 + 1u >= min(jblk + (uint32_t)kColsB, n)) return;  // no pair i < j in the block
+    if constexpr (CROSS) {
+        if (jblk >= n || i0 >= nr) return;
+    } else {
+        if (jblk >= n || i0 + 1u >= min(jblk + (uint32_t)kColsB, n)) return;  // no pair i < j in the block
+    }
     const int W = prm.window_dbu, M = prm.marker_dbu, tol = prm.edge_tol_dbu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ uint64_t grids[(32 + 8) * kGS];  // row clips' grids, then each warp's current column grid
@@ -188,29 +202,30 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     __shared__ int4 cp0[kColsB];      // smallest polygon of each column clip
     __shared__ int4 tq[8][kQueue];    // grid tests: {row | col << 8 | small_is_a << 16, sx, sy, 0}
     __shared__ int4 fq[8][kQueue];    // full checks: {row | col << 8 | small_is_a << 16, s0x, s0y, 0}
-    const int4 *rects4 = reinterpret_cast<const int4 *>(cs.rects);
+    const int4 *rrects = reinterpret_cast<const int4 *>(RS.rects), *crects = reinterpret_cast<const int4 *>(CS.rects);
     // flags: bit 0 has x edges, bit 1 has y edges, bit 2 touches the border
-    auto load_sig = [&](uint32_t c, int4 &s0, int4 &s1, int4 &p0) {
-        const int4 *e4 = reinterpret_cast<const int4 *>(cs.esig + (size_t)c * 8);
+    auto load_sig = [&](const pcl_clipset &cl, uint32_t c, int4 &s0, int4 &s1, int4 &p0) {
+        const int4 *e4 = reinterpret_cast<const int4 *>(cl.esig + (size_t)c * 8);
         const int4 lo = __ldg(e4), hi = __ldg(e4 + 1);  // {n, hasx, lox, hix}, {hasy, loy, hiy, border}
-        const uint32_t off = __ldg(cs.rect_off + c);
+        const uint32_t off = __ldg(cl.rect_off + c);
         s0 = make_int4(lo.x, (lo.y ? 1 : 0) | (hi.x ? 2 : 0) | (hi.w ? 4 : 0), lo.z + lo.w, hi.y + hi.z);
         s1 = make_int4(lo.w - lo.z, hi.z - hi.y, (int)off, 0);
-        p0 = lo.x > 0 ? __ldg(rects4 + off + __ldg(cs.rorder + off)) : make_int4(0, 0, 0, 0);
+        p0 = lo.x > 0 ? __ldg(reinterpret_cast<const int4 *>(cl.rects) + off + __ldg(cl.rorder + off))
+                      : make_int4(0, 0, 0, 0);
     };
     for (int c = threadIdx.x; c < kColsB; c += blockDim.x) {
         int4 s0 = make_int4(0, 0, 0, 0), s1 = s0, p0 = s0;
-        if (jblk + c < n) load_sig(jblk + c, s0, s1, p0);
+        if (jblk + c < n) load_sig(CS, jblk + c, s0, s1, p0);
         csig[c][0] = s0;
         csig[c][1] = s1;
         cp0[c] = p0;
     }
     for (int w = threadIdx.x; w < 32 * 64; w += blockDim.x)
-        grids[(w >> 6) * kGS + (w & 63)] = i0 + (w >> 6) < n ? __ldg(cs.occ + (size_t)i0 * 64 + w) : 0ull;
+        grids[(w >> 6) * kGS + (w & 63)] = i0 + (w >> 6) < nr ? __ldg(RS.occ + (size_t)i0 * 64 + w) : 0ull;
     // this lane's row clip
     const uint32_t i = i0 + lane;
     int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, pa = a0;
-    if (i < n) load_sig(i, a0, a1, pa);
+    if (i < nr) load_sig(RS, i, a0, a1, pa);
     const int na = a0.x;
     __syncthreads();
     const int csz = W / 64;
@@ -235,9 +250,10 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
             const bool sa = (e.x >> 16) & 1;
             const int offa = __shfl_sync(0xffffffffu, a1.z, r), nar = __shfl_sync(0xffffffffu, na, r);
             const int offb = csig[c][1].z, nbc = csig[c][0].x;
-            const int offs = sa ? offa : offb;
-            const bool ok = warp_correspond(rects4 + offs, cs.rorder + offs, sa ? nar : nbc,
-                                            rects4 + (sa ? offb : offa), sa ? nbc : nar, sa, e.y, e.z, lane);
+            // the small clip's polygons (and area order) and the large clip's
+            const int4 *sr = sa ? rrects + offa : crects + offb, *lr = sa ? crects + offb : rrects + offa;
+            const uint16_t *so = sa ? RS.rorder + offa : CS.rorder + offb;
+            const bool ok = warp_correspond(sr, so, sa ? nar : nbc, lr, sa ? nbc : nar, sa, e.y, e.z, lane);
             if (ok) {
                 if (q < 32) ok0 |= 1u << q;
                 else ok1 |= 1u << (q - 32);
@@ -281,9 +297,9 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
             const bool sa = (e.x >> 16) & 1;
             const int off = sa ? offa : csig[c][1].z;
             ns2 = sa ? nar : csig[c][0].x;
-            rs2 = rects4 + off;
-            ro2 = cs.rorder + off;
-            g2 = sa ? cs.occ + (size_t)(jblk + c) * 64 : grids + r * kGS;
+            rs2 = (sa ? rrects : crects) + off;
+            ro2 = (sa ? RS.rorder : CS.rorder) + off;
+            g2 = sa ? CS.occ + (size_t)(jblk + c) * 64 : grids + r * kGS;
             sx2 = e.y;
             sy2 = e.z;
             e2x = e.x;
@@ -311,22 +327,23 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     // into registers while the current one is processed
     const uint32_t jlast = min(jblk + (uint32_t)kColsB, n);  // one past the last column
     uint32_t c = warp;
-    while (c < (uint32_t)kColsB && jblk + c <= i0) c += 8;  // columns with no row below them
+    if constexpr (!CROSS)
+        while (c < (uint32_t)kColsB && jblk + c <= i0) c += 8;  // columns with no row below them
     ulonglong2 gnext = make_ulonglong2(0ull, 0ull);
-    if (jblk + c < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(cs.occ + (size_t)(jblk + c) * 64) + lane);
+    if (jblk + c < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(CS.occ + (size_t)(jblk + c) * 64) + lane);
     for (; jblk + c < jlast; c += 8) {
         const uint32_t j = jblk + c;
         __syncwarp();  // the previous column's grid is no longer read
         gcol[2 * lane] = gnext.x;
         gcol[2 * lane + 1] = gnext.y;
-        if (j + 8 < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(cs.occ + (size_t)(j + 8) * 64) + lane);
+        if (j + 8 < jlast) gnext = __ldg(reinterpret_cast<const ulonglong2 *>(CS.occ + (size_t)(j + 8) * 64) + lane);
         __syncwarp();
         const int4 b0 = csig[c][0];
         const int nb = b0.x;
         bool push_t = false, push_f = false, both_empty = false;
         bool sa = false;
         int s0x = 0, s0y = 0;
-        if (i < j) {
+        if (CROSS ? i < nr : i < j) {
             if (na == 0 || nb == 0) {
                 if (na == 0 && nb == 0) both_empty = true;
                 else ++g_e1;
@@ -409,9 +426,25 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
     const unsigned grid = (unsigned)((tiles - shard + n_shards - 1) / n_shards);
     const int csz = prm.window_dbu / 64;
     if ((csz & (csz - 1)) == 0)
-        edge_screen_kernel<true><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates, shard, n_shards);
+        edge_screen_kernel<true, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
     else
-        edge_screen_kernel<false><<<grid, 256, 0, st>>>(prm, cs, out, cap, count, gates, shard, n_shards);
+        edge_screen_kernel<false, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
+    return cudaGetLastError();
+}
+
+// query x library screen (serving): every (q, l) pair through E2 and E1, the
+// survivors written as (q, l); tiles of 32 queries x 256 library clips
+cudaError_t launch_edge_screen_cross(const pcl_params &prm, const pcl_clipset &q, const pcl_clipset &lib,
+                                     pcl_pair *out, uint64_t cap, unsigned long long *count,
+                                     unsigned long long *gates, cudaStream_t st) {
+    if (q.n_clips == 0 || lib.n_clips == 0) return cudaSuccess;
+    const uint64_t tiles = (uint64_t)((q.n_clips + 31) / 32) * ((lib.n_clips + kColsB - 1) / kColsB);
+    if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    const int csz = prm.window_dbu / 64;
+    if ((csz & (csz - 1)) == 0)
+        edge_screen_kernel<true, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1);
+    else
+        edge_screen_kernel<false, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1);
     return cudaGetLastError();
 }
 

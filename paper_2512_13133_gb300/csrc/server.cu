@@ -44,8 +44,10 @@ bool tc_supported(const Geo &);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
-cudaError_t launch_edge_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *, pcl_record *,
-                              uint64_t, unsigned long long *, int, cudaStream_t);
+cudaError_t launch_edge_screen_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *,
+                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t);
+cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
+                              const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
                               const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
                               unsigned long long *, unsigned long long *, int, cudaStream_t);
@@ -354,10 +356,13 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->counts, 0, 64, st);
     if (e == cudaSuccess) e = pcl::launch_raster(s->P, sl->q, st);
     if (s->engine == kEdge) {
-        // every (query, library) pair through the edge gates; the survivors'
-        // records come out of the same pass
+        // every (query, library) pair through the edge gates (the tiled screen
+        // of the self-join, rows = queries, columns = library clips), then
+        // the Min-Max record of each survivor, one pair per warp
         if (e == cudaSuccess)
-            e = pcl::launch_edge_cross(s->P, sl->q, s->lib, sl->cand, sl->rec, cap, sl->counts + 0, ctx->num_sms, st);
+            e = pcl::launch_edge_screen_cross(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, nullptr, st);
+        if (e == cudaSuccess)
+            e = pcl::launch_edge_match(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
     } else {
         if (e == cudaSuccess)
             e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws,
