@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
                                                           unsigned long long *count,
                                                           unsigned long long *gates, uint32_t shard,
                                                           uint32_t n_shards) {
-    const uint32_t nr = RS.n_clips, n = CS.n_clips;  // rows, columns
+    const pcl_clipset &RW = CROSS ? RS : CS;  // the row clips (the same set in the self-join)
+    const uint32_t nr = RW.n_clips, n = CS.n_clips;  // rows, columns
     uint32_t bx, by;
     if constexpr (CROSS) {
         const uint32_t nbx = (nr + 31) / 32;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     __shared__ int4 cp0[kColsB];      // smallest polygon of each column clip
     __shared__ int4 tq[8][kQueue];    // grid tests: {row | col << 8 | small_is_a << 16, sx, sy, 0}
     __shared__ int4 fq[8][kQueue];    // full checks: {row | col << 8 | small_is_a << 16, s0x, s0y, 0}
-    const int4 *rrects = reinterpret_cast<const int4 *>(RS.rects), *crects = reinterpret_cast<const int4 *>(CS.rects);
+    const int4 *rrects = reinterpret_cast<const int4 *>(RW.rects), *crects = reinterpret_cast<const int4 *>(CS.rects);
     // flags: bit 0 has x edges, bit 1 has y edges, bit 2 touches the border
     auto load_sig = [&](const pcl_clipset &cl, uint32_t c, int4 &s0, int4 &s1, int4 &p0) {
         const int4 *e4 = reinterpret_cast<const int4 *>(cl.esig + (size_t)c * 8);
@@ -221,11 +222,11 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
         cp0[c] = p0;
     }
     for (int w = threadIdx.x; w < 32 * 64; w += blockDim.x)
-        grids[(w >> 6) * kGS + (w & 63)] = i0 + (w >> 6) < nr ? __ldg(RS.occ + (size_t)i0 * 64 + w) : 0ull;
+        grids[(w >> 6) * kGS + (w & 63)] = i0 + (w >> 6) < nr ? __ldg(RW.occ + (size_t)i0 * 64 + w) : 0ull;
     // this lane's row clip
     const uint32_t i = i0 + lane;
     int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, pa = a0;
-    if (i < nr) load_sig(RS, i, a0, a1, pa);
+    if (i < nr) load_sig(RW, i, a0, a1, pa);
     const int na = a0.x;
     __syncthreads();
     const int csz = W / 64;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
             const int offb = csig[c][1].z, nbc = csig[c][0].x;
             // the small clip's polygons (and area order) and the large clip's
             const int4 *sr = sa ? rrects + offa : crects + offb, *lr = sa ? crects + offb : rrects + offa;
-            const uint16_t *so = sa ? RS.rorder + offa : CS.rorder + offb;
+            const uint16_t *so = sa ? RW.rorder + offa : CS.rorder + offb;
             const bool ok = warp_correspond(sr, so, sa ? nar : nbc, lr, sa ? nbc : nar, sa, e.y, e.z, lane);
             if (ok) {
                 if (q < 32) ok0 |= 1u << q;
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
             const int off = sa ? offa : csig[c][1].z;
             ns2 = sa ? nar : csig[c][0].x;
             rs2 = (sa ? rrects : crects) + off;
-            ro2 = (sa ? RS.rorder : CS.rorder) + off;
+            ro2 = (sa ? RW.rorder : CS.rorder) + off;
             g2 = sa ? CS.occ + (size_t)(jblk + c) * 64 : grids + r * kGS;
             sx2 = e.y;
             sy2 = e.z;
