@@ -180,48 +180,25 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
                 tB = (int)((int64_t)pb - um);
             }
             const int cnt = (int)min(32u, p1 - q0);
-            // the rest of the gates for member k after the pre-screen
-            auto finish = [&](uint32_t bk, int tAk, int tBk) {
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
                 const uint32_t *cwb = reinterpret_cast<const uint32_t *>(L.blk + (size_t)bk * 2 * nb2);
                 if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
                     ++g3;
-                    return;
+                    continue;
                 }
                 if (warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N, g.S,
                                          (int64_t)pa - tAk, lane)) {
                     ++g2;
-                    return;
+                    continue;
                 }
                 ++kept;
                 if (lane == 0) {
                     const unsigned long long idx = atomicAdd(count, 1ull);
                     if (idx < cap) out[idx] = pcl_pair{q, bk};
                 }
-            };
-            // Pre-screen two members at a time, as in the self-join: the
-            // query's deficit over the first 64 blocks against each member's
-            // neighbourhood sums, both sums in one reduction (16-bit halves:
-            // a lane's share is at most 2 * 256, a warp's at most 16384).
-            // Members it keeps get the full gates, which repeat this test.
-            const bool v0 = lane < words;
-            int k = 0;
-            for (; k + 1 < cnt; k += 2) {
-                const uint32_t b0 = __shfl_sync(0xffffffffu, b, k), b1 = __shfl_sync(0xffffffffu, b, k + 1);
-                const int tA0 = __shfl_sync(0xffffffffu, tA, k), tA1 = __shfl_sync(0xffffffffu, tA, k + 1);
-                const uint32_t *d0p = reinterpret_cast<const uint32_t *>(L.blk + (size_t)b0 * 2 * nb2) + words;
-                const uint32_t *d1p = reinterpret_cast<const uint32_t *>(L.blk + (size_t)b1 * 2 * nb2) + words;
-                const uint32_t n0 = v0 ? __ldg(d0p + lane) : 0u, n1 = v0 ? __ldg(d1p + lane) : 0u;
-                const uint32_t x0 = ca[0] - __vminu2(ca[0], n0), x1 = ca[0] - __vminu2(ca[0], n1);
-                const uint32_t both = ((x0 & 0xffffu) + (x0 >> 16)) | (((x1 & 0xffffu) + (x1 >> 16)) << 16);
-                const uint32_t sr = __reduce_add_sync(0xffffffffu, both);
-                const bool r0 = (int)(sr & 0xffffu) >= tA0, r1 = (int)(sr >> 16) >= tA1;
-                g3 += (r0 ? 1 : 0) + (r1 ? 1 : 0);
-                if (!r0) finish(b0, tA0, __shfl_sync(0xffffffffu, tB, k));
-                if (!r1) finish(b1, tA1, __shfl_sync(0xffffffffu, tB, k + 1));
             }
-            if (k < cnt)
-                finish(__shfl_sync(0xffffffffu, b, k), __shfl_sync(0xffffffffu, tA, k),
-                       __shfl_sync(0xffffffffu, tB, k));
         }
     }
     if (lane == 0) {
