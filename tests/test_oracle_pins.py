@@ -432,6 +432,29 @@ def test_setcover_path_graph():
     assert rep.tolist() == [1, 1, 1, 3, 3]
 
 
+def test_cluster_loop_by_hand():
+    """The loop's reading worked by hand on three small graphs (S = 2^32/f,
+    f = 1 + degree in the relaxed graph of the round; ties to the lower index)."""
+    # Path 0-1-2-3, all relaxed, 1-2 not strict.  S = 1/2, 1/3, 1/3, 1/2 (x 2^32):
+    # gains 0.83, 1.17, 1.17, 0.83 -> rep 1 covers {0, 1, 2}; then 3 alone (gain
+    # 1/2) -> rep 3.  Member 0 passes strict with 1; 2 fails with 1 and, as an
+    # orphan, tries reps 1, 3 in order: strict with 3 -> 2 joins 3.  One round.
+    rep, ncl, rounds = oracle.cluster_loop(4, [(0, 1), (1, 2), (2, 3)], np.array([True, False, True]),
+                                           np.array([True, True, True]))
+    assert (rep.tolist(), ncl, rounds) == ([1, 1, 3, 3], 2, 1)
+    # Path 0-1-2, 1-2 not strict, 2 has no strict partner: rep 1 covers all,
+    # 2 is an orphan no rep accepts, so it is re-injected and becomes its own
+    # representative in round 2.
+    rep, ncl, rounds = oracle.cluster_loop(3, [(0, 1), (1, 2)], np.array([True, False]), np.array([True, True]))
+    assert (rep.tolist(), ncl, rounds) == ([1, 1, 2], 2, 2)
+    # 0-1 and 2-3 strict, 1-2 relaxed only, 4 isolated: S = 1/2, 1/3, 1/3, 1/2, 1;
+    # rep 1 first (1.17), then the isolated 4 (gain 1, rarer than 3's 1/2), then 3;
+    # the orphan 2 joins 3 (reps tried in index order 1, 3, 4).
+    rep, ncl, rounds = oracle.cluster_loop(5, [(0, 1), (2, 3), (1, 2)], np.array([True, True, False]),
+                                           np.array([True, True, True]))
+    assert (rep.tolist(), ncl, rounds) == ([1, 1, 3, 3, 4], 3, 1)
+
+
 def test_cluster_loop_invariants(small_set):
     pairs, _ = small_set.candidates(oracle.MODE_EDGE, edge_tol_dbu=6)
     rec = small_set.match(pairs, oracle.MODE_EDGE, edge_tol_dbu=6)
