@@ -365,18 +365,99 @@ def test_cosine_empty_cases():
     assert r["pass_"] == 0 and r["sim"] == 0.0
 
 
-def test_gates_are_lossless_on_subset(small_wl):
-    sub = small_wl.subset(np.arange(220))
-    cs = oracle.ClipSet(sub)
+def _gate_pin_workload(seed, k=16, tol=4):
+    """Clips built so that both modes pass across every edge gate's bound
+    (Sec. 2.2.2, Sec. 3.1 stage 1).  Per random interior clip A:
+      T  A moved by a pixel multiple (cosine sim 1 at the re-aligning shift;
+         edge E = 0);
+      Q  A moved by a pixel multiple with every rectangle shrunk by tol on each
+         side: the bbox width and height differ from A's by exactly 2*tol and
+         the Min-Max residual is exactly tol, so the pair still passes while
+         E2 sits on its bound;
+      X  A plus two small rectangles placed symmetrically left and right of A's
+         bbox: one polygon count more on one side, the bbox centre unchanged,
+         the bbox width far beyond 2*tol; the pair passes both modes (every
+         polygon of A overlaps exactly its copy), and E2 may not judge it
+         because the counts differ."""
+    rng = np.random.default_rng(seed)
+    clips = []
+    for _ in range(k):
+        # 5-8 of the 9 cells of a 3 x 3 grid of 88-dbu cells, one rectangle of
+        # sides 40-60 dbu per cell, at most 8 dbu into it: >= 20 dbu apart
+        rects = []
+        for c in rng.permutation(9)[: int(rng.integers(5, 9))]:
+            ox, oy = (int(4 * v) for v in rng.integers(0, 3, size=2))
+            x0, y0 = 140 + 88 * int(c % 3) + ox, 140 + 88 * int(c // 3) + oy
+            w, h = (int(4 * v) for v in rng.integers(10, 16, size=2))
+            rects.append([x0, y0, x0 + w, y0 + h])
+        tx, ty = (int(4 * v) for v in rng.integers(-6, 7, size=2))
+        shrunk = [[r[0] + tol, r[1] + tol, r[2] - tol, r[3] - tol] for r in rects]
+        qx, qy = (int(4 * v) for v in rng.integers(-4, 5, size=2))
+        lx = min(r[0] for r in rects)
+        ux = max(r[2] for r in rects)
+        ly = min(r[1] for r in rects)
+        e = int(4 * rng.integers(15, 25))
+        extra = [[lx - e, ly, lx - e + 20, ly + 20], [ux + e - 20, ly, ux + e, ly + 20]]
+        clips += [rects, _translate(rects, tx, ty), _translate(shrunk, qx, qy), rects + extra]
+    return synth.from_lists(clips, 512, 4, 32)
+
+
+def _bbox(rects):
+    r = np.asarray(rects)
+    return int(r[:, 2].max() - r[:, 0].min()), int(r[:, 3].max() - r[:, 1].min())
+
+
+def test_gates_are_lossless_across_edge_bounds():
+    # Sec. 3.1 stage 1: a gate may only reject pairs that fail.  The set has
+    # passing pairs in both modes, among them edge pairs whose bbox sizes
+    # differ by exactly 2*tol (E2's bound) and passing pairs of unequal
+    # polygon counts whose bbox widths differ far more (E2 not applicable).
+    tol = 4
+    wl = _gate_pin_workload(41, tol=tol)
+    cs = oracle.ClipSet(wl)
     n = cs.n
     allp = np.array([(i, j) for i in range(n) for j in range(i + 1, n)], dtype=np.uint32)
+    passing = {}
     for mode in (oracle.MODE_COSINE, oracle.MODE_EDGE):
-        kept, counts = cs.candidates(mode)
+        kept, counts = cs.candidates(mode, edge_tol_dbu=tol)
         assert int(counts.sum()) == len(allp)
-        brute = cs.match(allp, mode, use_gates=False)
-        keep = set(map(tuple, kept.tolist()))
+        brute = cs.match(allp, mode, use_gates=False, edge_tol_dbu=tol)
+        passing[mode] = {(int(r["a"]), int(r["b"])) for r in brute if r["pass_"]}
+        assert passing[mode] <= set(map(tuple, kept.tolist()))
+    assert len(passing[oracle.MODE_COSINE]) >= 3 * 16
+    assert len(passing[oracle.MODE_EDGE]) >= 5 * 16
+    at_bound = unequal = 0
+    for a, b in passing[oracle.MODE_EDGE]:
+        ra, rb = wl.clip(a), wl.clip(b)
+        (wa, ha), (wb, hb) = _bbox(ra), _bbox(rb)
+        if len(ra) == len(rb) and max(abs(wa - wb), abs(ha - hb)) == 2 * tol:
+            at_bound += 1
+        if len(ra) != len(rb) and abs(wa - wb) > 2 * tol:
+            unequal += 1
+    assert at_bound >= 16 and unequal >= 16
+
+
+def _all_pairs(n):
+    iu = np.triu_indices(n, 1)
+    return np.stack(iu, 1).astype(np.uint32)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cos_num,tol", [(95, 4), (80, 8)])
+def test_gates_are_lossless_on_every_small_config_pair(small_set, cos_num, tol):
+    # brute force over all 499,500 pairs of the 1,000-clip set: at the
+    # configured thresholds (T = 0.95, tol = 4) and at relaxed ones where many
+    # copies pass (T = 0.80, tol = 8: jitter of +/-8 dbu per edge then puts
+    # bbox differences on both sides of E2's 2*tol = 16)
+    allp = _all_pairs(small_set.n)
+    for mode in (oracle.MODE_COSINE, oracle.MODE_EDGE):
+        kept, counts = small_set.candidates(mode, cos_num=cos_num, edge_tol_dbu=tol)
+        assert int(counts.sum()) == len(allp)
+        brute = small_set.match(allp, mode, use_gates=False, cos_num=cos_num, edge_tol_dbu=tol)
         passing = {(int(r["a"]), int(r["b"])) for r in brute if r["pass_"]}
-        assert passing <= keep
+        if cos_num == 80:
+            assert len(passing) >= 200
+        assert passing <= set(map(tuple, kept.tolist()))
 
 
 def test_gate_bounds_dominate_every_shift(small_set):
