@@ -227,20 +227,30 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
                        uint32_t n_list, pcl_stream stream);
 
 /* ---- a2: lossless pre-screening + candidate generation (Sec. 3.1 stage 1) --
-   Self-join of cs: emits every pair (a < b) that no gate of `mode` rejects.
-   COSINE: area-sorted band join (exactly the G1 survivors), then G3 density
-   and G2 profile bounds.  EDGE: all pairs, E2 bbox then E1 correspondence at
-   the pre-alignment (each polygon of the smaller clip, smallest first, is
-   first checked against the other clip's occupancy grid: no occupied cell
-   under it means no overlap, so E1 fails without scanning rectangles).  Pairs are written to d_out[0 .. min(count, cap)) in
-   unspecified order; *d_count (u64, device) receives the survivor count,
-   which may exceed cap (then re-run with a larger buffer).  d_gate_counts
-   (u64[16], device, may be NULL) is incremented: [0] survivors, [g] pairs
-   rejected by gate g.  Uses the context workspace.
-   Errors: PCL_ERR_INVALID, PCL_ERR_OOM (workspace), PCL_ERR_CUDA. */
-pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
-                          pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
-                          pcl_stream stream);
+   Emits every pair that no gate of `mode` rejects (Sec. 2.3: every pair of
+   patterns is a candidate before the screening).
+   b == NULL: self-join of a, pairs (i, j) with i < j.
+   b != NULL: every pair (i, j) of clip i of a and clip j of b (a query set
+     against a library, say); a and b are clip sets of the same parameters P.
+   COSINE: area-sorted band join (exactly the G1 survivors: a contiguous band
+   of the other set's area order), then G3 density and G2 profile bounds.
+   EDGE: every pair, E2 bbox then E1 correspondence at the pre-alignment
+   (each polygon of the smaller clip, smallest first, is first checked
+   against the other clip's occupancy grid: no occupied cell under it means
+   no overlap, so E1 fails without scanning rectangles); tiles of 32 clips
+   of a x 256 clips of b (or of a, for the self-join).  Pairs are written to
+   d_out[0 .. min(count, cap)) in unspecified order; *d_count (u64, device)
+   receives the survivor count, which may exceed cap (then re-run with a
+   larger buffer).  d_gate_counts (u64[16], device, may be NULL) is
+   incremented: [0] survivors, [g] pairs rejected by gate g (their sum is
+   the number of pairs screened).  COSINE uses the context workspace (two
+   sets: about 16 (N^2 + 2) + 16 |a| + 8 |b| bytes for the area orders of
+   both sets and the bands of a's clips).
+   Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with S > N/16),
+   PCL_ERR_OOM (workspace), PCL_ERR_CUDA. */
+pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *a,
+                          const pcl_clipset *b, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
+                          uint64_t *d_gate_counts, pcl_stream stream);
 
 /* One shard of the self-join of pcl_candidates, for n_shards GPUs (or calls)
    sharing one clip set: shard s of S (0 <= s < S) screens a fixed subset of
@@ -324,6 +334,19 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
 pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl_clipset *a,
                            pcl_clipset *b, const pcl_pair *d_pairs, uint64_t n, const uint64_t *d_n,
                            pcl_record *d_out, pcl_stream stream);
+
+/* Limit of each bounded device-side wait of the kernels launched through ctx
+   from now on, in nanoseconds (0 = the default of one second).  Only the
+   tensor-core engine waits on the device (its warps hand buffers over
+   through shared-memory barriers); a wait that runs out makes the kernel
+   give up its work, wait (always up to one second) for the tensor-core
+   operations it has in flight, release its tensor memory and return, and
+   is reported by pcl_device_error (pcl_match_pairs) or as a completion
+   status PCL_ERR_TIMEOUT (serving).  A limit shorter than the engine's
+   normal hand-over times makes every such launch time out: tests use that
+   to exercise the time-out path without any fault.  Errors:
+   PCL_ERR_INVALID (NULL ctx). */
+pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns);
 
 /* Synchronises the device and reports (then clears) the context's device
    error word: PCL_ERR_TIMEOUT if a kernel's bounded wait ran out (its records

@@ -83,6 +83,8 @@ def _load():
     lib = ctypes.CDLL(build())
     lib.orc_set_create.restype = P
     lib.orc_set_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int]
+    lib.orc_set_create_ex.restype = P
+    lib.orc_set_create_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int]
     lib.orc_set_free.argtypes = [P]
     lib.orc_set_N.argtypes = [P]
     lib.orc_set_pop.restype = ctypes.c_int64
@@ -108,6 +110,8 @@ def _load():
     lib.orc_match.argtypes = [P, P, ctypes.c_int, P, ctypes.c_size_t, P, ctypes.c_int]
     lib.orc_candidates.restype = ctypes.c_int64
     lib.orc_candidates.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int64, P, ctypes.c_int]
+    lib.orc_candidates_ab.restype = ctypes.c_int64
+    lib.orc_candidates_ab.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64, P, ctypes.c_int]
     _lib = lib
     return lib
 
@@ -174,9 +178,13 @@ def fft_size(N: int) -> int:
 
 
 class ClipSet:
-    """Rasters and gate signatures of a workload, held by the C oracle."""
+    """Rasters and gate signatures of a workload, held by the C oracle.
 
-    def __init__(self, wl, marker_dbu: int | None = None):
+    raster=False keeps the rectangles only (no images, no signatures): such a
+    set serves edge mode alone, whose procedure reads rectangles, and is
+    cheap to build for large workloads."""
+
+    def __init__(self, wl, marker_dbu: int | None = None, raster: bool = True):
         self._lib = _load()
         self.W = int(wl.window_dbu)
         self.p = int(wl.pitch_dbu)
@@ -186,8 +194,9 @@ class ClipSet:
         self.n = wl.n
         self.rect_off = np.ascontiguousarray(wl.rect_off, dtype=np.uint32)
         self.rects = np.ascontiguousarray(wl.rects, dtype=np.int32)
-        h = self._lib.orc_set_create(self.W, self.p, self.M, self.rect_off.ctypes.data,
-                                     self.rects.ctypes.data, self.n)
+        self.raster = bool(raster)
+        h = self._lib.orc_set_create_ex(self.W, self.p, self.M, self.rect_off.ctypes.data,
+                                        self.rects.ctypes.data, self.n, int(self.raster))
         if not h:
             raise ValueError("oracle rejected the clip-set parameters")
         self._h = ctypes.c_void_p(h)
@@ -202,18 +211,25 @@ class ClipSet:
         kw.setdefault("marker_dbu", self.M)
         return params(self.W, self.p, **kw)
 
+    def _need_raster(self):
+        if not self.raster:
+            raise ValueError("geometry-only oracle clip set: edge mode only")
+
     def image(self, c: int) -> np.ndarray:
+        self._need_raster()
         img = np.zeros((self.N, self.N), dtype=np.uint8)
         self._lib.orc_set_image(self._h, c, img.ctypes.data)
         return img
 
     def pop(self, c: int) -> int:
+        self._need_raster()
         return int(self._lib.orc_set_pop(self._h, c))
 
     def pops(self) -> np.ndarray:
         return np.array([self.pop(i) for i in range(self.n)], dtype=np.int64)
 
     def signature(self, c: int):
+        self._need_raster()
         nb = (self.N + 15) // 16
         rows = np.zeros(self.N, np.int32)
         cols = np.zeros(self.N, np.int32)
@@ -225,18 +241,22 @@ class ClipSet:
 
     def gate_bounds(self, a: int, b: int) -> np.ndarray:
         """upper bounds of c(s) over the window: [G1 area, G2 profile, G3 density]"""
+        self._need_raster()
         out = np.zeros(3, dtype=np.int64)
         self._lib.orc_gate_bounds(self._h, a, b, out.ctypes.data)
         return out
 
     def corr_window(self, a: int, b: int) -> np.ndarray:
         """exact c(s) for |dx|,|dy| <= S, indexed [dy + S, dx + S]"""
+        self._need_raster()
         K = 2 * self.S + 1
         out = np.zeros((K, K), dtype=np.int64)
         self._lib.orc_corr_window(self._h, a, b, out.ctypes.data)
         return out
 
     def pair(self, a: int, b: int, mode: int = MODE_COSINE, **kw) -> np.void:
+        if mode != MODE_EDGE:
+            self._need_raster()
         rec = np.zeros(1, dtype=REC_DTYPE)
         p = self.params(**kw)
         fn = {MODE_COSINE: self._lib.orc_cosine_pair, MODE_EDGE: self._lib.orc_edge_pair,
@@ -246,6 +266,8 @@ class ClipSet:
 
     def match(self, pairs, mode: int = MODE_COSINE, threads: int | None = None, **kw) -> np.ndarray:
         """one record per (a, b) pair, in order (brute-force shift scan)."""
+        if mode != MODE_EDGE:
+            self._need_raster()
         pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.uint32).reshape(-1, 2))
         out = np.zeros(pr.shape[0], dtype=REC_DTYPE)
         p = self.params(**kw)
@@ -255,6 +277,8 @@ class ClipSet:
 
     def candidates(self, mode: int = MODE_COSINE, threads: int | None = None, **kw):
         """exhaustive self-join gate screen; returns (pairs[m, 2], gate_counts[16])"""
+        if mode != MODE_EDGE:
+            self._need_raster()
         p = self.params(**kw)
         counts = np.zeros(16, dtype=np.uint64)
         m = self._lib.orc_candidates(self._h, ctypes.byref(p), mode, None, 0, counts.ctypes.data,
@@ -262,6 +286,21 @@ class ClipSet:
         pairs = np.zeros((max(int(m), 1), 2), dtype=np.uint32)
         self._lib.orc_candidates(self._h, ctypes.byref(p), mode, pairs.ctypes.data, m,
                                  counts.ctypes.data, threads or default_threads())
+        return pairs[:m], counts
+
+    def candidates_ab(self, n_a: int, mode: int = MODE_COSINE, threads: int | None = None, **kw):
+        """exhaustive two-set gate screen of a set holding the clips of A
+        (0 .. n_a - 1) then those of B: every pair (i, n_a + j); returns
+        (pairs[m, 2] as (i, j) with j relative to B, gate_counts[16])"""
+        if mode != MODE_EDGE:
+            self._need_raster()
+        p = self.params(**kw)
+        counts = np.zeros(16, dtype=np.uint64)
+        m = self._lib.orc_candidates_ab(self._h, ctypes.byref(p), mode, n_a, None, 0, counts.ctypes.data,
+                                        threads or default_threads())
+        pairs = np.zeros((max(int(m), 1), 2), dtype=np.uint32)
+        self._lib.orc_candidates_ab(self._h, ctypes.byref(p), mode, n_a, pairs.ctypes.data, m,
+                                    counts.ctypes.data, threads or default_threads())
         return pairs[:m], counts
 
     # -- phase correlation (Sec. 3.2.1, Eqs. 3-5) ---------------------------

@@ -183,13 +183,23 @@ void orc_set_free(orc_set *s) {
  * Signatures: |A| (ones), row counts r(j), column counts q(i), 16x16 block
  * counts and their (2*rb+1)^2 neighbourhood sums (rb = ceil(S/16)).
  */
-orc_set *orc_set_create(int W, int p, int M, const uint32_t *roff, const int32_t *rects, int n) {
+/* raster = 0 builds a geometry-only set (rectangles, no images or
+   signatures): enough for the edge procedure, which reads rectangles only */
+orc_set *orc_set_create_ex(int W, int p, int M, const uint32_t *roff, const int32_t *rects, int n,
+                           int raster) {
     if (p <= 0 || W % p != 0 || M % p != 0) return NULL;
     orc_set *s = (orc_set *)calloc(1, sizeof(orc_set));
     s->W = W; s->p = p; s->N = W / p; s->nw = (s->N + 63) / 64;
     s->M = M; s->S = M / p; s->n = n;
     s->nb = (s->N + 15) / 16;
     s->rb = (s->S + 15) / 16;
+    if (!raster) {
+        s->roff = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+        memcpy(s->roff, roff, sizeof(uint32_t) * ((size_t)n + 1));
+        s->rects = (int32_t *)malloc(sizeof(int32_t) * (4 * (size_t)roff[n] + 1));
+        memcpy(s->rects, rects, sizeof(int32_t) * 4 * (size_t)roff[n]);
+        return s;
+    }
     int N = s->N, nw = s->nw, nb = s->nb;
     s->img = (uint8_t *)malloc((size_t)n * N * N + 1);
     s->wd = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n * N * nw + 1));
@@ -227,6 +237,10 @@ orc_set *orc_set_create(int W, int p, int M, const uint32_t *roff, const int32_t
             }
     }
     return s;
+}
+
+orc_set *orc_set_create(int W, int p, int M, const uint32_t *roff, const int32_t *rects, int n) {
+    return orc_set_create_ex(W, p, M, roff, rects, n, 1);
 }
 
 int orc_set_N(const orc_set *s) { return s->N; }
@@ -775,6 +789,78 @@ int64_t orc_candidates(const orc_set *s, const orc_params *P, int mode, uint32_t
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j)
             if (c.keep[tri_index(n, i, j)]) {
+                if (m < cap) { pairs[2 * m] = (uint32_t)i; pairs[2 * m + 1] = (uint32_t)j; }
+                ++m;
+            }
+    for (int k = 0; k < 16; ++k) gate_counts[k] = c.counts[k];
+    free(c.keep);
+    pthread_mutex_destroy(&c.mu);
+    return m;
+}
+
+/*
+ * Two-set candidate generation by exhaustive gate evaluation: the set holds
+ * the clips of A (indices 0 .. n_a-1) followed by those of B, and every pair
+ * (i, n_a + j) goes through the same gates as in the self-join (Sec. 3.1
+ * stage 1; Sec. 2.3 makes every pair of patterns a candidate).  Survivors
+ * are written as (i, j), j relative to B, in row order; returns their count
+ * (or the required count if cap is too small).
+ */
+typedef struct {
+    const orc_set *s;
+    const orc_params *P;
+    int mode, n_a;
+    int next;
+    pthread_mutex_t mu;
+    uint8_t *keep;     /* n_a * n_b flags, row i then column j */
+    uint64_t counts[16];
+} cand_ab_job;
+
+static void *cand_ab_worker(void *arg) {
+    cand_ab_job *c = (cand_ab_job *)arg;
+    uint64_t local[16] = {0};
+    int n = c->s->n, na = c->n_a, nb = n - na;
+    for (;;) {
+        pthread_mutex_lock(&c->mu);
+        int i = c->next++;
+        pthread_mutex_unlock(&c->mu);
+        if (i >= na) break;
+        for (int j = 0; j < nb; ++j) {
+            int b = na + j, g;
+            if (c->mode == ORC_MODE_COSINE) {
+                if (c->s->pop[i] == 0 && c->s->pop[b] == 0) g = ORC_GATE_NONE;
+                else g = cosine_gate(c->s, i, b, c->P);
+            } else {
+                g = edge_gate(c->s, i, b, c->P);
+            }
+            local[g]++;
+            c->keep[(size_t)i * nb + j] = (uint8_t)(g == ORC_GATE_NONE);
+        }
+    }
+    pthread_mutex_lock(&c->mu);
+    for (int k = 0; k < 16; ++k) c->counts[k] += local[k];
+    pthread_mutex_unlock(&c->mu);
+    return NULL;
+}
+
+int64_t orc_candidates_ab(const orc_set *s, const orc_params *P, int mode, int n_a, uint32_t *pairs,
+                          int64_t cap, uint64_t *gate_counts, int threads) {
+    int nb = s->n - n_a;
+    if (n_a < 0 || nb < 0) return -1;
+    cand_ab_job c;
+    memset(&c, 0, sizeof(c));
+    c.s = s; c.P = P; c.mode = mode; c.n_a = n_a;
+    pthread_mutex_init(&c.mu, NULL);
+    c.keep = (uint8_t *)calloc((size_t)n_a * nb + 1, 1);
+    if (threads < 1) threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, cand_ab_worker, &c);
+    for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    int64_t m = 0;
+    for (int i = 0; i < n_a; ++i)
+        for (int j = 0; j < nb; ++j)
+            if (c.keep[(size_t)i * nb + j]) {
                 if (m < cap) { pairs[2 * m] = (uint32_t)i; pairs[2 * m + 1] = (uint32_t)j; }
                 ++m;
             }

@@ -151,8 +151,8 @@ def load(build_if_missing: bool = True):
         "pcl_clipset_sizes_get": ([ctypes.POINTER(Params), ctypes.c_uint32, _U64, ctypes.POINTER(_Sizes)], st),
         "pcl_rasterize": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP], st),
         "pcl_spectra": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, ctypes.c_uint32, _VP], st),
-        "pcl_candidates": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset), _VP, _U64,
-                            _VP, _VP, _VP], st),
+        "pcl_candidates": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
+                            ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_candidates_shard": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                                   ctypes.c_uint32, ctypes.c_uint32, _VP, _U64, _VP, _VP, _VP], st),
         "pcl_candidates_cosine_noalloc": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, _U64,
@@ -160,6 +160,7 @@ def load(build_if_missing: bool = True):
         "pcl_match_pairs": ([_VP, ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_Clipset),
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_device_error": ([_VP, ctypes.POINTER(ctypes.c_int)], st),
+        "pcl_set_wait_limit": ([_VP, _U64], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
         "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
@@ -329,12 +330,15 @@ def pcl_spectra(ctx: Context, P: Params, cs: ClipSet, clip_list=None, stream=Non
 
 
 def pcl_candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, out_pairs, d_count, d_gates=None,
-                   stream=None) -> None:
+                   stream=None, b: ClipSet | None = None) -> None:
     """out_pairs: int32 CUDA tensor [cap, 2]; d_count: int64 CUDA tensor [1];
-    d_gates: int64 CUDA tensor [16] (accumulated) or None."""
+    d_gates: int64 CUDA tensor [16] (accumulated) or None; b: second clip set
+    (pairs of cs x b) or None (self-join of cs)."""
     c = cs.cstruct()
+    cb = b.cstruct() if b is not None else None
     cap = 0 if out_pairs is None else int(out_pairs.shape[0])
-    ctx.check(ctx.lib.pcl_candidates(ctx.h, ctypes.byref(P), mode, ctypes.byref(c), _ptr(out_pairs), cap,
+    ctx.check(ctx.lib.pcl_candidates(ctx.h, ctypes.byref(P), mode, ctypes.byref(c),
+                                     ctypes.byref(cb) if cb is not None else None, _ptr(out_pairs), cap,
                                      _ptr(d_count), _ptr(d_gates), _stream_ptr(stream)), "pcl_candidates")
 
 
@@ -392,6 +396,11 @@ def pcl_device_error(ctx: Context) -> int:
     f = ctypes.c_int()
     ctx.check(ctx.lib.pcl_device_error(ctx.h, ctypes.byref(f)), "pcl_device_error")
     return int(f.value)
+
+
+def pcl_set_wait_limit(ctx: Context, ns: int) -> None:
+    """Limit of each bounded device-side wait (ns; 0 = one second)."""
+    ctx.check(ctx.lib.pcl_set_wait_limit(ctx.h, int(ns)), "pcl_set_wait_limit")
 
 
 def pcl_compact_pass(ctx: Context, rec, out_pairs, d_count, d_n=None, stream=None) -> None:
@@ -468,10 +477,11 @@ def signatures(cs: ClipSet):
 
 
 def candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, cap: int = 1 << 20, stream=None,
-               shard: int = 0, n_shards: int = 1):
+               shard: int = 0, n_shards: int = 1, b: ClipSet | None = None):
     """Self-join candidate pairs of `mode` (re-runs once with the exact capacity
-    if `cap` was too small), or those of one shard of the pair space.  Returns
-    (pairs int32 [m, 2] CUDA, gate counts numpy int64 [16])."""
+    if `cap` was too small), those of one shard of the pair space, or with
+    `b` the pairs of cs x b.  Returns (pairs int32 [m, 2] CUDA, gate counts
+    numpy int64 [16])."""
     torch = _torch()
     dev = cs.bits.device
     for _ in range(2):
@@ -479,7 +489,7 @@ def candidates(ctx: Context, P: Params, mode: int, cs: ClipSet, cap: int = 1 << 
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         gates = torch.zeros(16, dtype=torch.int64, device=dev)
         if n_shards == 1:
-            pcl_candidates(ctx, P, mode, cs, out, cnt, gates, stream)
+            pcl_candidates(ctx, P, mode, cs, out, cnt, gates, stream, b=b)
         else:
             pcl_candidates_shard(ctx, P, mode, cs, shard, n_shards, out, cnt, gates, stream)
         m = int(cnt.item())

@@ -15,6 +15,14 @@ cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, si
                              unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
 cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
                                unsigned long long *, unsigned long long *, cudaStream_t, uint32_t, uint32_t);
+cudaError_t launch_edge_screen_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *,
+                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t);
+cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
+                             int, cudaStream_t);
+size_t cross_join_workspace(const Geo &, uint32_t, uint32_t);
+cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
+                              const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
+                              unsigned long long *, unsigned long long *, int, cudaStream_t);
 cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                               const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32_t *, uint32_t, bool,
@@ -30,7 +38,8 @@ cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pc
                                uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
-                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
+                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, unsigned long long,
+                      cudaStream_t);
 cudaError_t launch_xysep(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                          const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
@@ -146,6 +155,12 @@ void pcl_destroy(pcl_ctx *ctx) {
 
 const char *pcl_last_error(const pcl_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
+pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns) {
+    if (!ctx) return PCL_ERR_INVALID;
+    ctx->wait_ns = ns;
+    return PCL_OK;
+}
+
 pcl_status pcl_params_validate(const pcl_params *P) {
     if (!P) return PCL_ERR_INVALID;
     if (P->pitch_dbu <= 0 || P->window_dbu <= 0 || P->window_dbu % P->pitch_dbu) return PCL_ERR_INVALID;
@@ -201,10 +216,40 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "spectra kernel");
 }
 
-pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
-                          pcl_pair *d_out, uint64_t cap, uint64_t *d_count, uint64_t *d_gate_counts,
-                          pcl_stream stream) {
-    return pcl_candidates_shard(ctx, P, mode, cs, 0, 1, d_out, cap, d_count, d_gate_counts, stream);
+pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *a,
+                          const pcl_clipset *b, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
+                          uint64_t *d_gate_counts, pcl_stream stream) {
+    if (!b) return pcl_candidates_shard(ctx, P, mode, a, 0, 1, d_out, cap, d_count, d_gate_counts, stream);
+    pcl_status s = enter(ctx);
+    if (s) return s;
+    if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
+    const bool edge = mode == PCL_MODE_EDGE;
+    if (!edge && mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
+    if ((s = check_clipset(ctx, a, edge)) || (s = check_clipset(ctx, b, edge))) return s;
+    if (!d_count || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL output%s%lld");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    auto *cnt = reinterpret_cast<unsigned long long *>(d_count);
+    auto *gates = reinterpret_cast<unsigned long long *>(d_gate_counts);
+    if (edge) {
+        e = launch_edge_screen_cross(*P, *a, *b, d_out, cap, cnt, gates, st);
+        return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge screen (two sets)");
+    }
+    const Geo g = make_geo(*P);
+    if (g.S > g.N / 16) return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine gates need S <= N/16%s%lld");
+    // workspace: B's area histogram, fill counters, area order and sorted
+    // areas, then the cross join's own part (16-byte aligned)
+    const uint32_t V = (uint32_t)g.N * g.N + 2, nb = b->n_clips;
+    const size_t sort_bytes = ((4 * (2 * (size_t)V + 2 * (size_t)nb)) + 15) & ~(size_t)15;
+    const size_t join_bytes = cross_join_workspace(g, a->n_clips, nb);
+    if ((s = ensure_ws(ctx, sort_bytes + join_bytes))) return s;
+    uint32_t *cum = static_cast<uint32_t *>(ctx->ws), *fill = cum + V, *order = fill + V, *spop = order + nb;
+    e = launch_area_sort(b->pop, nb, V, cum, fill, order, spop, ctx->num_sms, st);
+    if (e == cudaSuccess)
+        e = launch_cross_join(*P, *a, *b, order, spop, cum, static_cast<char *>(ctx->ws) + sort_bytes,
+                              ctx->ws_bytes - sort_bytes, d_out, cap, cnt, gates, ctx->num_sms, st);
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "band join (two sets)");
 }
 
 pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
@@ -262,7 +307,8 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
                         "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax%s%lld");
         if (n == 0) return PCL_OK;
         if ((s = ensure_ws(ctx, tc_workspace(n)))) return s;
-        e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err, st);
+        e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err,
+                      ctx->wait_ns, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "tensor-core correlation");
     }
     if (P->cos_engine == PCL_ENGINE_XYSEP) {

@@ -10,4 +10,5 @@ struct pcl_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int *d_err = nullptr;  // device error word set by kernels whose bounded waits ran out
+    unsigned long long wait_ns = 0;  // limit of each bounded device-side wait (0: one second)
 };

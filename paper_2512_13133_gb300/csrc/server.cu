@@ -43,7 +43,8 @@ size_t cross_join_workspace(const Geo &, uint32_t, uint32_t);
 bool tc_supported(const Geo &);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
-                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, cudaStream_t);
+                      const unsigned long long *, pcl_record *, void *, size_t, int, int *, unsigned long long,
+                      cudaStream_t);
 cudaError_t launch_edge_screen_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *,
                                      uint64_t, unsigned long long *, unsigned long long *, cudaStream_t);
 cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
@@ -372,7 +373,7 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
             // a bounded wait that runs out sets the request's own error word
             if (e == cudaSuccess)
                 e = pcl::launch_tc(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, sl->ws, sl->ws_bytes,
-                                   ctx->num_sms, reinterpret_cast<int *>(sl->counts + 2), st);
+                                   ctx->num_sms, reinterpret_cast<int *>(sl->counts + 2), ctx->wait_ns, st);
         } else {
             if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
             if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);

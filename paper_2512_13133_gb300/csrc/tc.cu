@@ -48,8 +48,9 @@
 // Buffers change hands through mbarriers (producers arrive; tcgen05.commit
 // releases), and the accumulators are double buffered in TMEM (2 x 256
 // columns), so the epilogue of one item overlaps the MMAs of the next.  Every
-// wait is bounded (one second): on time-out the CTA records an error, each role
-// leaves its loop, and the MMAs still in flight are waited for before the
+// wait is bounded (one second unless the context sets another limit): on
+// time-out the CTA records an error, each role leaves its loop, and the MMAs
+// still in flight are waited for (always with the one-second limit) before the
 // tensor memory is released.
 #include <climits>
 
@@ -219,19 +220,21 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// bounded wait for the phase of the given parity; false on time-out or when
-// another role has aborted (abort_flag may be null: wait regardless)
-__device__ __forceinline__ bool wait_phase_slow(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
+// bounded wait for the phase of the given parity; false after limit_ns or
+// when another role has aborted (abort_flag may be null: wait regardless)
+__device__ __forceinline__ bool wait_phase_slow(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag,
+                                                unsigned long long limit_ns) {
     const uint64_t t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 16; ++i)
             if (mbar_try_wait(mbar, parity)) return true;
         if (abort_flag && *abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag) {
-    return mbar_try_wait(mbar, parity) || wait_phase_slow(mbar, parity, abort_flag);
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, const volatile uint32_t *abort_flag,
+                                           unsigned long long limit_ns) {
+    return mbar_try_wait(mbar, parity) || wait_phase_slow(mbar, parity, abort_flag, limit_ns);
 }
 
 // barrier over `count` threads of one role that also ORs a flag
@@ -416,7 +419,8 @@ __device__ __forceinline__ void stage_load(uint64_t (&o)[C::TPT][C::WPT], const 
 template <int S, int NW, int OP>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_corr_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, const uint32_t *surv,
-                   const TcItem *items, const unsigned int *n_items, pcl_record *out, int *err) {
+                   const TcItem *items, const unsigned int *n_items, pcl_record *out, int *err,
+                   unsigned long long wait_ns) {
     using C = Tc<S, NW, OP>;
     constexpr int N = C::N, RR = C::RR;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -484,14 +488,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t idesc = idesc_of(128, ncols, OP);
                 uint32_t accum = 0;  // the first MMA of the item into this copy overwrites
                 const uint32_t ab = li & 1;
-                if (li >= 2 && !(ok = wait_phase(bar(kAccEmpty + ab), ((li >> 1) - 1) & 1, abortf))) break;
+                if (li >= 2 && !(ok = wait_phase(bar(kAccEmpty + ab), ((li >> 1) - 1) & 1, abortf, wait_ns))) break;
                 fence_after();
                 const uint32_t dcol = tmem + ab * (uint32_t)kMaxCols + (uint32_t)(iw * ncols);
                 // descriptors: only the start field (16-byte units) moves below
                 const uint64_t bd_item = smem_desc(sbase + C::OFF_RING, lbo, 128);
                 for (int ph = 0; ph < C::NPH && ok; ++ph, ++pc) {
                     const uint32_t abf = pc & 1;
-                    if (!(ok = wait_phase(bar(kAFull + abf), (pc >> 1) & 1, abortf))) break;
+                    if (!(ok = wait_phase(bar(kAFull + abf), (pc >> 1) & 1, abortf, wait_ns))) break;
                     // A copies interleaved per image row ([row][copy][16 B]): a core
                     // matrix is 8 copies of one row (128-byte aligned), the next K
                     // core matrix the next row (256 bytes), the next group of 8 M
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t e0 = e;
                     for (int st = -C::ZE + iw; st < C::NST; st += kIssuers) {
                         const uint32_t e = e0 + (uint32_t)(st + C::ZE);
-                        if (!(ok = wait_phase(bar(kBFull + e % RR), (e / RR) & 1, abortf))) break;
+                        if (!(ok = wait_phase(bar(kBFull + e % RR), (e / RR) & 1, abortf, wait_ns))) break;
                         if (st >= 0) {
                             // the operands were published by the producers' proxy fence
                             // and arrival; no tcgen05 fence is needed on this path
@@ -530,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) raise_abort();
             // every MMA issued so far has completed before the tensor memory is released
             mma_commit(bar(kFin));
-            if (!wait_phase(bar(kFin), 0, nullptr)) raise_abort();
+            if (!wait_phase(bar(kFin), 0, nullptr, kWaitNs)) raise_abort();  // always the full limit
         }
         __syncwarp();
     } else if (warp < kIssuers + kAProd / 32) {
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t *abits = A.bits + (size_t)pairs[surv[item.first]].a * N * NW;
             for (int ph = 0; ph < C::NPH; ++ph, ++pc) {
                 const uint32_t abf = pc & 1;
-                if (pc >= 2 && !(ok = wait_phase(bar(kAEmpty + abf), ((pc >> 1) - 1) & 1, abortf))) break;
+                if (pc >= 2 && !(ok = wait_phase(bar(kAEmpty + abf), ((pc >> 1) - 1) & 1, abortf, wait_ns))) break;
                 unsigned char *buf = sm + abf * C::ABYTES;
                 const int base = ph * C::CH - S;  // copy g, pixel k = A column base + g + k
                 // (row ridx, copy g) at 16 (16 ridx + g); a thread writes the 16
@@ -610,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             bool first = true;  // the layout changes with the item: wait for the previous item's MMAs
             // done(x): the MMAs of entry x (by issuer x % 2) have completed
-            auto done = [&](uint32_t x) { return wait_phase(bar(kBFull + RR + x % RR), (x / RR) & 1, abortf); };
+            auto done = [&](uint32_t x) { return wait_phase(bar(kBFull + RR + x % RR), (x / RR) & 1, abortf, wait_ns); };
             // entries e, e + 1 (stages st0, st0 + 1 of phase ph) from the words in b
             auto pair_step = [&](const uint64_t(&b)[2][C::TPT][C::WPT], int ph, int st0) -> bool {
                 const int sb = ph * C::CH - C::STRIP;
@@ -699,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const TcItem item = items[it];
             const uint32_t a = pairs[surv[item.first]].a;
             const uint32_t ab = li & 1;
-            const bool w = wait_phase(bar(kAccFull + ab), (li >> 1) & 1, abortf);
+            const bool w = wait_phase(bar(kAccFull + ab), (li >> 1) & 1, abortf, wait_ns);
             if (bar_any(kBarEpi, kEpi, !w)) {
                 ok = false;
                 break;
@@ -923,23 +927,25 @@ namespace {
 template <int S, int NW, int OP>
 cudaError_t launch_corr(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
                         const uint32_t *surv, const TcItem *items, const unsigned int *n_items, pcl_record *out,
-                        int num_sms, int *d_err, cudaStream_t st) {
+                        int num_sms, int *d_err, unsigned long long wait_ns, cudaStream_t st) {
     using C = Tc<S, NW, OP>;
     cudaError_t e = cudaFuncSetAttribute(tc_corr_kernel<S, NW, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::BYTES);
     if (e != cudaSuccess) return e;
-    tc_corr_kernel<S, NW, OP><<<num_sms, kThreads, C::BYTES, st>>>(prm, a, b, pairs, surv, items, n_items, out, d_err);
+    tc_corr_kernel<S, NW, OP><<<num_sms, kThreads, C::BYTES, st>>>(prm, a, b, pairs, surv, items, n_items, out, d_err,
+                                                                                wait_ns);
     return cudaGetLastError();
 }
 
 template <int S, int NW>
 cudaError_t launch_corr_op(int op, const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
                            const pcl_pair *pairs, const uint32_t *surv, const TcItem *items,
-                           const unsigned int *n_items, pcl_record *out, int num_sms, int *d_err, cudaStream_t st) {
+                           const unsigned int *n_items, pcl_record *out, int num_sms, int *d_err,
+                           unsigned long long wait_ns, cudaStream_t st) {
     switch (op) {
-        case kOpE4M3: return launch_corr<S, NW, kOpE4M3>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        case kOpBF16: return launch_corr<S, NW, kOpBF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        default: return launch_corr<S, NW, kOpF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case kOpE4M3: return launch_corr<S, NW, kOpE4M3>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+        case kOpBF16: return launch_corr<S, NW, kOpBF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+        default: return launch_corr<S, NW, kOpF16>(prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
     }
 }
 
@@ -952,9 +958,10 @@ int members_of() {
 
 cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
                       uint64_t n, const unsigned long long *d_n, pcl_record *out, void *ws, size_t ws_bytes,
-                      int num_sms, int *d_err, cudaStream_t st) {
+                      int num_sms, int *d_err, unsigned long long wait_ns, cudaStream_t st) {
     const Geo g = make_geo(prm);
     if (!tc_supported(g)) return cudaErrorNotSupported;
+    if (wait_ns == 0) wait_ns = kWaitNs;
     if (n == 0) return cudaSuccess;
     if (ws_bytes < tc_workspace(n) || n > 0xffffffffull) return cudaErrorInvalidValue;
     const int op = prm.cos_engine == PCL_ENGINE_TC_DIRECT_FP8   ? kOpE4M3
@@ -979,9 +986,9 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     tc_items_kernel<<<num_sms * 4, 256, 0, st>>>(keep, nullptr, pos + n, NB, items, n_items, (uint32_t)n + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (g.S) {
-        case 4: return launch_corr_op<4, 1>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        case 8: return launch_corr_op<8, 2>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
-        default: return launch_corr_op<16, 4>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, st);
+        case 4: return launch_corr_op<4, 1>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+        case 8: return launch_corr_op<8, 2>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+        default: return launch_corr_op<16, 4>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
     }
 }
 

@@ -155,6 +155,54 @@ def from_lists(clips, window_dbu: int, pitch_dbu: int = 4, marker_dbu: int = 0,
                     np.full(len(clips), -1, np.int32))
 
 
+def concat(first: Workload, second: Workload, name: str = "concat") -> Workload:
+    """The clips of `first` followed by those of `second` (same window, pitch
+    and marker); clip k of `second` becomes clip first.n + k."""
+    off = np.concatenate([first.rect_off[:-1], second.rect_off + first.rect_off[-1]]).astype(np.uint32)
+    rects = np.ascontiguousarray(np.concatenate([first.rects, second.rects]), dtype=np.int32)
+    return Workload(name, first.window_dbu, first.pitch_dbu, first.marker_dbu, off, rects,
+                    np.concatenate([first.label, second.label]), dict(first.meta))
+
+
+def gate_bounds_set(seed: int, k: int = 16, tol_dbu: int = 4) -> Workload:
+    """Clips placed so that both constraint modes pass across the edge gates'
+    bounds (W = 512 dbu, 4 dbu/px, marker half-width 32 dbu).  Per random
+    interior clip A (5-8 rectangles of sides 40-60 dbu, one in each chosen
+    cell of a 3 x 3 grid of 88-dbu cells, so >= 20 dbu apart), four clips:
+      A;
+      A moved by a pixel multiple (at most 24 dbu per axis);
+      A moved by a pixel multiple (at most 16 dbu) with every rectangle
+        shrunk by tol_dbu on each side (bbox width and height tol_dbu * 2
+        below A's);
+      A plus two 20 x 20 dbu rectangles placed symmetrically left and right
+        of A's bbox, 40-76 dbu beyond it (two polygons more, bbox centre
+        unchanged, bbox width far larger)."""
+    rng = np.random.default_rng(seed)
+    clips = []
+
+    def moved(rs, tx, ty):
+        return [[r[0] + tx, r[1] + ty, r[2] + tx, r[3] + ty] for r in rs]
+
+    for _ in range(k):
+        rects = []
+        for c in rng.permutation(9)[: int(rng.integers(5, 9))]:
+            ox, oy = (int(4 * v) for v in rng.integers(0, 3, size=2))
+            x0, y0 = 140 + 88 * int(c % 3) + ox, 140 + 88 * int(c // 3) + oy
+            w, h = (int(4 * v) for v in rng.integers(10, 16, size=2))
+            rects.append([x0, y0, x0 + w, y0 + h])
+        tx, ty = (int(4 * v) for v in rng.integers(-6, 7, size=2))
+        t = tol_dbu
+        shrunk = [[r[0] + t, r[1] + t, r[2] - t, r[3] - t] for r in rects]
+        qx, qy = (int(4 * v) for v in rng.integers(-4, 5, size=2))
+        lx = min(r[0] for r in rects)
+        ux = max(r[2] for r in rects)
+        ly = min(r[1] for r in rects)
+        e = int(4 * rng.integers(15, 25))
+        extra = [[lx - e, ly, lx - e + 20, ly + 20], [ux + e - 20, ly, ux + e, ly + 20]]
+        clips += [rects, moved(rects, tx, ty), moved(shrunk, qx, qy), rects + extra]
+    return from_lists(clips, 512, 4, 32, name="gate_bounds")
+
+
 def batched(seed: int = 1, clips_per_class: int = 1000, sizes=(64, 128, 256, 512), pitch_dbu: int = 4,
             zipf_s: float = 1.1, max_list: int = 5000, same_seed_frac: float = 0.5, min_rects: int = 5,
             max_rects: int = 40):

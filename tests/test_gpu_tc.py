@@ -118,3 +118,37 @@ def test_tc_rejects_uncovered_geometry(torch_cuda):
         pcl.match(ctx, P, pcl.MODE_COSINE, cs, cs, tp)
     assert ei.value.status == pcl.PCL_ERR_UNSUPPORTED
     ctx.close()
+
+
+def test_tc_wait_limit_times_out_and_context_recovers(torch_cuda):
+    """A wait limit far below the engine's hand-over times (1 ns) makes the
+    tensor-core launch give up: pcl_device_error reports PCL_ERR_TIMEOUT and
+    clears the word.  No GPU fault: the kernel drains its tensor-core work and
+    returns.  With the default limit restored, the same context gives the
+    oracle's records again."""
+    import paper_2512_13133_gb300 as pcl
+    wl = _workload("n256")
+    rng = np.random.default_rng(12)
+    pairs = _pairs(wl, rng, 800)
+    ctx = pcl.Context(0)
+    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_engine=pcl.ENGINE_TC_DIRECT,
+                    flags=pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(Pt, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, Pt, cs)
+    tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
+    assert pcl.pcl_device_error(ctx) == 0
+    pcl.pcl_set_wait_limit(ctx, 1)
+    pcl.match(ctx, Pt, pcl.MODE_COSINE, cs, cs, tp)
+    with pytest.raises(pcl.PclError) as e:
+        pcl.pcl_device_error(ctx)
+    assert e.value.status == pcl.PCL_ERR_TIMEOUT
+    assert pcl.pcl_device_error(ctx) == 0  # reported once, then cleared
+    pcl.pcl_set_wait_limit(ctx, 0)
+    g = pcl.records_to_numpy(pcl.match(ctx, Pt, pcl.MODE_COSINE, cs, cs, tp))
+    assert pcl.pcl_device_error(ctx) == 0
+    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=False)
+    np.testing.assert_array_equal(g["pass_"], o["pass_"])
+    for f in ("dx_dbu", "dy_dbu"):
+        np.testing.assert_array_equal(g[f], o[f])
+    np.testing.assert_array_equal(g["score"].astype(np.int64), o["score"])
+    ctx.close()

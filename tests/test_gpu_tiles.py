@@ -52,3 +52,38 @@ def test_candidates_at_tile_edges(ctx, n, mode):
     assert got == set(map(tuple, op.astype(np.int64).tolist()))
     np.testing.assert_array_equal(gcounts[:6], ocounts[:6].astype(np.int64))
     assert gcounts[:6].sum() == n * (n - 1) // 2
+
+
+@pytest.mark.parametrize("tol", [4, 6])
+def test_candidates_and_records_across_edge_gate_bounds(ctx, torch_cuda, tol):
+    """Clips whose passing edge pairs sit exactly on E2's bound (bbox sizes
+    2*tol apart, residual tol) or have unequal polygon counts with far wider
+    bboxes (synth.gate_bounds_set, built for tol = 4): candidate sets, gate
+    counts and the records of every pair equal the oracle's in both modes,
+    and the passing pairs are among the candidates."""
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.gate_bounds_set(41, tol_dbu=4)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, edge_tol_dbu=tol)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects)
+    pcl.pcl_rasterize(ctx, P, cs)
+    orc = oracle.ClipSet(wl)
+    n = wl.n
+    allp = np.array([(i, j) for i in range(n) for j in range(i + 1, n)], dtype=np.int64)
+    for mode in (1, 2):
+        gp, gcounts = pcl.candidates(ctx, P, mode, cs)
+        op, ocounts = orc.candidates(mode, edge_tol_dbu=tol)
+        got = set(map(tuple, gp.cpu().numpy().astype(np.int64).tolist()))
+        assert got == set(map(tuple, op.astype(np.int64).tolist()))
+        np.testing.assert_array_equal(gcounts[:6], ocounts[:6].astype(np.int64))
+        tp = torch_cuda.from_numpy(allp.astype(np.int32)).cuda()
+        g = pcl.records_to_numpy(pcl.match(ctx, P, mode, cs, cs, tp))
+        o = orc.match(allp, mode, edge_tol_dbu=tol)
+        np.testing.assert_array_equal(g["flags"] & 15, o["flags"] & 15)
+        np.testing.assert_array_equal(g["pass_"], o["pass_"])
+        al = (o["flags"] & oracle.F_ALIGNED) > 0
+        for f in ("dx_dbu", "dy_dbu"):
+            np.testing.assert_array_equal(g[f][al], o[f][al])
+        np.testing.assert_array_equal(g["score"][al].astype(np.int64), o["score"][al])
+        assert int(o["pass_"].sum()) >= 48
+        passing = {(int(a), int(b)) for a, b in allp[o["pass_"] > 0]}
+        assert passing <= got

@@ -365,43 +365,6 @@ def test_cosine_empty_cases():
     assert r["pass_"] == 0 and r["sim"] == 0.0
 
 
-def _gate_pin_workload(seed, k=16, tol=4):
-    """Clips built so that both modes pass across every edge gate's bound
-    (Sec. 2.2.2, Sec. 3.1 stage 1).  Per random interior clip A:
-      T  A moved by a pixel multiple (cosine sim 1 at the re-aligning shift;
-         edge E = 0);
-      Q  A moved by a pixel multiple with every rectangle shrunk by tol on each
-         side: the bbox width and height differ from A's by exactly 2*tol and
-         the Min-Max residual is exactly tol, so the pair still passes while
-         E2 sits on its bound;
-      X  A plus two small rectangles placed symmetrically left and right of A's
-         bbox: one polygon count more on one side, the bbox centre unchanged,
-         the bbox width far beyond 2*tol; the pair passes both modes (every
-         polygon of A overlaps exactly its copy), and E2 may not judge it
-         because the counts differ."""
-    rng = np.random.default_rng(seed)
-    clips = []
-    for _ in range(k):
-        # 5-8 of the 9 cells of a 3 x 3 grid of 88-dbu cells, one rectangle of
-        # sides 40-60 dbu per cell, at most 8 dbu into it: >= 20 dbu apart
-        rects = []
-        for c in rng.permutation(9)[: int(rng.integers(5, 9))]:
-            ox, oy = (int(4 * v) for v in rng.integers(0, 3, size=2))
-            x0, y0 = 140 + 88 * int(c % 3) + ox, 140 + 88 * int(c // 3) + oy
-            w, h = (int(4 * v) for v in rng.integers(10, 16, size=2))
-            rects.append([x0, y0, x0 + w, y0 + h])
-        tx, ty = (int(4 * v) for v in rng.integers(-6, 7, size=2))
-        shrunk = [[r[0] + tol, r[1] + tol, r[2] - tol, r[3] - tol] for r in rects]
-        qx, qy = (int(4 * v) for v in rng.integers(-4, 5, size=2))
-        lx = min(r[0] for r in rects)
-        ux = max(r[2] for r in rects)
-        ly = min(r[1] for r in rects)
-        e = int(4 * rng.integers(15, 25))
-        extra = [[lx - e, ly, lx - e + 20, ly + 20], [ux + e - 20, ly, ux + e, ly + 20]]
-        clips += [rects, _translate(rects, tx, ty), _translate(shrunk, qx, qy), rects + extra]
-    return synth.from_lists(clips, 512, 4, 32)
-
-
 def _bbox(rects):
     r = np.asarray(rects)
     return int(r[:, 2].max() - r[:, 0].min()), int(r[:, 3].max() - r[:, 1].min())
@@ -413,7 +376,7 @@ def test_gates_are_lossless_across_edge_bounds():
     # differ by exactly 2*tol (E2's bound) and passing pairs of unequal
     # polygon counts whose bbox widths differ far more (E2 not applicable).
     tol = 4
-    wl = _gate_pin_workload(41, tol=tol)
+    wl = synth.gate_bounds_set(41, tol_dbu=tol)
     cs = oracle.ClipSet(wl)
     n = cs.n
     allp = np.array([(i, j) for i in range(n) for j in range(i + 1, n)], dtype=np.uint32)
@@ -640,3 +603,19 @@ def test_xysep_dbu_shift_rounds_half_away_from_zero():
     for (tx, ty), want in [((6, -6), (-8, 8)), ((5, -7), (-4, 8))]:
         _, r = _xysep(base, _translate(base, tx, ty))
         assert (r["dx_dbu"], r["dy_dbu"]) == want
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_COSINE, oracle.MODE_EDGE])
+def test_two_set_screen_is_the_union_self_join_across_the_sets(small_wl, mode):
+    # Sec. 2.3: every pair of patterns is a candidate before the screening;
+    # the A x B screen must keep exactly the cross pairs the self-join of the
+    # union keeps, with A's clips first
+    a = small_wl.subset(np.arange(0, 150))
+    b = small_wl.subset(np.arange(150, 420))
+    cs = oracle.ClipSet(synth.concat(a, b))
+    p, c = cs.candidates_ab(a.n, mode, cos_num=80)
+    assert int(c.sum()) == a.n * b.n
+    q, _ = cs.candidates(mode, cos_num=80)
+    q = q.astype(np.int64)
+    sel = (q[:, 0] < a.n) & (q[:, 1] >= a.n)
+    assert set(map(tuple, p.astype(np.int64).tolist())) == set(map(tuple, (q[sel] - [0, a.n]).tolist()))
