@@ -436,7 +436,9 @@ def run_batched(pcl, ctx, dev, clips_per_class: int, steps: int, seed: int = 1):
     aligned = int(((rec["flags"] & pcl.F_ALIGNED) > 0).sum())
     unsupported = int(((rec["flags"] & 15) == pcl.GATE_UNSUPPORTED).sum())
     best_ms = min(eager_ms, graph_ms) if isinstance(graph_ms, float) else eager_ms
-    return {"clips": int(sum(w.n for w in wls)), "sizes": [w.raster_n for w in wls], "pairs": int(len(pairs)),
+    return {"config": f"batched recipe at {int(sum(w.n for w in wls)):,} clips ({clips_per_class:,} per size class; "
+                      "the configured 1,000,000 clips: --batch-clips 250000)",
+            "clips": int(sum(w.n for w in wls)), "sizes": [w.raster_n for w in wls], "pairs": int(len(pairs)),
             "cosine_pairs": n_cos, "aligned": aligned, "unsupported": unsupported,
             "ms_eager": eager_ms, "ms_graph": graph_ms, "pairs_per_s": len(pairs) / (best_ms / 1e3),
             "aligned_per_s": aligned / (best_ms / 1e3),
@@ -456,14 +458,34 @@ def workload(config: str, seed: int, clips: int = 0):
 
 # ---------------------------------------------------------------- oracle arm
 
-def oracle_sample(wl, n_clips: int):
+def cpu_model() -> str:
+    """host CPU model name (lscpu, else /proc/cpuinfo, else platform)"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(wl, n_clips: int, threads: int = 0):
     """Time the CPU oracle, as it stands, on the first n_clips clips of the
     workload: rasters + signatures, exhaustive gate screens of both modes,
     brute-force alignment of the survivors.  Returns (aligned pairs, seconds,
     threads)."""
     import oracle
     sub = wl.subset(np.arange(min(n_clips, wl.n)))
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     t0 = time.perf_counter()
     cs = oracle.ClipSet(sub)
     pc, _ = cs.candidates(oracle.MODE_COSINE, threads=threads)
@@ -871,6 +893,38 @@ def run_ours(args, rank, world, local_rank):
     roof["kernel"] = dom
     roof["peak_source"] = pk_kind
 
+    # rooflines of the other stages and of the correlation engines, each
+    # against its own bound (algorithmic work per launch / CUDA-event time)
+    def frac(r):
+        r["frac"] = r["achieved"] / r["peak"] if r.get("achieved") else None
+        r["peak_source"] = pk_kind if r["unit"] != "Tops/s" else "derived: 152 SMs x 128 lanes x 2.07 GHz"
+        return r
+
+    rooflines = {}
+    byts = n * (N * N / 8 + 4 + 4 * N + 4 * nb * nb + 32) + wl.rects.nbytes + wl.rect_off.nbytes
+    rooflines["raster"] = frac({"bound": "hbm", "achieved": byts / (per_stage["raster"] / 1e3) / 1e9,
+                                "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                "work": "N^2/8 + 4N + 4 nb^2 + 36 B written per clip + rectangles read"})
+    band = int(g[0][0] + g[0][2] + g[0][3])
+    rooflines["cand_cos"] = frac({"bound": "alu", "achieved": band * 4 * nb * nb / (per_stage["cand_cos"] / 1e3) / 1e12,
+                                  "peak": alu_peak_tops(2070.0), "unit": "Tops/s",
+                                  "work": f"{band} band pairs (G1 survivors) x 4 nb^2 integer ops (G3 both ways)"})
+    if dom == "cand_edge":
+        rooflines["cand_edge"] = dict(roof)
+    if fft:
+        L, Ls = cs.L, cs.Ls
+        rooflines["fft_pair"] = frac({"bound": "hbm", "achieved": fft["hbm_gbs_b_spectrum"], "peak": pk["hbm_gbs"],
+                                      "unit": "GB/s",
+                                      "work": f"B's spectrum per pair ({L * Ls * 8} B; A's from L2, the list sorted by "
+                                              f"representative), {fft['pairs']} same-seed pairs"})
+        tcd = fft.get("tc_engine", {})
+        for key in ("f16_dense32", "bf16_dense32", "f16_same_seed", "bf16_same_seed"):
+            if key in tcd:
+                t = tcd[key]
+                rooflines[f"tc_corr_{key}"] = frac({"bound": "tensor", "achieved": t["tflops_useful"],
+                                                    "peak": t["peak_tflops"], "unit": "TFLOP/s",
+                                                    "work": "2 (2S+1)^2 N^2 useful FLOP per pair (bf16 burst peak)"})
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": args.scaling,
@@ -884,7 +938,7 @@ def run_ours(args, rank, world, local_rank):
                    "gates_edge": {"E2": int(g[1][5]), "E1": int(g[1][4])},
                    "stage_ms": per_stage, "screened_pairs_per_s": 2 * total_pairs * world / (ms_max / 1e3),
                    "wall_s_timed": wall},
-        "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
+        "roofline": roof, "rooflines": rooflines, "clocks": clk, "e2e": e2e, "gpu_launches": None, "fft_engine": fft,
         "host_loop": host_loop,
         "serving": serving,
         "serving_edge": serving_edge,
@@ -898,9 +952,15 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline and world == 1:
         n_s = args.cpu_sample or default_sample(args.config)
         a, t, thr = oracle_sample(wl, n_s)
+        n_1 = max(2, n_s // 4)  # single thread: a quarter of the clips (1/16 of the pairs)
+        a1, t1, _ = oracle_sample(wl, n_1, threads=1)
         line["cpu_baseline"] = {"value": a / t, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "cpu_model": cpu_model(),
                                 "sample": f"first {n_s} clips of the {args.config} set ({n_s*(n_s-1)//2} pairs "
-                                          f"screened both modes, {a} aligned), {t:.1f} s"}
+                                          f"screened both modes, {a} aligned), {t:.1f} s on {thr} threads",
+                                "single_thread": {"value": a1 / t1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"first {n_1} clips ({n_1*(n_1-1)//2} pairs screened "
+                                                            f"both modes, {a1} aligned), {t1:.1f} s"}}
     print(json.dumps(line), flush=True)
 
 

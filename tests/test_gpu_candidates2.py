@@ -55,7 +55,7 @@ def _check(ctx, wa, wb, mode, cos_num=80):
 @pytest.mark.parametrize("na,nb", [(1, 1), (2, 3), (33, 300), (300, 257), (31, 1100)])
 @pytest.mark.parametrize("mode", [1, 2])
 def test_two_set_candidates_match_oracle(ctx, mode, na, nb):
-    base = synth.preset("small", seed=7)
+    base = synth.preset("small", seed=7, n_clips=1600, n_seeds=160, n_copies=960)
     wa = _with_empties(base.subset(np.arange(0, na)), 13)
     wb = _with_empties(base.subset(np.arange(na, na + nb)), 17)
     _check(ctx, wa, wb, mode)
