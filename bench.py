@@ -64,6 +64,8 @@ def parse():
                          "split with pcl_candidates_shard (strong)")
     ap.add_argument("--library-clips", type=int, default=2_000_000,
                     help="clips of the large serving library (tensor-core cosine and edge; 0: skip)")
+    ap.add_argument("--class-library-clips", type=int, default=100_000,
+                    help="clips of each 64^2, 128^2 and 512^2 px library of the size-class serving measurement")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
                     help="same-seed pairs checked against the FP64 oracle per engine (0: skip)")
@@ -232,12 +234,19 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
     give p50/p99 latency (arrival to device completion).  mode: cosine (the
     engine P names behind the area band join: FFT or tensor-core direct
     correlation) or edge (every query x library pair through the edge gates
-    and Min-Max)."""
+    and Min-Max).  P, cs and wl may be lists (one resident library per raster
+    size class): each request then draws its class uniformly."""
+    Ps = list(P) if isinstance(P, (list, tuple)) else [P]
+    css = list(cs) if isinstance(cs, (list, tuple)) else [cs]
+    wls = list(wl) if isinstance(wl, (list, tuple)) else [wl]
     if not cand_per_query:
         cand_per_query = 64 if mode == pcl.MODE_COSINE else 1024
-    srv = pcl.Server(ctx, P, cs, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
+    srv = pcl.Server(ctx, Ps, css, max_inflight=8, max_query_clips=4096, max_query_rects=4096 * 48,
                      cand_per_query=cand_per_query, mem_budget=24 << 30, mode=mode)
-    reqs = serving_requests(wl, 256)
+    per_class = [serving_requests(w, 256 // len(wls) or 1, seed=7 + c) for c, w in enumerate(wls)]
+    crng = np.random.default_rng(17)
+    reqs = [(c, *per_class[c][k % len(per_class[c])])
+            for k, c in enumerate(crng.integers(0, len(wls), size=256).tolist())]
 
     def drive(arrivals):
         """arrivals: monotonic ns per request (None: closed loop)"""
@@ -245,6 +254,7 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
         queue, done, nxt = [], {}, 0
         arr = {}
         lat, pairs, clips, bad = [], 0, 0, 0
+        lat_cls = {}
         n_total = len(arrivals) if arrivals is not None else None
         deadline = t0 + int(seconds * 1e9)
         rid = 0
@@ -260,13 +270,14 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
                     nxt += 1
             while queue:
                 r, ta = queue[0]
-                ro, rr = reqs[r % len(reqs)]
-                if not srv.submit(ro, rr, r):
+                cl, ro, rr = reqs[r % len(reqs)]
+                if not srv.submit(ro, rr, r, cls=cl):
                     break
                 arr[r] = ta
                 queue.pop(0)
             for c in srv.poll():
                 lat.append((c["t_done_ns"] - arr[c["id"]]) / 1e6)
+                lat_cls.setdefault(c["size_class"], []).append(lat[-1])
                 pairs += c["n_candidates"]
                 clips += c["n_queries"]
                 bad += c["status"] != 0  # candidate capacity exceeded (or a device wait ran out)
@@ -278,9 +289,14 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
                 break
             time.sleep(0.0002)
         wall = (time.monotonic_ns() - t0) / 1e9
-        return dict(requests=len(done), not_ok=bad, wall_s=wall, pairs_per_s=pairs / wall, query_clips_per_s=clips / wall,
-                    p50_ms=float(np.percentile(lat, 50)) if lat else None,
-                    p99_ms=float(np.percentile(lat, 99)) if lat else None)
+        out = dict(requests=len(done), not_ok=bad, wall_s=wall, pairs_per_s=pairs / wall, query_clips_per_s=clips / wall,
+                   p50_ms=float(np.percentile(lat, 50)) if lat else None,
+                   p99_ms=float(np.percentile(lat, 99)) if lat else None)
+        if len(wls) > 1:
+            out["per_class"] = {f"{wls[k].raster_n}px": {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                                                         "p99_ms": float(np.percentile(v, 99))}
+                                for k, v in sorted(lat_cls.items())}
+        return out
 
     drive(None)  # warm-up
     sat = drive(None)
@@ -288,8 +304,11 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
     rng = np.random.default_rng(3)
     eng = {pcl.ENGINE_FFT_PCM: "fft", pcl.ENGINE_TC_DIRECT: "tc_f16", pcl.ENGINE_TC_DIRECT_BF16: "tc_bf16",
            pcl.ENGINE_TC_DIRECT_FP8: "tc_e4m3"}
-    out = {"mode": "cosine" if mode == pcl.MODE_COSINE else "edge", "library_clips": wl.n,
-           "engine": eng.get(P.cos_engine, "?") if mode == pcl.MODE_COSINE else "min-max",
+    out = {"mode": "cosine" if mode == pcl.MODE_COSINE else "edge",
+           "library_clips": wls[0].n if len(wls) == 1 else {f"{w.raster_n}px": w.n for w in wls},
+           "engine": (eng.get(Ps[0].cos_engine, "?") if len(wls) == 1 else
+                      {f"{w.raster_n}px": ("exact scan" if w.raster_n == 512 else eng.get(p_.cos_engine, "?"))
+                       for w, p_ in zip(wls, Ps)}) if mode == pcl.MODE_COSINE else "min-max",
            "batch_clips": "log-uniform 1..4096", "saturation": sat, "poisson": []}
     for frac in (0.5, 0.9):
         lam = frac * rps_sat
@@ -786,7 +805,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- serving: continuous batching of query requests against the clip set
     # as a resident library (p50/p99 latency beside throughput)
-    serving = serving_edge = serving_tc = serving_large = None
+    serving = serving_edge = serving_tc = serving_large = serving_classes = None
     if not args.no_serving and world == 1:
         pcl.pcl_rasterize(ctx, P, cs)
         serving = run_serving(pcl, ctx, P, cs, wl)
@@ -795,6 +814,36 @@ def run_ours(args, rank, world, local_rank):
         Ptc = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
                          cos_engine=pcl.ENGINE_TC_DIRECT)
         serving_tc = run_serving(pcl, ctx, Ptc, cs, wl)
+        # the serving form's size mix: one resident library per raster size
+        # class (64^2, 128^2 and 512^2 px sub-libraries of the scale recipe at
+        # their size, W = 4N, S = N/16; the 256^2 class is this clip set),
+        # requests drawing their class uniformly; cosine on the tensor-core
+        # engine (the exact window scan at 512^2), and edge mode
+        if args.config == "scale":
+            import synth
+            sub_w, sub_P, sub_cs = [], [], []
+            for N in (64, 128, 256, 512):
+                if N == 256:
+                    w_, cs_ = wl, cs
+                else:
+                    k = args.class_library_clips
+                    w_ = synth.generate(args.seed + 200 + N, n_clips=k, n_seeds=k // 20, n_copies=7 * k // 10,
+                                        window_dbu=4 * N, margin_dbu=N // 4, min_rects=5, max_rects=40)
+                    cs_ = None
+                p_ = pcl.params(w_.window_dbu, w_.pitch_dbu, w_.marker_dbu, COS_NUM, COS_DEN, TOL,
+                                cos_engine=pcl.ENGINE_TC_DIRECT)
+                if cs_ is None:
+                    cs_ = pcl.alloc_clipset(p_, w_.rect_off, w_.rects, with_spec=False)
+                pcl.pcl_rasterize(ctx, p_, cs_)
+                sub_w.append(w_)
+                sub_P.append(p_)
+                sub_cs.append(cs_)
+            serving_classes = {"cosine": run_serving(pcl, ctx, sub_P, sub_cs, sub_w),
+                               "edge": run_serving(pcl, ctx, [pcl.params(w_.window_dbu, w_.pitch_dbu, w_.marker_dbu,
+                                                                         COS_NUM, COS_DEN, TOL) for w_ in sub_w],
+                                                   sub_cs, sub_w, mode=pcl.MODE_EDGE)}
+            del sub_cs
+            torch.cuda.empty_cache()
         if args.library_clips and args.config == "scale":
             # a resident library of the serving form's size: rasters and
             # signatures only (the tensor-core engine needs no spectra)
@@ -944,6 +993,7 @@ def run_ours(args, rank, world, local_rank):
         "serving_edge": serving_edge,
         "serving_tc": serving_tc,
         "serving_large_library": serving_large,
+        "serving_size_classes": serving_classes,
         "batched": batched,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4

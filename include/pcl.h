@@ -393,42 +393,52 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
                            const pcl_tuning *tune, pcl_stream stream);
 
 /* ---- a10: serving loop ----------------------------------------------------
-   A resident representative library and continuously batched query requests
-   (cfg mode COSINE: the engine P->cos_engine names, PCL_ENGINE_FFT_PCM or
-   PCL_ENGINE_TC_DIRECT(_BF16, _FP8); EDGE: Min-Max procedure).  For COSINE the
-   library must be rasterised (bits, pop, prof, blk) and pcl_server_create
-   sorts it by area; with the FFT engine it also computes the spectra of all
-   library clips (spec/spec_state buffers required), while the tensor-core
-   engine reads the rasters only (spec may be NULL: ~10.6 KB per 256^2 clip
-   instead of ~350 KB, so 2,000,000 library clips fit in ~21 GB).  An EDGE
-   library needs its rasters and edge signatures only (esig, occ, rorder).  It then allocates max_inflight
-   request slots (one stream each, pinned staging) and one device arena of
-   mem_budget bytes.  pcl_server_submit admits a request of n_clips query
-   clips (host rectangles, copied before return) when a slot is free and its
-   device footprint (its clip set, candidate/record buffers of cand_per_query
-   entries per clip) fits in the arena, else returns PCL_ERR_BUSY at once
-   (resubmit after a poll/release); the request then runs asynchronously:
-   rasterisation, query x library band join with the G1/G3/G2 gates,
-   spectra of the referenced query clips, phase-correlation matching with
-   the exact decision (tensor-core engine: the candidates grouped by query
-   clip through the direct correlation, exact argmax; its workspace of
-   20 bytes per candidate slot shares the band join's), pass compaction and
-   the copy of the pass list back
-   (EDGE: every query x library pair through E2 and E1 in the tiled screen of
-   pcl_candidates -- 32 query clips x 256 library clips per tile -- then the
-   Min-Max record of each survivor by a whole warp, pass compaction, copy).
-   pcl_server_poll returns finished requests (pass pairs are
-   (query index, library index), in server-owned host memory valid until
-   pcl_server_release frees the request's slot and arena region); a request
-   whose candidates exceeded its capacity completes with PCL_ERR_BUSY, and one
+   Resident representative libraries, one per raster size class, and
+   continuously batched query requests (cfg mode COSINE: per class the engine
+   its parameters name, PCL_ENGINE_FFT_PCM or PCL_ENGINE_TC_DIRECT(_BF16,
+   _FP8), and for a 512^2 px class the exact window scan of pcl_match_pairs;
+   EDGE: the Min-Max procedure).  pcl_server_create_classes takes n_classes
+   (1..16) parameter blocks and libraries (class c: params[c], libraries[c]);
+   pcl_server_create is the one-class form.  For COSINE each library must be
+   rasterised (bits, pop, prof, blk) and is sorted by area at creation; with
+   the FFT engine its spectra are computed too (spec/spec_state required),
+   while the tensor-core engine and the exact scan read the rasters only
+   (spec may be NULL: ~10.6 KB per 256^2 clip instead of ~350 KB, so
+   2,000,000 library clips fit in ~21 GB).  An EDGE library needs its rasters
+   and edge signatures only (esig, occ, rorder).  The server then allocates
+   max_inflight request slots (one stream each, pinned staging) and one
+   device arena of mem_budget bytes, shared by all classes.
+   pcl_server_submit_class admits a request of n_clips query clips of size
+   class `cls` (host rectangles h_rects indexed by h_rect_off, clip i owning
+   rectangles h_rect_off[i] .. h_rect_off[i+1]; copied before return) when
+   a slot is free and its device footprint (its clip set, candidate/record
+   buffers of cand_per_query entries per clip) fits in the arena, else
+   returns PCL_ERR_BUSY at once (resubmit after a poll/release); requests of
+   every class compete for the same slots and memory.  pcl_server_submit is
+   class 0.  A request then runs asynchronously on its stream:
+   rasterisation, query x library band join with the G1/G3/G2 gates, and the
+   class's engine (FFT: spectra of the referenced query clips and phase
+   correlation; tensor cores: the candidates grouped by query clip through
+   the direct correlation, its workspace of 20 bytes per candidate slot
+   sharing the band join's; 512^2 px: the exact scan), pass compaction and
+   the copies back (EDGE: every query x library pair through E2 and E1 in the
+   tiled screen of pcl_candidates -- 32 query clips x 256 library clips per
+   tile -- then the Min-Max record of each survivor by a whole warp).
+   pcl_server_poll returns finished requests: the pass pairs as (query
+   index, library index), and one pcl_record per candidate that reached the
+   engine (a = query index, b = library index; shift, similarity, overlap,
+   flags and decision, in unspecified order), both in server-owned host
+   memory valid until pcl_server_release frees the request's slot and arena
+   region.  A request whose candidates exceeded its capacity completes with
+   PCL_ERR_BUSY (records and passes cover the first cap candidates), one
    whose tensor-core wait ran out (records not valid) with PCL_ERR_TIMEOUT.
    Timestamps are steady-clock nanoseconds: submit, and device completion as
    stamped by a host callback on the request's stream.  One host thread at a
-   time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with
-   the FFT engine and N > 256 or S > N/16; the tensor-core engine outside
-   (N, S) = (64, 4), (128, 8), (256, 16) or with a shift rule other than
-   EXACT_ARGMAX; any other cosine engine), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not
-   admitted). */
+   time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE
+   with S > N/16; the FFT engine with N > 256; the tensor-core engine outside
+   (N, S) = (64, 4), (128, 8), (256, 16); a shift rule other than
+   EXACT_ARGMAX for the tensor-core engine or a 512^2 px class; any other
+   cosine engine), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not admitted). */
 typedef struct pcl_server pcl_server;
 
 typedef struct pcl_server_cfg {
@@ -436,7 +446,7 @@ typedef struct pcl_server_cfg {
     uint32_t max_query_clips;  /* clips per request */
     uint64_t max_query_rects;  /* rectangles per request */
     uint32_t cand_per_query;   /* candidate capacity per query clip */
-    uint32_t pass_copy;        /* pass pairs copied back without a second copy */
+    uint32_t pass_copy;        /* passes and records copied back without a second copy */
     uint64_t mem_budget;       /* device bytes for in-flight requests */
     uint32_t mode;             /* PCL_MODE_COSINE (or 0) or PCL_MODE_EDGE */
     uint32_t reserved;
@@ -450,17 +460,25 @@ typedef struct pcl_completion {
     uint64_t n_pass;
     const pcl_pair *pass;  /* (query, library) pairs, valid until pcl_server_release */
     int64_t t_submit_ns, t_done_ns;
+    uint32_t size_class;   /* the class the request was submitted to */
+    uint32_t reserved;
+    uint64_t n_records;    /* min(n_candidates, capacity) */
+    const pcl_record *records; /* one per candidate, valid until pcl_server_release */
 } pcl_completion;
 
+pcl_status pcl_server_create_classes(pcl_ctx *ctx, const pcl_params *params, const pcl_clipset *libraries,
+                                     uint32_t n_classes, const pcl_server_cfg *cfg, pcl_server **out);
 pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *library,
                              const pcl_server_cfg *cfg, pcl_server **out);
+pcl_status pcl_server_submit_class(pcl_server *srv, uint32_t cls, const uint32_t *h_rect_off,
+                                   const int32_t *h_rects, uint32_t n_clips, uint64_t request_id);
 pcl_status pcl_server_submit(pcl_server *srv, const uint32_t *h_rect_off, const int32_t *h_rects,
                              uint32_t n_clips, uint64_t request_id);
 pcl_status pcl_server_poll(pcl_server *srv, pcl_completion *out, uint32_t cap, uint32_t *n_out);
 pcl_status pcl_server_release(pcl_server *srv, uint64_t request_id);
 /* requests holding a slot, and free arena bytes (admission state) */
 pcl_status pcl_server_stats(pcl_server *srv, uint32_t *inflight, uint64_t *free_bytes);
-/* waits for in-flight work, frees the slots, arena and library index */
+/* waits for in-flight work, frees the slots, arena and library indexes */
 void pcl_server_destroy(pcl_server *srv);
 
 /* ---- a11: host set cover + coarse-to-fine loop (Sec. 3.3, Sec. 3.1) -------

@@ -118,7 +118,8 @@ class _ServerCfg(ctypes.Structure):
 class _Completion(ctypes.Structure):
     _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_queries", ctypes.c_uint32),
                 ("n_candidates", ctypes.c_uint64), ("n_pass", ctypes.c_uint64), ("pass_", ctypes.c_void_p),
-                ("t_submit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+                ("t_submit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64), ("size_class", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("n_records", ctypes.c_uint64), ("records", ctypes.c_void_p)]
 
 
 _lib = None
@@ -165,7 +166,10 @@ def load(build_if_missing: bool = True):
         "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
                                ctypes.POINTER(_VP)], st),
+        "pcl_server_create_classes": ([_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(_ServerCfg),
+                                       ctypes.POINTER(_VP)], st),
         "pcl_server_submit": ([_VP, _VP, _VP, ctypes.c_uint32, _U64], st),
+        "pcl_server_submit_class": ([_VP, ctypes.c_uint32, _VP, _VP, ctypes.c_uint32, _U64], st),
         "pcl_server_poll": ([_VP, ctypes.POINTER(_Completion), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], st),
         "pcl_server_release": ([_VP, _U64], st),
         "pcl_server_stats": ([_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_U64)], st),
@@ -508,36 +512,46 @@ def match(ctx: Context, P: Params, mode: int, a: ClipSet, b: ClipSet, pairs, str
 
 
 class Server:
-    """pcl_server_*: resident library + continuously batched query requests."""
+    """pcl_server_*: resident libraries (one per size class) and continuously
+    batched query requests.  `P` and `library` are one parameter block and
+    one clip set, or equal-length lists of them (size class c = P[c],
+    library[c])."""
 
-    def __init__(self, ctx: Context, P: Params, library: ClipSet, max_inflight: int = 8,
+    def __init__(self, ctx: Context, P, library, max_inflight: int = 8,
                  max_query_clips: int = 4096, max_query_rects: int = 4096 * 48, cand_per_query: int = 256,
                  pass_copy: int = 1 << 16, mem_budget: int = 8 << 30, mode: int = MODE_COSINE):
         self.ctx = ctx
         self.lib = ctx.lib
-        self.library = library  # keeps the library buffers alive
-        self._cl = library.cstruct()
+        Ps = list(P) if isinstance(P, (list, tuple)) else [P]
+        libs = list(library) if isinstance(library, (list, tuple)) else [library]
+        if len(Ps) != len(libs):
+            raise ValueError("one parameter block per library")
+        self.library = libs  # keeps the library buffers alive
+        self._P = (Params * len(Ps))(*Ps)
+        self._cl = (_Clipset * len(libs))(*[c.cstruct() for c in libs])
         cfg = _ServerCfg(max_inflight, max_query_clips, max_query_rects, cand_per_query, pass_copy, mem_budget,
                          mode, 0)
         h = _VP()
-        ctx.check(self.lib.pcl_server_create(ctx.h, ctypes.byref(P), ctypes.byref(self._cl), ctypes.byref(cfg),
-                                             ctypes.byref(h)), "pcl_server_create")
+        ctx.check(self.lib.pcl_server_create_classes(ctx.h, ctypes.cast(self._P, _VP), ctypes.cast(self._cl, _VP),
+                                                     len(libs), ctypes.byref(cfg), ctypes.byref(h)),
+                  "pcl_server_create")
         self.h = h
         self._keep = {}
 
-    def submit(self, rect_off: np.ndarray, rects: np.ndarray, request_id: int) -> bool:
+    def submit(self, rect_off: np.ndarray, rects: np.ndarray, request_id: int, cls: int = 0) -> bool:
         """True if admitted, False if busy (no slot or memory); raises on errors."""
         off = np.ascontiguousarray(rect_off, dtype=np.uint32)
         r = np.ascontiguousarray(rects, dtype=np.int32).reshape(-1)
-        st = self.lib.pcl_server_submit(self.h, off.ctypes.data, r.ctypes.data if r.size else None,
-                                        off.shape[0] - 1, request_id)
+        st = self.lib.pcl_server_submit_class(self.h, cls, off.ctypes.data, r.ctypes.data if r.size else None,
+                                              off.shape[0] - 1, request_id)
         if st == PCL_ERR_BUSY:
             return False
         self.ctx.check(st, "pcl_server_submit")
         return True
 
     def poll(self, cap: int = 64) -> list[dict]:
-        """Finished requests; their pass lists are copied out and the slots released."""
+        """Finished requests; their pass lists and records are copied out and
+        the slots released."""
         arr = (_Completion * cap)()
         n = ctypes.c_uint32()
         self.ctx.check(self.lib.pcl_server_poll(self.h, arr, cap, ctypes.byref(n)), "pcl_server_poll")
@@ -549,8 +563,15 @@ class Server:
                 pairs = np.frombuffer(buf, dtype=np.uint32).reshape(k, 2).copy()
             else:
                 pairs = np.zeros((0, 2), np.uint32)
+            nr = int(c.n_records)
+            if nr and c.records:
+                rbuf = (ctypes.c_uint8 * (40 * nr)).from_address(c.records)
+                recs = np.frombuffer(rbuf, dtype=np.uint8).copy().view(REC_DTYPE)
+            else:
+                recs = np.zeros(0, dtype=REC_DTYPE)
             out.append(dict(id=int(c.request_id), status=int(c.status), n_queries=int(c.n_queries),
-                            n_candidates=int(c.n_candidates), pass_pairs=pairs, t_submit_ns=int(c.t_submit_ns),
+                            n_candidates=int(c.n_candidates), pass_pairs=pairs, records=recs,
+                            size_class=int(c.size_class), t_submit_ns=int(c.t_submit_ns),
                             t_done_ns=int(c.t_done_ns)))
             self.ctx.check(self.lib.pcl_server_release(self.h, c.request_id), "pcl_server_release")
         return out

@@ -1,6 +1,10 @@
-// a10: serving loop -- a resident representative library and continuously
-// batched query requests (cosine mode with the FFT phase-correlation engine or
-// the tensor-core direct correlation, or edge mode with the Min-Max procedure).
+// a10: serving loop -- resident representative libraries, one per raster
+// size class, and continuously batched query requests (cosine mode with the
+// FFT phase-correlation engine, the tensor-core direct correlation or, for
+// 512^2 px clips, the exact window scan; or edge mode with the Min-Max
+// procedure).  Every request names its size class; all classes share the
+// request slots and the memory budget, so requests of different sizes are
+// admitted together as slots and memory free up.
 //
 // The library's rasters and signatures stay in device memory (with the FFT
 // engine also its spectra), with its clips sorted by area once.  The
@@ -52,6 +56,8 @@ cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl
 cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
                               const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
                               unsigned long long *, unsigned long long *, int, cudaStream_t);
+cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
+                               uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
 }  // namespace pcl
 
 namespace {
@@ -108,6 +114,7 @@ struct Arena {
 struct Slot {
     bool busy = false, done = false;
     uint64_t id = 0;
+    uint32_t cls = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     size_t off = 0, bytes = 0;
@@ -123,8 +130,10 @@ struct Slot {
     uint32_t *h_off = nullptr;
     int32_t *h_rects = nullptr;
     pcl_pair *h_pass = nullptr;
+    pcl_record *h_rec = nullptr;
     unsigned long long *h_counts = nullptr;
     std::vector<pcl_pair> overflow;
+    std::vector<pcl_record> rec_overflow;
     int64_t t_submit = 0;
     int64_t t_done = 0;  // written by the stream's host callback
     pcl_completion comp{};
@@ -134,14 +143,19 @@ void CUDART_CB stamp_done(void *p) { static_cast<Slot *>(p)->t_done = now_ns(); 
 
 }  // namespace
 
-struct pcl_server {
-    pcl_ctx *ctx = nullptr;
+// one resident library of one raster size class
+struct ServerClass {
     pcl_params P{};
     pcl::Geo g{};
-    pcl_server_cfg cfg{};
     pcl_clipset lib{};
-    int engine = 0;  // kEdge, kFft or kTc
+    int engine = 0;  // kEdge, kFft, kTc or kExact
     uint32_t *lib_cum = nullptr, *lib_fill = nullptr, *lib_order = nullptr, *lib_spop = nullptr;
+};
+
+struct pcl_server {
+    pcl_ctx *ctx = nullptr;
+    pcl_server_cfg cfg{};
+    std::vector<ServerClass> cls;
     char *arena_mem = nullptr;
     Arena arena;
     std::vector<Slot> slots;
@@ -150,15 +164,15 @@ struct pcl_server {
 
 namespace {
 
-// request pipelines
-constexpr int kEdge = 0, kFft = 1, kTc = 2;
+// request pipelines (kExact: the exact window scan of 512^2 px cosine pairs)
+constexpr int kEdge = 0, kFft = 1, kTc = 2, kExact = 3;
 
 // workspace of a cosine request: the band join's, then (same stream, after
 // it) the tensor-core engine's grouping buffers in the same bytes
 size_t request_ws(const pcl::Geo &g, int engine, uint32_t nq, uint32_t n_lib, uint64_t cap) {
     if (engine == kEdge) return 0;
     const size_t cj = pcl::cross_join_workspace(g, nq, n_lib);
-    if (engine == kFft) return cj;
+    if (engine == kFft || engine == kExact) return cj;
     const size_t tc = pcl::tc_workspace(cap);
     return cj > tc ? cj : tc;
 }
@@ -221,105 +235,131 @@ pcl_status fail(pcl_ctx *ctx, pcl_status s, const std::string &m) {
 
 extern "C" {
 
-pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *library,
-                             const pcl_server_cfg *cfg, pcl_server **out) {
+pcl_status pcl_server_create_classes(pcl_ctx *ctx, const pcl_params *params, const pcl_clipset *libraries,
+                                     uint32_t n_classes, const pcl_server_cfg *cfg, pcl_server **out) {
     if (!ctx || !out) return PCL_ERR_INVALID;
     *out = nullptr;
     ctx->err.clear();
-    if (pcl_params_validate(P) != PCL_OK) return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: invalid parameters");
-    if (!cfg || !library || cfg->max_inflight == 0 || cfg->max_inflight > 64 || cfg->max_query_clips == 0 ||
+    if (!params || !libraries || n_classes == 0 || n_classes > 16)
+        return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: 1 to 16 size classes");
+    if (!cfg || cfg->max_inflight == 0 || cfg->max_inflight > 64 || cfg->max_query_clips == 0 ||
         cfg->cand_per_query == 0)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: invalid configuration");
     const bool edge = cfg->mode == PCL_MODE_EDGE;
     if (cfg->mode != 0 && cfg->mode != PCL_MODE_COSINE && !edge)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: mode must be PCL_MODE_COSINE or PCL_MODE_EDGE");
-    const pcl::Geo g = pcl::make_geo(*P);
-    const bool tc = P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8 ||
-                    P->cos_engine == PCL_ENGINE_TC_DIRECT_BF16;
-    const int engine = edge ? kEdge : (tc ? kTc : kFft);
-    if (edge) {
-        if (!library->rect_off || !library->rects || !library->bits || !library->esig || !library->occ ||
-            !library->rorder)
-            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: edge library needs rectangles and edge signatures");
-    } else {
-        if (!library->pop || !library->blk || !library->prof || !library->bits)
-            return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: library needs rasters and signatures");
-        if (tc) {
-            if (!pcl::tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
-                return fail(ctx, PCL_ERR_UNSUPPORTED,
-                            "pcl_server_create: tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), "
-                            "exact argmax");
+    std::vector<ServerClass> classes(n_classes);
+    for (uint32_t c = 0; c < n_classes; ++c) {
+        const pcl_params *P = params + c;
+        const pcl_clipset *library = libraries + c;
+        const std::string who = "pcl_server_create (class " + std::to_string(c) + "): ";
+        if (pcl_params_validate(P) != PCL_OK) return fail(ctx, PCL_ERR_INVALID, who + "invalid parameters");
+        const pcl::Geo g = pcl::make_geo(*P);
+        const bool tc = P->cos_engine == PCL_ENGINE_TC_DIRECT || P->cos_engine == PCL_ENGINE_TC_DIRECT_FP8 ||
+                        P->cos_engine == PCL_ENGINE_TC_DIRECT_BF16;
+        int engine = kEdge;
+        if (edge) {
+            if (!library->rect_off || !library->rects || !library->bits || !library->esig || !library->occ ||
+                !library->rorder)
+                return fail(ctx, PCL_ERR_INVALID, who + "edge library needs rectangles and edge signatures");
         } else {
-            if (P->cos_engine != PCL_ENGINE_FFT_PCM)
-                return fail(ctx, PCL_ERR_UNSUPPORTED,
-                            "pcl_server_create: cosine serving takes the FFT or the tensor-core engine");
-            if (!library->spec || !library->spec_state)
-                return fail(ctx, PCL_ERR_INVALID, "pcl_server_create: FFT engine needs the library's spectra");
-            if (g.N > 256 || g.S > g.N / 16)
-                return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_server_create: FFT engine covers N <= 256, S <= N/16");
+            if (!library->pop || !library->blk || !library->prof || !library->bits)
+                return fail(ctx, PCL_ERR_INVALID, who + "library needs rasters and signatures");
+            if (g.S > g.N / 16)
+                return fail(ctx, PCL_ERR_UNSUPPORTED, who + "cosine serving covers S <= N/16");
+            if (g.N == 512) {
+                // 512^2 px: the exact window scan (no spectra, no tensor-core geometry)
+                if (P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+                    return fail(ctx, PCL_ERR_UNSUPPORTED, who + "512^2 px classes take the exact argmax rule");
+                engine = kExact;
+            } else if (tc) {
+                if (!pcl::tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
+                    return fail(ctx, PCL_ERR_UNSUPPORTED,
+                                who + "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax");
+                engine = kTc;
+            } else {
+                if (P->cos_engine != PCL_ENGINE_FFT_PCM)
+                    return fail(ctx, PCL_ERR_UNSUPPORTED,
+                                who + "cosine serving takes the FFT or the tensor-core engine");
+                if (!library->spec || !library->spec_state)
+                    return fail(ctx, PCL_ERR_INVALID, who + "FFT engine needs the library's spectra");
+                engine = kFft;
+            }
         }
+        classes[c].P = *P;
+        classes[c].g = g;
+        classes[c].lib = *library;
+        classes[c].engine = engine;
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail(ctx, PCL_ERR_CUDA, "cudaSetDevice");
     pcl_server *s = new (std::nothrow) pcl_server;
     if (!s) return PCL_ERR_OOM;
     s->ctx = ctx;
-    s->P = *P;
-    s->g = g;
     s->cfg = *cfg;
-    s->lib = *library;
-    s->engine = engine;
-    const uint32_t V = (uint32_t)g.N * g.N + 2;
-    const uint32_t nl = library->n_clips;
+    s->cls = classes;
     auto cleanup = [&](pcl_status st, const std::string &m) {
         pcl_server_destroy(s);
         return fail(ctx, st, m);
     };
-    if (cudaMalloc(&s->lib_cum, 4ull * V) || cudaMalloc(&s->lib_fill, 4ull * V) ||
-        cudaMalloc(&s->lib_order, 4ull * (nl ? nl : 1)) || cudaMalloc(&s->lib_spop, 4ull * (nl ? nl : 1)) ||
-        cudaMalloc(&s->arena_mem, cfg->mem_budget ? cfg->mem_budget : 1)) {
+    if (cudaMalloc(&s->arena_mem, cfg->mem_budget ? cfg->mem_budget : 1)) {
         cudaGetLastError();
         return cleanup(PCL_ERR_OOM, "pcl_server_create: device allocation failed");
     }
     s->arena.init(s->arena_mem, cfg->mem_budget);
-    // resident library (cosine): the area order, and with the FFT engine the
-    // spectra of every clip, once
-    if (!edge) {
-        if (engine == kFft) e = pcl::launch_spectra(*P, s->lib, nullptr, 0, false, 0);
+    // resident libraries (cosine): each class's area order, and with the FFT
+    // engine the spectra of every clip, once
+    for (auto &k : s->cls) {
+        if (edge) continue;
+        const uint32_t V = (uint32_t)k.g.N * k.g.N + 2;
+        const uint32_t nl = k.lib.n_clips;
+        if (cudaMalloc(&k.lib_cum, 4ull * V) || cudaMalloc(&k.lib_fill, 4ull * V) ||
+            cudaMalloc(&k.lib_order, 4ull * (nl ? nl : 1)) || cudaMalloc(&k.lib_spop, 4ull * (nl ? nl : 1))) {
+            cudaGetLastError();
+            return cleanup(PCL_ERR_OOM, "pcl_server_create: device allocation failed");
+        }
+        if (k.engine == kFft) e = pcl::launch_spectra(k.P, k.lib, nullptr, 0, false, 0);
         if (e == cudaSuccess)
-            e = pcl::launch_area_sort(library->pop, nl, V, s->lib_cum, s->lib_fill, s->lib_order, s->lib_spop,
+            e = pcl::launch_area_sort(k.lib.pop, nl, V, k.lib_cum, k.lib_fill, k.lib_order, k.lib_spop,
                                       ctx->num_sms, 0);
+        if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(PCL_ERR_CUDA, std::string("library preparation: ") + cudaGetErrorString(e));
     s->slots.resize(cfg->max_inflight);
-    const uint64_t cap_max = (uint64_t)cfg->cand_per_query * cfg->max_query_clips + 64;
     const uint32_t pass_copy = cfg->pass_copy ? cfg->pass_copy : 1;
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) ||
             cudaMallocHost(&sl.h_off, 4ull * (cfg->max_query_clips + 1)) ||
             cudaMallocHost(&sl.h_rects, 16ull * (cfg->max_query_rects ? cfg->max_query_rects : 1)) ||
-            cudaMallocHost(&sl.h_pass, 8ull * pass_copy) || cudaMallocHost(&sl.h_counts, 64)) {
+            cudaMallocHost(&sl.h_pass, 8ull * pass_copy) || cudaMallocHost(&sl.h_rec, 40ull * pass_copy) ||
+            cudaMallocHost(&sl.h_counts, 64)) {
             cudaGetLastError();
             return cleanup(PCL_ERR_OOM, "pcl_server_create: stream / pinned allocation failed");
         }
     }
-    (void)cap_max;
     *out = s;
     return PCL_OK;
 }
 
-pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const int32_t *h_rects, uint32_t n_clips,
-                             uint64_t request_id) {
+pcl_status pcl_server_create(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *library,
+                             const pcl_server_cfg *cfg, pcl_server **out) {
+    return pcl_server_create_classes(ctx, P, library, 1, cfg, out);
+}
+
+pcl_status pcl_server_submit_class(pcl_server *s, uint32_t cls, const uint32_t *h_rect_off, const int32_t *h_rects,
+                                   uint32_t n_clips, uint64_t request_id) {
     if (!s) return PCL_ERR_INVALID;
     std::lock_guard<std::mutex> lock(s->mu);
     pcl_ctx *ctx = s->ctx;
     ctx->err.clear();
+    if (cls >= s->cls.size()) return fail(ctx, PCL_ERR_INVALID, "pcl_server_submit: no such size class");
+    ServerClass &k = s->cls[cls];
     if (n_clips == 0 || n_clips > s->cfg.max_query_clips || !h_rect_off)
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_submit: clip count out of range");
-    const uint64_t R = h_rect_off[n_clips];
-    if (R > s->cfg.max_query_rects || (R && !h_rects))
+    const uint64_t R = h_rect_off[n_clips] - h_rect_off[0];
+    if (h_rect_off[n_clips] < h_rect_off[0] || R > s->cfg.max_query_rects || (R && !h_rects))
         return fail(ctx, PCL_ERR_INVALID, "pcl_server_submit: rectangle count out of range");
     Slot *sl = nullptr;
     for (auto &x : s->slots)
@@ -329,65 +369,71 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         }
     if (!sl) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: no free slot");
     const uint64_t cap = (uint64_t)s->cfg.cand_per_query * n_clips + 64;
-    const size_t bytes = footprint(s->g, n_clips, R, cap, s->engine, s->lib.n_clips);
+    const size_t bytes = footprint(k.g, n_clips, R, cap, k.engine, k.lib.n_clips);
     size_t off = 0;
     if (!s->arena.alloc(bytes, &off)) return fail(ctx, PCL_ERR_BUSY, "pcl_server_submit: memory budget full");
     cudaError_t e = cudaSetDevice(ctx->device);
     sl->busy = true;
     sl->done = false;
     sl->id = request_id;
+    sl->cls = cls;
     sl->off = off;
     sl->bytes = bytes;
     sl->nq = n_clips;
     sl->cap = cap;
     sl->overflow.clear();
+    sl->rec_overflow.clear();
     sl->t_done = 0;
     sl->t_submit = now_ns();
-    carve(*sl, s->g, s->arena.base + off, n_clips, R, cap, s->engine, s->lib.n_clips);
+    carve(*sl, k.g, s->arena.base + off, n_clips, R, cap, k.engine, k.lib.n_clips);
     std::memcpy(sl->h_off, h_rect_off, 4ull * (n_clips + 1));
-    if (R) std::memcpy(sl->h_rects, h_rects, 16ull * R);
+    const uint32_t base = h_rect_off[0];
+    if (R) std::memcpy(sl->h_rects, h_rects + 4ull * base, 16ull * R);
     cudaStream_t st = sl->st;
     // rect offsets of the request relative to its own rectangle array
-    const uint32_t base = h_rect_off[0];
     if (base)
         for (uint32_t i = 0; i <= n_clips; ++i) sl->h_off[i] -= base;
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)sl->q.rect_off, sl->h_off, 4ull * (n_clips + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && R)
         e = cudaMemcpyAsync((void *)sl->q.rects, sl->h_rects, 16ull * R, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->counts, 0, 64, st);
-    if (e == cudaSuccess) e = pcl::launch_raster(s->P, sl->q, st);
-    if (s->engine == kEdge) {
+    if (e == cudaSuccess) e = pcl::launch_raster(k.P, sl->q, st);
+    if (k.engine == kEdge) {
         // every (query, library) pair through the edge gates (the tiled screen
         // of the self-join, rows = queries, columns = library clips), then
         // the Min-Max record of each survivor, one pair per warp
         if (e == cudaSuccess)
-            e = pcl::launch_edge_screen_cross(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, nullptr, st);
+            e = pcl::launch_edge_screen_cross(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, nullptr, st);
         if (e == cudaSuccess)
-            e = pcl::launch_edge_match(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
+            e = pcl::launch_edge_match(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
     } else {
         if (e == cudaSuccess)
-            e = pcl::launch_cross_join(s->P, sl->q, s->lib, s->lib_order, s->lib_spop, s->lib_cum, sl->ws,
-                                       sl->ws_bytes, sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
-        if (s->engine == kTc) {
+            e = pcl::launch_cross_join(k.P, sl->q, k.lib, k.lib_order, k.lib_spop, k.lib_cum, sl->ws, sl->ws_bytes,
+                                       sl->cand, cap, sl->counts + 0, nullptr, ctx->num_sms, st);
+        if (k.engine == kTc) {
             // candidates grouped by query clip through the direct correlation;
             // a bounded wait that runs out sets the request's own error word
             if (e == cudaSuccess)
-                e = pcl::launch_tc(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, sl->ws, sl->ws_bytes,
+                e = pcl::launch_tc(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, sl->ws, sl->ws_bytes,
                                    ctx->num_sms, reinterpret_cast<int *>(sl->counts + 2), ctx->wait_ns, st);
-        } else {
-            if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, s->lib, st);
-            if (e == cudaSuccess) e = pcl::launch_spectra(s->P, sl->q, nullptr, 0, true, st);
+        } else if (k.engine == kExact) {
             if (e == cudaSuccess)
-                e = pcl::launch_pair_fft(s->P, sl->q, s->lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms,
+                e = pcl::launch_exact_pairs(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms,
+                                            st);
+        } else {
+            if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, k.lib, st);
+            if (e == cudaSuccess) e = pcl::launch_spectra(k.P, sl->q, nullptr, 0, true, st);
+            if (e == cudaSuccess)
+                e = pcl::launch_pair_fft(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms,
                                          st);
         }
     }
     if (e == cudaSuccess) e = pcl::launch_compact(sl->rec, cap, sl->counts + 0, sl->pass, cap, sl->counts + 1, st);
     const uint32_t pass_copy = s->cfg.pass_copy ? s->cfg.pass_copy : 1;
+    const uint64_t first = pass_copy < cap ? pass_copy : cap;
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_counts, sl->counts, 24, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl->h_pass, sl->pass, 8ull * (pass_copy < cap ? pass_copy : cap), cudaMemcpyDeviceToHost,
-                            st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_pass, sl->pass, 8ull * first, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl->h_rec, sl->rec, 40ull * first, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, stamp_done, sl);
     if (e == cudaSuccess) e = cudaEventRecord(sl->ev, st);
     if (e != cudaSuccess) {
@@ -398,6 +444,11 @@ pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const in
         return fail(ctx, PCL_ERR_CUDA, std::string("pcl_server_submit: ") + cudaGetErrorString(e));
     }
     return PCL_OK;
+}
+
+pcl_status pcl_server_submit(pcl_server *s, const uint32_t *h_rect_off, const int32_t *h_rects, uint32_t n_clips,
+                             uint64_t request_id) {
+    return pcl_server_submit_class(s, 0, h_rect_off, h_rects, n_clips, request_id);
 }
 
 pcl_status pcl_server_poll(pcl_server *s, pcl_completion *out, uint32_t cap, uint32_t *n_out) {
@@ -413,6 +464,7 @@ pcl_status pcl_server_poll(pcl_server *s, pcl_completion *out, uint32_t cap, uin
         pcl_completion &c = sl.comp;
         c = pcl_completion{};
         c.request_id = sl.id;
+        c.size_class = sl.cls;
         c.n_queries = sl.nq;
         c.t_submit_ns = sl.t_submit;
         c.t_done_ns = sl.t_done;
@@ -430,6 +482,16 @@ pcl_status pcl_server_poll(pcl_server *s, pcl_completion *out, uint32_t cap, uin
                 sl.overflow.resize(got);
                 cudaMemcpy(sl.overflow.data(), sl.pass, 8ull * got, cudaMemcpyDeviceToHost);
                 c.pass = sl.overflow.data();
+            }
+            // one record per candidate (those within the capacity)
+            const uint64_t nr = c.n_candidates < sl.cap ? c.n_candidates : sl.cap;
+            c.n_records = nr;
+            if (nr <= pass_copy) {
+                c.records = sl.h_rec;
+            } else {
+                sl.rec_overflow.resize(nr);
+                cudaMemcpy(sl.rec_overflow.data(), sl.rec, 40ull * nr, cudaMemcpyDeviceToHost);
+                c.records = sl.rec_overflow.data();
             }
         }
         sl.done = true;
@@ -474,12 +536,15 @@ void pcl_server_destroy(pcl_server *s) {
         if (sl.h_off) cudaFreeHost(sl.h_off);
         if (sl.h_rects) cudaFreeHost(sl.h_rects);
         if (sl.h_pass) cudaFreeHost(sl.h_pass);
+        if (sl.h_rec) cudaFreeHost(sl.h_rec);
         if (sl.h_counts) cudaFreeHost(sl.h_counts);
     }
-    cudaFree(s->lib_cum);
-    cudaFree(s->lib_fill);
-    cudaFree(s->lib_order);
-    cudaFree(s->lib_spop);
+    for (auto &k : s->cls) {
+        cudaFree(k.lib_cum);
+        cudaFree(k.lib_fill);
+        cudaFree(k.lib_order);
+        cudaFree(k.lib_spop);
+    }
     cudaFree(s->arena_mem);
     delete s;
 }

@@ -50,6 +50,38 @@ def _pairset(a):
     return set(map(tuple, np.asarray(a, dtype=np.int64).tolist()))
 
 
+def _sorted_records(r):
+    return r[np.lexsort((r["b"], r["a"]))]
+
+
+def _check_records_against_oracle(res, o, pairs, nq, n_lib, cosine):
+    """records returned for the candidates equal the oracle's records of the
+    same (query, library) pairs: gate, shift, overlap / residual, decision
+    exact, |sim diff| <= 1e-5; pairs[k] = (query, nq + library)"""
+    rec = res["records"]
+    assert len(rec) == res["n_candidates"]
+    idx = rec["a"].astype(np.int64) * n_lib + rec["b"].astype(np.int64)
+    oo = o[idx]
+    assert (pairs[idx, 0] == rec["a"]).all() and (pairs[idx, 1] - nq == rec["b"]).all()
+    np.testing.assert_array_equal(rec["flags"] & 15, oo["flags"] & 15)
+    np.testing.assert_array_equal(rec["pass_"], oo["pass_"])
+    al = (oo["flags"] & oracle.F_ALIGNED) > 0
+    for f in ("dx_dbu", "dy_dbu"):
+        np.testing.assert_array_equal(rec[f][al], oo[f][al])
+    np.testing.assert_array_equal(rec["score"][al].astype(np.int64), oo["score"][al])
+    if cosine:
+        assert np.abs(rec["sim"][al].astype(np.float64) - oo["sim"][al]).max(initial=0) <= 1e-5
+
+
+def _same_records(x, y):
+    """two record lists of one request hold the same records (order free)"""
+    a, b = _sorted_records(x), _sorted_records(y)
+    assert len(a) == len(b)
+    for f in ("a", "b", "dx_dbu", "dy_dbu", "score", "flags", "pass_", "mode", "pcm_dx_dbu", "pcm_dy_dbu"):
+        np.testing.assert_array_equal(a[f], b[f], err_msg=f)
+    assert np.abs(a["sim"].astype(np.float64) - b["sim"].astype(np.float64)).max(initial=0) <= 1e-5
+
+
 @pytest.fixture(scope="module")
 def served(torch_cuda):
     import paper_2512_13133_gb300 as pcl
@@ -86,6 +118,7 @@ def test_served_results_equal_oracle(served):
     opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
     assert _pairset(res["pass_pairs"]) == opass
     assert len(opass) >= q.n  # every query passes against the clip it was moved from
+    _check_records_against_oracle(res, o, pairs, q.n, lib.n, cosine=True)
 
 
 def test_same_alone_and_in_the_mix(served):
@@ -116,6 +149,7 @@ def test_same_alone_and_in_the_mix(served):
         assert c["status"] == a["status"] == 0
         assert c["n_candidates"] == a["n_candidates"]
         assert _pairset(c["pass_pairs"]) == _pairset(a["pass_pairs"])
+        _same_records(c["records"], a["records"])
     # requests did overlap in time on the device
     spans = sorted((c["t_submit_ns"], c["t_done_ns"]) for c in got.values())
     for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
@@ -178,6 +212,7 @@ def test_edge_served_results_equal_oracle(served, tol):
         assert res["n_candidates"] == int(cand.sum())
         opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
         assert _pairset(res["pass_pairs"]) == opass
+        _check_records_against_oracle(res, o, pairs, q.n, lib.n, cosine=False)
         total_pass += len(opass)
     assert total_pass > 0
     srv.close()
@@ -216,8 +251,23 @@ def test_tc_served_results_equal_oracle(served, engine):
         assert res["n_candidates"] == int(((o["flags"] & 15) == 0).sum())
         opass = {(int(a), int(b) - q.n) for a, b in pairs[o["pass_"] == 1]}
         assert _pairset(res["pass_pairs"]) == opass
+        _check_records_against_oracle(res, o, pairs, q.n, lib.n, cosine=True)
         total_pass += len(opass)
     assert total_pass >= sum(q.n for q in reqs[:5])
+    srv.close()
+    # a wait limit below the engine's hand-over times: the request completes
+    # with PCL_ERR_TIMEOUT (no fault), and the next one is served normally
+    srv = pcl.Server(ctx, P, cs, max_inflight=2, max_query_clips=512, cand_per_query=2048, mem_budget=1 << 30)
+    q = reqs[3]
+    pcl.pcl_set_wait_limit(ctx, 1)
+    assert srv.submit(q.rect_off, q.rects, 77)
+    assert _wait_all(srv, [77])[77]["status"] == pcl.PCL_ERR_TIMEOUT
+    pcl.pcl_set_wait_limit(ctx, 0)
+    assert srv.submit(q.rect_off, q.rects, 78)
+    again = _wait_all(srv, [78])[78]
+    assert again["status"] == 0
+    assert _pairset(again["pass_pairs"]) == _pairset(got[13]["pass_pairs"])
+    _same_records(again["records"], got[13]["records"])
     srv.close()
     # the FFT engine still needs the library's spectra; other engines and rules are refused
     with pytest.raises(pcl.PclError):
