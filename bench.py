@@ -817,8 +817,8 @@ def run_ours(args, rank, world, local_rank):
         # the serving form's size mix: one resident library per raster size
         # class (64^2, 128^2 and 512^2 px sub-libraries of the scale recipe at
         # their size, W = 4N, S = N/16; the 256^2 class is this clip set),
-        # requests drawing their class uniformly; cosine on the tensor-core
-        # engine (the exact window scan at 512^2), and edge mode
+        # requests drawing their class uniformly; cosine on the FFT engine
+        # (spectra resident; the exact window scan at 512^2), and edge mode
         if args.config == "scale":
             import synth
             sub_w, sub_P, sub_cs = [], [], []
@@ -830,10 +830,9 @@ def run_ours(args, rank, world, local_rank):
                     w_ = synth.generate(args.seed + 200 + N, n_clips=k, n_seeds=k // 20, n_copies=7 * k // 10,
                                         window_dbu=4 * N, margin_dbu=N // 4, min_rects=5, max_rects=40)
                     cs_ = None
-                p_ = pcl.params(w_.window_dbu, w_.pitch_dbu, w_.marker_dbu, COS_NUM, COS_DEN, TOL,
-                                cos_engine=pcl.ENGINE_TC_DIRECT)
+                p_ = pcl.params(w_.window_dbu, w_.pitch_dbu, w_.marker_dbu, COS_NUM, COS_DEN, TOL)
                 if cs_ is None:
-                    cs_ = pcl.alloc_clipset(p_, w_.rect_off, w_.rects, with_spec=False)
+                    cs_ = pcl.alloc_clipset(p_, w_.rect_off, w_.rects, with_spec=N < 512)
                 pcl.pcl_rasterize(ctx, p_, cs_)
                 sub_w.append(w_)
                 sub_P.append(p_)
