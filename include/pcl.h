@@ -481,6 +481,20 @@ pcl_status pcl_server_stats(pcl_server *srv, uint32_t *inflight, uint64_t *free_
 /* waits for in-flight work, frees the slots, arena and library indexes */
 void pcl_server_destroy(pcl_server *srv);
 
+/* ---- a11 on the GPU: degrees and surprisal of the pass graph --------------
+   For the undirected graph d_edges[0..min(n_edges, *d_n)) on n_nodes nodes
+   (device pairs; d_n as in pcl_match_pairs, may be NULL): d_degree[i] (u32)
+   = edges at node i, d_weight[i] (u64) = S_i = floor(2^32 / (1 + deg(i)))
+   (Sec. 3.3.1, Eqs. 7-8, 32-bit fixed point), d_score[j] (u64) = S_j + sum
+   of S_k over the neighbours k of j (Eq. 9 with every node uncovered: the
+   scores the lazy greedy of pcl_setcover starts from).  Each listed edge
+   counts once per endpoint; edges with an endpoint >= n_nodes or with
+   a == b are ignored.  Integer atomics: exact and order independent.
+   Errors: PCL_ERR_INVALID (NULL buffer), PCL_ERR_CUDA. */
+pcl_status pcl_surprisal(pcl_ctx *ctx, const pcl_pair *d_edges, uint64_t n_edges, const uint64_t *d_n,
+                         uint32_t n_nodes, uint32_t *d_degree, uint64_t *d_weight, uint64_t *d_score,
+                         pcl_stream stream);
+
 /* ---- a11: host set cover + coarse-to-fine loop (Sec. 3.3, Sec. 3.1) -------
    Surprisal lazy greedy over the undirected graph h_edges[0..n_edges) on
    n_nodes nodes: f_i = 1 + deg(i), S_i = floor(2^32 / f_i), Score_j =

@@ -394,6 +394,25 @@ def setcover_eager(n: int, edges) -> tuple[list[int], np.ndarray]:
     return order, rep_of
 
 
+def surprisal_scores(n: int, edges):
+    """Degrees, surprisal weights and first-step scores of Sec. 3.3.1 with
+    every node uncovered: deg(i) = number of edges at i, S_i =
+    floor(2^32 / (1 + deg(i))) (Eqs. 7-8), Score_j = S_j + sum of S_k over
+    the neighbours k of j (Eq. 9).  Plain loops over the edge list (each
+    listed edge counts once per endpoint).  Returns (deg, S, Score) as int64
+    arrays."""
+    deg = np.zeros(n, dtype=np.int64)
+    for a, b in np.asarray(edges, dtype=np.int64).reshape(-1, 2).tolist():
+        deg[a] += 1
+        deg[b] += 1
+    w = np.array([(1 << 32) // (1 + int(d)) for d in deg], dtype=np.int64)
+    score = w.copy()
+    for a, b in np.asarray(edges, dtype=np.int64).reshape(-1, 2).tolist():
+        score[a] += w[b]
+        score[b] += w[a]
+    return deg, w, score
+
+
 def score_of(n: int, edges, uncovered: np.ndarray, j: int) -> int:
     """Score_j of Eq. 9 for a given uncovered set (j assumed uncovered)."""
     e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)

@@ -162,6 +162,7 @@ def load(build_if_missing: bool = True):
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_device_error": ([_VP, ctypes.POINTER(ctypes.c_int)], st),
         "pcl_set_wait_limit": ([_VP, _U64], st),
+        "pcl_surprisal": ([_VP, _VP, _U64, _VP, ctypes.c_uint32, _VP, _VP, _VP, _VP], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
         "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
@@ -400,6 +401,20 @@ def pcl_device_error(ctx: Context) -> int:
     f = ctypes.c_int()
     ctx.check(ctx.lib.pcl_device_error(ctx.h, ctypes.byref(f)), "pcl_device_error")
     return int(f.value)
+
+
+def pcl_surprisal(ctx: Context, edges, n_nodes: int, d_n=None, stream=None):
+    """Degrees (int32), surprisal weights and first-step scores (int64) of
+    the graph of an int32 CUDA pair tensor [m, 2] on n_nodes nodes, as CUDA
+    tensors (Sec. 3.3.1, Eqs. 7-9)."""
+    torch = _torch()
+    dev = edges.device
+    deg = torch.empty(max(n_nodes, 1), dtype=torch.int32, device=dev)
+    w = torch.empty(max(n_nodes, 1), dtype=torch.int64, device=dev)
+    sc = torch.empty(max(n_nodes, 1), dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.pcl_surprisal(ctx.h, _ptr(edges), int(edges.shape[0]), _ptr(d_n), n_nodes, _ptr(deg), _ptr(w),
+                                    _ptr(sc), _stream_ptr(stream)), "pcl_surprisal")
+    return deg[:n_nodes], w[:n_nodes], sc[:n_nodes]
 
 
 def pcl_set_wait_limit(ctx: Context, ns: int) -> None:

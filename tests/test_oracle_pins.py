@@ -470,6 +470,21 @@ def test_surprisal_scores_by_hand():
     assert rep.tolist() == [1, 1, 2, 3, 4, 4, 4, 1, 1, 1]
 
 
+def test_first_step_scores_by_hand():
+    # the graph of test_surprisal_scores_by_hand, every node uncovered:
+    # degrees 3,4,4,4,2,1,1,3,3,3; node 5: S_5 + S_4 = 2^31 + floor(2^32/3)
+    edges = [(0, 1), (0, 2), (0, 3), (4, 5), (4, 6)]
+    edges += [(u, v) for u in (1, 2, 3) for v in (7, 8, 9)]
+    deg, w, sc = oracle.surprisal_scores(10, edges)
+    assert deg.tolist() == [3, 4, 4, 4, 2, 1, 1, 3, 3, 3]
+    assert w[0] == 1 << 30 and w[1] == 858993459 and w[5] == 1 << 31
+    assert sc[5] == (1 << 31) + 1431655765
+    assert sc[4] == 1431655765 + 2 * (1 << 31)
+    unc = np.ones(10, bool)
+    for j in range(10):
+        assert sc[j] == oracle.score_of(10, edges, unc, j)
+
+
 def test_setcover_path_graph():
     order, rep = oracle.setcover_eager(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
     assert order == [1, 3]
