@@ -44,6 +44,7 @@ class _Cfg(ctypes.Structure):
         ("spacing", ctypes.c_int32),
         ("edge_jitter", ctypes.c_int32),
         ("shift_max", ctypes.c_int32),
+        ("halo_dbu", ctypes.c_int32),
     ]
 
 
@@ -119,11 +120,13 @@ PRESETS = {
 def generate(seed: int = 1, *, n_clips: int, n_seeds: int, n_copies: int, window_dbu: int,
              margin_dbu: int, min_rects: int, max_rects: int, min_side: int = 20,
              max_side: int = 120, grid: int = 10, spacing: int = 20, edge_jitter: int = 8,
-             shift_max: int | None = None, pitch_dbu: int = 4, name: str = "custom") -> Workload:
+             shift_max: int | None = None, pitch_dbu: int = 4, name: str = "custom", halo_dbu: int = 0) -> Workload:
+    """halo_dbu > 0 keeps each clip's rectangles over [-halo, W + halo)^2
+    (the layout around the window) instead of cutting them to the window."""
     lib = _load()
     cfg = _Cfg(seed, n_clips, n_seeds, n_copies, window_dbu, margin_dbu, min_rects, max_rects,
                min_side, max_side, grid, spacing, edge_jitter,
-               margin_dbu if shift_max is None else shift_max)
+               margin_dbu if shift_max is None else shift_max, halo_dbu)
     cap = int(n_clips) * int(max(max_rects, 1))
     off = np.zeros(n_clips + 1, dtype=np.uint32)
     rects = np.zeros((cap, 4), dtype=np.int32)
@@ -134,7 +137,7 @@ def generate(seed: int = 1, *, n_clips: int, n_seeds: int, n_copies: int, window
         raise ValueError("pcl_synth_generate rejected the configuration")
     return Workload(name, window_dbu, pitch_dbu, margin_dbu, off, rects[:total].copy(), label,
                     dict(seed=seed, n_seeds=n_seeds, n_copies=n_copies, min_rects=min_rects,
-                         max_rects=max_rects))
+                         max_rects=max_rects, halo_dbu=halo_dbu))
 
 
 def preset(name: str, seed: int = 1, **over) -> Workload:

@@ -12,7 +12,9 @@
  *   - seed clips: R ~ U{min_rects..max_rects} rectangles, sides on a `grid`
  *     dbu grid in [min_side, max_side], positions on the same grid, placed
  *     without overlap and at least `spacing` dbu apart, on the extended region
- *     [-margin, W + margin)^2, then cut to the window [0, W)^2;
+ *     [-margin, W + margin)^2, then cut to the window [0, W)^2 (or, with a
+ *     halo h, to [-h, W + h)^2: the clip then carries the layout around its
+ *     window);
  *   - perturbed copies: a uniformly drawn seed, every rectangle edge moved by
  *     U{-jitter..jitter} dbu, the whole clip moved by U{-shift..shift} dbu per
  *     axis, then cut to the window;
@@ -40,6 +42,7 @@ typedef struct pcl_synth_cfg {
     int32_t spacing;      /* minimum gap between rectangles of one seed */
     int32_t edge_jitter;  /* per-edge perturbation of copies, +/- dbu */
     int32_t shift_max;    /* whole-clip perturbation of copies, +/- dbu */
+    int32_t halo_dbu;     /* rectangles are cut to [-halo, W + halo)^2 (0: to the window) */
 } pcl_synth_cfg;
 
 static uint64_t sm64(uint64_t *s) {
@@ -105,14 +108,14 @@ static int gen_seed(const pcl_synth_cfg *c, uint64_t st, rect_t *out, int cap) {
     return n;
 }
 
-/* cut to [0, W)^2 and append non-empty rectangles; returns appended count */
-static int cut_append(const rect_t *in, int n, int W, int32_t *dst) {
+/* cut to [lo, hi)^2 and append non-empty rectangles; returns appended count */
+static int cut_append(const rect_t *in, int n, int lo, int hi, int32_t *dst) {
     int m = 0;
     for (int i = 0; i < n; ++i) {
-        int x0 = in[i].x0 < 0 ? 0 : in[i].x0;
-        int y0 = in[i].y0 < 0 ? 0 : in[i].y0;
-        int x1 = in[i].x1 > W ? W : in[i].x1;
-        int y1 = in[i].y1 > W ? W : in[i].y1;
+        int x0 = in[i].x0 < lo ? lo : in[i].x0;
+        int y0 = in[i].y0 < lo ? lo : in[i].y0;
+        int x1 = in[i].x1 > hi ? hi : in[i].x1;
+        int y1 = in[i].y1 > hi ? hi : in[i].y1;
         if (x0 < x1 && y0 < y1) {
             dst[4 * m + 0] = x0; dst[4 * m + 1] = y0;
             dst[4 * m + 2] = x1; dst[4 * m + 3] = y1;
@@ -165,14 +168,14 @@ int64_t pcl_synth_generate(const pcl_synth_cfg *cfg, uint32_t *rect_off, int32_t
     for (uint32_t k = 0; k < c->n_clips; ++k) inv[perm[k]] = k;
 
     int64_t total = 0;
-    int W = c->window_dbu;
+    const int lo = -c->halo_dbu, hi = c->window_dbu + c->halo_dbu;
     for (uint32_t pos = 0; pos < c->n_clips; ++pos) {
         uint32_t k = inv[pos];
         rect_off[pos] = (uint32_t)total;
         if (total + cap > rect_cap) { total = -1; break; }
         int m = 0;
         if (k < c->n_seeds) {
-            m = cut_append(seedbuf + (size_t)k * cap, seedn[k], W, rects + 4 * total);
+            m = cut_append(seedbuf + (size_t)k * cap, seedn[k], lo, hi, rects + 4 * total);
             label[pos] = (int32_t)k;
         } else if (k < c->n_seeds + c->n_copies) {
             uint64_t st = stream_of(c->seed, 2, k);
@@ -192,11 +195,11 @@ int64_t pcl_synth_generate(const pcl_synth_cfg *cfg, uint32_t *rect_off, int32_t
                 r.x0 += tx; r.x1 += tx; r.y0 += ty; r.y1 += ty;
                 tmp[i] = r;
             }
-            m = cut_append(tmp, n, W, rects + 4 * total);
+            m = cut_append(tmp, n, lo, hi, rects + 4 * total);
             label[pos] = (int32_t)s;
         } else {
             int n = gen_seed(c, stream_of(c->seed, 3, k), tmp, cap);
-            m = cut_append(tmp, n, W, rects + 4 * total);
+            m = cut_append(tmp, n, lo, hi, rects + 4 * total);
             label[pos] = -1;
         }
         total += m;

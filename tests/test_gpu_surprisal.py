@@ -105,4 +105,4 @@ def test_low_resolution_coarse_stage_matches_oracle(ctx, torch_cuda, small_wl, m
     rep2, ncl2, _ = oracle.cluster_loop(small_wl.n, op, strict, relaxed)
     assert ncl == ncl2
     assert rep.tolist() == rep2.tolist()
-    assert ncl < small_wl.n - 50
+    assert ncl < small_wl.n - (50 if mode == 1 else 20)  # clusters form
