@@ -11,6 +11,8 @@ Pieces and the passages they follow:
 * rasterisation, correlation, cosine decision, gates, brute-force shift scan,
   edge Min-Max procedure: ``pcl_oracle.c`` (Sec. 2.2.1 Eq. 2, Sec. 2.2.2,
   Sec. 3.2.1 Eqs. 3-5, Sec. 3.2.2 Eq. 6, Sec. 3.1 stage 1);
+* cosine with re-extraction of the member's window at each shift (Sec. 2.1,
+  Eq. 2; halo rasters over [-M, W + M)^2): ``pcl_oracle.c``;
 * phase-correlation surface: numpy FFT in float64 (Sec. 3.2.1 Eqs. 3-5) --
   a library FFT used as one step, with no blocking or pruning;
 * surprisal set cover, eager greedy (Sec. 3.3, Eqs. 7-9) and the
@@ -35,6 +37,7 @@ _SRC = os.path.join(_HERE, "pcl_oracle.c")
 MODE_COSINE = 1
 MODE_EDGE = 2
 MODE_COSINE_XYSEP = 3  # cosine mode, shift by XY-separation interval competition (Sec. 3.2.1 (2))
+MODE_COSINE_HALO = 4   # cosine mode, the member's window re-extracted at each shift (Sec. 2.1)
 
 GATE_NONE = 0
 GATE_G1_AREA = 1
@@ -83,6 +86,9 @@ def _load():
     lib = ctypes.CDLL(build())
     lib.orc_set_create.restype = P
     lib.orc_set_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int]
+    lib.orc_set_add_halo.argtypes = [P]
+    lib.orc_halo_window.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.orc_halo_pair.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.orc_set_create_ex.restype = P
     lib.orc_set_create_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int]
     lib.orc_set_free.argtypes = [P]
@@ -182,9 +188,11 @@ class ClipSet:
 
     raster=False keeps the rectangles only (no images, no signatures): such a
     set serves edge mode alone, whose procedure reads rectangles, and is
-    cheap to build for large workloads."""
+    cheap to build for large workloads.  halo=True also rasterises each
+    clip over [-M, W + M)^2 (its halo raster, side N + 2S) for the
+    re-extraction mode MODE_COSINE_HALO."""
 
-    def __init__(self, wl, marker_dbu: int | None = None, raster: bool = True):
+    def __init__(self, wl, marker_dbu: int | None = None, raster: bool = True, halo: bool = False):
         self._lib = _load()
         self.W = int(wl.window_dbu)
         self.p = int(wl.pitch_dbu)
@@ -200,6 +208,23 @@ class ClipSet:
         if not h:
             raise ValueError("oracle rejected the clip-set parameters")
         self._h = ctypes.c_void_p(h)
+        self.halo = bool(halo) and self.raster
+        if self.halo:
+            self._lib.orc_set_add_halo(self._h)
+
+    def _need_halo(self):
+        if not self.halo:
+            raise ValueError("oracle clip set built without halo rasters")
+
+    def halo_window(self, a: int, b: int):
+        """(c(s), n_B(s)) of the re-extraction reading for every shift,
+        indexed [dy + S, dx + S]"""
+        self._need_halo()
+        K = 2 * self.S + 1
+        c = np.zeros((K, K), dtype=np.int64)
+        nb = np.zeros((K, K), dtype=np.int64)
+        self._lib.orc_halo_window(self._h, a, b, c.ctypes.data, nb.ctypes.data)
+        return c, nb
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -259,8 +284,10 @@ class ClipSet:
             self._need_raster()
         rec = np.zeros(1, dtype=REC_DTYPE)
         p = self.params(**kw)
+        if mode == MODE_COSINE_HALO:
+            self._need_halo()
         fn = {MODE_COSINE: self._lib.orc_cosine_pair, MODE_EDGE: self._lib.orc_edge_pair,
-              MODE_COSINE_XYSEP: self._lib.orc_xysep_pair}[mode]
+              MODE_COSINE_XYSEP: self._lib.orc_xysep_pair, MODE_COSINE_HALO: self._lib.orc_halo_pair}[mode]
         fn(self._h, a, b, ctypes.byref(p), rec.ctypes.data)
         return rec[0]
 
@@ -268,6 +295,8 @@ class ClipSet:
         """one record per (a, b) pair, in order (brute-force shift scan)."""
         if mode != MODE_EDGE:
             self._need_raster()
+        if mode == MODE_COSINE_HALO:
+            self._need_halo()
         pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.uint32).reshape(-1, 2))
         out = np.zeros(pr.shape[0], dtype=REC_DTYPE)
         p = self.params(**kw)

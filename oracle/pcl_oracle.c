@@ -31,6 +31,7 @@ enum {
     ORC_MODE_COSINE = 1,
     ORC_MODE_EDGE = 2,
     ORC_MODE_COSINE_XYSEP = 3,  /* cosine mode, shift by interval competition */
+    ORC_MODE_COSINE_HALO = 4,   /* cosine mode, member window re-extracted at each shift */
 };
 
 /* gate / outcome codes (low 4 bits of flags) */
@@ -86,6 +87,7 @@ typedef struct orc_set {
     int32_t *dil;   /* n * nb * nb: ones in the (2rb+1)^2 block neighbourhood */
     uint32_t *roff; /* n + 1 */
     int32_t *rects; /* 4 * roff[n] */
+    uint8_t *himg;  /* n * (N + 2S)^2 or NULL: rasters of [-M, W + M)^2, see orc_set_add_halo */
 } orc_set;
 
 /*
@@ -174,7 +176,7 @@ int64_t orc_corr_words_img(const uint8_t *A, const uint8_t *B, int N, int dx, in
 void orc_set_free(orc_set *s) {
     if (!s) return;
     free(s->img); free(s->wd); free(s->pop); free(s->rows); free(s->cols);
-    free(s->blk); free(s->dil); free(s->roff); free(s->rects);
+    free(s->blk); free(s->dil); free(s->roff); free(s->rects); free(s->himg);
     free(s);
 }
 
@@ -682,6 +684,8 @@ static int edge_gate(const orc_set *s, int a, int b, const orc_params *P) {
 
 /* ---------------------------------------------------------------- batches */
 
+void orc_halo_pair(const orc_set *s, int a, int b, const orc_params *P, orc_rec *out);
+
 typedef struct {
     const orc_set *s;
     const orc_params *P;
@@ -706,6 +710,7 @@ static void *match_worker(void *arg) {
             int a = (int)j->pairs[2 * i], b = (int)j->pairs[2 * i + 1];
             if (j->mode == ORC_MODE_COSINE) orc_cosine_pair(j->s, a, b, j->P, &j->out[i]);
             else if (j->mode == ORC_MODE_COSINE_XYSEP) orc_xysep_pair(j->s, a, b, j->P, &j->out[i]);
+            else if (j->mode == ORC_MODE_COSINE_HALO) orc_halo_pair(j->s, a, b, j->P, &j->out[i]);
             else orc_edge_pair(j->s, a, b, j->P, &j->out[i]);
         }
     }
@@ -868,4 +873,132 @@ int64_t orc_candidates_ab(const orc_set *s, const orc_params *P, int mode, int n
     free(c.keep);
     pthread_mutex_destroy(&c.mu);
     return m;
+}
+
+
+/* ---------------------------------------------------------- re-extraction */
+
+/*
+ * Halo rasters for re-extraction (Sec. 2.1: a pattern is the layout cut out
+ * around its centre, and the centre may lie anywhere in the marker region).
+ * Reading: each clip carries its rectangles over [-M, W + M)^2, and its halo
+ * raster samples that region at the pixel centres p*i + p/2 for
+ * i in [-S, N + S); pixel i is stored at index i + S.  Computed by the
+ * rasteriser above on the rectangles moved by +M in a window of W + 2M.
+ */
+void orc_set_add_halo(orc_set *s) {
+    int NH = s->N + 2 * s->S, M = s->M;
+    free(s->himg);
+    s->himg = (uint8_t *)malloc((size_t)s->n * NH * NH + 1);
+    int32_t *tmp = NULL;
+    size_t cap = 0;
+    for (int c = 0; c < s->n; ++c) {
+        int k = (int)(s->roff[c + 1] - s->roff[c]);
+        if ((size_t)k > cap) {
+            cap = (size_t)k;
+            tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * 4 * cap);
+        }
+        const int32_t *r = s->rects + 4 * (size_t)s->roff[c];
+        for (int q = 0; q < 4 * k; ++q) tmp[q] = r[q] + M;
+        orc_rasterize(s->W + 2 * M, s->p, tmp, k, s->himg + (size_t)c * NH * NH);
+    }
+    free(tmp);
+}
+
+/* c(s) and the moved window's pixel count n_B(s) for one shift, pixel loops:
+   the member's window moved by s holds B's halo pixels x - s, x in [0, N)^2 */
+static void halo_shift(const orc_set *s, const uint8_t *A, const uint8_t *Bh, int dx, int dy, int64_t *c,
+                       int64_t *nb) {
+    int N = s->N, S = s->S, NH = N + 2 * S;
+    int64_t cc = 0, nn = 0;
+    for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x) {
+            int v = Bh[(size_t)(y - dy + S) * NH + (x - dx + S)];
+            nn += v;
+            cc += v & A[(size_t)y * N + x];
+        }
+    *c = cc;
+    *nb = nn;
+}
+
+/* the window of c(s) and n_B(s), indexed [dy + S][dx + S] */
+void orc_halo_window(const orc_set *s, int a, int b, int64_t *c_out, int64_t *n_out) {
+    int N = s->N, S = s->S, K = 2 * S + 1, NH = N + 2 * S;
+    const uint8_t *A = s->img + (size_t)a * N * N, *Bh = s->himg + (size_t)b * NH * NH;
+    for (int dy = -S; dy <= S; ++dy)
+        for (int dx = -S; dx <= S; ++dx)
+            halo_shift(s, A, Bh, dx, dy, c_out + (size_t)(dy + S) * K + (dx + S), n_out + (size_t)(dy + S) * K + (dx + S));
+}
+
+/* cosine at a shift as the exact rational num/den of its square:
+   both windows empty -> 1, exactly one empty -> 0, else c^2 / (|A| n_B) */
+static void halo_sim2(int64_t c, int64_t pa, int64_t nb, unsigned __int128 *num, unsigned __int128 *den) {
+    if (pa == 0 || nb == 0) {
+        *num = (pa == 0 && nb == 0) ? 1 : 0;
+        *den = 1;
+    } else {
+        *num = (unsigned __int128)c * (unsigned __int128)c;
+        *den = (unsigned __int128)pa * (unsigned __int128)nb;
+    }
+}
+
+/*
+ * Cosine pair test with re-extraction (Sec. 2.1 and Eq. 2): the
+ * representative A keeps its window, the member's window moves with the
+ * shift s, |dx|, |dy| <= S, so content from B's halo enters it, and its norm
+ * is the pixel count n_B(s) of the moved window.  sim(s) = c(s) /
+ * sqrt(|A| n_B(s)); the best shift maximises sim (exact rational
+ * comparison; ties: smaller |dx| + |dy|, then dy, then dx); pass iff
+ * c* > 0 and den^2 c*^2 > num^2 |A| n_B(s*), or both windows are empty at
+ * s*.  No gates (the lossless bounds assume fixed norms).  The record's pad
+ * holds n_B(s*).  Needs orc_set_add_halo.
+ */
+void orc_halo_pair(const orc_set *s, int a, int b, const orc_params *P, orc_rec *out) {
+    memset(out, 0, sizeof(*out));
+    out->a = (uint32_t)a; out->b = (uint32_t)b; out->mode = ORC_MODE_COSINE;
+    int N = s->N, S = s->S, NH = N + 2 * S;
+    const uint8_t *A = s->img + (size_t)a * N * N, *Bh = s->himg + (size_t)b * NH * NH;
+    int64_t pa = s->pop[a];
+    int have = 0, bdx = 0, bdy = 0;
+    int64_t bc = 0, bn = 0;
+    unsigned __int128 bnum = 0, bden = 1;
+    for (int dy = -S; dy <= S; ++dy)
+        for (int dx = -S; dx <= S; ++dx) {
+            int64_t c, nb;
+            halo_shift(s, A, Bh, dx, dy, &c, &nb);
+            unsigned __int128 num, den;
+            halo_sim2(c, pa, nb, &num, &den);
+            int take = 0;
+            if (!have) take = 1;
+            else {
+                unsigned __int128 l = num * bden, r = bnum * den;
+                if (l != r) take = l > r;
+                else {
+                    int l1 = abs(dx) + abs(dy), l2 = abs(bdx) + abs(bdy);
+                    if (l1 != l2) take = l1 < l2;
+                    else if (dy != bdy) take = dy < bdy;
+                    else take = dx < bdx;
+                }
+            }
+            if (take) {
+                have = 1; bdx = dx; bdy = dy; bc = c; bn = nb; bnum = num; bden = den;
+            }
+        }
+    out->dx_dbu = bdx * s->p;
+    out->dy_dbu = bdy * s->p;
+    out->score = bc;
+    out->pad = (int32_t)bn;
+    out->flags = ORC_F_ALIGNED;
+    if (pa == 0 && bn == 0) {
+        out->sim = 1.0;
+        out->pass = 1;
+        out->flags |= ORC_F_EMPTY;
+    } else if (pa == 0 || bn == 0) {
+        out->sim = 0.0;
+    } else {
+        out->sim = (double)bc / sqrt((double)pa * (double)bn);
+        unsigned __int128 l = (unsigned __int128)P->cos_den * P->cos_den * (unsigned __int128)bc * (unsigned __int128)bc;
+        unsigned __int128 r = (unsigned __int128)P->cos_num * P->cos_num * (unsigned __int128)pa * (unsigned __int128)bn;
+        out->pass = bc > 0 && l > r;
+    }
 }

@@ -634,3 +634,75 @@ def test_two_set_screen_is_the_union_self_join_across_the_sets(small_wl, mode):
     q = q.astype(np.int64)
     sel = (q[:, 0] < a.n) & (q[:, 1] >= a.n)
     assert set(map(tuple, p.astype(np.int64).tolist())) == set(map(tuple, (q[sel] - [0, a.n]).tolist()))
+
+
+# ---------------------------------------------------------------- re-extraction (Sec. 2.1)
+
+def test_halo_without_border_content_equals_window_cosine():
+    # every rectangle at least M from the window border: the moved window
+    # never meets halo content, n_B(s) = |B| at every shift, and the
+    # re-extraction reading reduces to the fixed-window cosine of Eq. 2
+    wl = synth.gate_bounds_set(43)
+    cs = oracle.ClipSet(wl, halo=True)
+    n = cs.n
+    pairs = np.array([(i, j) for i in range(n) for j in range(n) if i != j], dtype=np.int64)[::7]
+    h = cs.match(pairs, oracle.MODE_COSINE_HALO)
+    w = cs.match(pairs, oracle.MODE_COSINE, use_gates=False)
+    for f in ("dx_dbu", "dy_dbu", "score", "pass_"):
+        np.testing.assert_array_equal(h[f], w[f])
+    np.testing.assert_allclose(h["sim"], w["sim"], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(h["pad"], cs.pops()[pairs[:, 1]])
+    assert h["pass_"].sum() >= 10
+
+
+def test_halo_translate_across_the_border_gives_sim_one():
+    # the layout around a clip moved by t: re-extracting the member's window
+    # at s = -t/p recovers the representative's window exactly (sim 1), even
+    # where geometry crosses the window border; the fixed-window reading does
+    # not (content that left the window is lost)
+    W, M = 512, 32
+    a = [[-20, 40, 60, 100], [200, -24, 260, 30], [300, 300, 530, 340], [100, 480, 180, 540], [240, 200, 300, 260]]
+    clips = [a]
+    for tx, ty in [(12, -20), (-32, 8), (28, 28), (-4, 32)]:
+        b = [[r[0] + tx, r[1] + ty, r[2] + tx, r[3] + ty] for r in a]
+        b = [[max(r[0], -M), max(r[1], -M), min(r[2], W + M), min(r[3], W + M)] for r in b]
+        clips.append(b)
+    cs = oracle.ClipSet(synth.from_lists(clips, W, 4, M), halo=True)
+    for k, (tx, ty) in enumerate([(12, -20), (-32, 8), (28, 28), (-4, 32)], start=1):
+        r = cs.pair(0, k, oracle.MODE_COSINE_HALO)
+        assert (r["dx_dbu"], r["dy_dbu"]) == (-tx, -ty)
+        assert r["sim"] == 1.0 and r["pass_"] == 1
+        assert r["score"] == cs.pop(0) == r["pad"]
+        assert cs.pair(0, k, use_gates=False)["sim"] < 1.0
+
+
+def test_halo_windows_equal_numpy_slices_and_exact_argmax():
+    from fractions import Fraction
+    wl = synth.generate(9, n_clips=24, n_seeds=4, n_copies=14, window_dbu=256, margin_dbu=16, min_rects=3,
+                        max_rects=12, halo_dbu=16)
+    cs = oracle.ClipSet(wl, halo=True)
+    S, N, p, M = cs.S, cs.N, cs.p, cs.M
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        a, b = (int(v) for v in rng.integers(0, wl.n, size=2))
+        A = oracle.rasterize(wl.window_dbu, p, wl.clip(a))
+        Hb = oracle.rasterize(wl.window_dbu + 2 * M, p, wl.clip(b) + M)
+        c, nb = cs.halo_window(a, b)
+        best = None
+        pa = int(A.sum())
+        for dy in range(-S, S + 1):
+            for dx in range(-S, S + 1):
+                win = Hb[S - dy:S - dy + N, S - dx:S - dx + N].astype(np.int64)
+                assert c[dy + S, dx + S] == int((win * A).sum())
+                assert nb[dy + S, dx + S] == int(win.sum())
+                cc, nn = int(c[dy + S, dx + S]), int(nb[dy + S, dx + S])
+                sim2 = Fraction(1) if pa == 0 and nn == 0 else (Fraction(0) if pa == 0 or nn == 0
+                                                                 else Fraction(cc * cc, pa * nn))
+                key = (-sim2, abs(dx) + abs(dy), dy, dx)
+                if best is None or key < best[0]:
+                    best = (key, dx, dy, cc, nn, sim2)
+        r = cs.pair(a, b, oracle.MODE_COSINE_HALO)
+        assert (r["dx_dbu"], r["dy_dbu"]) == (best[1] * p, best[2] * p)
+        assert r["score"] == best[3] and r["pad"] == best[4]
+        assert r["pass_"] == int(best[3] > 0 and best[5] > Fraction(95 * 95, 100 * 100)
+                                 or (pa == 0 and best[4] == 0))
