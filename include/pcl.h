@@ -348,6 +348,40 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
    PCL_ERR_INVALID (NULL ctx). */
 pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns);
 
+/* ---- NEXT: cosine with re-extraction of the member's window --------------
+   Sec. 2.1 extracts a pattern as the layout around its centre, and that
+   centre may lie anywhere in the marker region; read as: each clip carries
+   its rectangles over [-M, W + M)^2 (the layout around its window, a halo
+   of M; rectangles may extend past the window), and at the shift s the
+   member's window moves with the shift, so content from the halo enters it
+   and its norm is the pixel count n_B(s) of the moved window:
+     c(s) = sum_x A(x) Bh(x - s), n_B(s) = sum_x Bh(x - s), x in [0, N)^2,
+     sim(s) = c(s) / sqrt(|A| n_B(s))  (Eq. 2 at every shift).
+   The best shift maximises sim (compared exactly as c1^2 n2 vs c2^2 n1;
+   ties: smaller |dx| + |dy|, then dy, then dx); pass iff c* > 0 and
+   den^2 c*^2 > num^2 |A| n_B(s*) (both windows empty: sim 1, pass).  Needs
+   S <= 32 and S <= N/2.
+   pcl_halo_sizes_get: bytes of the halo rasters ([n][N + 2S][ceil((N +
+   2S) / 64)] u64: row j + S, bit i + S holds the pixel of centre (p i +
+   p/2, p j + p/2), i, j in [-S, N + S)) and of the moved-window pixel
+   counts ([n][(2S + 1)^2] u32, index (dy + S)(2S + 1) + dx + S).
+   pcl_rasterize_halo: fills both for every clip of cs from its rectangles
+   (one CTA per clip); the window rasters of cs are not touched.
+   pcl_match_halo: one record per pair (a = clip of set a, rasterised by
+   pcl_rasterize; b = clip of set b with the halo buffers above), in list
+   order: dx/dy the best shift (dbu), score c(s*), sim (FP32, FP64 inside
+   the near band), pass, reserved = n_B(s*), flags ALIGNED (| EMPTY); no
+   gates run (the lossless bounds assume fixed norms) and pcm fields are 0.
+   One CTA per pair with both rasters in shared memory; d_n as in
+   pcl_match_pairs.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED,
+   PCL_ERR_CUDA. */
+pcl_status pcl_halo_sizes_get(const pcl_params *P, uint32_t n_clips, uint64_t *hbits_bytes, uint64_t *norms_bytes);
+pcl_status pcl_rasterize_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *cs, uint64_t *d_hbits,
+                              uint32_t *d_norms, pcl_stream stream);
+pcl_status pcl_match_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *a, const pcl_clipset *b,
+                          const uint64_t *d_hbits_b, const uint32_t *d_norms_b, const pcl_pair *d_pairs, uint64_t n,
+                          const uint64_t *d_n, pcl_record *d_out, pcl_stream stream);
+
 /* Synchronises the device and reports (then clears) the context's device
    error word: PCL_ERR_TIMEOUT if a kernel's bounded wait ran out (its records
    are then incomplete), PCL_OK otherwise; *flag (may be NULL) gets the word. */

@@ -163,6 +163,11 @@ def load(build_if_missing: bool = True):
         "pcl_device_error": ([_VP, ctypes.POINTER(ctypes.c_int)], st),
         "pcl_set_wait_limit": ([_VP, _U64], st),
         "pcl_surprisal": ([_VP, _VP, _U64, _VP, ctypes.c_uint32, _VP, _VP, _VP, _VP], st),
+        "pcl_halo_sizes_get": ([ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_U64),
+                                ctypes.POINTER(_U64)], st),
+        "pcl_rasterize_halo": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), _VP, _VP, _VP], st),
+        "pcl_match_halo": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_Clipset), _VP,
+                            _VP, _VP, _U64, _VP, _VP, _VP], st),
         "pcl_compact_pass": ([_VP, _VP, _U64, _VP, _VP, _U64, _VP, _VP], st),
         "pcl_match_mixed": ([_VP, _VP, _VP, ctypes.c_uint32, _VP, _U64, _U64, _VP, ctypes.POINTER(Tuning), _VP], st),
         "pcl_server_create": ([_VP, ctypes.POINTER(Params), ctypes.POINTER(_Clipset), ctypes.POINTER(_ServerCfg),
@@ -415,6 +420,35 @@ def pcl_surprisal(ctx: Context, edges, n_nodes: int, d_n=None, stream=None):
     ctx.check(ctx.lib.pcl_surprisal(ctx.h, _ptr(edges), int(edges.shape[0]), _ptr(d_n), n_nodes, _ptr(deg), _ptr(w),
                                     _ptr(sc), _stream_ptr(stream)), "pcl_surprisal")
     return deg[:n_nodes], w[:n_nodes], sc[:n_nodes]
+
+
+def alloc_halo(P: Params, cs: ClipSet):
+    """device buffers (halo rasters, moved-window pixel counts) for the
+    clips of cs under P"""
+    torch = _torch()
+    hb, nb = _U64(), _U64()
+    s = load().pcl_halo_sizes_get(ctypes.byref(P), cs.n, ctypes.byref(hb), ctypes.byref(nb))
+    if s != PCL_OK:
+        raise PclError(s, "pcl_halo_sizes_get")
+    dev = cs.bits.device
+    return (torch.empty(max(int(hb.value), 16), dtype=torch.uint8, device=dev),
+            torch.empty(max(int(nb.value), 16), dtype=torch.uint8, device=dev))
+
+
+def pcl_rasterize_halo(ctx: Context, P: Params, cs: ClipSet, hbits, norms, stream=None) -> None:
+    c = cs.cstruct()
+    ctx.check(ctx.lib.pcl_rasterize_halo(ctx.h, ctypes.byref(P), ctypes.byref(c), _ptr(hbits), _ptr(norms),
+                                         _stream_ptr(stream)), "pcl_rasterize_halo")
+
+
+def pcl_match_halo(ctx: Context, P: Params, a: ClipSet, b: ClipSet, hbits_b, norms_b, pairs, out_rec, d_n=None,
+                   stream=None) -> None:
+    """records of the re-extraction reading for an int32 CUDA pair tensor
+    [n, 2] into a uint8 CUDA tensor [n, 40]"""
+    ca, cb = a.cstruct(), b.cstruct()
+    ctx.check(ctx.lib.pcl_match_halo(ctx.h, ctypes.byref(P), ctypes.byref(ca), ctypes.byref(cb), _ptr(hbits_b),
+                                     _ptr(norms_b), _ptr(pairs), int(pairs.shape[0]), _ptr(d_n), _ptr(out_rec),
+                                     _stream_ptr(stream)), "pcl_match_halo")
 
 
 def pcl_set_wait_limit(ctx: Context, ns: int) -> None:

@@ -20,7 +20,7 @@ LIB = os.path.join(OUTDIR, "libpcl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++20", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
            "-I", INCLUDE, "-I", CSRC]
-CUDA_SOURCES = ["api.cu", "raster.cu", "gates.cu", "edge.cu", "fft.cu", "noalloc.cu", "cross.cu", "server.cu", "mixed.cu", "tc.cu", "xysep.cu", "surprisal.cu"]
+CUDA_SOURCES = ["api.cu", "raster.cu", "gates.cu", "edge.cu", "fft.cu", "noalloc.cu", "cross.cu", "server.cu", "mixed.cu", "tc.cu", "xysep.cu", "surprisal.cu", "halo.cu"]
 CXX_SOURCES = ["host_scp.cpp"]
 
 

@@ -1,0 +1,348 @@
+// Cosine matching with re-extraction of the member's window (Sec. 2.1: a
+// pattern is the layout cut out around its centre, and the centre may lie
+// anywhere in the marker region; Eq. 2 at every shift).
+//
+// Each clip carries its rectangles over [-M, W + M)^2.  Its halo raster
+// samples that region at the pixel centres p i + p/2, i in [-S, N + S): row
+// j + S, bit i + S of a row of NWH = ceil((N + 2S) / 64) words.  For the
+// shift s the member's window moved by s holds the halo pixels x - s,
+// x in [0, N)^2, so
+//   c(s)   = sum_x A(x) Bh(x - s)         (A: the representative's window)
+//   n_B(s) = sum_x Bh(x - s)              (pixels of the moved window)
+//   sim(s) = c(s) / sqrt(|A| n_B(s)).
+// n_B depends on the member alone: halo_raster_kernel tabulates it for every
+// shift once per clip (the window sums of the halo raster, as a summed-area
+// table would give them), beside the halo raster itself.  halo_pair_kernel
+// counts c(s) for every shift by AND + popcount with both rasters staged in
+// shared memory and keeps the shift of largest sim, compared exactly as
+// c1^2 n2 vs c2^2 n1 (|A| is common; products < 2^55 up to 512^2 px), ties by
+// smaller |dx| + |dy|, then dy, then dx; the decision is Eq. 2's exact rule
+// with n_B(s*) for |B|.  No lossless gates here: they bound c against fixed
+// norms.
+#include "common.cuh"
+#include "ctx.h"
+
+using pcl::cos_exceeds;
+using pcl::Geo;
+using pcl::make_geo;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline int halo_side(int N, int S) { return N + 2 * S; }
+__host__ __device__ inline int halo_words(int N, int S) { return (N + 2 * S + 63) / 64; }
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
+
+// one CTA per clip: halo raster rows, then the window sums n_B(s)
+__global__ void __launch_bounds__(kThreads) halo_raster_kernel(pcl_params prm, pcl_clipset cs, uint64_t *hbits,
+                                                               uint32_t *norms) {
+    const Geo g = make_geo(prm);
+    const int N = g.N, S = g.S, p = g.p, NH = halo_side(N, S), NWH = halo_words(N, S), K = 2 * S + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *rows = reinterpret_cast<uint64_t *>(smem);                     // [NH][NWH]
+    uint16_t *cnt = reinterpret_cast<uint16_t *>(rows + (size_t)NH * NWH);   // [NH][K]
+    const uint32_t c = blockIdx.x;
+    const int32_t *r = cs.rects + 4 * (size_t)cs.rect_off[c];
+    const int nr = (int)(cs.rect_off[c + 1] - cs.rect_off[c]);
+    // row t = j + S has its pixel centres at y = p j + p/2 (doubled: 2 p j + p)
+    for (int t = threadIdx.x; t < NH; t += blockDim.x) {
+        uint64_t w[9];
+        for (int k = 0; k < NWH; ++k) w[k] = 0ull;
+        const int Y2 = 2 * p * (t - S) + p;
+        for (int q = 0; q < nr; ++q) {
+            const int x0 = r[4 * q], y0 = r[4 * q + 1], x1 = r[4 * q + 2], y1 = r[4 * q + 3];
+            if (!(2 * y0 <= Y2 && Y2 < 2 * y1)) continue;
+            // columns i with 2 x0 <= 2 p i + p < 2 x1, as halo bits i + S
+            int b0 = ceil_div(2 * x0 - p, 2 * p) + S, b1 = ceil_div(2 * x1 - p, 2 * p) + S;
+            b0 = b0 < 0 ? 0 : b0;
+            b1 = b1 > NH ? NH : b1;
+            for (int k = 0; k < NWH; ++k) {
+                const int lo = max(b0, 64 * k), hi = min(b1, 64 * k + 64);
+                if (lo >= hi) continue;
+                const int n = hi - lo, o = lo - 64 * k;
+                w[k] |= (n == 64 ? ~0ull : ((1ull << n) - 1ull)) << o;
+            }
+        }
+        for (int k = 0; k < NWH; ++k) {
+            rows[(size_t)t * NWH + k] = w[k];
+            hbits[((size_t)c * NH + t) * NWH + k] = w[k];
+        }
+    }
+    __syncthreads();
+    // cnt[t][dx + S]: bits of halo row t at positions [S - dx, S - dx + N)
+    for (int task = threadIdx.x; task < NH * K; task += blockDim.x) {
+        const int t = task / K, dx = task % K - S;
+        const int lo = S - dx, hi = lo + N;
+        uint32_t n = 0;
+        for (int k = lo >> 6; k <= (hi - 1) >> 6; ++k) {
+            uint64_t m = ~0ull;
+            if (64 * k < lo) m &= ~0ull << (lo - 64 * k);
+            if (64 * k + 64 > hi) m &= (hi - 64 * k) >= 64 ? ~0ull : ((1ull << (hi - 64 * k)) - 1ull);
+            n += (uint32_t)__popcll(rows[(size_t)t * NWH + k] & m);
+        }
+        cnt[(size_t)t * K + dx + S] = (uint16_t)n;
+    }
+    __syncthreads();
+    // n_B(dx, dy) = sum over window rows y of cnt[y - dy + S][dx]
+    for (int task = threadIdx.x; task < K * K; task += blockDim.x) {
+        const int dy = task / K - S, kx = task % K;
+        uint32_t s = 0;
+        for (int y = 0; y < N; ++y) s += cnt[(size_t)(y - dy + S) * K + kx];
+        norms[(size_t)c * K * K + task] = s;
+    }
+}
+
+// sim(c1, n1) > sim(c2, n2), with |A| = pa common to both
+__device__ __forceinline__ int sim_cmp(uint32_t c1, uint32_t n1, uint32_t c2, uint32_t n2, uint64_t pa) {
+    uint64_t a1, d1, a2, d2;
+    if (pa == 0 || n1 == 0) {
+        a1 = (pa == 0 && n1 == 0) ? 1u : 0u;
+        d1 = 1;
+    } else {
+        a1 = (uint64_t)c1 * c1;
+        d1 = n1;
+    }
+    if (pa == 0 || n2 == 0) {
+        a2 = (pa == 0 && n2 == 0) ? 1u : 0u;
+        d2 = 1;
+    } else {
+        a2 = (uint64_t)c2 * c2;
+        d2 = n2;
+    }
+    const uint64_t l = a1 * d2, r = a2 * d1;
+    return l > r ? 1 : (l < r ? -1 : 0);
+}
+
+struct Best {
+    uint32_t c, n;
+    int dx, dy;
+    bool valid;
+};
+
+// b1 before b2 in the order (-sim, |dx| + |dy|, dy, dx)
+__device__ __forceinline__ bool before(const Best &b1, const Best &b2, uint64_t pa) {
+    if (!b2.valid) return b1.valid;
+    if (!b1.valid) return false;
+    const int s = sim_cmp(b1.c, b1.n, b2.c, b2.n, pa);
+    if (s) return s > 0;
+    const int l1 = abs(b1.dx) + abs(b1.dy), l2 = abs(b2.dx) + abs(b2.dy);
+    if (l1 != l2) return l1 < l2;
+    if (b1.dy != b2.dy) return b1.dy < b2.dy;
+    return b1.dx < b2.dx;
+}
+
+// one CTA per pair (CTAs stride the list)
+template <int NW>
+__global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
+                                                             const uint64_t *__restrict__ hbits,
+                                                             const uint32_t *__restrict__ norms, const pcl_pair *pairs,
+                                                             uint64_t npairs, const unsigned long long *d_n,
+                                                             pcl_record *out) {
+    constexpr int N = 64 * NW;
+    const Geo g = make_geo(prm);
+    const int S = g.S, NH = halo_side(N, S), NWH = halo_words(N, S), K = 2 * S + 1, KK = K * K;
+    const int RW = NWH + 1;  // halo row words in shared memory, one zero word of padding
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sa = reinterpret_cast<uint64_t *>(smem);          // [N][NW]
+    uint64_t *sh = sa + (size_t)N * NW;                         // [NH][RW]
+    uint32_t *sn = reinterpret_cast<uint32_t *>(sh + (size_t)NH * RW);  // [K*K]
+    Best *wb = reinterpret_cast<Best *>(sn + ((KK + 3) & ~3));  // [warps]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (d_n && *d_n < npairs) npairs = *d_n;
+    for (uint64_t pid = blockIdx.x; pid < npairs; pid += gridDim.x) {
+        const pcl_pair pr = pairs[pid];
+        pcl_record rec{};
+        rec.a = pr.a;
+        rec.b = pr.b;
+        rec.mode = PCL_MODE_COSINE;
+        if (pr.a >= A.n_clips || pr.b >= B.n_clips) {
+            if (threadIdx.x == 0) {
+                rec.flags = PCL_GATE_BAD_INDEX;
+                out[pid] = rec;
+            }
+            continue;
+        }
+        __syncthreads();  // the previous pair's buffers are no longer read
+        const uint64_t *ga = A.bits + (size_t)pr.a * N * NW;
+        const uint64_t *gh = hbits + (size_t)pr.b * NH * NWH;
+        for (int t = threadIdx.x; t < N * NW; t += blockDim.x) sa[t] = __ldg(ga + t);
+        for (int t = threadIdx.x; t < NH * RW; t += blockDim.x) {
+            const int row = t / RW, k = t % RW;
+            sh[t] = k < NWH ? __ldg(gh + (size_t)row * NWH + k) : 0ull;
+        }
+        for (int t = threadIdx.x; t < KK; t += blockDim.x) sn[t] = __ldg(norms + (size_t)pr.b * KK + t);
+        __syncthreads();
+        const uint64_t pa = A.pop[pr.a];
+        Best best{0, 0, 0, 0, false};
+        // warp task: (dy, 8 consecutive dx); lanes take rows y and count the
+        // 8 shifts from registers
+        constexpr int DXC = 8;
+        const int nch = (K + DXC - 1) / DXC;
+        for (int task = warp; task < K * nch; task += nwarps) {
+            const int dy = task / nch - S, dx0 = (task % nch) * DXC - S;
+            uint32_t cnt[DXC];
+#pragma unroll
+            for (int u = 0; u < DXC; ++u) cnt[u] = 0;
+            for (int y = lane; y < N; y += 32) {
+                const uint64_t *ra = sa + (size_t)y * NW;
+                const uint64_t *rh = sh + (size_t)(y - dy + S) * RW;
+#pragma unroll
+                for (int u = 0; u < DXC; ++u) {
+                    const int dx = dx0 + u;
+                    if (dx > S) break;
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        // halo bits [64 w + S - dx, +64) line up with A's word w
+                        const int q = 64 * w + S - dx, qi = q >> 6, qs = q & 63;
+                        const uint64_t v = qs ? (rh[qi] >> qs) | (rh[qi + 1] << (64 - qs)) : rh[qi];
+                        sum += (uint32_t)__popcll(ra[w] & v);
+                    }
+                    cnt[u] += sum;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < DXC; ++u) {
+                const int dx = dx0 + u;
+                const uint32_t c = __reduce_add_sync(0xffffffffu, cnt[u]);
+                if (dx <= S) {
+                    const Best cand{c, sn[(dy + S) * K + dx + S], dx, dy, true};
+                    if (before(cand, best, pa)) best = cand;
+                }
+            }
+        }
+        if (lane == 0) wb[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Best b = wb[0];
+            for (int w = 1; w < nwarps; ++w)
+                if (before(wb[w], b, pa)) b = wb[w];
+            rec.dx_dbu = b.dx * g.p;
+            rec.dy_dbu = b.dy * g.p;
+            rec.score = b.c;
+            rec.reserved = b.n;
+            uint16_t fl = PCL_F_ALIGNED;
+            float sim = 0.0f;
+            if (pa == 0 && b.n == 0) {
+                sim = 1.0f;
+                rec.pass = 1;
+                fl |= PCL_F_EMPTY;
+            } else if (pa && b.n) {
+                sim = (float)b.c / sqrtf((float)pa * (float)b.n);
+                const float T = (float)prm.cos_num / (float)prm.cos_den;
+                if (fabsf(sim - T) < prm.near_band) {
+                    fl |= PCL_F_NEAR_BAND;
+                    sim = (float)((double)b.c / sqrt((double)pa * (double)b.n));
+                }
+                rec.pass = cos_exceeds(b.c, pa, b.n, prm.cos_num, prm.cos_den) ? 1 : 0;
+            }
+            rec.sim = sim;
+            rec.flags = fl;
+            out[pid] = rec;
+        }
+    }
+}
+
+size_t raster_smem(const Geo &g) {
+    const int NH = halo_side(g.N, g.S), NWH = halo_words(g.N, g.S), K = 2 * g.S + 1;
+    return 8ull * NH * NWH + 2ull * NH * K;
+}
+
+size_t pair_smem(const Geo &g) {
+    const int NH = halo_side(g.N, g.S), NWH = halo_words(g.N, g.S), K = 2 * g.S + 1;
+    return 8ull * g.N * g.nw + 8ull * NH * (NWH + 1) + 4ull * (((size_t)K * K + 3) & ~size_t(3)) +
+           sizeof(Best) * (kThreads / 32);
+}
+
+template <int NW>
+cudaError_t launch_pair(const pcl_params &prm, const Geo &g, const pcl_clipset &a, const pcl_clipset &b,
+                        const uint64_t *hb, const uint32_t *nb, const pcl_pair *pairs, uint64_t n,
+                        const unsigned long long *d_n, pcl_record *out, int num_sms, cudaStream_t st) {
+    const size_t sm = pair_smem(g);
+    cudaError_t e = cudaFuncSetAttribute(halo_pair_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_pair_kernel<NW>, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    halo_pair_kernel<NW><<<(unsigned)(n < cap ? n : cap), kThreads, sm, st>>>(prm, a, b, hb, nb, pairs, n, d_n, out);
+    return cudaGetLastError();
+}
+
+pcl_status fail(pcl_ctx *ctx, pcl_status s, const char *m) {
+    ctx->err = m;
+    return s;
+}
+
+pcl_status cuda_fail(pcl_ctx *ctx, cudaError_t e, const char *where) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return PCL_ERR_CUDA;
+}
+
+bool halo_geometry_ok(const Geo &g) { return g.S <= 32 && g.S <= g.N / 2; }
+
+}  // namespace
+
+extern "C" {
+
+pcl_status pcl_halo_sizes_get(const pcl_params *P, uint32_t n_clips, uint64_t *hbits_bytes, uint64_t *norms_bytes) {
+    if (pcl_params_validate(P) != PCL_OK || !hbits_bytes || !norms_bytes) return PCL_ERR_INVALID;
+    const Geo g = make_geo(*P);
+    if (!halo_geometry_ok(g)) return PCL_ERR_UNSUPPORTED;
+    const uint64_t K = 2ull * g.S + 1;
+    *hbits_bytes = 8ull * n_clips * halo_side(g.N, g.S) * halo_words(g.N, g.S);
+    *norms_bytes = 4ull * n_clips * K * K;
+    return PCL_OK;
+}
+
+pcl_status pcl_rasterize_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *cs, uint64_t *d_hbits,
+                              uint32_t *d_norms, pcl_stream stream) {
+    if (!ctx) return PCL_ERR_INVALID;
+    ctx->err.clear();
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (pcl_params_validate(P) != PCL_OK) return fail(ctx, PCL_ERR_INVALID, "pcl_rasterize_halo: invalid parameters");
+    const Geo g = make_geo(*P);
+    if (!halo_geometry_ok(g)) return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_rasterize_halo: needs S <= 32 and S <= N/2");
+    if (!cs || (cs->n_clips && (!cs->rect_off || !cs->rects || !d_hbits || !d_norms)))
+        return fail(ctx, PCL_ERR_INVALID, "pcl_rasterize_halo: NULL buffer");
+    if (cs->n_clips == 0) return PCL_OK;
+    const size_t sm = raster_smem(g);
+    e = cudaFuncSetAttribute(halo_raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        halo_raster_kernel<<<cs->n_clips, kThreads, sm, (cudaStream_t)stream>>>(*P, *cs, d_hbits, d_norms);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "halo raster kernel");
+}
+
+pcl_status pcl_match_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *a, const pcl_clipset *b,
+                          const uint64_t *d_hbits_b, const uint32_t *d_norms_b, const pcl_pair *d_pairs, uint64_t n,
+                          const uint64_t *d_n, pcl_record *d_out, pcl_stream stream) {
+    if (!ctx) return PCL_ERR_INVALID;
+    ctx->err.clear();
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (pcl_params_validate(P) != PCL_OK) return fail(ctx, PCL_ERR_INVALID, "pcl_match_halo: invalid parameters");
+    const Geo g = make_geo(*P);
+    if (!halo_geometry_ok(g)) return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_match_halo: needs S <= 32 and S <= N/2");
+    if (!a || !b || (n && (!d_pairs || !d_out || !d_hbits_b || !d_norms_b)) ||
+        (a->n_clips && (!a->bits || !a->pop)))
+        return fail(ctx, PCL_ERR_INVALID, "pcl_match_halo: NULL buffer");
+    if (n == 0) return PCL_OK;
+    const auto *dn = reinterpret_cast<const unsigned long long *>(d_n);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (g.nw) {
+        case 1: e = launch_pair<1>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
+        case 2: e = launch_pair<2>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
+        case 4: e = launch_pair<4>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
+        case 8: e = launch_pair<8>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
+        default: return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_match_halo: raster side");
+    }
+    return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "halo pair kernel");
+}
+
+}  // extern "C"
