@@ -66,6 +66,8 @@ def parse():
                     help="clips of the large serving library (tensor-core cosine and edge; 0: skip)")
     ap.add_argument("--class-library-clips", type=int, default=100_000,
                     help="clips of each 64^2, 128^2 and 512^2 px library of the size-class serving measurement")
+    ap.add_argument("--topo-clips", type=int, default=1_000_000,
+                    help="clips of the topological pre-screen recall measurement (0: skip)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
                     help="same-seed pairs checked against the FP64 oracle per engine (0: skip)")
@@ -463,6 +465,63 @@ def run_batched(pcl, ctx, dev, clips_per_class: int, steps: int, seed: int = 1):
             "aligned_per_s": aligned / (best_ms / 1e3),
             "tuning": {"fft_radix": int(tune.fft_radix), "ctas_per_sm": int(tune.ctas_per_sm),
                        "candidates_ms": tinfo.get("ms")}}
+
+
+def run_topo(pcl, ctx, dev, clips: int, seed: int):
+    """The lossy topological pre-screen (PCL_P_TOPO_HASH: pairs of equal
+    polygon count only) against the lossless screens on a scale-recipe set of
+    `clips` clips: candidates kept, screen time, and the recall of the
+    lossless screen's passing pairs (a pair it passes survives the
+    pre-screen iff both clips have the same class, and the alignment engines
+    are the same, so the recall needs one matching run).  Edge mode at the
+    configured tolerance and at 8 dbu; cosine (tensor-core engine, no
+    spectra) at the configured threshold."""
+    import torch
+
+    import synth
+    k = clips
+    wl = synth.preset("scale", seed=seed + 300, n_clips=k, n_seeds=k // 20, n_copies=7 * k // 10)
+    cls = np.minimum(np.diff(wl.rect_off.astype(np.int64)), 63)
+    out = {"clips": k, "workload": f"scale recipe at {k:,} clips (256^2 px)"}
+    P0 = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL, cos_engine=pcl.ENGINE_TC_DIRECT)
+    cs = pcl.alloc_clipset(P0, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P0, cs)
+    torch.cuda.synchronize()
+
+    def timed_cand(P, mode):
+        w, _ = pcl.candidates(ctx, P, mode, cs, cap=1 << 20)  # warm-up, gives the exact count
+        m = int(w.shape[0])
+        del w
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pairs, gates = pcl.candidates(ctx, P, mode, cs, cap=max(m, 1))
+        e1.record()
+        torch.cuda.synchronize()
+        return pairs, gates, e0.elapsed_time(e1)
+
+    dcls = torch.from_numpy(cls).to(dev)
+
+    for name, mode, num, tol in (("edge_tol4", pcl.MODE_EDGE, COS_NUM, TOL), ("edge_tol8", pcl.MODE_EDGE, COS_NUM, 8),
+                                 ("cosine_t95", pcl.MODE_COSINE, COS_NUM, TOL)):
+        P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, num, COS_DEN, tol, cos_engine=pcl.ENGINE_TC_DIRECT)
+        Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, num, COS_DEN, tol, cos_engine=pcl.ENGINE_TC_DIRECT,
+                        flags=pcl.P_TOPO_HASH)
+        lp, lg, lms = timed_cand(P, mode)
+        tp, tg, tms = timed_cand(Pt, mode)
+        rec = pcl.match(ctx, P, mode, cs, cs, lp)  # uint8 [m, 40]; the decision is byte 34
+        passing = rec[:, 34] > 0
+        la, lb = lp[:, 0].long(), lp[:, 1].long()
+        n_pass = int(passing.sum().item())
+        kept = int((passing & (dcls[la] == dcls[lb])).sum().item())
+        out[name] = {"pairs": k * (k - 1) // 2, "lossless_candidates": int(len(lp)), "topo_candidates": int(len(tp)),
+                     "lossless_ms": lms, "topo_ms": tms, "topo_rejected": int(tg[pcl.GATE_T0_TOPO]),
+                     "passes": n_pass, "passes_kept": kept, "recall": kept / n_pass if n_pass else None,
+                     "screened_out_by_topo_frac": float(tg[pcl.GATE_T0_TOPO]) / (k * (k - 1) // 2)}
+        del lp, tp, rec
+        torch.cuda.empty_cache()
+    del cs
+    torch.cuda.empty_cache()
+    return out
 
 
 def workload(config: str, seed: int, clips: int = 0):
@@ -873,6 +932,12 @@ def run_ours(args, rank, world, local_rank):
         batched = run_batched(pcl, ctx, dev, args.batch_clips, args.steps)
         torch.cuda.synchronize()
 
+    # ---- the lossy topological pre-screen against the lossless screens
+    topo = None
+    if args.topo_clips and world == 1:
+        topo = run_topo(pcl, ctx, dev, args.topo_clips, args.seed)
+        torch.cuda.synchronize()
+
     # ---- end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -994,6 +1059,7 @@ def run_ours(args, rank, world, local_rank):
         "serving_large_library": serving_large,
         "serving_size_classes": serving_classes,
         "batched": batched,
+        "topo_prescreen": topo,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
     # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2

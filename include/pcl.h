@@ -71,7 +71,8 @@ enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
 /* pcl_params.flags */
 enum {
     PCL_P_NO_GATES = 1u << 0, /* match every listed pair without the lossless gates */
-    PCL_P_NO_PCM = 1u << 1    /* FFT engine: skip the phase-correlation surface */
+    PCL_P_NO_PCM = 1u << 1,   /* FFT engine: skip the phase-correlation surface */
+    PCL_P_TOPO_HASH = 1u << 2 /* self-join candidates: lossy topological pre-screen (see pcl_candidates) */
 };
 
 /*
@@ -112,6 +113,7 @@ enum {
     PCL_GATE_G3_DENSITY = 3,  /* 16x16 block-density bound */
     PCL_GATE_E1_MATCH = 4,    /* no polygon correspondence at the pre-alignment */
     PCL_GATE_E2_BBOX = 5,     /* bbox size differs by more than 2*tol */
+    PCL_GATE_T0_TOPO = 6,     /* topological classes differ (lossy pre-screen, PCL_P_TOPO_HASH) */
     PCL_GATE_UNSUPPORTED = 14, /* size class outside the engine's range (no work done) */
     PCL_GATE_BAD_INDEX = 15,  /* pair index outside its clip set (no work done) */
     PCL_F_NEAR_BAND = 1u << 4,
@@ -246,8 +248,19 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
    the number of pairs screened).  COSINE uses the context workspace (two
    sets: about 16 (N^2 + 2) + 16 |a| + 8 |b| bytes for the area orders of
    both sets and the bands of a's clips).
-   Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with S > N/16),
-   PCL_ERR_OOM (workspace), PCL_ERR_CUDA. */
+   With P->flags & PCL_P_TOPO_HASH (self-join only) a lossy topological
+   pre-screen runs first (Sec. 3.1 stage 1 filters with topological hashing
+   before the exact tests): a pair is kept only if both clips have the same
+   class, the polygon count saturated at 63 (the number of connected pieces,
+   which edge moves that keep the polygons apart do not change); rejected
+   pairs count under PCL_GATE_T0_TOPO.  Cosine sorts the clips by (class,
+   area) so that each band stays inside its class (workspace 64 times the
+   area histogram); edge mode checks the classes first in the screen's
+   lockstep test.  Pairs of different polygon counts that would pass are
+   lost: the recall is a measured quantity, not a guarantee.
+   Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE with S > N/16; the
+   topological pre-screen with b != NULL), PCL_ERR_OOM (workspace),
+   PCL_ERR_CUDA. */
 pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *a,
                           const pcl_clipset *b, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
                           uint64_t *d_gate_counts, pcl_stream stream);
@@ -267,7 +280,8 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
              0 .. min(8y + 8, ceil(n/32)) - 1 and starts at tile 4y(y + 1)
              while 8y <= ceil(n/32), then grows by ceil(n/32) per block).
    pcl_candidates is shard 0 of 1.  Errors: those of pcl_candidates, and
-   PCL_ERR_INVALID when s >= S or S = 0. */
+   PCL_ERR_INVALID when s >= S or S = 0, PCL_ERR_UNSUPPORTED for the
+   topological pre-screen with S > 1. */
 pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, const pcl_clipset *cs,
                                 uint32_t shard, uint32_t n_shards, pcl_pair *d_out, uint64_t cap, uint64_t *d_count,
                                 uint64_t *d_gate_counts, pcl_stream stream);

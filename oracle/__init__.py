@@ -45,6 +45,7 @@ GATE_G2_PROFILE = 2
 GATE_G3_DENSITY = 3
 GATE_E1_MATCH = 4
 GATE_E2_BBOX = 5
+GATE_T0_TOPO = 6  # lossy topological pre-screen (candidate screens only)
 
 F_NEAR_BAND = 1 << 4
 F_EDGE_VERIFY_FAIL = 1 << 7
@@ -61,7 +62,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("pitch_dbu", ctypes.c_int32), ("window_dbu", ctypes.c_int32),
                 ("marker_dbu", ctypes.c_int32), ("cos_num", ctypes.c_uint32),
                 ("cos_den", ctypes.c_uint32), ("edge_tol_dbu", ctypes.c_int32),
-                ("use_gates", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("use_gates", ctypes.c_int32), ("use_topo", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -127,9 +128,9 @@ def default_threads() -> int:
 
 
 def params(window_dbu: int, pitch_dbu: int = 4, marker_dbu: int = 32, cos_num: int = 95,
-           cos_den: int = 100, edge_tol_dbu: int = 4, use_gates: bool = True) -> _Params:
+           cos_den: int = 100, edge_tol_dbu: int = 4, use_gates: bool = True, topo: bool = False) -> _Params:
     return _Params(pitch_dbu, window_dbu, marker_dbu, cos_num, cos_den, edge_tol_dbu,
-                   int(bool(use_gates)), 0)
+                   int(bool(use_gates)), int(bool(topo)))
 
 
 def rasterize(window_dbu: int, pitch_dbu: int, rects) -> np.ndarray:

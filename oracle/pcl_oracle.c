@@ -42,6 +42,7 @@ enum {
     ORC_GATE_G3_DENSITY = 3,
     ORC_GATE_E1_MATCH = 4,
     ORC_GATE_E2_BBOX = 5,
+    ORC_GATE_T0_TOPO = 6,  /* lossy pre-screen: different topological classes */
 };
 enum {
     ORC_F_NEAR_BAND = 1u << 4,
@@ -68,7 +69,7 @@ typedef struct orc_params {
     uint32_t cos_num, cos_den;  /* T = num / den */
     int32_t edge_tol_dbu;
     int32_t use_gates;          /* 0: evaluate every pair by brute force */
-    int32_t pad;
+    int32_t use_topo;           /* candidate screens: lossy topological pre-screen first */
 } orc_params;
 
 /* ---------------------------------------------------------------- clip set */
@@ -738,6 +739,18 @@ typedef struct {
     uint64_t counts[16];
 } cand_job;
 
+/*
+ * Topological class of a clip for the lossy pre-screen (Sec. 3.1 stage 1
+ * names topological hashing): its polygon count, saturated at 63.  Reading:
+ * each rectangle is a polygon (as in edge mode), and a count is what small
+ * edge moves that keep polygons apart leave unchanged.  A pair of different
+ * classes is screened out before any exact test.
+ */
+static int topo_class_of(const orc_set *s, int c) {
+    int n = (int)(s->roff[c + 1] - s->roff[c]);
+    return n < 63 ? n : 63;
+}
+
 static size_t tri_index(int n, int i, int j) {  /* i < j */
     return (size_t)i * (size_t)(2 * n - i - 1) / 2 + (size_t)(j - i - 1);
 }
@@ -753,7 +766,9 @@ static void *cand_worker(void *arg) {
         if (i >= n) break;
         for (int j = i + 1; j < n; ++j) {
             int g;
-            if (c->mode == ORC_MODE_COSINE) {
+            if (c->P->use_topo && topo_class_of(c->s, i) != topo_class_of(c->s, j)) {
+                g = ORC_GATE_T0_TOPO;
+            } else if (c->mode == ORC_MODE_COSINE) {
                 if (c->s->pop[i] == 0 && c->s->pop[j] == 0) g = ORC_GATE_NONE;
                 else g = cosine_gate(c->s, i, j, c->P);
             } else {

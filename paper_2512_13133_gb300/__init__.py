@@ -36,6 +36,7 @@ SHIFT_EXACT_ARGMAX = 0
 SHIFT_PCM_PEAK = 1
 P_NO_GATES = 1
 P_NO_PCM = 2
+P_TOPO_HASH = 4  # self-join candidates: lossy topological pre-screen first
 
 GATE_NONE = 0
 GATE_G1_AREA = 1
@@ -43,6 +44,7 @@ GATE_G2_PROFILE = 2
 GATE_G3_DENSITY = 3
 GATE_E1_MATCH = 4
 GATE_E2_BBOX = 5
+GATE_T0_TOPO = 6
 GATE_UNSUPPORTED = 14
 GATE_BAD_INDEX = 15
 F_NEAR_BAND = 1 << 4

@@ -10,7 +10,7 @@
 
 namespace pcl {
 cudaError_t launch_raster(const pcl_params &, const pcl_clipset &, cudaStream_t);
-size_t band_join_workspace(const Geo &, uint32_t);
+size_t band_join_workspace(const Geo &, uint32_t, bool);
 cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
                              unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
 cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
@@ -225,6 +225,8 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
     if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
     const bool edge = mode == PCL_MODE_EDGE;
     if (!edge && mode != PCL_MODE_COSINE) return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);
+    if (P->flags & PCL_P_TOPO_HASH)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "the topological pre-screen is a self-join screen%s%lld");
     if ((s = check_clipset(ctx, a, edge)) || (s = check_clipset(ctx, b, edge))) return s;
     if (!d_count || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL output%s%lld");
     cudaStream_t st = (cudaStream_t)stream;
@@ -259,7 +261,10 @@ pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode
     if (s) return s;
     if (pcl_params_validate(P)) return fail(ctx, PCL_ERR_INVALID, "invalid parameters%s%lld");
     if (n_shards == 0 || shard >= n_shards) return fail(ctx, PCL_ERR_INVALID, "shard out of range%s%lld");
-    if ((s = check_clipset(ctx, cs, mode == PCL_MODE_EDGE))) return s;
+    const bool topo = (P->flags & PCL_P_TOPO_HASH) != 0;
+    if ((s = check_clipset(ctx, cs, mode == PCL_MODE_EDGE || topo))) return s;
+    if (topo && n_shards != 1)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "the topological pre-screen takes the whole self-join%s%lld");
     if (!d_count || (cap && !d_out)) return fail(ctx, PCL_ERR_INVALID, "NULL output%s%lld");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st);
@@ -269,7 +274,7 @@ pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode
     if (mode == PCL_MODE_COSINE) {
         const Geo g = make_geo(*P);
         if (g.S > g.N / 16) return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine gates need S <= N/16%s%lld");
-        const size_t need = band_join_workspace(g, cs->n_clips);
+        const size_t need = band_join_workspace(g, cs->n_clips, topo);
         if ((s = ensure_ws(ctx, need))) return s;
         e = launch_band_join(*P, *cs, ctx->ws, ctx->ws_bytes, d_out, cap, cnt, gates, ctx->num_sms, st, shard,
                              n_shards);

@@ -39,6 +39,12 @@ __host__ __device__ inline Geo make_geo(const pcl_params &q) {
 // ------------------------------------------------------------ edge signature
 enum { ES_N = 0, ES_HASX, ES_LOX, ES_HIX, ES_HASY, ES_LOY, ES_HIY, ES_BORDER };
 
+// classes of the topological pre-screen: the polygon count, saturated
+constexpr int kTopoClasses = 64;
+__host__ __device__ inline int topo_class(int n_polygons) {
+    return n_polygons < kTopoClasses - 1 ? n_polygons : kTopoClasses - 1;
+}
+
 // ------------------------------------------------------------ complex math
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     const unsigned lt = (1u << lane) - 1u;
     uint64_t *gcol = grids + (32 + warp) * kGS;  // this warp's current column grid
 
-    uint32_t g_e1 = 0, g_e2 = 0, kept = 0;
+    uint32_t g_e1 = 0, g_e2 = 0, g_t0 = 0, kept = 0;
+    const bool topo = (prm.flags & PCL_P_TOPO_HASH) != 0;  // lossy pre-screen: equal polygon-count classes
     int qn = 0, fn = 0;  // queue lengths (warp-uniform)
     // grid-test state of this lane
     bool h2 = false;
@@ -345,7 +346,9 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
         bool sa = false;
         int s0x = 0, s0y = 0;
         if (CROSS ? i < nr : i < j) {
-            if (na == 0 || nb == 0) {
+            if (topo && topo_class(na) != topo_class(nb)) {
+                ++g_t0;
+            } else if (na == 0 || nb == 0) {
                 if (na == 0 && nb == 0) both_empty = true;
                 else ++g_e1;
             } else {
@@ -383,11 +386,13 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     // gate counters: one atomic per warp and counter
     g_e1 = __reduce_add_sync(0xffffffffu, g_e1);
     g_e2 = __reduce_add_sync(0xffffffffu, g_e2);
+    g_t0 = __reduce_add_sync(0xffffffffu, g_t0);
     kept = __reduce_add_sync(0xffffffffu, kept);
     if (lane == 0 && gates) {
         if (kept) atomicAdd(gates + 0, (unsigned long long)kept);
         if (g_e1) atomicAdd(gates + PCL_GATE_E1_MATCH, (unsigned long long)g_e1);
         if (g_e2) atomicAdd(gates + PCL_GATE_E2_BBOX, (unsigned long long)g_e2);
+        if (g_t0) atomicAdd(gates + PCL_GATE_T0_TOPO, (unsigned long long)g_t0);
     }
 }
 

@@ -42,6 +42,16 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
     return lo;
 }
 
+// sort keys of the topological pre-screen: class * V + area, the class
+// being the polygon count saturated at kTopoClasses - 1
+__global__ void topo_key_kernel(const uint32_t *pop, const int32_t *esig, uint32_t n, uint32_t V, uint32_t *key) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t np = esig[(size_t)i * 8 + ES_N];
+        const uint32_t cls = np < kTopoClasses - 1 ? (uint32_t)np : (uint32_t)(kTopoClasses - 1);
+        key[i] = cls * V + pop[i];
+    }
+}
+
 __global__ void hist_kernel(const uint32_t *pop, uint32_t n, uint32_t *hist) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         atomicAdd(hist + pop[i], 1u);
@@ -92,9 +102,11 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
     }
 }
 
+// spop holds the sorted keys: the area, or with the topological pre-screen
+// class * V + area (V = N^2 + 2), so that a band never leaves its class
 template <int WPL>
 __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
-                                                        const uint32_t *spop, const uint32_t *cum,
+                                                        const uint32_t *spop, const uint32_t *cum, uint32_t V,
                                                         uint32_t vmax_all, pcl_pair *out, uint64_t cap,
                                                         unsigned long long *count,
                                                         unsigned long long *local_gates,
@@ -112,10 +124,12 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= n) break;
         const uint32_t a = order[p];
-        const uint64_t pa = spop[p];
+        const uint32_t kp = spop[p];
+        const uint64_t pa = kp % V;
+        const uint32_t base = kp - (uint32_t)pa;  // first key of the class
         uint64_t vmax = pa == 0 ? 0 : (den2 * pa - 1) / num2;
         if (vmax > vmax_all) vmax = vmax_all;
-        const uint32_t end = cum[vmax + 1];
+        const uint32_t end = cum[base + vmax + 1];
         const uint32_t *cwa = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)a * 2 * nb2);
         uint32_t ca[WPL], da[WPL];
 #pragma unroll
@@ -147,7 +161,7 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             int tA = 0, tB = 0;  // areas are below 2^31, so are the thresholds (clamped below)
             if (q < end) {
                 b = order[q];
-                const uint64_t pb = spop[q];
+                const uint64_t pb = spop[q] % V;
                 const int64_t um = cos_umax(pa, pb, prm.cos_num, prm.cos_den);
                 tA = (int)max((int64_t)pa - um, (int64_t)INT_MIN);
                 tB = (int)max((int64_t)pb - um, (int64_t)INT_MIN);
@@ -216,14 +230,26 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
 }
 
 // add this call's gate counts to the caller's array; G1 = all pairs minus the
-// pairs the band join enumerated
+// pairs the band join enumerated.  With the topological pre-screen (cum of
+// the class keys given, C classes of V keys) the pairs of different classes
+// count as its rejections and G1 takes the rest.
 __global__ void finish_gates_kernel(const unsigned long long *local, unsigned long long *gates,
-                                    unsigned long long total) {
+                                    unsigned long long total, const uint32_t *cum, uint32_t V, uint32_t C,
+                                    uint32_t n) {
     if (threadIdx.x == 0 && gates) {
         const unsigned long long seen =
             local[0] + local[PCL_GATE_G2_PROFILE] + local[PCL_GATE_G3_DENSITY];
+        unsigned long long same = total;
+        if (cum) {
+            same = 0;
+            for (uint32_t c = 0; c < C; ++c) {
+                const unsigned long long k = (c + 1 < C ? cum[(c + 1) * V] : n) - cum[c * V];
+                same += k * (k ? k - 1 : 0) / 2;
+            }
+            gates[PCL_GATE_T0_TOPO] += total - same;
+        }
         gates[0] += local[0];
-        gates[PCL_GATE_G1_AREA] += total - seen;
+        gates[PCL_GATE_G1_AREA] += same - seen;
         gates[PCL_GATE_G2_PROFILE] += local[PCL_GATE_G2_PROFILE];
         gates[PCL_GATE_G3_DENSITY] += local[PCL_GATE_G3_DENSITY];
     }
@@ -244,10 +270,12 @@ cudaError_t launch_area_sort(const uint32_t *pop, uint32_t n, uint32_t V, uint32
     return cudaGetLastError();
 }
 
-// workspace bytes for the band join of n clips under g
-size_t band_join_workspace(const Geo &g, uint32_t n) {
+// workspace bytes for the band join of n clips under g (topo: the
+// topological pre-screen's class keys as well)
+size_t band_join_workspace(const Geo &g, uint32_t n, bool topo) {
     const size_t V = (size_t)g.N * g.N + 2;  // areas 0..N^2, plus the end slot
-    return 4 * (2 * V + 2 * (size_t)n) + 8 * 16 + 64;
+    const size_t Vt = V * (topo ? kTopoClasses : 1);
+    return 4 * (2 * Vt + (topo ? 3 : 2) * (size_t)n) + 8 * 16 + 64;
 }
 
 // pairs i < j < n with (i + j) mod S = s: for each i, the j in (i, n) of one residue
@@ -269,36 +297,45 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     if (n_shards == 0 || shard >= n_shards) return cudaErrorInvalidValue;
     const Geo g = make_geo(prm);
     const uint32_t n = cs.n_clips;
-    if (ws_bytes < band_join_workspace(g, n)) return cudaErrorInvalidValue;
+    const bool topo = (prm.flags & PCL_P_TOPO_HASH) != 0;
+    if (topo && (n_shards != 1 || (n && !cs.esig))) return cudaErrorInvalidValue;
+    if (ws_bytes < band_join_workspace(g, n, topo)) return cudaErrorInvalidValue;
     const uint32_t V = (uint32_t)g.N * g.N + 2;
+    const uint32_t C = topo ? (uint32_t)kTopoClasses : 1u, Vt = V * C;
     char *w = static_cast<char *>(ws);
     unsigned long long *local = reinterpret_cast<unsigned long long *>(w);
     unsigned int *next_pos = reinterpret_cast<unsigned int *>(w + 8 * 16);
     uint32_t *cum = reinterpret_cast<uint32_t *>(w + 8 * 16 + 64);
-    uint32_t *fill = cum + V;
-    uint32_t *order = fill + V;
+    uint32_t *fill = cum + Vt;
+    uint32_t *order = fill + Vt;
     uint32_t *spop = order + n;
+    uint32_t *key = topo ? spop + n : nullptr;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(w, 0, 8 * 16 + 64 + 4 * (size_t)2 * V, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w, 0, 8 * 16 + 64 + 4 * (size_t)2 * Vt, st)) != cudaSuccess) return e;
     if (n == 0) {
-        finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, 0ull);
+        finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, 0ull, nullptr, V, 1, 0);
         return cudaGetLastError();
     }
-    hist_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum);
-    scan_kernel<<<1, 1024, 0, st>>>(cum, V);
-    scatter_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, n, cum, fill, order, spop);
+    const uint32_t *k = cs.pop;
+    if (topo) {
+        topo_key_kernel<<<num_sms * 4, 256, 0, st>>>(cs.pop, cs.esig, n, V, key);
+        k = key;
+    }
+    hist_kernel<<<num_sms * 4, 256, 0, st>>>(k, n, cum);
+    scan_kernel<<<1, 1024, 0, st>>>(cum, Vt);
+    scatter_kernel<<<num_sms * 4, 256, 0, st>>>(k, n, cum, fill, order, spop);
     const uint32_t vall = (uint32_t)g.N * g.N;
     switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
-        case 1: band_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
+        case 1: band_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
                                                                  local, next_pos, shard, n_shards); break;
-        case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
+        case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
                                                                  local, next_pos, shard, n_shards); break;
-        case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, vall, out, cap, count,
-                                                                   local, next_pos, shard, n_shards); break;
+        case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap,
+                                                                   count, local, next_pos, shard, n_shards); break;
         default: return cudaErrorInvalidValue;
     }
     const unsigned long long total = shard_pairs(n, shard, n_shards);
-    finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, total);
+    finish_gates_kernel<<<1, 32, 0, st>>>(local, gates, total, topo ? cum : nullptr, V, C, n);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@
 #include "ctx.h"
 
 namespace pcl {
-size_t band_join_workspace(const Geo &, uint32_t);
+size_t band_join_workspace(const Geo &, uint32_t, bool);
 cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
                              unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
 }  // namespace pcl
@@ -81,7 +81,12 @@ extern "C" pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_para
         ctx->err = "pcl_candidates_cosine_noalloc: cosine gates need S <= N/16";
         return PCL_ERR_UNSUPPORTED;
     }
-    const size_t need = pcl::band_join_workspace(g, cs->n_clips);
+    const bool topo = (P->flags & PCL_P_TOPO_HASH) != 0;
+    if (topo && cs->n_clips && !cs->esig) {
+        ctx->err = "pcl_candidates_cosine_noalloc: the topological pre-screen needs esig";
+        return PCL_ERR_INVALID;
+    }
+    const size_t need = pcl::band_join_workspace(g, cs->n_clips, topo);
     if (need > kScratchBytes) {
         ctx->err = "pcl_candidates_cosine_noalloc: " + std::to_string(cs->n_clips) + " clips of " +
                    std::to_string(g.N) + "^2 px need " + std::to_string(need) +

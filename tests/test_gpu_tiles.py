@@ -87,3 +87,21 @@ def test_candidates_and_records_across_edge_gate_bounds(ctx, torch_cuda, tol):
         assert int(o["pass_"].sum()) >= 48
         passing = {(int(a), int(b)) for a, b in allp[o["pass_"] > 0]}
         assert passing <= got
+
+
+@pytest.mark.parametrize("n", [33, 300, 1000])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_topological_prescreen_candidates_match_oracle(ctx, torch_cuda, n, mode):
+    """the lossy topological pre-screen (PCL_P_TOPO_HASH): candidate sets and
+    gate counts (T0 included) equal the oracle's screen with the same rule"""
+    import paper_2512_13133_gb300 as pcl
+    wl = _workload(n)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80, edge_tol_dbu=8, flags=pcl.P_TOPO_HASH)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    gp, gc = pcl.candidates(ctx, P, mode, cs)
+    op, oc = oracle.ClipSet(wl).candidates(mode, cos_num=80, edge_tol_dbu=8, topo=True)
+    got = set(map(tuple, gp.cpu().numpy().astype(np.int64).tolist()))
+    assert got == set(map(tuple, op.astype(np.int64).tolist()))
+    np.testing.assert_array_equal(gc[:7], oc[:7].astype(np.int64))
+    assert gc[:7].sum() == n * (n - 1) // 2

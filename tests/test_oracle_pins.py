@@ -706,3 +706,22 @@ def test_halo_windows_equal_numpy_slices_and_exact_argmax():
         assert r["score"] == best[3] and r["pad"] == best[4]
         assert r["pass_"] == int(best[3] > 0 and best[5] > Fraction(95 * 95, 100 * 100)
                                  or (pa == 0 and best[4] == 0))
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_COSINE, oracle.MODE_EDGE])
+def test_topological_prescreen_keeps_the_same_class_pairs_of_the_lossless_screen(small_wl, mode):
+    # the lossy pre-screen keeps exactly the lossless candidates whose clips
+    # have the same polygon count (saturated at 63), and counts every pair of
+    # different counts as its rejection (sum over classes of the pair counts)
+    sub = small_wl.subset(np.arange(400))
+    cs = oracle.ClipSet(sub)
+    cnt = np.minimum(np.diff(sub.rect_off.astype(np.int64)), 63)
+    full, fc = cs.candidates(mode, cos_num=80, edge_tol_dbu=8)
+    topo, tc = cs.candidates(mode, cos_num=80, edge_tol_dbu=8, topo=True)
+    keep = {(int(a), int(b)) for a, b in full.astype(np.int64) if cnt[a] == cnt[b]}
+    assert set(map(tuple, topo.astype(np.int64).tolist())) == keep
+    n = sub.n
+    same = sum(int(k) * (int(k) - 1) // 2 for k in np.bincount(cnt))
+    assert int(tc[oracle.GATE_T0_TOPO]) == n * (n - 1) // 2 - same
+    assert int(tc.sum()) == n * (n - 1) // 2
+    assert 0 < len(keep) < len(full)
