@@ -173,7 +173,7 @@ __device__ inline void screen_tile(uint32_t idx, uint32_t nbx, uint32_t &bx, uin
 // (the query x library screen of the serving loop; tiles numbered column
 // block after column block, row tile fastest); otherwise RS = CS and the
 // pairs i < j of the triangular tile numbering.
-template <bool P2, bool CROSS>
+template <bool P2, bool CROSS, bool TOPO = false>
 __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl_clipset RS, pcl_clipset CS,
                                                           pcl_pair *out, uint64_t cap,
                                                           unsigned long long *count,
@@ -235,7 +235,6 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     uint64_t *gcol = grids + (32 + warp) * kGS;  // this warp's current column grid
 
     uint32_t g_e1 = 0, g_e2 = 0, g_t0 = 0, kept = 0;
-    const bool topo = (prm.flags & PCL_P_TOPO_HASH) != 0;  // lossy pre-screen: equal polygon-count classes
     int qn = 0, fn = 0;  // queue lengths (warp-uniform)
     // grid-test state of this lane
     bool h2 = false;
@@ -346,7 +345,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
         bool sa = false;
         int s0x = 0, s0y = 0;
         if (CROSS ? i < nr : i < j) {
-            if (topo && topo_class(na) != topo_class(nb)) {
+            if (TOPO && topo_class(na) != topo_class(nb)) {  // lossy pre-screen: equal polygon-count classes
                 ++g_t0;
             } else if (na == 0 || nb == 0) {
                 if (na == 0 && nb == 0) both_empty = true;
@@ -431,7 +430,14 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
     if (tiles <= shard) return cudaSuccess;
     const unsigned grid = (unsigned)((tiles - shard + n_shards - 1) / n_shards);
     const int csz = prm.window_dbu / 64;
-    if ((csz & (csz - 1)) == 0)
+    const bool p2 = (csz & (csz - 1)) == 0, topo = (prm.flags & PCL_P_TOPO_HASH) != 0;
+    if (topo && p2)
+        edge_screen_kernel<true, false, true><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard,
+                                                                    n_shards);
+    else if (topo)
+        edge_screen_kernel<false, false, true><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard,
+                                                                     n_shards);
+    else if (p2)
         edge_screen_kernel<true, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
     else
         edge_screen_kernel<false, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
