@@ -68,6 +68,7 @@ def parse():
                     help="clips of each 64^2, 128^2 and 512^2 px library of the size-class serving measurement")
     ap.add_argument("--topo-clips", type=int, default=1_000_000,
                     help="clips of the topological pre-screen recall measurement (0: skip)")
+    ap.add_argument("--no-next", action="store_true", help="skip re-extraction, GPU surprisal and the coarse loop")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
                     help="same-seed pairs checked against the FP64 oracle per engine (0: skip)")
@@ -524,6 +525,85 @@ def run_topo(pcl, ctx, dev, clips: int, seed: int):
     return out
 
 
+def same_seed_pairs(wl) -> np.ndarray:
+    """all pairs (a < b) of clips derived from the same seed, sorted"""
+    lab = wl.label
+    order = np.argsort(lab, kind="stable")
+    ls = lab[order]
+    out = []
+    for s0 in np.flatnonzero(np.r_[True, ls[1:] != ls[:-1]]):
+        if ls[s0] < 0:
+            continue
+        grp = np.sort(order[s0:s0 + int(np.sum(ls == ls[s0]))])
+        i, j = np.triu_indices(len(grp), 1)
+        out.append(np.stack([grp[i], grp[j]], 1))
+    p = np.concatenate(out) if out else np.zeros((0, 2), np.int64)
+    return p[np.lexsort((p[:, 1], p[:, 0]))].astype(np.int32)
+
+
+def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
+    """The rows beyond the plain path, measured on the scale recipe:
+    re-extraction (the member's window moved at each shift, clips carrying a
+    halo of M) on the same-seed pairs of a 100,000-clip set with halo;
+    degrees / surprisal / first-step scores of a pass graph on the GPU; the
+    coarse-to-fine loop with a low-resolution coarse stage (pitch x 2,
+    relaxed thresholds) on the scale set."""
+    import torch
+
+    import synth
+    from paper_2512_13133_gb300 import loop
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(reps, 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    out = {}
+    # re-extraction
+    hw = synth.preset("scale", seed=seed + 400, n_clips=wl.n, halo_dbu=wl.marker_dbu)
+    Ph = pcl.params(hw.window_dbu, hw.pitch_dbu, hw.marker_dbu, COS_NUM, COS_DEN, TOL)
+    hcs = pcl.alloc_clipset(Ph, hw.rect_off, hw.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, Ph, hcs)
+    hb, nb = pcl.alloc_halo(Ph, hcs)
+    r_ms = timed(lambda: pcl.pcl_rasterize_halo(ctx, Ph, hcs, hb, nb), steps)
+    hp = torch.from_numpy(same_seed_pairs(hw)).to(dev)
+    hrec = torch.empty((hp.shape[0], 40), dtype=torch.uint8, device=dev)
+    m_ms = timed(lambda: pcl.pcl_match_halo(ctx, Ph, hcs, hcs, hb, nb, hp, hrec), steps)
+    hr = pcl.records_to_numpy(hrec)
+    K, NW = 2 * hcs.S + 1, hcs.N // 64
+    ops = 6.0 * K * K * hcs.N * NW  # per pair: funnel shift, AND, popcount, add over every shift and word
+    out["reextraction"] = {"clips": hw.n, "halo_dbu": hw.marker_dbu, "pairs": int(hp.shape[0]),
+                           "halo_raster_ms": r_ms, "match_ms": m_ms,
+                           "pairs_per_s": hp.shape[0] / (m_ms / 1e3), "passes": int(hr["pass_"].sum()),
+                           "roofline": {"bound": "alu", "achieved": hp.shape[0] * ops / (m_ms / 1e3) / 1e12,
+                                        "peak": alu_peak_tops(2070.0), "unit": "Tops/s",
+                                        "work": f"{ops:.3g} int ops per pair (6 per shift, row and word)"}}
+    out["reextraction"]["roofline"]["frac"] = out["reextraction"]["roofline"]["achieved"] / alu_peak_tops(2070.0)
+    del hcs, hb, nb, hp, hrec
+    # surprisal of a pass graph: 1,000,000 nodes, 16,000,000 random edges
+    rng = np.random.default_rng(seed)
+    n_nodes, n_edges = 1_000_000, 16_000_000
+    e = torch.from_numpy(rng.integers(0, n_nodes, size=(n_edges, 2)).astype(np.int32)).to(dev)
+    s_ms = timed(lambda: pcl.pcl_surprisal(ctx, e, n_nodes), steps)
+    out["surprisal"] = {"nodes": n_nodes, "edges": n_edges, "ms": s_ms, "edges_per_s": n_edges / (s_ms / 1e3)}
+    del e
+    # coarse-to-fine loop, coarse stage at half the resolution
+    t0 = time.perf_counter()
+    rep, ncl, rounds, info = loop.coarse_to_fine(ctx, P, cs, wl.rect_off, wl.rects, mode=pcl.MODE_COSINE)
+    out["coarse_to_fine_cosine"] = {"clips": wl.n, "coarse_pitch_dbu": 2 * wl.pitch_dbu, "clusters": ncl,
+                                    "rounds": rounds, "wall_s": time.perf_counter() - t0, **info}
+    torch.cuda.empty_cache()
+    return out
+
+
 def workload(config: str, seed: int, clips: int = 0):
     import synth
     if not clips:
@@ -932,6 +1012,15 @@ def run_ours(args, rank, world, local_rank):
         batched = run_batched(pcl, ctx, dev, args.batch_clips, args.steps)
         torch.cuda.synchronize()
 
+    # ---- the rows beyond the plain path (re-extraction, GPU surprisal,
+    # low-resolution coarse stage)
+    nxt = None
+    if not args.no_next and world == 1 and args.config == "scale":
+        pcl.pcl_rasterize(ctx, P, cs)
+        nxt = run_next(pcl, ctx, dev, wl, cs, P, args.steps, args.seed)
+        pcl.pcl_rasterize(ctx, P, cs)
+        torch.cuda.synchronize()
+
     # ---- the lossy topological pre-screen against the lossless screens
     topo = None
     if args.topo_clips and world == 1:
@@ -1060,6 +1149,7 @@ def run_ours(args, rank, world, local_rank):
         "serving_size_classes": serving_classes,
         "batched": batched,
         "topo_prescreen": topo,
+        "next": nxt,
     }
     # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
     # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2
