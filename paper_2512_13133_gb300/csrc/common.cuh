@@ -264,6 +264,31 @@ __device__ __forceinline__ unsigned long long shift_key(uint32_t c, int dx, int 
 
 // exact overlap c(dx, dy) = sum_x A(x) B(x - s) of two bit-packed rasters,
 // computed by one warp (lanes stride the rows); every lane gets the sum.
+// this thread's share of c(dx, dy) over the rows j0 + first, j0 + first +
+// step, ... (first in [0, step)): summed over all threads of a CTA (first =
+// thread index, step = thread count) it gives the exact overlap
+__device__ __forceinline__ uint32_t corr_rows_partial(const uint64_t *__restrict__ A,
+                                                      const uint64_t *__restrict__ B, int N, int nw,
+                                                      int dx, int dy, int first, int step) {
+    uint32_t acc = 0;
+    const int j0 = dy > 0 ? dy : 0, j1 = dy < 0 ? N + dy : N;
+    const int base0 = -dx;
+    const int wsh = base0 >= 0 ? base0 / 64 : -((-base0 + 63) / 64);
+    const int off = base0 - 64 * wsh;
+    for (int j = j0 + first; j < j1; j += step) {
+        const uint64_t *ra = A + (size_t)j * nw;
+        const uint64_t *rb = B + (size_t)(j - dy) * nw;
+        for (int w = 0; w < nw; ++w) {
+            const int wi = w + wsh;
+            const uint64_t lo = (wi >= 0 && wi < nw) ? rb[wi] : 0ull;
+            const uint64_t hi = (wi + 1 >= 0 && wi + 1 < nw) ? rb[wi + 1] : 0ull;
+            const uint64_t sh = off ? ((lo >> off) | (hi << (64 - off))) : lo;
+            acc += (uint32_t)__popcll(ra[w] & sh);
+        }
+    }
+    return acc;
+}
+
 __device__ __forceinline__ uint32_t warp_corr_exact(const uint64_t *__restrict__ A,
                                                     const uint64_t *__restrict__ B, int N, int nw,
                                                     int dx, int dy, int lane) {

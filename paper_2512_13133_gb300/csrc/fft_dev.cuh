@@ -49,9 +49,12 @@ struct PairSmem {
     static constexpr size_t tw = 0;                                          // L float2
     static constexpr size_t out1 = tw + sizeof(float2) * L;                  // [2][NO][LH] float2
     static constexpr size_t v2 = out1 + sizeof(float2) * 2 * NO * LH;        // [NO][9][P+1] float2
-    static constexpr size_t misc = v2 + sizeof(float2) * NO * 9 * (P + 1);   // keys [2][32] u64, flags [4]
-    static constexpr size_t bytes = misc + 2 * 32 * 8 + 4 * 4;
-    // surfaces reuse out1 once pass 2 has read it: [2][NO][NO] float
+    static constexpr size_t misc = v2 + sizeof(float2) * NO * 9 * (P + 1);   // keys [2][32] u64, flags [8]
+    static constexpr size_t two = misc + 2 * 32 * 8 + 8 * 4;                 // [9][NO] float2: pass-1 twiddles
+    static constexpr size_t bytes = two + sizeof(float2) * 9 * NO;
+    // pass 1's second half accumulates in v2 ([2][NO][LH] float2 fits its
+    // NO * 9 * (P + 1) entries: 2 LH = 9P + 2); surfaces reuse out1 once
+    // pass 2 has read it: [2][NO][NO] float
 };
 
 // One pair on the whole CTA.  gates_done: the caller has already checked the
@@ -73,10 +76,10 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
     float2 *out1 = reinterpret_cast<float2 *>(smem + SM::out1);
     float2 *v2 = reinterpret_cast<float2 *>(smem + SM::v2);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem + SM::misc);  // [2][32]
-    int *flags = reinterpret_cast<int *>(smem + SM::misc + 2 * 32 * 8);                 // [4]
+    int *flags = reinterpret_cast<int *>(smem + SM::misc + 2 * 32 * 8);                 // [8]
     float *surf = reinterpret_cast<float *>(smem + SM::out1);                           // [2][NO][NO]
 
-    if (threadIdx.x < 4) flags[threadIdx.x] = 0;
+    if (threadIdx.x < 8) flags[threadIdx.x] = 0;
     pcl_record rec{};
     rec.a = pr.a;
     rec.b = pr.b;
@@ -115,6 +118,13 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
     }
     build_twiddles(tw, L, +1);
     __syncthreads();
+    // pass-1 twiddles of output row o = dy + HW at step k2: w^(k2 n), n = dy mod L
+    float2 *two = reinterpret_cast<float2 *>(smem + SM::two);  // [9][NO]
+    for (int t = threadIdx.x; t < 9 * NO; t += blockDim.x) {
+        const int k2 = t / NO, dy = t % NO - HW;
+        two[t] = tw[(k2 * (dy >= 0 ? dy : L + dy)) % L];
+    }
+    __syncthreads();
 
     const float2 *fa = reinterpret_cast<const float2 *>(A.spec) + (size_t)pr.a * L * LS;
     const float2 *fb = reinterpret_cast<const float2 *>(B.spec) + (size_t)pr.b * L * LS;
@@ -122,46 +132,67 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
     const float thr2 = thr * thr;
     const bool want_pcm = !(prm.flags & PCL_P_NO_PCM);
 
-    // ---- pass 1: along ky, pruned to |dy| <= HW; warp task = (signal, chunk)
-    for (int task = warp; task < 2 * CHUNKS; task += nwarps) {
-        const int sig = task / CHUNKS;  // 0: phase correlation R, 1: correlation C
-        const int kx = (task % CHUNKS) * 32 + lane;
-        const bool valid = kx < LH;
-        if (sig == 0 && !want_pcm) {
-            if (valid)
-                for (int o = 0; o < NO; ++o) out1[(size_t)o * LH + kx] = make_float2(0.f, 0.f);
-            continue;
-        }
-        float2 acc[NO];
+    // ---- pass 1: along ky, pruned to |dy| <= HW.  Warp task = (column
+    // chunk, half of the k2 steps): the task loads both spectra of its 32
+    // columns once per step, forms C = F_A conj(F_B) and from it the phase-
+    // correlation R = C/|C|, and runs the P-point DFT of both; the NO outputs
+    // of each signal accumulate in shared memory (out1 for the first half of
+    // the k2 steps, v2 for the second, added after the pass), not in
+    // registers, so that the 2P loads of a step can all be in flight.
+    {
+        float2 *part = v2;  // [2][NO][LH] partial sums of the second half
+        constexpr int K2H = 5;  // first half: k2 = 0..4, second half: 5..8
+        for (int task = warp; task < 2 * CHUNKS; task += nwarps) {
+            const int half = task / CHUNKS;
+            const int kx = (task % CHUNKS) * 32 + lane;
+            const bool valid = kx < LH;
+            float2 *dst = (half ? part : out1) + kx;  // signal s, output o at dst[(s NO + o) LH]
+            const int kb = half ? K2H : 0, ke = half ? 9 : K2H;
+            if (!want_pcm && valid)
+                for (int o = 0; o < NO; ++o) dst[(size_t)o * LH] = make_float2(0.f, 0.f);
+            for (int k2 = kb; k2 < ke; ++k2) {
+                float2 c[P];
+                {
+                    float2 ra[P], rb[P];
 #pragma unroll
-        for (int o = 0; o < NO; ++o) acc[o] = make_float2(0.f, 0.f);
-        for (int k2 = 0; k2 < 9; ++k2) {
-            float2 v[P];
+                    for (int k1 = 0; k1 < P; ++k1) {
+                        const int ky = 9 * k1 + k2;
+                        ra[k1] = valid ? __ldg(fa + (size_t)ky * LS + kx) : make_float2(0.f, 0.f);
+                        rb[k1] = valid ? __ldg(fb + (size_t)ky * LS + kx) : make_float2(0.f, 0.f);
+                    }
 #pragma unroll
-            for (int k1 = 0; k1 < P; ++k1) {
-                const int ky = 9 * k1 + k2;
-                float2 c = make_float2(0.f, 0.f);
-                if (valid) c = cmulc(__ldg(fa + (size_t)ky * LS + kx), __ldg(fb + (size_t)ky * LS + kx));
-                if (sig == 0) {
-                    const float m2 = fmaf(c.x, c.x, c.y * c.y);
-                    c = (m2 > thr2) ? cscale(c, rsqrtf(m2)) : make_float2(0.f, 0.f);
+                    for (int k1 = 0; k1 < P; ++k1) c[k1] = cmulc(ra[k1], rb[k1]);
                 }
-                v[k1] = c;
-            }
-            dft_p<P, +1, RADIX>(v);
+                const float2 *w2 = two + k2 * NO;
 #pragma unroll
-            for (int o = 0; o < NO; ++o) {
-                const int dy = o - HW;
-                const int n = dy >= 0 ? dy : L + dy;
-                const int n1 = dy >= 0 ? dy : P + dy;
-                const float2 w = tw[(k2 * n) % L];
-                acc[o] = cadd(acc[o], cmul(v[n1], w));
+                for (int sig = 0; sig < 2; ++sig) {  // 0: phase correlation R, 1: correlation C
+                    if (sig == 0 && !want_pcm) continue;
+                    float2 v[P];
+#pragma unroll
+                    for (int k1 = 0; k1 < P; ++k1) {
+                        float2 x = c[k1];
+                        if (sig == 0) {
+                            const float m2 = fmaf(x.x, x.x, x.y * x.y);
+                            x = (m2 > thr2) ? cscale(x, rsqrtf(m2)) : make_float2(0.f, 0.f);
+                        }
+                        v[k1] = x;
+                    }
+                    dft_p<P, +1, RADIX>(v);
+                    if (valid) {
+                        float2 *d = dst + (size_t)sig * NO * LH;
+#pragma unroll
+                        for (int o = 0; o < NO; ++o) {
+                            const int dy = o - HW;
+                            const int n1 = dy >= 0 ? dy : P + dy;
+                            const float2 t = cmul(v[n1], w2[o]);
+                            d[(size_t)o * LH] = k2 == kb ? t : cadd(d[(size_t)o * LH], t);
+                        }
+                    }
+                }
             }
         }
-        if (valid) {
-#pragma unroll
-            for (int o = 0; o < NO; ++o) out1[((size_t)sig * NO + o) * LH + kx] = acc[o];
-        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * NO * LH; t += blockDim.x) out1[t] = cadd(out1[t], part[t]);
     }
     __syncthreads();
     // ---- pass 2 step 1: along kx (packed R + iC), DFT_P per (row, k2)
@@ -243,12 +274,16 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
     int gflag = flags[1];
     const uint64_t *ba = A.bits + (size_t)pr.a * N * NW;
     const uint64_t *bbits = B.bits + (size_t)pr.b * N * NW;
-    // popcount check of the chosen shift (warp 0), fall back on mismatch
+    // popcount check of the chosen shift (rows spread over the whole CTA),
+    // fall back on mismatch
     if (!gflag) {
-        if (warp == 0) {
-            const uint32_t ce = warp_corr_exact(ba, bbits, N, NW, sdx, sdy, lane);
-            if (lane == 0 && ce != cbest) flags[2] = 1;
-        }
+        if (threadIdx.x == 0) flags[4] = 0;
+        __syncthreads();
+        const uint32_t part = __reduce_add_sync(
+            0xffffffffu, corr_rows_partial(ba, bbits, N, NW, sdx, sdy, (int)threadIdx.x, (int)blockDim.x));
+        if (lane == 0) atomicAdd(flags + 4, (int)part);
+        __syncthreads();
+        if (threadIdx.x == 0 && (uint32_t)flags[4] != cbest) flags[2] = 1;
         __syncthreads();
         gflag = flags[2];
     }
