@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--topo-clips", type=int, default=1_000_000,
                     help="clips of the topological pre-screen recall measurement (0: skip)")
     ap.add_argument("--no-next", action="store_true", help="skip re-extraction, GPU surprisal and the coarse loop")
+    ap.add_argument("--only", default="", choices=["", "edge", "band", "fft", "tc"],
+                    help="time one stage alone with only its buffers (single-kernel profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
                     help="same-seed pairs checked against the FP64 oracle per engine (0: skip)")
@@ -867,6 +869,26 @@ def run_ours(args, rank, world, local_rank):
         reps = rngd.choice(wl.n, 4096, replace=False)
         dense = np.stack([np.repeat(reps, 32), rngd.integers(0, wl.n, 4096 * 32)], 1)
         dense = dense[dense[:, 0] != dense[:, 1]].astype(np.int32)
+        # the FFT engine on the dense list too (like for like with the tensor-core rows)
+        tdn = torch.from_numpy(np.ascontiguousarray(dense)).to(dev)
+        rdn = torch.empty((len(dense), 40), dtype=torch.uint8, device=dev)
+        pcl.pcl_match_pairs(ctx, Pn, pcl.MODE_COSINE, cs, cs, tdn, rdn)
+        torch.cuda.synchronize()
+        d_ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            pcl.pcl_match_pairs(ctx, Pn, pcl.MODE_COSINE, cs, cs, tdn, rdn)
+            a1.record()
+            torch.cuda.synchronize()
+            d_ms.append(a0.elapsed_time(a1))
+        dms = float(np.mean(d_ms))
+        fft["dense32"] = {"pairs": int(len(dense)), "ms": dms, "pairs_per_s": len(dense) / (dms / 1e3),
+                          "hbm_gbs_b_spectrum": len(dense) * spec_b / (dms / 1e3) / 1e9}
+        dense_fft = pcl.records_to_numpy(rdn)
+        del tdn, rdn
         tc = {}
         same_seed_recs = {"fft": recs}
         for eng_name, eng, peak_mult in (("f16", pcl.ENGINE_TC_DIRECT, 1.0), ("bf16", pcl.ENGINE_TC_DIRECT_BF16, 1.0),
@@ -895,7 +917,15 @@ def run_ours(args, rank, world, local_rank):
                            "tflops_useful": flop / (ms / 1e3) / 1e12,
                            "peak_tflops": pk["bf16_tflops"] * peak_mult,
                            "frac_of_peak": flop / (ms / 1e3) / 1e12 / (pk["bf16_tflops"] * peak_mult)}
+                if name == "dense32":
+                    rt = pcl.records_to_numpy(rl)
+                    tc[key]["agrees_with_fft"] = bool((rt["score"] == dense_fft["score"]).all() and
+                                                      (rt["dx_dbu"] == dense_fft["dx_dbu"]).all() and
+                                                      (rt["dy_dbu"] == dense_fft["dy_dbu"]).all() and
+                                                      (rt["pass_"] == dense_fft["pass_"]).all())
+                    tc[key]["speedup_vs_fft"] = fft["dense32"]["ms"] / ms
                 if name == "same_seed":
+                    tc[key]["speedup_vs_fft"] = fms / ms
                     rt = pcl.records_to_numpy(rl)
                     same_seed_recs[f"tc_{eng_name}"] = rt
                     tc[key]["agrees_with_fft"] = bool((rt["score"] == recs["score"]).all() and
@@ -1169,8 +1199,65 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_only(args):
+    """One stage alone on the workload, with only the device buffers it needs
+    (the command ncu captures of a single kernel run): edge screen, cosine
+    band join, FFT engine on the same-seed list, or the tensor-core engine
+    (FP16) on the dense 32-member list.  Prints one JSON line with the mean
+    CUDA-event time of the timed launches."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2512_13133_gb300 as pcl
+    dev = torch.device("cuda", 0)
+    wl = workload(args.config, args.seed, args.clips)
+    eng = pcl.ENGINE_TC_DIRECT if args.only == "tc" else pcl.ENGINE_FFT_PCM
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL, cos_engine=eng,
+                   flags=pcl.P_NO_GATES if args.only in ("fft", "tc") else 0)
+    ctx = pcl.Context(0)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=args.only == "fft")
+    pcl.pcl_rasterize(ctx, P, cs)
+    n = wl.n
+    if args.only in ("edge", "band"):
+        mode = pcl.MODE_EDGE if args.only == "edge" else pcl.MODE_COSINE
+        out = torch.empty((1 << 24, 2), dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        fn = lambda: pcl.pcl_candidates(ctx, P, mode, cs, out, cnt)  # noqa: E731
+        units, unit = n * (n - 1) // 2, "pairs screened"
+    else:
+        if args.only == "fft":
+            pcl.pcl_spectra(ctx, P, cs)
+            lst = same_seed_pairs(wl)
+        else:
+            rng = np.random.default_rng(5)
+            reps = rng.choice(n, min(4096, n), replace=False)
+            lst = np.stack([np.repeat(reps, 32), rng.integers(0, n, len(reps) * 32)], 1)
+            lst = lst[lst[:, 0] != lst[:, 1]].astype(np.int32)
+        tl = torch.from_numpy(np.ascontiguousarray(lst)).to(dev)
+        rec = torch.empty((len(lst), 40), dtype=torch.uint8, device=dev)
+        fn = lambda: pcl.pcl_match_pairs(ctx, P, pcl.MODE_COSINE, cs, cs, tl, rec)  # noqa: E731
+        units, unit = len(lst), "pairs aligned"
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"only": args.only, "clips": n, "units": units, "unit": unit, "ms": float(np.mean(ms)),
+                      "per_s": units / (float(np.mean(ms)) / 1e3)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.only:
+        run_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
