@@ -87,21 +87,34 @@ def peaks():
         return dict(PEAKS_FALLBACK), "fallback"
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels on the default
-# scale workload, from one single-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum; command and figures in profiles/dram_scale_100k.md).
-# A figure counts only while the kernel's sources hash as they did when it
-# was taken; otherwise the bench reports null.
+# DRAM bytes (read + write) per launch of the kernels on the default scale
+# workload, from single-pass ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum) of `bench.py --only edge|band` at 100,000 clips
+# (profiles/dram_scale_100k.md) and of `bench.py --only fft --clips 10000`
+# (profiles/pair_fft_10k.md; the FFT figure is per pair: every pair reads
+# its member's spectrum, so a launch's traffic grows with its pairs).  A
+# figure counts only while the kernel's sources hash as they did when it was
+# taken; otherwise the bench reports null.
 TRAFFIC = {
     "cand_edge": {"sources": {"paper_2512_13133_gb300/csrc/edge.cu":
-                              "26b5418aa595c4c3d96c8803ce9d091cfb7116d8349a568c364168b3be66500e",
+                              "75a598e7343c36e62c318632fa346bbed144ce683135a77d5b90c843656fe823",
                               "paper_2512_13133_gb300/csrc/edge_dev.cuh":
                               "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
-                  "bytes": 1.926e9 + 23.23e6},
+                  "bytes": 1.94e9 + 25.36e6},
+    "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
+                             "31db8bf47d4ba4f4836912a8085b092fe7ef91fd792c765a13d15a6bb4450bc3",
+                             "paper_2512_13133_gb300/csrc/gates.cuh":
+                             "adc2c8cb55cdf1852c51c72423a8c5db0fb50baece80cf4b0416d36c2b505b4f"},
+                 "bytes": 188.67e6 + 3.81e6},
+    "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
+                             "b7919a67fbe9b30e76edd15b5646077e4080a902be20489993918c3da4040fa3",
+                             "paper_2512_13133_gb300/csrc/fft_dev.cuh":
+                             "d21ce6c2098c71d27113a18fc3af9dca02fa6238d4679f830fc51ffc89fbbc77"},
+                 "bytes_per_pair": (21.164862e9 + 6.676224e6) / 56470},
 }
 
 
-def captured_traffic(stage: str, default_workload: bool):
+def captured_traffic(stage: str, default_workload: bool, pairs: int = 0):
     """per-launch DRAM bytes of a stage's kernel if the capture still applies"""
     import hashlib
     t = TRAFFIC.get(stage)
@@ -114,7 +127,7 @@ def captured_traffic(stage: str, default_workload: bool):
                     return None
         except OSError:
             return None
-    return t["bytes"]
+    return t["bytes_per_pair"] * pairs if "bytes_per_pair" in t else t["bytes"]
 
 
 def alu_peak_tops(sm_mhz: float) -> float:
@@ -1140,7 +1153,8 @@ def run_ours(args, rank, world, local_rank):
     band = int(g[0][0] + g[0][2] + g[0][3])
     rooflines["cand_cos"] = frac({"bound": "alu", "achieved": band * 4 * nb * nb / (per_stage["cand_cos"] / 1e3) / 1e12,
                                   "peak": alu_peak_tops(2070.0), "unit": "Tops/s",
-                                  "work": f"{band} band pairs (G1 survivors) x 4 nb^2 integer ops (G3 both ways)"})
+                                  "work": f"{band} band pairs (G1 survivors) x 4 nb^2 integer ops (G3 both ways)",
+                                  "traffic": captured_traffic("cand_cos", args.config == "scale" and not args.clips)})
     if dom == "cand_edge":
         rooflines["cand_edge"] = dict(roof)
     if fft:
@@ -1148,7 +1162,9 @@ def run_ours(args, rank, world, local_rank):
         rooflines["fft_pair"] = frac({"bound": "hbm", "achieved": fft["hbm_gbs_b_spectrum"], "peak": pk["hbm_gbs"],
                                       "unit": "GB/s",
                                       "work": f"B's spectrum per pair ({L * Ls * 8} B; A's from L2, the list sorted by "
-                                              f"representative), {fft['pairs']} same-seed pairs"})
+                                              f"representative), {fft['pairs']} same-seed pairs",
+                                      "traffic": captured_traffic("fft_pair", args.config == "scale" and not args.clips,
+                                                                  fft["pairs"])})
         tcd = fft.get("tc_engine", {})
         for key in ("f16_dense32", "bf16_dense32", "f16_same_seed", "bf16_same_seed"):
             if key in tcd:
