@@ -187,19 +187,29 @@ __global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl
 #pragma unroll
             for (int u = 0; u < DXC; ++u) cnt[u] = 0;
             for (int y = lane; y < N; y += 32) {
+                // A's row and the halo row into registers once (RW = NW + 2
+                // words for 1 <= S <= 32, NW + 1 for S = 0)
                 const uint64_t *ra = sa + (size_t)y * NW;
                 const uint64_t *rh = sh + (size_t)(y - dy + S) * RW;
+                uint64_t a[NW], h[NW + 2];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) a[w] = ra[w];
+#pragma unroll
+                for (int k = 0; k < NW + 2; ++k) h[k] = k < RW ? rh[k] : 0ull;
 #pragma unroll
                 for (int u = 0; u < DXC; ++u) {
                     const int dx = dx0 + u;
                     if (dx > S) break;
+                    // halo bits [64 w + S - dx, +64) line up with A's word w;
+                    // S - dx is in [0, 64], so they start in word w or w + 1
+                    const int sd = S - dx, qs = sd & 63;
+                    const bool up = sd >= 64;
                     uint32_t sum = 0;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) {
-                        // halo bits [64 w + S - dx, +64) line up with A's word w
-                        const int q = 64 * w + S - dx, qi = q >> 6, qs = q & 63;
-                        const uint64_t v = qs ? (rh[qi] >> qs) | (rh[qi + 1] << (64 - qs)) : rh[qi];
-                        sum += (uint32_t)__popcll(ra[w] & v);
+                        const uint64_t lo = up ? h[w + 1] : h[w], hi = up ? h[w + 2] : h[w + 1];
+                        const uint64_t v = qs ? (lo >> qs) | (hi << (64 - qs)) : lo;
+                        sum += (uint32_t)__popcll(a[w] & v);
                     }
                     cnt[u] += sum;
                 }
