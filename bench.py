@@ -479,7 +479,7 @@ def run_batched(pcl, ctx, dev, clips_per_class: int, steps: int, seed: int = 1):
             "cosine_pairs": n_cos, "aligned": aligned, "unsupported": unsupported,
             "ms_eager": eager_ms, "ms_graph": graph_ms, "pairs_per_s": len(pairs) / (best_ms / 1e3),
             "aligned_per_s": aligned / (best_ms / 1e3),
-            "tuning": {"fft_radix": int(tune.fft_radix), "ctas_per_sm": int(tune.ctas_per_sm),
+            "tuning": {"fft_radix": int(tune.fft_radix), "items_per_warp": int(tune.items_per_warp),
                        "candidates_ms": tinfo.get("ms")}}
 
 

@@ -419,10 +419,13 @@ typedef struct pcl_work {
 
 /* Launch parameters picked by the autotuner: fft_radix 2 or 4 (register DFT
    of the FFT engine), ctas_per_sm (persistent CTAs per SM, 0 = as many as
-   fit). */
+   fit), items_per_warp (cosine items each warp claims and gates per round,
+   1..64, 0 = 16: a CTA's round aligns the survivors of its 10 warps' claims,
+   so this sets the pairs per CTA per round). */
 typedef struct pcl_tuning {
     uint32_t fft_radix;
     uint32_t ctas_per_sm;
+    uint32_t items_per_warp;
 } pcl_tuning;
 
 /* One record per work item, in list order, for n_classes (1..4) size classes

@@ -103,7 +103,7 @@ class _Pair(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("fft_radix", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+    _fields_ = [("fft_radix", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("items_per_warp", ctypes.c_uint32)]
 
 
 WORK_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("cls", "<u2"), ("mode", "<u2")])

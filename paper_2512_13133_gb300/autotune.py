@@ -1,7 +1,10 @@
 """Autotuner for the mixed-batch launch: picks the register DFT radix of the
-FFT engine (2 or 4) and the persistent CTAs per SM by timing the candidates
+FFT engine (2 or 4) and the cosine items each warp claims per round (8, 16
+32 or 64: the pairs a CTA gates and aligns per round) by timing the candidates
 on the batch itself, and remembers the choice in a JSON cache keyed by the
-batch's size classes (raster side N, shift half-range S) and mode mix.
+batch's size classes (raster side N, shift half-range S) and mode mix.  The
+launch's shared memory fits one persistent CTA per SM, so CTAs per SM are
+left at "as many as fit".
 
 The cache lives next to the built library (``_lib/autotune.json``), so it is
 per machine and per build.
@@ -14,7 +17,7 @@ import os
 from . import Tuning, _build, pcl_match_mixed
 
 CACHE = os.path.join(_build.OUTDIR, "autotune.json")
-CANDIDATES = [(2, 1), (4, 1), (2, 2), (4, 2)]
+CANDIDATES = [(radix, items) for radix in (2, 4) for items in (8, 16, 32, 64)]
 
 
 def _key(params_list, n_cosine: int, n: int) -> str:
@@ -45,14 +48,14 @@ def tune_mixed(ctx, params_list, sets, work, n_cosine: int, out_rec, reps: int =
     measurements (ms).  ``reset`` (optional callable) restores state that a
     launch changes (e.g. the spectra cache) before each timed launch."""
     import torch
-    key = _key(params_list, n_cosine, int(work.shape[0]))
+    key = _key(params_list, n_cosine, int(work.shape[0])) + "|items"
     cache = load_cache()
     if not force and key in cache:
         c = cache[key]
-        return Tuning(c["fft_radix"], c["ctas_per_sm"]), c
+        return Tuning(c["fft_radix"], 0, c["items_per_warp"]), c
     times = {}
-    for radix, ctas in CANDIDATES:
-        t = Tuning(radix, ctas)
+    for radix, items in CANDIDATES:
+        t = Tuning(radix, 0, items)
         best = None
         for _ in range(reps):
             if reset:
@@ -65,9 +68,9 @@ def tune_mixed(ctx, params_list, sets, work, n_cosine: int, out_rec, reps: int =
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
-        times[f"r{radix}c{ctas}"] = best
-    radix, ctas = min(CANDIDATES, key=lambda rc: times[f"r{rc[0]}c{rc[1]}"])
-    entry = {"fft_radix": radix, "ctas_per_sm": ctas, "ms": times}
+        times[f"r{radix}i{items}"] = best
+    radix, items = min(CANDIDATES, key=lambda rc: times[f"r{rc[0]}i{rc[1]}"])
+    entry = {"fft_radix": radix, "items_per_warp": items, "ms": times}
     cache[key] = entry
     save_cache(cache)
-    return Tuning(radix, ctas), entry
+    return Tuning(radix, 0, items), entry

@@ -43,7 +43,7 @@ cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset
 cudaError_t launch_xysep(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                          const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_mixed(const pcl_params *, const pcl_clipset *, uint32_t, const pcl_work *, uint64_t, uint64_t,
-                         pcl_record *, unsigned long long *, uint32_t, uint32_t, int, cudaStream_t);
+                         pcl_record *, unsigned long long *, uint32_t, uint32_t, uint32_t, int, cudaStream_t);
 }  // namespace pcl
 
 #include "ctx.h"
@@ -358,9 +358,11 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
     }
     const uint32_t radix = tune && tune->fft_radix == 4 ? 4 : 2;
     const uint32_t ctas = tune ? tune->ctas_per_sm : 0;
+    const uint32_t ipw = tune ? tune->items_per_warp : 0;
+    if (ipw > 64) return fail(ctx, PCL_ERR_INVALID, "pcl_match_mixed: items_per_warp above 64%s%lld");
     if ((s = ensure_ws(ctx, 256))) return s;
     const cudaError_t e = launch_mixed(params, sets, n_classes, d_work, n_cosine, n, d_out,
-                                       static_cast<unsigned long long *>(ctx->ws), radix, ctas, ctx->num_sms,
+                                       static_cast<unsigned long long *>(ctx->ws), radix, ctas, ipw, ctx->num_sms,
                                        (cudaStream_t)stream);
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "mixed batch");
 }

@@ -25,7 +25,7 @@ using namespace edge_dev;
 constexpr int kMaxClasses = 4;
 constexpr int kThreads = 320;  // ten warps: the pass-1 tasks of P = 32
 constexpr int kWarps = kThreads / 32;
-constexpr int kClaim = 16;     // cosine items a warp claims per round
+constexpr int kClaimMax = 64;  // cosine items a warp claims per round, at most (a tuning parameter)
 
 struct MixedArgs {
     pcl_params prm[kMaxClasses];
@@ -48,17 +48,17 @@ __global__ void mark_mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t
 template <int RADIX>
 __global__ void __launch_bounds__(kThreads, 1)
     mixed_kernel(MixedArgs args, const pcl_work *work, uint64_t n_cos, uint64_t n, pcl_record *out,
-                 unsigned long long *cursor) {
-    __shared__ uint64_t surv[kWarps * kClaim];
+                 unsigned long long *cursor, int claim) {
+    __shared__ uint64_t surv[kWarps * kClaimMax];
     __shared__ int n_surv, exhausted;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // while gating, the alignment bodies' shared memory is free: each warp
     // takes a slice of it for the G2 profiles
     extern __shared__ __align__(16) unsigned char mixed_sm[];
     uint16_t *g2_scratch = reinterpret_cast<uint16_t *>(mixed_sm);
-    // ---- cosine items, in rounds: every warp claims kClaim consecutive items
+    // ---- cosine items, in rounds: every warp claims `claim` consecutive items
     // and gates them one after the other (the gate cost varies a lot between
-    // items, so a round evens it out over kClaim items); the survivors of the
+    // items, so a round evens it out over `claim` items); the survivors of the
     // round are then aligned one after the other by the whole CTA
     for (;;) {
         if (threadIdx.x == 0) {
@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncthreads();
         uint64_t t0 = 0;
-        if (lane == 0) t0 = atomicAdd(cursor, (unsigned long long)kClaim);
+        if (lane == 0) t0 = atomicAdd(cursor, (unsigned long long)claim);
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= n_cos && lane == 0) exhausted = 1;
-        for (uint64_t t = t0; t < t0 + kClaim && t < n_cos; ++t) {
+        for (uint64_t t = t0; t < t0 + (uint64_t)claim && t < n_cos; ++t) {
             const pcl_work w = work[t];
             pcl_record rec{};
             rec.a = w.a;
@@ -168,8 +168,10 @@ cudaError_t launch_spectra(const pcl_params &, const pcl_clipset &, const uint32
 
 cudaError_t launch_mixed(const pcl_params *prm, const pcl_clipset *sets, uint32_t n_classes, const pcl_work *work,
                          uint64_t n_cos, uint64_t n, pcl_record *out, unsigned long long *cursor, uint32_t radix,
-                         uint32_t ctas_per_sm, int num_sms, cudaStream_t st) {
+                         uint32_t ctas_per_sm, uint32_t items_per_warp, int num_sms, cudaStream_t st) {
     if (n_classes == 0 || n_classes > kMaxClasses) return cudaErrorInvalidValue;
+    const int claim = items_per_warp == 0 ? 16 : (int)items_per_warp;
+    if (claim > kClaimMax) return cudaErrorInvalidValue;
     MixedArgs args{};
     args.n_classes = n_classes;
     for (uint32_t c = 0; c < n_classes; ++c) {
@@ -199,8 +201,8 @@ cudaError_t launch_mixed(const pcl_params *prm, const pcl_clipset *sets, uint32_
     const int ctas = (ctas_per_sm == 0 || (int)ctas_per_sm > per_sm) ? per_sm : (int)ctas_per_sm;
     const unsigned grid = (unsigned)(num_sms * ctas);
     if (n == 0) return cudaSuccess;
-    if (radix == 4) mixed_kernel<4><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor);
-    else mixed_kernel<2><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor);
+    if (radix == 4) mixed_kernel<4><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor, claim);
+    else mixed_kernel<2><<<grid, kThreads, sm, st>>>(args, work, n_cos, n, out, cursor, claim);
     return cudaGetLastError();
 }
 

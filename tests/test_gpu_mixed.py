@@ -44,20 +44,22 @@ def batch(torch_cuda):
     return dict(pcl=pcl, wls=wls, pairs=pairs, modes=modes, ctx=ctx, Ps=Ps, sets=sets, tw=tw, n_cos=n_cos)
 
 
-def _run_mixed(b, radix, torch):
+def _run_mixed(b, radix, torch, items=0):
     pcl = b["pcl"]
     out = torch.empty((b["tw"].shape[0], 40), dtype=torch.uint8, device="cuda")
-    pcl.pcl_match_mixed(b["ctx"], b["Ps"], b["sets"], b["tw"], b["n_cos"], out, pcl.Tuning(radix, 0))
+    pcl.pcl_match_mixed(b["ctx"], b["Ps"], b["sets"], b["tw"], b["n_cos"], out, pcl.Tuning(radix, 0, items))
     return pcl.records_to_numpy(out)
 
 
 EXACT = ["a", "b", "dx_dbu", "dy_dbu", "score", "pass_", "mode"]
 
 
-@pytest.mark.parametrize("radix", [2, 4])
-def test_mixed_equals_per_class_entry_points(batch, torch_cuda, radix):
+@pytest.mark.parametrize("radix,items", [(2, 0), (4, 0), (2, 8), (4, 32), (2, 64), (2, 1)])
+def test_mixed_equals_per_class_entry_points(batch, torch_cuda, radix, items):
+    """every tuning (register DFT radix, cosine items per warp per round)
+    gives the per-class entry points' records"""
     pcl = batch["pcl"]
-    g = _run_mixed(batch, radix, torch_cuda)
+    g = _run_mixed(batch, radix, torch_cuda, items)
     pairs, modes = batch["pairs"], batch["modes"]
     for k, wl in enumerate(batch["wls"]):
         for mode in (1, 2):
