@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--topo-clips", type=int, default=1_000_000,
                     help="clips of the topological pre-screen recall measurement (0: skip)")
     ap.add_argument("--no-next", action="store_true", help="skip re-extraction, GPU surprisal and the coarse loop")
-    ap.add_argument("--only", default="", choices=["", "edge", "band", "fft", "tc"],
+    ap.add_argument("--only", default="", choices=["", "edge", "band", "fft", "tc", "exact", "halo"],
                     help="time one stage alone with only its buffers (single-kernel profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
@@ -272,7 +272,7 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
         queue, done, nxt = [], {}, 0
         arr = {}
         lat, pairs, clips, bad = [], 0, 0, 0
-        lat_cls = {}
+        lat_cls, work_cls = {}, {}
         n_total = len(arrivals) if arrivals is not None else None
         deadline = t0 + int(seconds * 1e9)
         rid = 0
@@ -296,6 +296,9 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
             for c in srv.poll():
                 lat.append((c["t_done_ns"] - arr[c["id"]]) / 1e6)
                 lat_cls.setdefault(c["size_class"], []).append(lat[-1])
+                wk = work_cls.setdefault(c["size_class"], [0, 0])
+                wk[0] += c["n_candidates"]
+                wk[1] += c["n_queries"]
                 pairs += c["n_candidates"]
                 clips += c["n_queries"]
                 bad += c["status"] != 0  # candidate capacity exceeded (or a device wait ran out)
@@ -312,7 +315,9 @@ def run_serving(pcl, ctx, P, cs, wl, seconds: float = 2.0, mode: int = 1, cand_p
                    p99_ms=float(np.percentile(lat, 99)) if lat else None)
         if len(wls) > 1:
             out["per_class"] = {f"{wls[k].raster_n}px": {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
-                                                         "p99_ms": float(np.percentile(v, 99))}
+                                                         "p99_ms": float(np.percentile(v, 99)),
+                                                         "candidates_per_query_clip":
+                                                             work_cls[k][0] / max(work_cls[k][1], 1)}
                                 for k, v in sorted(lat_cls.items())}
         return out
 
@@ -562,7 +567,8 @@ def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
     halo of M) on the same-seed pairs of a 100,000-clip set with halo;
     degrees / surprisal / first-step scores of a pass graph on the GPU; the
     coarse-to-fine loop with a low-resolution coarse stage (pitch x 2,
-    relaxed thresholds) on the scale set."""
+    relaxed thresholds) on the scale set; and the exact window scan that
+    aligns 512^2 rasters."""
     import torch
 
     import synth
@@ -582,6 +588,25 @@ def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
         return float(np.mean(ms))
 
     out = {}
+    # 512^2 rasters: the exact window scan (S = 32) on the same-seed pairs of
+    # a 10,000-clip set of the scale recipe at that size, gates off
+    w5 = exact512_workload(seed, 10_000)
+    P5 = pcl.params(w5.window_dbu, w5.pitch_dbu, w5.marker_dbu, COS_NUM, COS_DEN, TOL, flags=pcl.P_NO_GATES)
+    cs5 = pcl.alloc_clipset(P5, w5.rect_off, w5.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P5, cs5)
+    p5 = torch.from_numpy(same_seed_pairs(w5)).to(dev)
+    rec5 = torch.empty((p5.shape[0], 40), dtype=torch.uint8, device=dev)
+    e_ms = timed(lambda: pcl.pcl_match_pairs(ctx, P5, pcl.MODE_COSINE, cs5, cs5, p5, rec5), steps)
+    K5, NW5 = 2 * cs5.S + 1, cs5.N // 64
+    ops5 = 6.0 * K5 * K5 * cs5.N * NW5
+    ach5 = p5.shape[0] * ops5 / (e_ms / 1e3) / 1e12
+    out["exact_scan_512"] = {"clips": w5.n, "pairs": int(p5.shape[0]), "ms": e_ms,
+                             "pairs_per_s": p5.shape[0] / (e_ms / 1e3),
+                             "passes": int(pcl.records_to_numpy(rec5)["pass_"].sum()),
+                             "roofline": {"bound": "alu", "achieved": ach5, "peak": alu_peak_tops(2070.0),
+                                          "unit": "Tops/s", "frac": ach5 / alu_peak_tops(2070.0),
+                                          "work": f"{ops5:.3g} int ops per pair (6 per shift, row and 64-bit word)"}}
+    del cs5, p5, rec5
     # re-extraction
     hw = synth.preset("scale", seed=seed + 400, n_clips=wl.n, halo_dbu=wl.marker_dbu)
     Ph = pcl.params(hw.window_dbu, hw.pitch_dbu, hw.marker_dbu, COS_NUM, COS_DEN, TOL)
@@ -619,14 +644,21 @@ def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
     return out
 
 
-def workload(config: str, seed: int, clips: int = 0):
+def exact512_workload(seed: int, clips: int):
+    """the scale recipe at 512^2 px (W = 2048 dbu, M = 128 dbu: S = 32)"""
+    import synth
+    return synth.generate(seed + 712, n_clips=clips, n_seeds=max(1, clips // 20), n_copies=7 * clips // 10,
+                          window_dbu=2048, margin_dbu=128, min_rects=5, max_rects=40)
+
+
+def workload(config: str, seed: int, clips: int = 0, **kw):
     import synth
     if not clips:
-        return synth.preset(config, seed=seed)
+        return synth.preset(config, seed=seed, **kw)
     base = synth.PRESETS[config]
     f = clips / base["n_clips"]
     return synth.preset(config, seed=seed, n_clips=clips, n_seeds=max(1, int(base["n_seeds"] * f)),
-                        n_copies=int(base["n_copies"] * f))
+                        n_copies=int(base["n_copies"] * f), **kw)
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -1218,19 +1250,27 @@ def run_ours(args, rank, world, local_rank):
 def run_only(args):
     """One stage alone on the workload, with only the device buffers it needs
     (the command ncu captures of a single kernel run): edge screen, cosine
-    band join, FFT engine on the same-seed list, or the tensor-core engine
-    (FP16) on the dense 32-member list.  Prints one JSON line with the mean
-    CUDA-event time of the timed launches."""
+    band join, FFT engine on the same-seed list, the tensor-core engine
+    (FP16) on the dense 32-member list, the exact window scan of 512^2
+    rasters on the same-seed list of a 10,000-clip set (gates off), or
+    re-extraction on the same-seed list of a set with halo.  Prints one JSON
+    line with the mean CUDA-event time of the timed launches."""
     import torch
 
     import __graft_entry__ as ge
     ge.build()
+    import synth
     import paper_2512_13133_gb300 as pcl
     dev = torch.device("cuda", 0)
-    wl = workload(args.config, args.seed, args.clips)
+    if args.only == "exact":
+        wl = exact512_workload(args.seed, args.clips or 10_000)
+    elif args.only == "halo":
+        wl = workload(args.config, args.seed + 400, args.clips, halo_dbu=synth.PRESETS[args.config]["margin_dbu"])
+    else:
+        wl = workload(args.config, args.seed, args.clips)
     eng = pcl.ENGINE_TC_DIRECT if args.only == "tc" else pcl.ENGINE_FFT_PCM
     P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL, cos_engine=eng,
-                   flags=pcl.P_NO_GATES if args.only in ("fft", "tc") else 0)
+                   flags=pcl.P_NO_GATES if args.only in ("fft", "tc", "exact") else 0)
     ctx = pcl.Context(0)
     cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=args.only == "fft")
     pcl.pcl_rasterize(ctx, P, cs)
@@ -1245,6 +1285,8 @@ def run_only(args):
         if args.only == "fft":
             pcl.pcl_spectra(ctx, P, cs)
             lst = same_seed_pairs(wl)
+        elif args.only in ("exact", "halo"):
+            lst = same_seed_pairs(wl)
         else:
             rng = np.random.default_rng(5)
             reps = rng.choice(n, min(4096, n), replace=False)
@@ -1252,7 +1294,12 @@ def run_only(args):
             lst = lst[lst[:, 0] != lst[:, 1]].astype(np.int32)
         tl = torch.from_numpy(np.ascontiguousarray(lst)).to(dev)
         rec = torch.empty((len(lst), 40), dtype=torch.uint8, device=dev)
-        fn = lambda: pcl.pcl_match_pairs(ctx, P, pcl.MODE_COSINE, cs, cs, tl, rec)  # noqa: E731
+        if args.only == "halo":
+            hb, nb = pcl.alloc_halo(P, cs)
+            pcl.pcl_rasterize_halo(ctx, P, cs, hb, nb)
+            fn = lambda: pcl.pcl_match_halo(ctx, P, cs, cs, hb, nb, tl, rec)  # noqa: E731
+        else:
+            fn = lambda: pcl.pcl_match_pairs(ctx, P, pcl.MODE_COSINE, cs, cs, tl, rec)  # noqa: E731
         units, unit = len(lst), "pairs aligned"
     for _ in range(args.warmup):
         fn()
@@ -1265,8 +1312,11 @@ def run_only(args):
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(json.dumps({"only": args.only, "clips": n, "units": units, "unit": unit, "ms": float(np.mean(ms)),
-                      "per_s": units / (float(np.mean(ms)) / 1e3)}), flush=True)
+    line = {"only": args.only, "clips": n, "units": units, "unit": unit, "ms": float(np.mean(ms)),
+            "per_s": units / (float(np.mean(ms)) / 1e3)}
+    if args.only in ("edge", "band"):
+        line["candidates"] = int(cnt.item())
+    print(json.dumps(line), flush=True)
 
 
 def main():

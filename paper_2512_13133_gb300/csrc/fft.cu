@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(32 * 2 * ((9 * P / 2 + 1 + 31) / 32), 1)
 // iteration, persistent grid.
 constexpr int kExactThreads = 320;
 
-__global__ void __launch_bounds__(kExactThreads, 1)
+__global__ void __launch_bounds__(kExactThreads, 2)
     exact_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, uint64_t npairs,
                       const unsigned long long *d_n, pcl_record *out) {
     if (d_n && *d_n < npairs) npairs = *d_n;

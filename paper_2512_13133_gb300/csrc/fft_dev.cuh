@@ -344,70 +344,78 @@ __device__ __forceinline__ void pair_body(const pcl_params &prm, const pcl_clips
 
 // Exact window scan for rasters the FFT body does not cover (N = 64 NW, here
 // 512²): c(s) = sum_x A(x) B(x - s) counted with AND + popcount for every shift
-// |dx|, |dy| <= S (S <= SMAX) -- the definition itself, so the record is the
-// oracle's.  Both rasters are staged in shared memory (2 N²/8 bytes); warps take
-// (dy, 8 consecutive dx), lanes take row pairs (A row y, B row y - dy) and
-// count the 8 shifts of a row pair from registers.  No phase-correlation surface is formed (pcm fields 0).  Meant
-// for the few pairs that pass the lossless gates.  The caller has checked the
-// indices, emptiness and gates.
+// |dx|, |dy| <= S (S <= SMAX <= 32) -- the definition itself, so the record is
+// the oracle's.  Both rasters are staged in shared memory (2 N²/8 bytes).  Warps
+// take (dy, 8 consecutive dx starting at a multiple of 8); lanes take row pairs
+// (A row y, B row y - dy) as 32-bit words and count the 8 shifts of a row pair
+// from registers, one funnel shift per word and shift: B's row moved by
+// dx = 32 q + r is word w - q funnel-shifted by r with word w - q - 1, and q is
+// the same for the 8 shifts of a task because the chunk starts at a multiple
+// of 8.  No phase-correlation surface is formed (pcm fields 0).  The caller has
+// checked the indices, emptiness and gates.
+template <int NW32, int Q>
+__device__ __forceinline__ void exact_row_counts(const uint32_t (&a)[NW32], const uint32_t (&bp)[NW32 + 3], int rb,
+                                                 uint32_t (&cnt)[8]) {
+    // bp[i] = B's word i - 2 (zero outside the row); B moved by 32 Q + r has
+    // word w = funnel(b[w - Q - 1], b[w - Q], r) = funnel(bp[w + 1 - Q], bp[w + 2 - Q], r)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int r = rb + u;  // 0..31
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < NW32; ++w) sum += (uint32_t)__popc(a[w] & __funnelshift_l(bp[w + 1 - Q], bp[w + 2 - Q], r));
+        cnt[u] += sum;
+    }
+}
+
 template <int NW, int SMAX>
 __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
                                            const pcl_pair pr, pcl_record *dst) {
-    constexpr int N = 64 * NW;
+    static_assert(SMAX <= 32, "shift words: q in {-1, 0, 1}");
+    constexpr int N = 64 * NW, NW32 = 2 * NW, NV = NW32 / 4;  // 32-bit words and 16-byte vectors per row
     const Geo g = make_geo(prm);
     const int S = g.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *sa = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *sb = sa + N * NW;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * NW);  // [32]
-    const uint64_t *ga = A.bits + (size_t)pr.a * N * NW, *gb = B.bits + (size_t)pr.b * N * NW;
+    uint4 *sa = reinterpret_cast<uint4 *>(smem);
+    uint4 *sb = sa + N * NV;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * NV);  // [32]
+    const uint4 *ga = reinterpret_cast<const uint4 *>(A.bits + (size_t)pr.a * N * NW);
+    const uint4 *gb = reinterpret_cast<const uint4 *>(B.bits + (size_t)pr.b * N * NW);
     __syncthreads();  // the shared memory may still be read by the previous item
-    for (int t = threadIdx.x; t < N * NW; t += blockDim.x) {
+    for (int t = threadIdx.x; t < N * NV; t += blockDim.x) {
         sa[t] = __ldg(ga + t);
         sb[t] = __ldg(gb + t);
     }
     __syncthreads();
     unsigned long long best = 0ull;
-    // (dy, chunk of 8 dx) per warp task; lanes take the row pairs and count the
-    // chunk's 8 shifts from registers
-    constexpr int DXC = 8;
-    const int K = 2 * S + 1, nch = (K + DXC - 1) / DXC;
+    // dx chunks [8 c, 8 c + 7] for c = floor(-S / 8) .. floor(S / 8)
+    const int K = 2 * S + 1, c0 = -((S + 7) / 8), nch = S / 8 - c0 + 1;
     for (int task = warp; task < K * nch; task += nwarps) {
-        const int dy = task / nch - S, dx0 = (task % nch) * DXC - S;
-        uint32_t cnt[DXC];
+        const int dy = task / nch - S, dx0 = (c0 + task % nch) * 8;  // -32 <= dx0 <= 32
+        const int q = (dx0 + 32) / 32 - 1, rb = dx0 - 32 * q;        // dx0 = 32 q + rb, rb in {0, 8, 16, 24}
+        uint32_t cnt[8];
 #pragma unroll
-        for (int u = 0; u < DXC; ++u) cnt[u] = 0;
+        for (int u = 0; u < 8; ++u) cnt[u] = 0;
         const int j0 = dy > 0 ? dy : 0, j1 = dy < 0 ? N + dy : N;
         for (int j = j0 + lane; j < j1; j += 32) {
-            uint64_t a[NW], b[NW + 2];  // b[w + 1] = word w of B's row j - dy
-            b[0] = 0ull;
-            b[NW + 1] = 0ull;
+            uint32_t a[NW32], bp[NW32 + 3];
+            bp[0] = bp[1] = bp[NW32 + 2] = 0u;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                a[w] = sa[j * NW + w];
-                b[w + 1] = sb[(j - dy) * NW + w];
+            for (int v = 0; v < NV; ++v) {
+                const uint4 x = sa[j * NV + v], y = sb[(j - dy) * NV + v];
+                a[4 * v] = x.x, a[4 * v + 1] = x.y, a[4 * v + 2] = x.z, a[4 * v + 3] = x.w;
+                bp[4 * v + 2] = y.x, bp[4 * v + 3] = y.y, bp[4 * v + 4] = y.z, bp[4 * v + 5] = y.w;
             }
-#pragma unroll
-            for (int u = 0; u < DXC; ++u) {
-                const int dx = dx0 + u;  // B's pixel x - dx lands on A's pixel x (|dx| <= S < 64)
-                uint32_t sum = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    uint64_t sh;
-                    if (dx > 0) sh = (b[w + 1] << dx) | (b[w] >> (64 - dx));
-                    else if (dx < 0) sh = (b[w + 1] >> (-dx)) | (b[w + 2] << (64 + dx));
-                    else sh = b[w + 1];
-                    sum += (uint32_t)__popcll(a[w] & sh);
-                }
-                cnt[u] += sum;
-            }
+            if (q < 0) exact_row_counts<NW32, -1>(a, bp, rb, cnt);
+            else if (q == 0) exact_row_counts<NW32, 0>(a, bp, rb, cnt);
+            else exact_row_counts<NW32, 1>(a, bp, rb, cnt);
         }
 #pragma unroll
-        for (int u = 0; u < DXC; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const int dx = dx0 + u;
             const uint32_t c = __reduce_add_sync(0xffffffffu, cnt[u]);
-            if (dx <= S) {
+            if (dx >= -S && dx <= S) {
                 const unsigned long long k = shift_key(c, dx, dy, S);
                 best = k > best ? k : best;
             }

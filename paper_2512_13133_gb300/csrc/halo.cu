@@ -95,6 +95,21 @@ __global__ void __launch_bounds__(kThreads) halo_raster_kernel(pcl_params prm, p
     }
 }
 
+// c for 8 shifts of one row pair: A's 32-bit word w against halo bits
+// [32 (w + QQ) + r, +32), r = rb + u
+template <int NW32, int QQ>
+__device__ __forceinline__ void halo_row_counts(const uint32_t (&a)[NW32], const uint32_t (&h)[NW32 + 4], int rb,
+                                                uint32_t (&cnt)[8]) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int r = rb + u;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < NW32; ++w) sum += (uint32_t)__popc(a[w] & __funnelshift_r(h[w + QQ], h[w + QQ + 1], r));
+        cnt[u] += sum;
+    }
+}
+
 // sim(c1, n1) > sim(c2, n2), with |A| = pa common to both
 __device__ __forceinline__ int sim_cmp(uint32_t c1, uint32_t n1, uint32_t c2, uint32_t n2, uint64_t pa) {
     uint64_t a1, d1, a2, d2;
@@ -177,48 +192,45 @@ __global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl
         __syncthreads();
         const uint64_t pa = A.pop[pr.a];
         Best best{0, 0, 0, 0, false};
-        // warp task: (dy, 8 consecutive dx); lanes take rows y and count the
-        // 8 shifts from registers
-        constexpr int DXC = 8;
-        const int nch = (K + DXC - 1) / DXC;
+        // warp task: (dy, 8 consecutive sd = S - dx starting at a multiple of
+        // 8); lanes take rows y and count the 8 shifts from registers as
+        // 32-bit words: A's word w lines up with halo bits [32 w + sd, +32),
+        // which start in halo word w + sd / 32, the same word for the 8
+        // shifts of a task
+        const int nch = (2 * S) / 8 + 1;
         for (int task = warp; task < K * nch; task += nwarps) {
-            const int dy = task / nch - S, dx0 = (task % nch) * DXC - S;
-            uint32_t cnt[DXC];
+            const int dy = task / nch - S, sd0 = (task % nch) * 8;
+            const int qq = sd0 >> 5, rb = sd0 & 31;  // sd = 32 qq + rb + u, rb + u <= 31
+            uint32_t cnt[8];
 #pragma unroll
-            for (int u = 0; u < DXC; ++u) cnt[u] = 0;
+            for (int u = 0; u < 8; ++u) cnt[u] = 0;
             for (int y = lane; y < N; y += 32) {
                 // A's row and the halo row into registers once (RW = NW + 2
                 // words for 1 <= S <= 32, NW + 1 for S = 0)
                 const uint64_t *ra = sa + (size_t)y * NW;
                 const uint64_t *rh = sh + (size_t)(y - dy + S) * RW;
-                uint64_t a[NW], h[NW + 2];
+                uint32_t a[2 * NW], h[2 * NW + 4];
 #pragma unroll
-                for (int w = 0; w < NW; ++w) a[w] = ra[w];
-#pragma unroll
-                for (int k = 0; k < NW + 2; ++k) h[k] = k < RW ? rh[k] : 0ull;
-#pragma unroll
-                for (int u = 0; u < DXC; ++u) {
-                    const int dx = dx0 + u;
-                    if (dx > S) break;
-                    // halo bits [64 w + S - dx, +64) line up with A's word w;
-                    // S - dx is in [0, 64], so they start in word w or w + 1
-                    const int sd = S - dx, qs = sd & 63;
-                    const bool up = sd >= 64;
-                    uint32_t sum = 0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        const uint64_t lo = up ? h[w + 1] : h[w], hi = up ? h[w + 2] : h[w + 1];
-                        const uint64_t v = qs ? (lo >> qs) | (hi << (64 - qs)) : lo;
-                        sum += (uint32_t)__popcll(a[w] & v);
-                    }
-                    cnt[u] += sum;
+                for (int w = 0; w < NW; ++w) {
+                    const uint64_t v = ra[w];
+                    a[2 * w] = (uint32_t)v;
+                    a[2 * w + 1] = (uint32_t)(v >> 32);
                 }
+#pragma unroll
+                for (int k = 0; k < NW + 2; ++k) {
+                    const uint64_t v = k < RW ? rh[k] : 0ull;
+                    h[2 * k] = (uint32_t)v;
+                    h[2 * k + 1] = (uint32_t)(v >> 32);
+                }
+                if (qq == 0) halo_row_counts<2 * NW, 0>(a, h, rb, cnt);
+                else if (qq == 1) halo_row_counts<2 * NW, 1>(a, h, rb, cnt);
+                else halo_row_counts<2 * NW, 2>(a, h, rb, cnt);
             }
 #pragma unroll
-            for (int u = 0; u < DXC; ++u) {
-                const int dx = dx0 + u;
+            for (int u = 0; u < 8; ++u) {
+                const int sd = sd0 + u, dx = S - sd;
                 const uint32_t c = __reduce_add_sync(0xffffffffu, cnt[u]);
-                if (dx <= S) {
+                if (sd <= 2 * S) {
                     const Best cand{c, sn[(dy + S) * K + dx + S], dx, dy, true};
                     if (before(cand, best, pa)) best = cand;
                 }

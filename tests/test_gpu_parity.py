@@ -300,3 +300,33 @@ def test_cosine_512_exact_scan_matches_oracle(ctx, torch_cuda, gates):
         np.testing.assert_array_equal(g[f][al], o[f][al])
     np.testing.assert_array_equal(g["score"][al].astype(np.int64), o["score"][al])
     assert np.abs(g["sim"][al].astype(np.float64) - o["sim"][al]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("M", [4, 52, 100])
+def test_cosine_512_exact_scan_other_markers(ctx, torch_cuda, M):
+    """512² exact window scan at markers whose shift range S = M / p is not a
+    multiple of 8 (1, 13, 25 px): the dx chunks start at multiples of 8 and the
+    shifts outside the window are dropped; records equal the oracle's."""
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.generate(21, n_clips=40, n_seeds=6, n_copies=28, window_dbu=2048, margin_dbu=128,
+                        min_rects=5, max_rects=40)
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, M, cos_num=80, flags=pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    rng = np.random.default_rng(M)
+    lab = wl.label
+    same = np.array([(i, j) for i in range(wl.n) for j in range(wl.n) if i != j and lab[i] >= 0 and lab[i] == lab[j]])
+    pairs = np.concatenate([same[rng.choice(len(same), min(10, len(same)), replace=False)],
+                            rng.integers(0, wl.n, size=(4, 2)), [[3, 3]]]).astype(np.int64)
+    tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
+    g = pcl.records_to_numpy(pcl.match(ctx, P, pcl.MODE_COSINE, cs, cs, tp))
+    o = oracle.ClipSet(wl, marker_dbu=M).match(pairs, oracle.MODE_COSINE, use_gates=False, cos_num=80)
+    al = (o["flags"] & oracle.F_ALIGNED) > 0
+    assert al.sum() >= 10
+    assert np.abs(o["dx_dbu"][al]).max() <= M and np.abs(o["dy_dbu"][al]).max() <= M
+    np.testing.assert_array_equal(g["flags"] & 15, o["flags"] & 15)
+    np.testing.assert_array_equal(g["pass_"], o["pass_"])
+    for f in ("dx_dbu", "dy_dbu"):
+        np.testing.assert_array_equal(g[f][al], o[f][al])
+    np.testing.assert_array_equal(g["score"][al].astype(np.int64), o["score"][al])
+    assert np.abs(g["sim"][al].astype(np.float64) - o["sim"][al]).max() <= 1e-5
