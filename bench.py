@@ -107,10 +107,10 @@ TRAFFIC = {
                              "adc2c8cb55cdf1852c51c72423a8c5db0fb50baece80cf4b0416d36c2b505b4f"},
                  "bytes": 188.67e6 + 3.81e6},
     "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
-                             "b7919a67fbe9b30e76edd15b5646077e4080a902be20489993918c3da4040fa3",
+                             "6c6ce5615f6c402501f1e80cd10a1ffd5aff917c0e1f4532fb8fd46b90b7a3fa",
                              "paper_2512_13133_gb300/csrc/fft_dev.cuh":
-                             "d21ce6c2098c71d27113a18fc3af9dca02fa6238d4679f830fc51ffc89fbbc77"},
-                 "bytes_per_pair": (21.164862e9 + 6.676224e6) / 56470},
+                             "ca1d5f0ece6d2e027523f3670de2c95b26f1b59b303a044168b7b3b5edb999b5"},
+                 "bytes_per_pair": (21.09e9 + 6.04e6) / 56470},
 }
 
 
@@ -133,6 +133,23 @@ def captured_traffic(stage: str, default_workload: bool, pairs: int = 0):
 def alu_peak_tops(sm_mhz: float) -> float:
     # 152 SMs x 128 INT32/FP32 lanes per SM per clock
     return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
+def popc_peak_t(sm_mhz: float) -> float:
+    # 152 SMs x 16 population counts per SM per clock (a quarter of the
+    # 64-lane integer pipe)
+    return 152 * 16 * sm_mhz * 1e6 / 1e12
+
+
+def popc_bound(pairs: int, ms: float, K: int, N: int) -> dict:
+    """Popcount view of a window scan: by definition (2S+1)^2 N N/32 popcounts
+    of 32-bit words per pair; the carry-save sums issue 11 per 16 words, so
+    this is an effective rate."""
+    per = K * K * N * N / 32
+    ach = pairs * per / (ms / 1e3) / 1e12
+    return {"achieved": ach, "peak": popc_peak_t(2070.0), "unit": "T popc/s", "frac": ach / popc_peak_t(2070.0),
+            "work": f"{per:.3g} 32-bit popcounts per pair by definition",
+            "peak_source": "derived: 152 SMs x 16 popcounts x 2.07 GHz"}
 
 
 class Clocks:
@@ -605,7 +622,8 @@ def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
                              "passes": int(pcl.records_to_numpy(rec5)["pass_"].sum()),
                              "roofline": {"bound": "alu", "achieved": ach5, "peak": alu_peak_tops(2070.0),
                                           "unit": "Tops/s", "frac": ach5 / alu_peak_tops(2070.0),
-                                          "work": f"{ops5:.3g} int ops per pair (6 per shift, row and 64-bit word)"}}
+                                          "work": f"{ops5:.3g} int ops per pair (6 per shift, row and 64-bit word)"},
+                             "popc_bound": popc_bound(int(p5.shape[0]), e_ms, K5, cs5.N)}
     del cs5, p5, rec5
     # re-extraction
     hw = synth.preset("scale", seed=seed + 400, n_clips=wl.n, halo_dbu=wl.marker_dbu)
@@ -627,6 +645,7 @@ def run_next(pcl, ctx, dev, wl, cs, P, steps: int, seed: int):
                                         "peak": alu_peak_tops(2070.0), "unit": "Tops/s",
                                         "work": f"{ops:.3g} int ops per pair (6 per shift, row and word)"}}
     out["reextraction"]["roofline"]["frac"] = out["reextraction"]["roofline"]["achieved"] / alu_peak_tops(2070.0)
+    out["reextraction"]["popc_bound"] = popc_bound(int(hp.shape[0]), m_ms, K, hcs.N)
     del hcs, hb, nb, hp, hrec
     # surprisal of a pass graph: 1,000,000 nodes, 16,000,000 random edges
     rng = np.random.default_rng(seed)

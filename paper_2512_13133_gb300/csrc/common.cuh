@@ -329,4 +329,21 @@ __device__ __forceinline__ bool cos_exceeds(uint64_t c, uint64_t pa, uint64_t pb
     return lh > rh || (lh == rh && ll > rl);
 }
 
+// sum of the popcounts of n words with fewer popcounts: per bit position a
+// full adder gives x + y + z = (x ^ y ^ z) + 2 maj(x, y, z), so three words
+// cost two popcounts and two logic operations.  Population counts issue at a
+// quarter of the integer rate, so this balances the two pipes.
+template <int n>
+__device__ __forceinline__ uint32_t popc_sum(const uint32_t (&x)[n]) {
+    uint32_t s1 = 0, s2 = 0;
+#pragma unroll
+    for (int w = 0; w + 2 < n; w += 3) {
+        s1 += (uint32_t)__popc(x[w] ^ x[w + 1] ^ x[w + 2]);
+        s2 += (uint32_t)__popc((x[w] & x[w + 1]) | (x[w + 2] & (x[w] ^ x[w + 1])));
+    }
+#pragma unroll
+    for (int w = n / 3 * 3; w < n; ++w) s1 += (uint32_t)__popc(x[w]);
+    return s1 + 2u * s2;
+}
+
 }  // namespace pcl

@@ -361,10 +361,10 @@ __device__ __forceinline__ void exact_row_counts(const uint32_t (&a)[NW32], cons
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int r = rb + u;  // 0..31
-        uint32_t sum = 0;
+        uint32_t x[NW32];
 #pragma unroll
-        for (int w = 0; w < NW32; ++w) sum += (uint32_t)__popc(a[w] & __funnelshift_l(bp[w + 1 - Q], bp[w + 2 - Q], r));
-        cnt[u] += sum;
+        for (int w = 0; w < NW32; ++w) x[w] = a[w] & __funnelshift_l(bp[w + 1 - Q], bp[w + 2 - Q], r);
+        cnt[u] += popc_sum<NW32>(x);
     }
 }
 
@@ -373,19 +373,23 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
                                            const pcl_pair pr, pcl_record *dst) {
     static_assert(SMAX <= 32, "shift words: q in {-1, 0, 1}");
     constexpr int N = 64 * NW, NW32 = 2 * NW, NV = NW32 / 4;  // 32-bit words and 16-byte vectors per row
+    // row stride in shared memory: NV + 1 vectors (odd), so that the 8 lanes of
+    // a quarter-warp reading 8 consecutive rows hit 8 different bank groups
+    constexpr int SV = NV + 1;
     const Geo g = make_geo(prm);
     const int S = g.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     uint4 *sa = reinterpret_cast<uint4 *>(smem);
-    uint4 *sb = sa + N * NV;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * NV);  // [32]
+    uint4 *sb = sa + N * SV;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * SV);  // [32]
     const uint4 *ga = reinterpret_cast<const uint4 *>(A.bits + (size_t)pr.a * N * NW);
     const uint4 *gb = reinterpret_cast<const uint4 *>(B.bits + (size_t)pr.b * N * NW);
     __syncthreads();  // the shared memory may still be read by the previous item
     for (int t = threadIdx.x; t < N * NV; t += blockDim.x) {
-        sa[t] = __ldg(ga + t);
-        sb[t] = __ldg(gb + t);
+        const int st = (t / NV) * SV + t % NV;
+        sa[st] = __ldg(ga + t);
+        sb[st] = __ldg(gb + t);
     }
     __syncthreads();
     unsigned long long best = 0ull;
@@ -403,7 +407,7 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
             bp[0] = bp[1] = bp[NW32 + 2] = 0u;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const uint4 x = sa[j * NV + v], y = sb[(j - dy) * NV + v];
+                const uint4 x = sa[j * SV + v], y = sb[(j - dy) * SV + v];
                 a[4 * v] = x.x, a[4 * v + 1] = x.y, a[4 * v + 2] = x.z, a[4 * v + 3] = x.w;
                 bp[4 * v + 2] = y.x, bp[4 * v + 3] = y.y, bp[4 * v + 4] = y.z, bp[4 * v + 5] = y.w;
             }
@@ -453,7 +457,7 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
 
 // shared memory of exact_body
 template <int NW>
-constexpr size_t exact_smem() { return 2 * sizeof(uint64_t) * 64 * NW * NW + 32 * 8; }
+constexpr size_t exact_smem() { return 2 * 16 * 64 * NW * (NW / 2 + 1) + 32 * 8; }
 
 }  // namespace fft_dev
 }  // namespace pcl

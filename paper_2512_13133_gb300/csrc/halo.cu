@@ -33,6 +33,12 @@ constexpr int kThreads = 256;
 __host__ __device__ inline int halo_side(int N, int S) { return N + 2 * S; }
 __host__ __device__ inline int halo_words(int N, int S) { return (N + 2 * S + 63) / 64; }
 
+// shared-memory row strides in 64-bit words, odd so that the 16 lanes of a
+// half-warp reading 16 consecutive rows hit 16 different bank pairs: A's rows
+// (NW words) and the halo rows (NWH words and a zero word)
+__host__ __device__ inline int a_stride(int NW) { return NW | 1; }
+__host__ __device__ inline int h_stride(int NWH) { return (NWH + 1) | 1; }
+
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
 
@@ -103,10 +109,10 @@ __device__ __forceinline__ void halo_row_counts(const uint32_t (&a)[NW32], const
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int r = rb + u;
-        uint32_t sum = 0;
+        uint32_t x[NW32];
 #pragma unroll
-        for (int w = 0; w < NW32; ++w) sum += (uint32_t)__popc(a[w] & __funnelshift_r(h[w + QQ], h[w + QQ + 1], r));
-        cnt[u] += sum;
+        for (int w = 0; w < NW32; ++w) x[w] = a[w] & __funnelshift_r(h[w + QQ], h[w + QQ + 1], r);
+        cnt[u] += pcl::popc_sum<NW32>(x);
     }
 }
 
@@ -151,7 +157,7 @@ __device__ __forceinline__ bool before(const Best &b1, const Best &b2, uint64_t 
 
 // one CTA per pair (CTAs stride the list)
 template <int NW>
-__global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
+__global__ void __launch_bounds__(kThreads, NW >= 8 ? 2 : 4) halo_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B,
                                                              const uint64_t *__restrict__ hbits,
                                                              const uint32_t *__restrict__ norms, const pcl_pair *pairs,
                                                              uint64_t npairs, const unsigned long long *d_n,
@@ -159,11 +165,12 @@ __global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl
     constexpr int N = 64 * NW;
     const Geo g = make_geo(prm);
     const int S = g.S, NH = halo_side(N, S), NWH = halo_words(N, S), K = 2 * S + 1, KK = K * K;
-    const int RW = NWH + 1;  // halo row words in shared memory, one zero word of padding
+    const int RW = NWH + 1;  // halo row words read: NWH and one zero word of padding
+    const int SA = a_stride(NW), SH = h_stride(NWH);  // row strides in shared memory
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *sa = reinterpret_cast<uint64_t *>(smem);          // [N][NW]
-    uint64_t *sh = sa + (size_t)N * NW;                         // [NH][RW]
-    uint32_t *sn = reinterpret_cast<uint32_t *>(sh + (size_t)NH * RW);  // [K*K]
+    uint64_t *sa = reinterpret_cast<uint64_t *>(smem);          // [N][SA]
+    uint64_t *sh = sa + (size_t)N * SA;                         // [NH][SH]
+    uint32_t *sn = reinterpret_cast<uint32_t *>(sh + (size_t)NH * SH);  // [K*K]
     Best *wb = reinterpret_cast<Best *>(sn + ((KK + 3) & ~3));  // [warps]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (d_n && *d_n < npairs) npairs = *d_n;
@@ -183,10 +190,10 @@ __global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl
         __syncthreads();  // the previous pair's buffers are no longer read
         const uint64_t *ga = A.bits + (size_t)pr.a * N * NW;
         const uint64_t *gh = hbits + (size_t)pr.b * NH * NWH;
-        for (int t = threadIdx.x; t < N * NW; t += blockDim.x) sa[t] = __ldg(ga + t);
+        for (int t = threadIdx.x; t < N * NW; t += blockDim.x) sa[(t / NW) * SA + t % NW] = __ldg(ga + t);
         for (int t = threadIdx.x; t < NH * RW; t += blockDim.x) {
             const int row = t / RW, k = t % RW;
-            sh[t] = k < NWH ? __ldg(gh + (size_t)row * NWH + k) : 0ull;
+            sh[row * SH + k] = k < NWH ? __ldg(gh + (size_t)row * NWH + k) : 0ull;
         }
         for (int t = threadIdx.x; t < KK; t += blockDim.x) sn[t] = __ldg(norms + (size_t)pr.b * KK + t);
         __syncthreads();
@@ -207,8 +214,8 @@ __global__ void __launch_bounds__(kThreads) halo_pair_kernel(pcl_params prm, pcl
             for (int y = lane; y < N; y += 32) {
                 // A's row and the halo row into registers once (RW = NW + 2
                 // words for 1 <= S <= 32, NW + 1 for S = 0)
-                const uint64_t *ra = sa + (size_t)y * NW;
-                const uint64_t *rh = sh + (size_t)(y - dy + S) * RW;
+                const uint64_t *ra = sa + (size_t)y * SA;
+                const uint64_t *rh = sh + (size_t)(y - dy + S) * SH;
                 uint32_t a[2 * NW], h[2 * NW + 4];
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
@@ -275,7 +282,7 @@ size_t raster_smem(const Geo &g) {
 
 size_t pair_smem(const Geo &g) {
     const int NH = halo_side(g.N, g.S), NWH = halo_words(g.N, g.S), K = 2 * g.S + 1;
-    return 8ull * g.N * g.nw + 8ull * NH * (NWH + 1) + 4ull * (((size_t)K * K + 3) & ~size_t(3)) +
+    return 8ull * g.N * a_stride(g.nw) + 8ull * NH * h_stride(NWH) + 4ull * (((size_t)K * K + 3) & ~size_t(3)) +
            sizeof(Best) * (kThreads / 32);
 }
 

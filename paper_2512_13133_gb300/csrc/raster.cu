@@ -30,26 +30,43 @@ __device__ __forceinline__ int cell_of(int v, int csz) {
     return q < 0 ? 0 : (q > 63 ? 63 : q);
 }
 
-__device__ __forceinline__ int ceil_div_i(long long a, long long b) {  // b > 0
+// first pixel index i (clamped to [0, N]) whose centre p i + p/2 is >= v:
+// ceil((2 v - p) / (2 p)), the pixel-centre rule of a rectangle edge at v
+__device__ __forceinline__ int pix_from(int v, long long p, int N) {
+    const long long a = 2LL * v - p, b = 2 * p;
     long long q = a / b;
     if (a % b != 0 && a > 0) ++q;
-    return (int)q;
+    return (int)(q < 0 ? 0 : (q > N ? N : q));
+}
+
+// 32 x 32 bit transpose across a warp: on entry lane l holds row l (bit b =
+// column b), on return lane l holds column l (bit b = row b).  Five rounds of
+// exchanging the off-diagonal halves of 2s x 2s blocks with lane l ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2 ? 0x33333333u : 0x55555555u;  // bit positions b with (b & s) == 0
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
 }
 
 template <int NW>
 __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset cs) {
+    constexpr int NR = 64 * NW;  // rows (N = 64 NW: 64^2 .. 512^2)
     const Geo g = make_geo(prm);
     const int c = blockIdx.x;
     const int j = threadIdx.x;  // row (y index)
     const int N = g.N;
-    __shared__ int4 rs[kRectChunk];
-    __shared__ uint64_t rows[512 * NW];
+    __shared__ int4 rs[kRectChunk];          // pixel ranges {i0, i1, j0, j1} of staged rectangles
+    __shared__ uint64_t rows[NR * NW];
+    __shared__ uint8_t colpart[NR / 32][NR];  // column counts over each warp's 32 rows
     __shared__ uint32_t red[32];
 
     const uint32_t r0 = cs.rect_off[c], r1 = cs.rect_off[c + 1];
     const long long p = g.p;
-    // pixel centre of row j in doubled coordinates: 2 p j + p
-    const long long Y2 = 2 * p * j + p;
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
@@ -57,18 +74,18 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
     for (uint32_t base = r0; base < r1; base += kRectChunk) {
         const uint32_t cnt = min((uint32_t)kRectChunk, r1 - base);
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x)
-            rs[t] = reinterpret_cast<const int4 *>(cs.rects)[base + t];
+        // pixel (i, j) is set when x0 <= p i + p/2 < x1 and y0 <= p j + p/2 < y1
+        // (doubled: 2 x0 <= 2 p i + p < 2 x1): columns [i0, i1), rows [j0, j1)
+        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int4 q = reinterpret_cast<const int4 *>(cs.rects)[base + t];
+            rs[t] = make_int4(pix_from(q.x, p, N), pix_from(q.z, p, N), pix_from(q.y, p, N), pix_from(q.w, p, N));
+        }
         __syncthreads();
         if (j < N) {
             for (uint32_t t = 0; t < cnt; ++t) {
                 const int4 q = rs[t];
-                if (!(2LL * q.y <= Y2 && Y2 < 2LL * q.w)) continue;
-                // columns i with 2 x0 <= 2 p i + p < 2 x1
-                int i0 = ceil_div_i(2LL * q.x - p, 2 * p);
-                int i1 = ceil_div_i(2LL * q.z - p, 2 * p);
-                i0 = max(i0, 0);
-                i1 = min(i1, N);
+                if (!(q.z <= j && j < q.w)) continue;
+                const int i0 = q.x, i1 = q.y;
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
                     const int lo = max(i0, 64 * k), hi = min(i1, 64 * k + 64);
@@ -101,13 +118,22 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
         for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) s += red[k];
         cs.pop[c] = s;
     }
-    // column counts: thread i counts bit i over all rows
+    // column counts: each warp transposes its 32 rows in 32-column chunks
+    // (lane l then holds column l of the chunk) and counts them; the warps'
+    // partial counts are summed per column (blockDim = N, a multiple of 32)
+    {
+        const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+#pragma unroll
+        for (int h = 0; h < 2 * NW; ++h) {
+            const uint32_t x = (h & 1) ? (uint32_t)(w[h >> 1] >> 32) : (uint32_t)w[h >> 1];
+            colpart[wr][32 * h + lane] = (uint8_t)__popc(warp_transpose32(x, lane));
+        }
+    }
+    __syncthreads();
     if (j < N) {
-        const int i = j;
-        const int k = i >> 6, b = i & 63;
         uint32_t q = 0;
-        for (int jj = 0; jj < N; ++jj) q += (uint32_t)((rows[jj * NW + k] >> b) & 1ull);
-        cs.prof[(size_t)c * 2 * N + N + i] = (uint16_t)q;
+        for (int wr = 0; wr < N / 32; ++wr) q += colpart[wr][j];
+        cs.prof[(size_t)c * 2 * N + N + j] = (uint16_t)q;
     }
     // 16x16 block counts, then neighbourhood sums, each stored in the order of
     // blk_pos: blocks spread over the whole clip come first, so the gates'
@@ -169,20 +195,22 @@ __global__ void __launch_bounds__(512) raster_kernel(pcl_params prm, pcl_clipset
     // 64 x 64 occupancy grid (cell side W/64): a cell is marked when it holds an
     // integer point of some rectangle's interior, so two rectangles that
     // overlap with positive area always share a marked cell
+    // (one thread per rectangle ORs its cells into the grid rows it spans)
     const int csz = g.W / 64;
     const int4 *r4 = reinterpret_cast<const int4 *>(cs.rects);
-    for (int cy = threadIdx.x; cy < 64; cy += blockDim.x) {
-        uint64_t m = 0ull;
-        for (uint32_t t = r0; t < r1; ++t) {
-            const int4 q = r4[t];
-            if (q.z <= q.x || q.w <= q.y) continue;
-            const int y0 = cell_of(q.y, csz), y1 = cell_of(q.w - 1, csz);
-            if (cy < y0 || cy > y1) continue;
-            const int x0 = cell_of(q.x, csz), x1 = cell_of(q.z - 1, csz);
-            m |= (~0ull >> (63 - (x1 - x0))) << x0;
-        }
-        cs.occ[(size_t)c * 64 + cy] = m;
+    __shared__ unsigned long long occ_s[64];
+    for (int cy = threadIdx.x; cy < 64; cy += blockDim.x) occ_s[cy] = 0ull;
+    __syncthreads();
+    for (uint32_t t = r0 + threadIdx.x; t < r1; t += blockDim.x) {
+        const int4 q = r4[t];
+        if (q.z <= q.x || q.w <= q.y) continue;
+        const int y0 = cell_of(q.y, csz), y1 = cell_of(q.w - 1, csz);
+        const int x0 = cell_of(q.x, csz), x1 = cell_of(q.z - 1, csz);
+        const unsigned long long m = (~0ull >> (63 - (x1 - x0))) << x0;
+        for (int cy = y0; cy <= y1; ++cy) atomicOr(&occ_s[cy], m);
     }
+    __syncthreads();
+    for (int cy = threadIdx.x; cy < 64; cy += blockDim.x) cs.occ[(size_t)c * 64 + cy] = occ_s[cy];
     // rectangles by ascending area (ties by index): rank by counting
     const uint32_t nr = r1 - r0;
     for (uint32_t t = threadIdx.x; t < nr; t += blockDim.x) {

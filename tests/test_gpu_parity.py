@@ -57,7 +57,7 @@ def _edge_case_workload(W=512, M=32):
     return synth.from_lists(clips, W, 4, M)
 
 
-@pytest.mark.parametrize("W,M", [(256, 16), (512, 32), (1024, 64)])
+@pytest.mark.parametrize("W,M", [(256, 16), (512, 32), (1024, 64), (2048, 128)])
 def test_raster_and_signatures_bit_exact(ctx, W, M):
     import paper_2512_13133_gb300 as pcl
     base = synth.generate(3, n_clips=60, n_seeds=10, n_copies=30, window_dbu=W, margin_dbu=M,
@@ -78,6 +78,51 @@ def test_raster_and_signatures_bit_exact(ctx, W, M):
         np.testing.assert_array_equal(sig["cols"][c], so["cols"])
         np.testing.assert_array_equal(sig["blk"][c], so["blk"])
         np.testing.assert_array_equal(sig["dil"][c], so["dil"])
+
+
+@pytest.mark.parametrize("W,M", [(256, 16), (1024, 64), (2048, 128)])
+def test_edge_screen_signatures(ctx, W, M):
+    """The edge screen's per-clip structures against their definitions: the
+    64 x 64 occupancy grid (cell side W/64; a rectangle of positive area marks
+    the cells floor(x0 / c) .. floor((x1 - 1) / c) on both axes, clamped), the
+    rectangles' ascending-area order (ties by index) and the bounding box of
+    the edges not on the window border."""
+    base = synth.generate(5, n_clips=60, n_seeds=10, n_copies=30, window_dbu=W, margin_dbu=M,
+                          min_rects=1, max_rects=40)
+    ec = _edge_case_workload(W, M)
+    wl = synth.from_lists([base.clip(i).tolist() for i in range(base.n)] +
+                          [ec.clip(i).tolist() for i in range(ec.n)], W, 4, M)
+    cs = _gpu_set(ctx, wl, _P(wl))
+    n, nr = wl.n, int(wl.rect_off[-1])
+    occ = cs.occ[:n * 512].cpu().numpy().view(np.uint64).reshape(n, 64)
+    ro = cs.rorder[:2 * nr].cpu().numpy().view(np.uint16)
+    es = cs.esig[:n * 32].cpu().numpy().view(np.int32).reshape(n, 8)
+    csz = W // 64
+
+    def cell(v):
+        return min(max(v // csz, 0), 63)
+
+    for c in range(n):
+        r = wl.clip(c).astype(np.int64)
+        grid = np.zeros(64, np.uint64)
+        for x0, y0, x1, y1 in r.tolist():
+            if x1 <= x0 or y1 <= y0:
+                continue
+            m = 0
+            for cx in range(cell(x0), cell(x1 - 1) + 1):
+                m |= 1 << cx
+            for cy in range(cell(y0), cell(y1 - 1) + 1):
+                grid[cy] |= np.uint64(m)
+        np.testing.assert_array_equal(occ[c], grid, err_msg=f"grid of clip {c}")
+        o0 = int(wl.rect_off[c])
+        area = (r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1])
+        np.testing.assert_array_equal(ro[o0:o0 + len(r)], np.argsort(area, kind="stable"), err_msg=f"order {c}")
+        xs = [x0 for x0 in r[:, 0].tolist() if x0 != 0] + [x1 for x1 in r[:, 2].tolist() if x1 != W]
+        ys = [y0 for y0 in r[:, 1].tolist() if y0 != 0] + [y1 for y1 in r[:, 3].tolist() if y1 != W]
+        border = int(len(xs) + len(ys) < 4 * len(r))
+        exp = [len(r), int(bool(xs)), min(xs) if xs else 0, max(xs) if xs else 0,
+               int(bool(ys)), min(ys) if ys else 0, max(ys) if ys else 0, border]
+        np.testing.assert_array_equal(es[c], exp, err_msg=f"edge signature of clip {c}")
 
 
 def _pairs_set(t):
