@@ -313,10 +313,14 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    with the tie order (-c, |dx|+|dy|, dy, dx); c_best verified by popcount;
    decision den^2 c_best^2 > num^2 |A||B|.  Spectra of referenced clips are
    computed first when missing (spec_state == 0).  512^2 rasters (S <= 32)
-   hold no spectra: after the gates their pairs take an exact window scan of
-   every shift with popcounts in shared memory (pcm fields 0, spectra not
-   read), which requires shift_rule = EXACT_ARGMAX (else
-   PCL_ERR_UNSUPPORTED).
+   hold no spectra: after the gates their pairs take an exact window scan
+   with popcounts in shared memory (pcm fields 0, spectra not read), which
+   requires shift_rule = EXACT_ARGMAX (else PCL_ERR_UNSUPPORTED).  The scan
+   skips the groups of shifts whose projection-profile bound (the bound of
+   gate G2: c(dx, dy) <= min(sum_y min(r_A(y), r_B(y - dy)), the same over
+   the columns)) is below an overlap it has already counted, so the argmax
+   and its ties are those of the full scan; pcl_stats_get reports how much of
+   the window was counted.
    With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands),
    PCL_ENGINE_TC_DIRECT_BF16 (BF16 operands) or PCL_ENGINE_TC_DIRECT_FP8
    (E4M3 operands) the overlaps of every shift come
@@ -361,6 +365,16 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
    to exercise the time-out path without any fault.  Errors:
    PCL_ERR_INVALID (NULL ctx). */
 pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns);
+
+/* Work counters of the kernels launched through ctx since it was created or
+   last reset, read synchronously (waits for the device): out[0] = the
+   (dy, 8 consecutive dx) groups of shifts the 512^2 exact window scan
+   counted, out[1] = the groups in the windows of the pairs it aligned
+   (pcl_match_pairs and serving; not the mixed batch).  out[0] / out[1] is the
+   fraction of the definition's work the profile bounds left.  reset != 0
+   zeroes the counters after reading them.  out: host array of 2.  Errors:
+   PCL_ERR_INVALID (NULL ctx or out), PCL_ERR_CUDA. */
+pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset);
 
 /* ---- NEXT: cosine with re-extraction of the member's window --------------
    Sec. 2.1 extracts a pattern as the layout around its centre, and that

@@ -164,6 +164,7 @@ def load(build_if_missing: bool = True):
                              ctypes.POINTER(_Clipset), _VP, _U64, _VP, _VP, _VP], st),
         "pcl_device_error": ([_VP, ctypes.POINTER(ctypes.c_int)], st),
         "pcl_set_wait_limit": ([_VP, _U64], st),
+        "pcl_stats_get": ([_VP, _VP, ctypes.c_int], st),
         "pcl_surprisal": ([_VP, _VP, _U64, _VP, ctypes.c_uint32, _VP, _VP, _VP, _VP], st),
         "pcl_halo_sizes_get": ([ctypes.POINTER(Params), ctypes.c_uint32, ctypes.POINTER(_U64),
                                 ctypes.POINTER(_U64)], st),
@@ -456,6 +457,14 @@ def pcl_match_halo(ctx: Context, P: Params, a: ClipSet, b: ClipSet, hbits_b, nor
 def pcl_set_wait_limit(ctx: Context, ns: int) -> None:
     """Limit of each bounded device-side wait (ns; 0 = one second)."""
     ctx.check(ctx.lib.pcl_set_wait_limit(ctx.h, int(ns)), "pcl_set_wait_limit")
+
+
+def pcl_stats_get(ctx: Context, reset: bool = False) -> tuple:
+    """(groups of shifts the 512^2 exact scan counted, groups in its windows)
+    since the context was created or last reset; synchronous."""
+    out = (ctypes.c_uint64 * 2)()
+    ctx.check(ctx.lib.pcl_stats_get(ctx.h, ctypes.cast(out, _VP), 1 if reset else 0), "pcl_stats_get")
+    return int(out[0]), int(out[1])
 
 
 def pcl_compact_pass(ctx: Context, rec, out_pairs, d_count, d_n=None, stream=None) -> None:

@@ -35,7 +35,8 @@ cudaError_t launch_compact(const pcl_record *, uint64_t, const unsigned long lon
                            unsigned long long *, cudaStream_t);
 bool tc_supported(const Geo &);
 cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
-                               uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
+                               uint64_t, const unsigned long long *, pcl_record *, int, unsigned long long *,
+                               cudaStream_t);
 size_t tc_workspace(uint64_t);
 cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, unsigned long long,
@@ -136,8 +137,11 @@ pcl_status pcl_create(pcl_ctx **out, int device) {
     c->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMalloc(&c->d_err, 256) != cudaSuccess || cudaMemset(c->d_err, 0, 256) != cudaSuccess) {
+        cudaMalloc(&c->d_err, 256) != cudaSuccess || cudaMemset(c->d_err, 0, 256) != cudaSuccess ||
+        cudaMalloc(&c->d_stats, 64) != cudaSuccess || cudaMemset(c->d_stats, 0, 64) != cudaSuccess) {
         cudaGetLastError();
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->d_stats) cudaFree(c->d_stats);
         delete c;
         return PCL_ERR_CUDA;
     }
@@ -150,10 +154,26 @@ void pcl_destroy(pcl_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_stats) cudaFree(ctx->d_stats);
     delete ctx;
 }
 
 const char *pcl_last_error(const pcl_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset) {
+    if (!ctx || !out) return PCL_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    unsigned long long h[2] = {0ull, 0ull};
+    cudaError_t e = cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(ctx->d_stats, 0, sizeof(h));
+    if (e != cudaSuccess) {
+        ctx->err = std::string("pcl_stats_get: ") + cudaGetErrorString(e);
+        return PCL_ERR_CUDA;
+    }
+    out[0] = h[0];
+    out[1] = h[1];
+    return PCL_OK;
+}
 
 pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns) {
     if (!ctx) return PCL_ERR_INVALID;
@@ -326,7 +346,7 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
         // 512²: gates, then the exact window scan (no phase-correlation surface)
         if (P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
             return fail(ctx, PCL_ERR_UNSUPPORTED, "512² rasters take the exact argmax only%s%lld");
-        e = launch_exact_pairs(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
+        e = launch_exact_pairs(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, ctx->d_stats, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "exact window scan");
     }
     if (g.N > 256 || g.S > g.N / 16)

@@ -239,9 +239,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
     // grid-test state of this lane
     bool h2 = false;
     int k2 = 0, ns2 = 0, sx2 = 0, sy2 = 0, e2x = 0;
-    const int4 *rs2 = nullptr;
-    const uint16_t *ro2 = nullptr;
-    const uint64_t *g2 = nullptr;
+    int off2 = 0;  // rectangle offset of the pair's smaller clip (its set and grid follow from e2x)
 
     auto run_full = [&]() {  // warp-uniform: check and emit every queued pair
         unsigned ok0 = 0u, ok1 = 0u;
@@ -298,9 +296,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
             const bool sa = (e.x >> 16) & 1;
             const int off = sa ? offa : csig[c][1].z;
             ns2 = sa ? nar : csig[c][0].x;
-            rs2 = (sa ? rrects : crects) + off;
-            ro2 = (sa ? RW.rorder : CS.rorder) + off;
-            g2 = sa ? CS.occ + (size_t)(jblk + c) * 64 : grids + r * kGS;
+            off2 = off;
             sx2 = e.y;
             sy2 = e.z;
             e2x = e.x;
@@ -311,7 +307,9 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
         __syncwarp();
         bool done = false;
         if (h2) {
-            const int4 q = __ldg(rs2 + __ldg(ro2 + k2));
+            const bool s2 = (e2x >> 16) & 1;
+            const int4 q = __ldg((s2 ? rrects : crects) + off2 + __ldg((s2 ? RW.rorder : CS.rorder) + off2 + k2));
+            const uint64_t *g2 = s2 ? CS.occ + (size_t)(jblk + ((e2x >> 8) & 0xff)) * 64 : grids + (e2x & 0xff) * kGS;
             if (!grid_hit_any<P2>(g2, q.x + sx2, q.y + sy2, q.z + sx2, q.w + sy2, csz, csh)) {
                 ++g_e1;
                 h2 = false;

@@ -163,7 +163,7 @@ constexpr int kExactThreads = 320;
 
 __global__ void __launch_bounds__(kExactThreads, 2)
     exact_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, uint64_t npairs,
-                      const unsigned long long *d_n, pcl_record *out) {
+                      const unsigned long long *d_n, pcl_record *out, unsigned long long *stats) {
     if (d_n && *d_n < npairs) npairs = *d_n;
     __shared__ int gate_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kExactThreads, 2)
             if (threadIdx.x == 0) out[pid] = rec;
             continue;
         }
-        exact_body<8, 32>(prm, A, B, pr, out + pid);
+        exact_body<8, 32>(prm, A, B, pr, out + pid, stats);
     }
 }
 
@@ -260,7 +260,7 @@ cudaError_t launch_mark(const pcl_pair *pairs, uint64_t n, const unsigned long l
 
 cudaError_t launch_exact_pairs(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
                                const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
-                               int num_sms, cudaStream_t st) {
+                               int num_sms, unsigned long long *stats, cudaStream_t st) {
     const Geo g = make_geo(prm);
     if (g.N != 512 || g.S > 32) return cudaErrorNotSupported;
     const size_t sm = exact_smem<8>();
@@ -271,7 +271,7 @@ cudaError_t launch_exact_pairs(const pcl_params &prm, const pcl_clipset &a, cons
     if (e != cudaSuccess) return e;
     const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(n < cap ? n : cap);
-    exact_pair_kernel<<<grid, kExactThreads, sm, st>>>(prm, a, b, pairs, n, d_n, out);
+    exact_pair_kernel<<<grid, kExactThreads, sm, st>>>(prm, a, b, pairs, n, d_n, out, stats);
     return cudaGetLastError();
 }
 

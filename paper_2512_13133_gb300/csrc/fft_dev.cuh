@@ -370,7 +370,8 @@ __device__ __forceinline__ void exact_row_counts(const uint32_t (&a)[NW32], cons
 
 template <int NW, int SMAX>
 __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
-                                           const pcl_pair pr, pcl_record *dst) {
+                                           const pcl_pair pr, pcl_record *dst,
+                                           unsigned long long *stats = nullptr) {
     static_assert(SMAX <= 32, "shift words: q in {-1, 0, 1}");
     constexpr int N = 64 * NW, NW32 = 2 * NW, NV = NW32 / 4;  // 32-bit words and 16-byte vectors per row
     // row stride in shared memory: NV + 1 vectors (odd), so that the 8 lanes of
@@ -383,6 +384,10 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
     uint4 *sa = reinterpret_cast<uint4 *>(smem);
     uint4 *sb = sa + N * SV;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(sb + N * SV);  // [32]
+    uint32_t *rbound = reinterpret_cast<uint32_t *>(keys + 32);                      // [2 SMAX + 1]: R(dy)
+    uint32_t *cbound = rbound + 2 * SMAX + 1;                                         // [2 SMAX + 1]: C(dx)
+    uint32_t *lbest = cbound + 2 * SMAX + 1;  // [0]: L, [1]: tasks evaluated
+    uint16_t *prof = reinterpret_cast<uint16_t *>(lbest + 3);                         // [2][2N]: A's, B's
     const uint4 *ga = reinterpret_cast<const uint4 *>(A.bits + (size_t)pr.a * N * NW);
     const uint4 *gb = reinterpret_cast<const uint4 *>(B.bits + (size_t)pr.b * N * NW);
     __syncthreads();  // the shared memory may still be read by the previous item
@@ -391,11 +396,45 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
         sa[st] = __ldg(ga + t);
         sb[st] = __ldg(gb + t);
     }
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+        prof[t] = __ldg(A.prof + (size_t)pr.a * 2 * N + t);
+        prof[2 * N + t] = __ldg(B.prof + (size_t)pr.b * 2 * N + t);
+    }
+    if (threadIdx.x == 0) lbest[0] = lbest[1] = 0u;
     __syncthreads();
+    const int K = 2 * S + 1;
+    // Upper bounds from the projection profiles (the bound of gate G2): rows y
+    // of A and y - dy of B overlap in at most min(r_A(y), r_B(y - dy)) pixels,
+    // so c(dx, dy) <= R(dy) = sum_y min(r_A(y), r_B(y - dy)), and likewise
+    // c(dx, dy) <= C(dx) over the columns.
+    for (int v = warp; v < 2 * K; v += nwarps) {
+        const bool col = v >= K;
+        const int d = (col ? v - K : v) - S;
+        const uint16_t *pa_ = prof + (col ? N : 0), *pb_ = prof + 2 * N + (col ? N : 0);
+        uint32_t sum = 0;
+        for (int y = lane; y < N; y += 32) {
+            const int yb = y - d;
+            if (yb >= 0 && yb < N) sum += min((uint32_t)pa_[y], (uint32_t)pb_[yb]);
+        }
+        sum = __reduce_add_sync(0xffffffffu, sum);
+        if (lane == 0) (col ? cbound : rbound)[d + S] = sum;
+    }
+    __syncthreads();
+    // dx chunks [8 c, 8 c + 7] for c = floor(-S / 8) .. floor(S / 8); a task
+    // (dy, chunk) is bounded by min(R(dy), max of C over its shifts)
+    const int c0 = -((S + 7) / 8), nch = S / 8 - c0 + 1;
+    auto task_bound = [&](int task) -> uint32_t {
+        const int dy = task / nch - S, dx0 = (c0 + task % nch) * 8;
+        uint32_t cm = 0;
+        for (int u = 0; u < 8; ++u) {
+            const int dx = dx0 + u;
+            if (dx >= -S && dx <= S) cm = max(cm, cbound[dx + S]);
+        }
+        return min(rbound[dy + S], cm);
+    };
     unsigned long long best = 0ull;
-    // dx chunks [8 c, 8 c + 7] for c = floor(-S / 8) .. floor(S / 8)
-    const int K = 2 * S + 1, c0 = -((S + 7) / 8), nch = S / 8 - c0 + 1;
-    for (int task = warp; task < K * nch; task += nwarps) {
+    // c(s) for the 8 shifts of one task; returns their largest overlap
+    auto eval_task = [&](int task) -> uint32_t {
         const int dy = task / nch - S, dx0 = (c0 + task % nch) * 8;  // -32 <= dx0 <= 32
         const int q = (dx0 + 32) / 32 - 1, rb = dx0 - 32 * q;        // dx0 = 32 q + rb, rb in {0, 8, 16, 24}
         uint32_t cnt[8];
@@ -415,6 +454,7 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
             else if (q == 0) exact_row_counts<NW32, 0>(a, bp, rb, cnt);
             else exact_row_counts<NW32, 1>(a, bp, rb, cnt);
         }
+        uint32_t cmax = 0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int dx = dx0 + u;
@@ -422,12 +462,59 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
             if (dx >= -S && dx <= S) {
                 const unsigned long long k = shift_key(c, dx, dy, S);
                 best = k > best ? k : best;
+                cmax = max(cmax, c);
             }
+        }
+        return cmax;
+    };
+    // Seeds: the shift of the largest bound min(R, C) is (argmax R, argmax C);
+    // warp w takes the task of that chunk at dy* + 0, +1, -1, +2, ... (clamped
+    // rows are skipped), which gives a lower bound L on the best overlap.
+    int dys = 0, dxs = 0;
+    {
+        uint32_t br = 0, bc = 0;
+        for (int d = 0; d < K; ++d) {  // every thread, the same result
+            if (rbound[d] > br) br = rbound[d], dys = d - S;
+            if (cbound[d] > bc) bc = cbound[d], dxs = d - S;
+        }
+    }
+    const int cs = (dxs >= 0 ? dxs / 8 : -((-dxs + 7) / 8)) - c0;  // chunk of dxs
+    auto seed_dy = [&](int w) { return dys + ((w & 1) ? (w + 1) / 2 : -(w / 2)); };
+    {
+        const int dy = seed_dy(warp);
+        if (dy >= -S && dy <= S) {
+            const uint32_t cm = eval_task((dy + S) * nch + cs);
+            if (lane == 0) {
+                atomicMax(lbest, cm);
+                atomicAdd(lbest + 1, 1u);
+            }
+        }
+    }
+    __syncthreads();
+    // every other task whose bound reaches L (L only grows: each evaluated
+    // task raises it to its largest overlap); a task below L holds no shift
+    // whose overlap reaches the best, so the argmax and its ties are unchanged
+    for (int task = warp; task < K * nch; task += nwarps) {
+        if (task % nch == cs) {
+            const int off = task / nch - S - dys;  // seeded by warp 2 off - 1 (off > 0) or -2 off (off <= 0)
+            const int w = off > 0 ? 2 * off - 1 : -2 * off;
+            if (w < nwarps) continue;
+        }
+        const uint32_t lnow = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile uint32_t *>(lbest), 0);
+        if (task_bound(task) < lnow) continue;  // warp-uniform
+        const uint32_t cm = eval_task(task);
+        if (lane == 0) {
+            atomicMax(lbest, cm);
+            atomicAdd(lbest + 1, 1u);
         }
     }
     if (lane == 0) keys[warp] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (stats) {
+            atomicAdd(stats, (unsigned long long)lbest[1]);
+            atomicAdd(stats + 1, (unsigned long long)(K * nch));
+        }
         unsigned long long bk = 0ull;
         for (int w = 0; w < nwarps; ++w) bk = keys[w] > bk ? keys[w] : bk;
         const int dx = S - (int)(bk & 0xffu), dy = S - (int)((bk >> 8) & 0xffu);
@@ -457,7 +544,10 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
 
 // shared memory of exact_body
 template <int NW>
-constexpr size_t exact_smem() { return 2 * 16 * 64 * NW * (NW / 2 + 1) + 32 * 8; }
+constexpr size_t exact_smem() {
+    // rasters (odd row stride), keys[32], R and C bounds (2 x 65), L (+ 2 pad), profiles [2][2N] u16
+    return 2 * 16 * 64 * NW * (NW / 2 + 1) + 32 * 8 + 4 * (2 * 65 + 3) + 2 * 2 * 2 * 64 * NW;
+}
 
 }  // namespace fft_dev
 }  // namespace pcl

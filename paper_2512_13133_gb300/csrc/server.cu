@@ -57,7 +57,8 @@ cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl
                               const uint32_t *, const uint32_t *, void *, size_t, pcl_pair *, uint64_t,
                               unsigned long long *, unsigned long long *, int, cudaStream_t);
 cudaError_t launch_exact_pairs(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *,
-                               uint64_t, const unsigned long long *, pcl_record *, int, cudaStream_t);
+                               uint64_t, const unsigned long long *, pcl_record *, int, unsigned long long *,
+                               cudaStream_t);
 }  // namespace pcl
 
 namespace {
@@ -419,7 +420,7 @@ pcl_status pcl_server_submit_class(pcl_server *s, uint32_t cls, const uint32_t *
         } else if (k.engine == kExact) {
             if (e == cudaSuccess)
                 e = pcl::launch_exact_pairs(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms,
-                                            st);
+                                            ctx->d_stats, st);
         } else {
             if (e == cudaSuccess) e = pcl::launch_mark(sl->cand, cap, sl->counts + 0, sl->q, k.lib, st);
             if (e == cudaSuccess) e = pcl::launch_spectra(k.P, sl->q, nullptr, 0, true, st);

@@ -375,3 +375,43 @@ def test_cosine_512_exact_scan_other_markers(ctx, torch_cuda, M):
         np.testing.assert_array_equal(g[f][al], o[f][al])
     np.testing.assert_array_equal(g["score"][al].astype(np.int64), o["score"][al])
     assert np.abs(g["sim"][al].astype(np.float64) - o["sim"][al]).max() <= 1e-5
+
+
+def test_exact_scan_prunes_by_profile_bounds(ctx, torch_cuda):
+    """The 512² scan counts only the groups of shifts whose profile bound
+    reaches an overlap already found: a clip against itself needs a few
+    groups, a clip against an empty clip (bounds 0 = the best overlap) every
+    group; the counters add up per aligned pair and the records stay the
+    oracle's."""
+    import paper_2512_13133_gb300 as pcl
+    wl = synth.generate(12, n_clips=30, n_seeds=6, n_copies=20, window_dbu=2048, margin_dbu=128,
+                        min_rects=5, max_rects=40)
+    clips = [wl.clip(i).tolist() for i in range(wl.n)] + [[]]
+    wl = synth.from_lists(clips, 2048, 4, 128)
+    empty = wl.n - 1
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80, flags=pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, cs)
+    S = wl.marker_dbu // wl.pitch_dbu
+    groups = (2 * S + 1) * (S // 8 + (S + 7) // 8 + 1)
+
+    def run(pairs):
+        pcl.pcl_stats_get(ctx, reset=True)
+        tp = torch_cuda.tensor(pairs, dtype=torch_cuda.int32, device="cuda")
+        g = pcl.records_to_numpy(pcl.match(ctx, P, pcl.MODE_COSINE, cs, cs, tp))
+        return g, pcl.pcl_stats_get(ctx, reset=True)
+
+    same = [[i, i] for i in range(6)]
+    g, (ev, tot) = run(same)
+    assert tot == len(same) * groups
+    assert 0 < ev <= 0.25 * tot
+    assert (g["dx_dbu"] == 0).all() and (g["dy_dbu"] == 0).all() and (g["pass_"] == 1).all()
+    g, (ev, tot) = run([[0, empty], [empty, 1]])
+    assert ev == tot == 2 * groups
+    pairs = np.array([[0, 1], [2, 7], [3, 11], [empty, 4]], dtype=np.int64)
+    g, (ev, tot) = run(pairs.tolist())
+    assert 0 < ev <= tot == len(pairs) * groups
+    o = oracle.ClipSet(wl).match(pairs, oracle.MODE_COSINE, use_gates=False, cos_num=80)
+    for f in ("dx_dbu", "dy_dbu", "pass_"):
+        np.testing.assert_array_equal(g[f], o[f])
+    np.testing.assert_array_equal(g["score"].astype(np.int64), o["score"])
