@@ -1005,6 +1005,38 @@ def run_ours(args, rank, world, local_rank):
                                                       (rt["pass_"] == recs["pass_"]).all())
         tc["device_error"] = pcl.pcl_device_error(ctx)
         fft["tc_engine"] = tc
+        # the bound-pruned exact window scan as a cosine engine (no spectra):
+        # both lists, records against the FFT engine's, share of the window counted
+        Pe = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL,
+                        cos_engine=pcl.ENGINE_EXACT_SCAN, flags=pcl.P_NO_GATES)
+        ex = {}
+        for name, lst, ref, ref_ms in (("same_seed", fp, recs, fms), ("dense32", dense, dense_fft, dms)):
+            tl = torch.from_numpy(np.ascontiguousarray(lst)).to(dev)
+            rl = torch.empty((len(lst), 40), dtype=torch.uint8, device=dev)
+            pcl.pcl_match_pairs(ctx, Pe, pcl.MODE_COSINE, cs, cs, tl, rl)
+            torch.cuda.synchronize()
+            pcl.pcl_stats_get(ctx, reset=True)
+            x_ms = []
+            for _ in range(max(args.steps, 1)):
+                flush.zero_()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record()
+                pcl.pcl_match_pairs(ctx, Pe, pcl.MODE_COSINE, cs, cs, tl, rl)
+                a1.record()
+                torch.cuda.synchronize()
+                x_ms.append(a0.elapsed_time(a1))
+            ev, tot = pcl.pcl_stats_get(ctx, reset=True)
+            ms = float(np.mean(x_ms))
+            rt = pcl.records_to_numpy(rl)
+            ex[name] = {"pairs": int(len(lst)), "ms": ms, "pairs_per_s": len(lst) / (ms / 1e3),
+                        "speedup_vs_fft": ref_ms / ms, "window_counted": ev / tot if tot else None,
+                        "agrees_with_fft": bool((rt["score"] == ref["score"]).all() and
+                                                (rt["dx_dbu"] == ref["dx_dbu"]).all() and
+                                                (rt["dy_dbu"] == ref["dy_dbu"]).all() and
+                                                (rt["pass_"] == ref["pass_"]).all())}
+            del tl, rl
+        fft["exact_scan_engine"] = ex
         # per-result error against the FP64 oracle (the precision form's report)
         if args.precision_sample and rank == 0:
             fft["precision_vs_fp64_oracle"] = precision_report(wl, fp.astype(np.int64), same_seed_recs,

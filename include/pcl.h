@@ -64,7 +64,8 @@ enum {
     PCL_ENGINE_TC_DIRECT = 1,      /* tensor cores, FP16 operands */
     PCL_ENGINE_TC_DIRECT_FP8 = 2,  /* tensor cores, E4M3 operands */
     PCL_ENGINE_XYSEP = 3,
-    PCL_ENGINE_TC_DIRECT_BF16 = 4  /* tensor cores, BF16 operands */
+    PCL_ENGINE_TC_DIRECT_BF16 = 4, /* tensor cores, BF16 operands */
+    PCL_ENGINE_EXACT_SCAN = 5      /* bound-pruned popcount scan of the window (N = 128, 256, 512) */
 };
 enum { PCL_SHIFT_EXACT_ARGMAX = 0, PCL_SHIFT_PCM_PEAK = 1 };
 
@@ -320,7 +321,9 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    gate G2: c(dx, dy) <= min(sum_y min(r_A(y), r_B(y - dy)), the same over
    the columns)) is below an overlap it has already counted, so the argmax
    and its ties are those of the full scan; pcl_stats_get reports how much of
-   the window was counted.
+   the window was counted.  cos_engine = PCL_ENGINE_EXACT_SCAN takes the same
+   scan at 128^2 and 256^2 (S <= N/16; no spectra: spec/spec_state may be
+   NULL, EXACT_ARGMAX only).
    With cos_engine = PCL_ENGINE_TC_DIRECT (FP16 operands),
    PCL_ENGINE_TC_DIRECT_BF16 (BF16 operands) or PCL_ENGINE_TC_DIRECT_FP8
    (E4M3 operands) the overlaps of every shift come
@@ -460,8 +463,9 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
 /* ---- a10: serving loop ----------------------------------------------------
    Resident representative libraries, one per raster size class, and
    continuously batched query requests (cfg mode COSINE: per class the engine
-   its parameters name, PCL_ENGINE_FFT_PCM or PCL_ENGINE_TC_DIRECT(_BF16,
-   _FP8), and for a 512^2 px class the exact window scan of pcl_match_pairs;
+   its parameters name, PCL_ENGINE_FFT_PCM, PCL_ENGINE_TC_DIRECT(_BF16,
+   _FP8) or PCL_ENGINE_EXACT_SCAN (from 128^2 px), and for a 512^2 px class
+   the exact window scan of pcl_match_pairs;
    EDGE: the Min-Max procedure).  pcl_server_create_classes takes n_classes
    (1..16) parameter blocks and libraries (class c: params[c], libraries[c]);
    pcl_server_create is the one-class form.  For COSINE each library must be

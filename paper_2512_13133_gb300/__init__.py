@@ -32,6 +32,7 @@ ENGINE_TC_DIRECT = 1
 ENGINE_TC_DIRECT_FP8 = 2
 ENGINE_XYSEP = 3  # shift by XY-separation interval competition (Sec. 3.2.1 (2))
 ENGINE_TC_DIRECT_BF16 = 4
+ENGINE_EXACT_SCAN = 5  # bound-pruned exact window scan (N = 128, 256, 512; no spectra)
 SHIFT_EXACT_ARGMAX = 0
 SHIFT_PCM_PEAK = 1
 P_NO_GATES = 1

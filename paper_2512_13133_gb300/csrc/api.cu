@@ -190,7 +190,7 @@ pcl_status pcl_params_validate(const pcl_params *P) {
     if (P->cos_den == 0 || P->cos_den > 65535 || P->cos_num == 0 || P->cos_num >= P->cos_den)
         return PCL_ERR_INVALID;
     if (P->edge_tol_dbu < 0) return PCL_ERR_INVALID;
-    if (P->cos_engine > PCL_ENGINE_TC_DIRECT_BF16 || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
+    if (P->cos_engine > PCL_ENGINE_EXACT_SCAN || P->shift_rule > PCL_SHIFT_PCM_PEAK) return PCL_ERR_INVALID;
     if (!(P->near_band >= 0.0f)) return PCL_ERR_INVALID;
     return PCL_OK;
 }
@@ -340,15 +340,18 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
         e = launch_xysep(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "interval-competition shift");
     }
-    if (P->cos_engine != PCL_ENGINE_FFT_PCM)
+    if (P->cos_engine != PCL_ENGINE_FFT_PCM && P->cos_engine != PCL_ENGINE_EXACT_SCAN)
         return fail(ctx, PCL_ERR_UNSUPPORTED, "cosine engine %s%lld not built", "", P->cos_engine);
-    if (g.N == 512 && g.S <= 32) {
-        // 512²: gates, then the exact window scan (no phase-correlation surface)
+    if ((g.N == 512 || (P->cos_engine == PCL_ENGINE_EXACT_SCAN && g.N >= 128)) && g.S <= g.N / 16) {
+        // 512² (or the exact-scan engine): gates, then the bound-pruned exact
+        // window scan (no phase-correlation surface, no spectra)
         if (P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
-            return fail(ctx, PCL_ERR_UNSUPPORTED, "512² rasters take the exact argmax only%s%lld");
+            return fail(ctx, PCL_ERR_UNSUPPORTED, "the exact window scan takes the exact argmax only%s%lld");
         e = launch_exact_pairs(*P, *a, *b, d_pairs, n, dn, d_out, ctx->num_sms, ctx->d_stats, st);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "exact window scan");
     }
+    if (P->cos_engine == PCL_ENGINE_EXACT_SCAN)
+        return fail(ctx, PCL_ERR_UNSUPPORTED, "exact-scan engine covers N = 128, 256, 512 and S <= N/16%s%lld");
     if (g.N > 256 || g.S > g.N / 16)
         return fail(ctx, PCL_ERR_UNSUPPORTED, "FFT engine covers N <= 256 (512 by exact scan) and S <= N/16%s%lld");
     if (!a->spec || !a->spec_state || !b->spec || !b->spec_state)

@@ -155,12 +155,14 @@ __global__ void __launch_bounds__(32 * 2 * ((9 * P / 2 + 1 + 31) / 32), 1)
     }
 }
 
-// 512² rasters: the FFT body's buffers exceed shared memory at this size, so
-// a pair passes the indices, emptiness and lossless gates as in pair_body and
-// the survivors take the exact window scan (exact_body).  One pair per CTA
-// iteration, persistent grid.
+// The exact window scan: at 512² the FFT body's buffers exceed shared memory,
+// and at 128² / 256² it is the exact-scan engine.  A pair passes the indices,
+// emptiness and lossless gates as in pair_body and the survivors take the
+// bound-pruned scan (exact_body<NW, SMAX>, N = 64 NW, S <= SMAX = N/16).  One
+// pair per CTA iteration, persistent grid.
 constexpr int kExactThreads = 320;
 
+template <int NW, int SMAX>
 __global__ void __launch_bounds__(kExactThreads, 2)
     exact_pair_kernel(pcl_params prm, pcl_clipset A, pcl_clipset B, const pcl_pair *pairs, uint64_t npairs,
                       const unsigned long long *d_n, pcl_record *out, unsigned long long *stats) {
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kExactThreads, 2)
             if (threadIdx.x == 0) out[pid] = rec;
             continue;
         }
-        exact_body<8, 32>(prm, A, B, pr, out + pid, stats);
+        exact_body<NW, SMAX>(prm, A, B, pr, out + pid, stats);
     }
 }
 
@@ -258,21 +260,34 @@ cudaError_t launch_mark(const pcl_pair *pairs, uint64_t n, const unsigned long l
     return cudaGetLastError();
 }
 
+template <int NW, int SMAX>
+cudaError_t exact_t(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b, const pcl_pair *pairs,
+                    uint64_t n, const unsigned long long *d_n, pcl_record *out, int num_sms,
+                    unsigned long long *stats, cudaStream_t st) {
+    const size_t sm = exact_smem<NW>();
+    auto *kern = exact_pair_kernel<NW, SMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess || n == 0) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExactThreads, sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(n < cap ? n : cap);
+    kern<<<grid, kExactThreads, sm, st>>>(prm, a, b, pairs, n, d_n, out, stats);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_exact_pairs(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,
                                const pcl_pair *pairs, uint64_t n, const unsigned long long *d_n, pcl_record *out,
                                int num_sms, unsigned long long *stats, cudaStream_t st) {
     const Geo g = make_geo(prm);
-    if (g.N != 512 || g.S > 32) return cudaErrorNotSupported;
-    const size_t sm = exact_smem<8>();
-    cudaError_t e = cudaFuncSetAttribute(exact_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess || n == 0) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_pair_kernel, kExactThreads, sm);
-    if (e != cudaSuccess) return e;
-    const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const unsigned grid = (unsigned)(n < cap ? n : cap);
-    exact_pair_kernel<<<grid, kExactThreads, sm, st>>>(prm, a, b, pairs, n, d_n, out, stats);
-    return cudaGetLastError();
+    if (g.S > g.N / 16) return cudaErrorNotSupported;
+    switch (g.N) {
+        case 128: return exact_t<2, 8>(prm, a, b, pairs, n, d_n, out, num_sms, stats, st);
+        case 256: return exact_t<4, 16>(prm, a, b, pairs, n, d_n, out, num_sms, stats, st);
+        case 512: return exact_t<8, 32>(prm, a, b, pairs, n, d_n, out, num_sms, stats, st);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 cudaError_t launch_pair_fft(const pcl_params &prm, const pcl_clipset &a, const pcl_clipset &b,

@@ -372,11 +372,11 @@ template <int NW, int SMAX>
 __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clipset &A, const pcl_clipset &B,
                                            const pcl_pair pr, pcl_record *dst,
                                            unsigned long long *stats = nullptr) {
-    static_assert(SMAX <= 32, "shift words: q in {-1, 0, 1}");
+    static_assert(SMAX <= 32 && NW >= 2, "shift words: q in {-1, 0, 1}; rows of whole 16-byte vectors");
     constexpr int N = 64 * NW, NW32 = 2 * NW, NV = NW32 / 4;  // 32-bit words and 16-byte vectors per row
-    // row stride in shared memory: NV + 1 vectors (odd), so that the 8 lanes of
-    // a quarter-warp reading 8 consecutive rows hit 8 different bank groups
-    constexpr int SV = NV + 1;
+    // row stride in shared memory: an odd number of vectors, so that the 8
+    // lanes of a quarter-warp reading 8 consecutive rows hit 8 bank groups
+    constexpr int SV = NV | 1;
     const Geo g = make_geo(prm);
     const int S = g.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -387,7 +387,8 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
     uint32_t *rbound = reinterpret_cast<uint32_t *>(keys + 32);                      // [2 SMAX + 1]: R(dy)
     uint32_t *cbound = rbound + 2 * SMAX + 1;                                         // [2 SMAX + 1]: C(dx)
     uint32_t *lbest = cbound + 2 * SMAX + 1;  // [0]: L, [1]: tasks evaluated
-    uint16_t *prof = reinterpret_cast<uint16_t *>(lbest + 3);                         // [2][2N]: A's, B's
+    uint32_t *order = lbest + 4;                                                      // [1024] sort keys
+    uint16_t *prof = reinterpret_cast<uint16_t *>(order + 1024);                      // [2][2N]: A's, B's
     const uint4 *ga = reinterpret_cast<const uint4 *>(A.bits + (size_t)pr.a * N * NW);
     const uint4 *gb = reinterpret_cast<const uint4 *>(B.bits + (size_t)pr.b * N * NW);
     __syncthreads();  // the shared memory may still be read by the previous item
@@ -467,42 +468,39 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
         }
         return cmax;
     };
-    // Seeds: the shift of the largest bound min(R, C) is (argmax R, argmax C);
-    // warp w takes the task of that chunk at dy* + 0, +1, -1, +2, ... (clamped
-    // rows are skipped), which gives a lower bound L on the best overlap.
-    int dys = 0, dxs = 0;
-    {
-        uint32_t br = 0, bc = 0;
-        for (int d = 0; d < K; ++d) {  // every thread, the same result
-            if (rbound[d] > br) br = rbound[d], dys = d - S;
-            if (cbound[d] > bc) bc = cbound[d], dxs = d - S;
-        }
-    }
-    const int cs = (dxs >= 0 ? dxs / 8 : -((-dxs + 7) / 8)) - c0;  // chunk of dxs
-    auto seed_dy = [&](int w) { return dys + ((w & 1) ? (w + 1) / 2 : -(w / 2)); };
-    {
-        const int dy = seed_dy(warp);
-        if (dy >= -S && dy <= S) {
-            const uint32_t cm = eval_task((dy + S) * nch + cs);
-            if (lane == 0) {
-                atomicMax(lbest, cm);
-                atomicAdd(lbest + 1, 1u);
-            }
-        }
-    }
+    // Best first: the tasks sorted by bound, descending (bitonic sort of
+    // keys bound << 12 | 4095 - task in shared memory; ties by task index);
+    // warp w takes sorted positions w, w + nwarps, ...  The first round (the
+    // nwarps largest bounds) sets L, the largest overlap counted so far, and
+    // every counted task raises it (shared atomic max).  A warp stops at its
+    // first position whose bound is below L: the positions after it have
+    // bounds no larger, and a task below L holds no shift whose overlap
+    // reaches the best, so the argmax and its ties are the full scan's.
+    const int ntask = K * nch;  // <= 65 x 9 = 585
+    int nsort = 32;
+    while (nsort < ntask) nsort <<= 1;
+    for (int t = threadIdx.x; t < nsort; t += blockDim.x)
+        order[t] = t < ntask ? (task_bound(t) << 12) | (uint32_t)(4095 - t) : 0u;
     __syncthreads();
-    // every other task whose bound reaches L (L only grows: each evaluated
-    // task raises it to its largest overlap); a task below L holds no shift
-    // whose overlap reaches the best, so the argmax and its ties are unchanged
-    for (int task = warp; task < K * nch; task += nwarps) {
-        if (task % nch == cs) {
-            const int off = task / nch - S - dys;  // seeded by warp 2 off - 1 (off > 0) or -2 off (off <= 0)
-            const int w = off > 0 ? 2 * off - 1 : -2 * off;
-            if (w < nwarps) continue;
+    for (int k = 2; k <= nsort; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < nsort; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = order[i], y = order[l];
+                    if (((i & k) == 0) ? (x < y) : (x > y)) {  // descending runs first
+                        order[i] = y;
+                        order[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
         }
+    for (int p = warp; p < ntask; p += nwarps) {
+        const uint32_t key = order[p];
         const uint32_t lnow = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile uint32_t *>(lbest), 0);
-        if (task_bound(task) < lnow) continue;  // warp-uniform
-        const uint32_t cm = eval_task(task);
+        if ((key >> 12) < lnow) break;  // warp-uniform
+        const uint32_t cm = eval_task(4095 - (int)(key & 4095u));
         if (lane == 0) {
             atomicMax(lbest, cm);
             atomicAdd(lbest + 1, 1u);
@@ -545,8 +543,9 @@ __device__ __forceinline__ void exact_body(const pcl_params &prm, const pcl_clip
 // shared memory of exact_body
 template <int NW>
 constexpr size_t exact_smem() {
-    // rasters (odd row stride), keys[32], R and C bounds (2 x 65), L (+ 2 pad), profiles [2][2N] u16
-    return 2 * 16 * 64 * NW * (NW / 2 + 1) + 32 * 8 + 4 * (2 * 65 + 3) + 2 * 2 * 2 * 64 * NW;
+    // rasters (odd row stride), keys[32], R and C bounds (2 x 65), L and the task count (+ 2 pad),
+    // 1024 sort keys, profiles [2][2N] u16
+    return 2 * 16 * 64 * NW * ((NW / 2) | 1) + 32 * 8 + 4 * (2 * 65 + 4) + 4 * 1024 + 2 * 2 * 2 * 64 * NW;
 }
 
 }  // namespace fft_dev

@@ -268,10 +268,11 @@ pcl_status pcl_server_create_classes(pcl_ctx *ctx, const pcl_params *params, con
                 return fail(ctx, PCL_ERR_INVALID, who + "library needs rasters and signatures");
             if (g.S > g.N / 16)
                 return fail(ctx, PCL_ERR_UNSUPPORTED, who + "cosine serving covers S <= N/16");
-            if (g.N == 512) {
-                // 512^2 px: the exact window scan (no spectra, no tensor-core geometry)
+            if (g.N == 512 || (P->cos_engine == PCL_ENGINE_EXACT_SCAN && g.N >= 128)) {
+                // 512^2 px, or the exact-scan engine: the bound-pruned exact
+                // window scan (no spectra, no tensor-core geometry)
                 if (P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
-                    return fail(ctx, PCL_ERR_UNSUPPORTED, who + "512^2 px classes take the exact argmax rule");
+                    return fail(ctx, PCL_ERR_UNSUPPORTED, who + "the exact window scan takes the exact argmax rule");
                 engine = kExact;
             } else if (tc) {
                 if (!pcl::tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
@@ -281,7 +282,8 @@ pcl_status pcl_server_create_classes(pcl_ctx *ctx, const pcl_params *params, con
             } else {
                 if (P->cos_engine != PCL_ENGINE_FFT_PCM)
                     return fail(ctx, PCL_ERR_UNSUPPORTED,
-                                who + "cosine serving takes the FFT or the tensor-core engine");
+                                who + "cosine serving takes the FFT, tensor-core or exact-scan engine (the "
+                                      "exact scan from 128^2 px)");
                 if (!library->spec || !library->spec_state)
                     return fail(ctx, PCL_ERR_INVALID, who + "FFT engine needs the library's spectra");
                 engine = kFft;
