@@ -371,11 +371,12 @@ pcl_status pcl_set_wait_limit(pcl_ctx *ctx, uint64_t ns);
 
 /* Work counters of the kernels launched through ctx since it was created or
    last reset, read synchronously (waits for the device): out[0] = the
-   (dy, 8 consecutive dx) groups of shifts the 512^2 exact window scan
-   counted, out[1] = the groups in the windows of the pairs it aligned
-   (pcl_match_pairs and serving; not the mixed batch).  out[0] / out[1] is the
-   fraction of the definition's work the profile bounds left.  reset != 0
-   zeroes the counters after reading them.  out: host array of 2.  Errors:
+   (dy, 8 consecutive dx) groups of shifts the exact window scan counted,
+   out[1] = the groups in the windows of the pairs it aligned
+   (pcl_match_pairs and serving; not the mixed batch); out[2], out[3] = the
+   same for the re-extraction pair kernel (pcl_match_halo).  out[0] / out[1]
+   is the fraction of the definition's work the bounds left.  reset != 0
+   zeroes the counters after reading them.  out: host array of 4.  Errors:
    PCL_ERR_INVALID (NULL ctx or out), PCL_ERR_CUDA. */
 pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset);
 
@@ -395,7 +396,10 @@ pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset);
    pcl_halo_sizes_get: bytes of the halo rasters ([n][N + 2S][ceil((N +
    2S) / 64)] u64: row j + S, bit i + S holds the pixel of centre (p i +
    p/2, p j + p/2), i, j in [-S, N + S)) and of the moved-window pixel
-   counts ([n][(2S + 1)^2] u32, index (dy + S)(2S + 1) + dx + S).
+   counts with the pair kernel's bounds ([n][(2S + 1)^2 + 2 (N + 2S)] u32:
+   n_B at index (dy + S)(2S + 1) + dx + S, then per halo row the most ones it
+   has in the columns of a moved window, then per halo column the most ones
+   it has in the rows of a moved window).
    pcl_rasterize_halo: fills both for every clip of cs from its rectangles
    (one CTA per clip); the window rasters of cs are not touched.
    pcl_match_halo: one record per pair (a = clip of set a, rasterised by
@@ -403,8 +407,11 @@ pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset);
    order: dx/dy the best shift (dbu), score c(s*), sim (FP32, FP64 inside
    the near band), pass, reserved = n_B(s*), flags ALIGNED (| EMPTY); no
    gates run (the lossless bounds assume fixed norms) and pcm fields are 0.
-   One CTA per pair with both rasters in shared memory; d_n as in
-   pcl_match_pairs.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED,
+   One CTA per pair with both rasters in shared memory; groups of shifts
+   are counted best first and skipped when min(row bound, column bound)^2
+   n_best < c_best^2 n_B(s) for each of their shifts (a's profiles against
+   b's bounds above), which leaves the chosen shift unchanged
+   (pcl_stats_get reports the share counted); d_n as in pcl_match_pairs.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED,
    PCL_ERR_CUDA. */
 pcl_status pcl_halo_sizes_get(const pcl_params *P, uint32_t n_clips, uint64_t *hbits_bytes, uint64_t *norms_bytes);
 pcl_status pcl_rasterize_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *cs, uint64_t *d_hbits,

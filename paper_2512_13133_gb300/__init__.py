@@ -460,12 +460,14 @@ def pcl_set_wait_limit(ctx: Context, ns: int) -> None:
     ctx.check(ctx.lib.pcl_set_wait_limit(ctx.h, int(ns)), "pcl_set_wait_limit")
 
 
-def pcl_stats_get(ctx: Context, reset: bool = False) -> tuple:
-    """(groups of shifts the 512^2 exact scan counted, groups in its windows)
-    since the context was created or last reset; synchronous."""
-    out = (ctypes.c_uint64 * 2)()
+def pcl_stats_get(ctx: Context, reset: bool = False, kernel: str = "exact") -> tuple:
+    """(groups of shifts counted, groups in the windows) of the exact window
+    scan (kernel="exact") or of the re-extraction pair kernel ("halo") since
+    the context was created or last reset; synchronous."""
+    out = (ctypes.c_uint64 * 4)()
     ctx.check(ctx.lib.pcl_stats_get(ctx.h, ctypes.cast(out, _VP), 1 if reset else 0), "pcl_stats_get")
-    return int(out[0]), int(out[1])
+    k = {"exact": 0, "halo": 2}[kernel]
+    return int(out[k]), int(out[k + 1])
 
 
 def pcl_compact_pass(ctx: Context, rec, out_pairs, d_count, d_n=None, stream=None) -> None:

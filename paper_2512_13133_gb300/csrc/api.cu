@@ -163,15 +163,14 @@ const char *pcl_last_error(const pcl_ctx *ctx) { return ctx ? ctx->err.c_str() :
 pcl_status pcl_stats_get(pcl_ctx *ctx, uint64_t *out, int reset) {
     if (!ctx || !out) return PCL_ERR_INVALID;
     cudaSetDevice(ctx->device);
-    unsigned long long h[2] = {0ull, 0ull};
+    unsigned long long h[4] = {0ull, 0ull, 0ull, 0ull};
     cudaError_t e = cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && reset) e = cudaMemset(ctx->d_stats, 0, sizeof(h));
     if (e != cudaSuccess) {
         ctx->err = std::string("pcl_stats_get: ") + cudaGetErrorString(e);
         return PCL_ERR_CUDA;
     }
-    out[0] = h[0];
-    out[1] = h[1];
+    for (int k = 0; k < 4; ++k) out[k] = h[k];
     return PCL_OK;
 }
 

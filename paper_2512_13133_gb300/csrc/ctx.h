@@ -11,6 +11,7 @@ struct pcl_ctx {
     size_t ws_bytes = 0;
     int *d_err = nullptr;  // device error word set by kernels whose bounded waits ran out
     unsigned long long wait_ns = 0;  // limit of each bounded device-side wait (0: one second)
-    // device work counters: [0] window tasks the exact scan evaluated, [1] tasks in its windows
+    // device work counters: [0] window tasks the exact scan counted, [1] tasks in its windows,
+    // [2], [3] the same for the re-extraction pair kernel
     unsigned long long *d_stats = nullptr;
 };

@@ -32,6 +32,9 @@ constexpr int kThreads = 256;
 
 __host__ __device__ inline int halo_side(int N, int S) { return N + 2 * S; }
 __host__ __device__ inline int halo_words(int N, int S) { return (N + 2 * S + 63) / 64; }
+// u32 per clip in the norms buffer: n_B(s) for the K^2 shifts, then the row
+// bounds hrow[NH] and the column bounds hcol[NH] of the pair kernel's pruning
+__host__ __device__ inline int norms_stride(int N, int S) { return (2 * S + 1) * (2 * S + 1) + 2 * halo_side(N, S); }
 
 // shared-memory row strides in 64-bit words, odd so that the 16 lanes of a
 // half-warp reading 16 consecutive rows hit 16 different bank pairs: A's rows
@@ -93,11 +96,33 @@ __global__ void __launch_bounds__(kThreads) halo_raster_kernel(pcl_params prm, p
     }
     __syncthreads();
     // n_B(dx, dy) = sum over window rows y of cnt[y - dy + S][dx]
+    uint32_t *nrm = norms + (size_t)c * norms_stride(N, S);
     for (int task = threadIdx.x; task < K * K; task += blockDim.x) {
         const int dy = task / K - S, kx = task % K;
         uint32_t s = 0;
         for (int y = 0; y < N; ++y) s += cnt[(size_t)(y - dy + S) * K + kx];
-        norms[(size_t)c * K * K + task] = s;
+        nrm[task] = s;
+    }
+    // bounds for the pair kernel: hrow[t] = the most ones halo row t has in
+    // the N columns of a moved window (max over dx), hcol[x] = the most ones
+    // halo column x has in the N rows of a moved window (max over dy: rows
+    // [t0, t0 + N), t0 = S - dy = 0 .. 2S, a sliding sum)
+    for (int t = threadIdx.x; t < NH; t += blockDim.x) {
+        uint32_t m = 0;
+        for (int k = 0; k < K; ++k) m = max(m, (uint32_t)cnt[(size_t)t * K + k]);
+        nrm[K * K + t] = m;
+    }
+    for (int x = threadIdx.x; x < NH; x += blockDim.x) {
+        const int w = x >> 6, b = x & 63;
+        uint32_t win = 0;
+        for (int t = 0; t < N; ++t) win += (uint32_t)((rows[(size_t)t * NWH + w] >> b) & 1ull);
+        uint32_t m = win;
+        for (int t0 = 1; t0 <= 2 * S; ++t0) {
+            win += (uint32_t)((rows[(size_t)(t0 + N - 1) * NWH + w] >> b) & 1ull);
+            win -= (uint32_t)((rows[(size_t)(t0 - 1) * NWH + w] >> b) & 1ull);
+            m = max(m, win);
+        }
+        nrm[K * K + NH + x] = m;
     }
 }
 
@@ -161,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, NW >= 8 ? 2 : 4) halo_pair_kernel(pc
                                                              const uint64_t *__restrict__ hbits,
                                                              const uint32_t *__restrict__ norms, const pcl_pair *pairs,
                                                              uint64_t npairs, const unsigned long long *d_n,
-                                                             pcl_record *out) {
+                                                             pcl_record *out, unsigned long long *stats) {
     constexpr int N = 64 * NW;
     const Geo g = make_geo(prm);
     const int S = g.S, NH = halo_side(N, S), NWH = halo_words(N, S), K = 2 * S + 1, KK = K * K;
@@ -172,6 +197,12 @@ __global__ void __launch_bounds__(kThreads, NW >= 8 ? 2 : 4) halo_pair_kernel(pc
     uint64_t *sh = sa + (size_t)N * SA;                         // [NH][SH]
     uint32_t *sn = reinterpret_cast<uint32_t *>(sh + (size_t)NH * SH);  // [K*K]
     Best *wb = reinterpret_cast<Best *>(sn + ((KK + 3) & ~3));  // [warps]
+    unsigned long long *order = reinterpret_cast<unsigned long long *>(wb + kThreads / 32);  // [1024] sort keys
+    unsigned long long *bestcn = order + 1024;                  // best (c << 32 | n) so far
+    uint32_t *hbd = reinterpret_cast<uint32_t *>(bestcn + 1);   // [2 NH]: hrow, hcol of B
+    uint32_t *rhb = hbd + 2 * NH, *chb = rhb + K;               // [K] Rh(dy), [K] Ch(dx)
+    uint32_t *ntasks_done = chb + K;                            // [1]
+    uint16_t *prA = reinterpret_cast<uint16_t *>(ntasks_done + 1);  // [2N]: A's row, column counts
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (d_n && *d_n < npairs) npairs = *d_n;
     for (uint64_t pid = blockIdx.x; pid < npairs; pid += gridDim.x) {
@@ -195,17 +226,57 @@ __global__ void __launch_bounds__(kThreads, NW >= 8 ? 2 : 4) halo_pair_kernel(pc
             const int row = t / RW, k = t % RW;
             sh[row * SH + k] = k < NWH ? __ldg(gh + (size_t)row * NWH + k) : 0ull;
         }
-        for (int t = threadIdx.x; t < KK; t += blockDim.x) sn[t] = __ldg(norms + (size_t)pr.b * KK + t);
+        const uint32_t *gn = norms + (size_t)pr.b * norms_stride(N, S);
+        for (int t = threadIdx.x; t < KK; t += blockDim.x) sn[t] = __ldg(gn + t);
+        for (int t = threadIdx.x; t < 2 * NH; t += blockDim.x) hbd[t] = __ldg(gn + KK + t);
+        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) prA[t] = __ldg(A.prof + (size_t)pr.a * 2 * N + t);
+        if (threadIdx.x == 0) {
+            *bestcn = 0ull;
+            *ntasks_done = 0u;
+        }
         __syncthreads();
         const uint64_t pa = A.pop[pr.a];
+        // Upper bounds of c(s): A's row y meets halo row y - dy + S in at most
+        // min(r_A(y), hrow) ones, so c(dx, dy) <= Rh(dy) = sum_y min(r_A(y),
+        // hrow(y - dy + S)), and c(dx, dy) <= Ch(dx) over the columns; with the
+        // moved-window count n_B(s), sim(s) <= min(Rh, Ch) / sqrt(|A| n_B(s)).
+        for (int v = warp; v < 2 * K; v += nwarps) {
+            const bool col = v >= K;
+            const int d = (col ? v - K : v) - S;
+            const uint16_t *pa_ = prA + (col ? N : 0);
+            const uint32_t *hb_ = hbd + (col ? NH : 0);
+            uint32_t sum = 0;
+            for (int y = lane; y < N; y += 32) sum += min((uint32_t)pa_[y], hb_[y - d + S]);
+            sum = __reduce_add_sync(0xffffffffu, sum);
+            if (lane == 0) (col ? chb : rhb)[d + S] = sum;
+        }
+        __syncthreads();
         Best best{0, 0, 0, 0, false};
         // warp task: (dy, 8 consecutive sd = S - dx starting at a multiple of
         // 8); lanes take rows y and count the 8 shifts from registers as
         // 32-bit words: A's word w lines up with halo bits [32 w + sd, +32),
         // which start in halo word w + sd / 32, the same word for the 8
         // shifts of a task
-        const int nch = (2 * S) / 8 + 1;
-        for (int task = warp; task < K * nch; task += nwarps) {
+        const int nch = (2 * S) / 8 + 1, ntask = K * nch;
+        // a task can be skipped when every shift's bound is below the best
+        // similarity found so far, (cb, nb): U^2 nb < cb^2 n_B(s), exactly in
+        // integers (U^2 n < 2^54 up to 512^2); not for an empty A (sim 1
+        // for an empty window)
+        auto prunable = [&](int task, uint32_t cb, uint32_t nb) -> bool {
+            if (pa == 0 || cb == 0) return false;
+            const int dy = task / nch - S, sd0 = (task % nch) * 8;
+            for (int u = 0; u < 8; ++u) {
+                const int sd = sd0 + u;
+                if (sd > 2 * S) break;
+                const int dx = S - sd;
+                const uint32_t n = sn[(dy + S) * K + dx + S];
+                if (n == 0) continue;  // c = 0 there: sim 0 < the best
+                const uint64_t U = min(rhb[dy + S], chb[dx + S]);
+                if (U * U * nb >= (uint64_t)cb * cb * n) return false;
+            }
+            return true;
+        };
+        auto eval_task = [&](int task) {
             const int dy = task / nch - S, sd0 = (task % nch) * 8;
             const int qq = sd0 >> 5, rb = sd0 & 31;  // sd = 32 qq + rb + u, rb + u <= 31
             uint32_t cnt[8];
@@ -242,10 +313,68 @@ __global__ void __launch_bounds__(kThreads, NW >= 8 ? 2 : 4) halo_pair_kernel(pc
                     if (before(cand, best, pa)) best = cand;
                 }
             }
+        };
+        // best first: tasks sorted by their largest bound of U^2 / n_B (float
+        // keys, descending; ties by task index), bitonic sort in shared memory;
+        // the keys only order the work, the skip test above is exact
+        int nsort = 32;
+        while (nsort < ntask) nsort <<= 1;
+        for (int t = threadIdx.x; t < nsort; t += blockDim.x) {
+            unsigned long long key = 0ull;
+            if (t < ntask) {
+                const int dy = t / nch - S, sd0 = (t % nch) * 8;
+                float kb = 0.0f;
+                for (int u = 0; u < 8 && sd0 + u <= 2 * S; ++u) {
+                    const int dx = S - (sd0 + u);
+                    const uint32_t n = sn[(dy + S) * K + dx + S];
+                    const float U = (float)min(rhb[dy + S], chb[dx + S]);
+                    if (n) kb = fmaxf(kb, U * U / (float)n);
+                }
+                key = ((unsigned long long)__float_as_uint(kb) << 32) | (0xffffffffu - (uint32_t)t);
+            }
+            order[t] = key;
+        }
+        __syncthreads();
+        for (int k = 2; k <= nsort; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < nsort; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long x = order[i], y = order[l];
+                        if (((i & k) == 0) ? (x < y) : (x > y)) {
+                            order[i] = y;
+                            order[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int q = warp; q < ntask; q += nwarps) {
+            const int task = (int)(0xffffffffu - (uint32_t)order[q]);
+            const unsigned long long bc =
+                __shfl_sync(0xffffffffu, *reinterpret_cast<volatile unsigned long long *>(bestcn), 0);
+            if (prunable(task, (uint32_t)(bc >> 32), (uint32_t)bc)) continue;  // warp-uniform
+            eval_task(task);
+            if (lane == 0) {
+                atomicAdd(ntasks_done, 1u);
+                if (best.valid && best.c > 0 && best.n > 0) {  // raise the shared best to this warp's
+                    unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(bestcn), seen;
+                    do {
+                        seen = old;
+                        const uint32_t c0 = (uint32_t)(seen >> 32), n0 = (uint32_t)seen;
+                        if (c0 && (uint64_t)best.c * best.c * n0 <= (uint64_t)c0 * c0 * best.n) break;
+                        old = atomicCAS(bestcn, seen, ((unsigned long long)best.c << 32) | best.n);
+                    } while (old != seen);
+                }
+            }
         }
         if (lane == 0) wb[warp] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
+            if (stats) {
+                atomicAdd(stats + 2, (unsigned long long)*ntasks_done);
+                atomicAdd(stats + 3, (unsigned long long)ntask);
+            }
             Best b = wb[0];
             for (int w = 1; w < nwarps; ++w)
                 if (before(wb[w], b, pa)) b = wb[w];
@@ -283,13 +412,14 @@ size_t raster_smem(const Geo &g) {
 size_t pair_smem(const Geo &g) {
     const int NH = halo_side(g.N, g.S), NWH = halo_words(g.N, g.S), K = 2 * g.S + 1;
     return 8ull * g.N * a_stride(g.nw) + 8ull * NH * h_stride(NWH) + 4ull * (((size_t)K * K + 3) & ~size_t(3)) +
-           sizeof(Best) * (kThreads / 32);
+           sizeof(Best) * (kThreads / 32) + 8ull * 1024 + 8 + 4ull * (2 * NH + 2 * K + 1) + 2ull * 2 * g.N + 16;
 }
 
 template <int NW>
 cudaError_t launch_pair(const pcl_params &prm, const Geo &g, const pcl_clipset &a, const pcl_clipset &b,
                         const uint64_t *hb, const uint32_t *nb, const pcl_pair *pairs, uint64_t n,
-                        const unsigned long long *d_n, pcl_record *out, int num_sms, cudaStream_t st) {
+                        const unsigned long long *d_n, pcl_record *out, int num_sms, unsigned long long *stats,
+                        cudaStream_t st) {
     const size_t sm = pair_smem(g);
     cudaError_t e = cudaFuncSetAttribute(halo_pair_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -297,7 +427,8 @@ cudaError_t launch_pair(const pcl_params &prm, const Geo &g, const pcl_clipset &
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_pair_kernel<NW>, kThreads, sm);
     if (e != cudaSuccess) return e;
     const uint64_t cap = (uint64_t)num_sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    halo_pair_kernel<NW><<<(unsigned)(n < cap ? n : cap), kThreads, sm, st>>>(prm, a, b, hb, nb, pairs, n, d_n, out);
+    halo_pair_kernel<NW><<<(unsigned)(n < cap ? n : cap), kThreads, sm, st>>>(prm, a, b, hb, nb, pairs, n, d_n, out,
+                                                                             stats);
     return cudaGetLastError();
 }
 
@@ -321,9 +452,8 @@ pcl_status pcl_halo_sizes_get(const pcl_params *P, uint32_t n_clips, uint64_t *h
     if (pcl_params_validate(P) != PCL_OK || !hbits_bytes || !norms_bytes) return PCL_ERR_INVALID;
     const Geo g = make_geo(*P);
     if (!halo_geometry_ok(g)) return PCL_ERR_UNSUPPORTED;
-    const uint64_t K = 2ull * g.S + 1;
     *hbits_bytes = 8ull * n_clips * halo_side(g.N, g.S) * halo_words(g.N, g.S);
-    *norms_bytes = 4ull * n_clips * K * K;
+    *norms_bytes = 4ull * n_clips * (uint64_t)norms_stride(g.N, g.S);
     return PCL_OK;
 }
 
@@ -359,16 +489,20 @@ pcl_status pcl_match_halo(pcl_ctx *ctx, const pcl_params *P, const pcl_clipset *
     const Geo g = make_geo(*P);
     if (!halo_geometry_ok(g)) return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_match_halo: needs S <= 32 and S <= N/2");
     if (!a || !b || (n && (!d_pairs || !d_out || !d_hbits_b || !d_norms_b)) ||
-        (a->n_clips && (!a->bits || !a->pop)))
+        (a->n_clips && (!a->bits || !a->pop || !a->prof)))
         return fail(ctx, PCL_ERR_INVALID, "pcl_match_halo: NULL buffer");
     if (n == 0) return PCL_OK;
     const auto *dn = reinterpret_cast<const unsigned long long *>(d_n);
     cudaStream_t st = (cudaStream_t)stream;
     switch (g.nw) {
-        case 1: e = launch_pair<1>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
-        case 2: e = launch_pair<2>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
-        case 4: e = launch_pair<4>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
-        case 8: e = launch_pair<8>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms, st); break;
+        case 1: e = launch_pair<1>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms,
+                                       ctx->d_stats, st); break;
+        case 2: e = launch_pair<2>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms,
+                                       ctx->d_stats, st); break;
+        case 4: e = launch_pair<4>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms,
+                                       ctx->d_stats, st); break;
+        case 8: e = launch_pair<8>(*P, g, *a, *b, d_hbits_b, d_norms_b, d_pairs, n, dn, d_out, ctx->num_sms,
+                                       ctx->d_stats, st); break;
         default: return fail(ctx, PCL_ERR_UNSUPPORTED, "pcl_match_halo: raster side");
     }
     return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "halo pair kernel");

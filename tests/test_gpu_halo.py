@@ -119,3 +119,32 @@ def test_halo_pair_count_on_the_device(ctx, torch_cuda):
     o = oracle.ClipSet(wl, halo=True).match(pairs[:31], oracle.MODE_COSINE_HALO)
     _compare(g[:31], o)
     assert (g[31:]["flags"] == 0).all() and (g[31:]["a"] == 0).all()  # not written
+
+
+def test_halo_bounds_skip_groups_of_shifts(ctx, torch_cuda):
+    """The pair kernel skips the groups of shifts whose similarity bound is
+    below the best found: on same-seed pairs part of the window is counted,
+    with an empty representative every group is (no bound applies), and the
+    records stay the oracle's."""
+    import paper_2512_13133_gb300 as pcl
+    W = 1024
+    wl = synth.generate(41, n_clips=80, n_seeds=8, n_copies=56, window_dbu=W, margin_dbu=64,
+                        min_rects=5, max_rects=40, halo_dbu=64)
+    clips = [wl.clip(i).tolist() for i in range(wl.n)] + [[]]
+    wl = synth.Workload(wl.name, W, 4, 64, *_offsets(clips), np.r_[wl.label, -1].astype(np.int32))
+    P, cs, hb, nb = _gpu(ctx, wl)
+    S = 16
+    groups = (2 * S + 1) * ((2 * S) // 8 + 1)
+    lab = wl.label
+    same = np.array([(i, j) for i in range(wl.n) for j in range(wl.n)
+                     if i != j and lab[i] >= 0 and lab[i] == lab[j]], dtype=np.int64)[:60]
+    pcl.pcl_stats_get(ctx, reset=True, kernel="halo")
+    g = _match(ctx, torch_cuda, P, cs, hb, nb, same)
+    ev, tot = pcl.pcl_stats_get(ctx, reset=True, kernel="halo")
+    assert tot == len(same) * groups and 0 < ev < 0.6 * tot
+    o = oracle.ClipSet(wl, halo=True).match(same, oracle.MODE_COSINE_HALO)
+    _compare(g, o)
+    empty = wl.n - 1
+    g = _match(ctx, torch_cuda, P, cs, hb, nb, np.array([[empty, 3], [empty, 7]]))
+    ev, tot = pcl.pcl_stats_get(ctx, reset=True, kernel="halo")
+    assert ev == tot == 2 * groups
