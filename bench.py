@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--topo-clips", type=int, default=1_000_000,
                     help="clips of the topological pre-screen recall measurement (0: skip)")
     ap.add_argument("--no-next", action="store_true", help="skip re-extraction, GPU surprisal and the coarse loop")
-    ap.add_argument("--only", default="", choices=["", "edge", "band", "fft", "tc", "exact", "halo"],
+    ap.add_argument("--only", default="", choices=["", "edge", "band", "fft", "tc", "exact", "halo", "scan"],
                     help="time one stage alone with only its buffers (single-kernel profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision-sample", type=int, default=100_000,
@@ -1315,7 +1315,8 @@ def run_only(args):
     (the command ncu captures of a single kernel run): edge screen, cosine
     band join, FFT engine on the same-seed list, the tensor-core engine
     (FP16) on the dense 32-member list, the exact window scan of 512^2
-    rasters on the same-seed list of a 10,000-clip set (gates off), or
+    rasters on the same-seed list of a 10,000-clip set (gates off), the
+    exact-scan engine on the same-seed list of the workload (gates off), or
     re-extraction on the same-seed list of a set with halo.  Prints one JSON
     line with the mean CUDA-event time of the timed launches."""
     import torch
@@ -1331,9 +1332,9 @@ def run_only(args):
         wl = workload(args.config, args.seed + 400, args.clips, halo_dbu=synth.PRESETS[args.config]["margin_dbu"])
     else:
         wl = workload(args.config, args.seed, args.clips)
-    eng = pcl.ENGINE_TC_DIRECT if args.only == "tc" else pcl.ENGINE_FFT_PCM
+    eng = {"tc": pcl.ENGINE_TC_DIRECT, "scan": pcl.ENGINE_EXACT_SCAN}.get(args.only, pcl.ENGINE_FFT_PCM)
     P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN, TOL, cos_engine=eng,
-                   flags=pcl.P_NO_GATES if args.only in ("fft", "tc", "exact") else 0)
+                   flags=pcl.P_NO_GATES if args.only in ("fft", "tc", "exact", "scan") else 0)
     ctx = pcl.Context(0)
     cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=args.only == "fft")
     pcl.pcl_rasterize(ctx, P, cs)
@@ -1348,7 +1349,7 @@ def run_only(args):
         if args.only == "fft":
             pcl.pcl_spectra(ctx, P, cs)
             lst = same_seed_pairs(wl)
-        elif args.only in ("exact", "halo"):
+        elif args.only in ("exact", "halo", "scan"):
             lst = same_seed_pairs(wl)
         else:
             rng = np.random.default_rng(5)

@@ -26,6 +26,7 @@
 // chosen shift fall back to an exact popcount scan of the whole window.
 #include <climits>
 
+#include "exact_dev.cuh"
 #include "fft_dev.cuh"
 
 namespace pcl {
@@ -33,6 +34,7 @@ namespace pcl {
 namespace {
 
 using namespace fft_dev;
+using namespace exact_dev;
 
 // ---------------------------------------------------------------- forward
 template <int P>

@@ -13,6 +13,7 @@
 // run their items' gates, and the whole warp evaluates the survivors.  The register DFT radix (2 or 4) and the number
 // of CTAs per SM are tuning parameters (chosen by the autotuner).
 #include "edge_dev.cuh"
+#include "exact_dev.cuh"
 #include "fft_dev.cuh"
 
 namespace pcl {
@@ -20,6 +21,7 @@ namespace pcl {
 namespace {
 
 using namespace fft_dev;
+using namespace exact_dev;
 using namespace edge_dev;
 
 constexpr int kMaxClasses = 4;
