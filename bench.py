@@ -107,10 +107,10 @@ TRAFFIC = {
                              "adc2c8cb55cdf1852c51c72423a8c5db0fb50baece80cf4b0416d36c2b505b4f"},
                  "bytes": 188.67e6 + 3.81e6},
     "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
-                             "6c6ce5615f6c402501f1e80cd10a1ffd5aff917c0e1f4532fb8fd46b90b7a3fa",
+                             "177f4ab710f11721ca4eafa1eb5504eab2340ddff890639dd517e226bbcea14a",
                              "paper_2512_13133_gb300/csrc/fft_dev.cuh":
-                             "ca1d5f0ece6d2e027523f3670de2c95b26f1b59b303a044168b7b3b5edb999b5"},
-                 "bytes_per_pair": (21.09e9 + 6.04e6) / 56470},
+                             "4d9f3af534542246324fde57ec52870a89fd65b7e26992bfb3de8f32547de133"},
+                 "bytes_per_pair": (21.04e9 + 6.18e6) / 56470},
 }
 
 
