@@ -331,8 +331,10 @@ pcl_status pcl_candidates_cosine_noalloc(pcl_ctx *ctx, const pcl_params *P, cons
    pixels; the L-shaped edge of the window, the row dy = S and the column
    dx = S, is counted with popcounts): pairs are grouped by representative
    (a list sorted by a, b runs fastest), no phase-correlation surface is formed
-   (pcm fields 0), and the engine covers (N, S) = (64, 4), (128, 8) and
-   (256, 16) with shift_rule = EXACT_ARGMAX (else PCL_ERR_UNSUPPORTED).  A
+   (pcm fields 0), and the engine covers N = 64, 128 and 256 with any
+   S <= N/16 (the kernel of each size correlates the window S = N/16 and the
+   argmax keeps the marker's shifts) and shift_rule = EXACT_ARGMAX (else
+   PCL_ERR_UNSUPPORTED).  A
    device-side wait that runs out is reported by pcl_device_error.
    With cos_engine = PCL_ENGINE_XYSEP the shift is not searched but
    synthesised by the XY-separation interval competition of Sec. 3.2.1 (2):
@@ -511,8 +513,8 @@ pcl_status pcl_match_mixed(pcl_ctx *ctx, const pcl_params *params, pcl_clipset *
    Timestamps are steady-clock nanoseconds: submit, and device completion as
    stamped by a host callback on the request's stream.  One host thread at a
    time per server.  Errors: PCL_ERR_INVALID, PCL_ERR_UNSUPPORTED (COSINE
-   with S > N/16; the FFT engine with N > 256; the tensor-core engine outside
-   (N, S) = (64, 4), (128, 8), (256, 16); a shift rule other than
+   with S > N/16; the FFT engine with N > 256; the tensor-core engine with
+   N = 512; a shift rule other than
    EXACT_ARGMAX for the tensor-core engine or a 512^2 px class; any other
    cosine engine), PCL_ERR_OOM, PCL_ERR_CUDA, PCL_ERR_BUSY (not admitted). */
 typedef struct pcl_server pcl_server;

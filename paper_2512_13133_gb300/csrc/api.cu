@@ -328,7 +328,7 @@ pcl_status pcl_match_pairs(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, pcl
         P->cos_engine == PCL_ENGINE_TC_DIRECT_BF16) {
         if (!tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
             return fail(ctx, PCL_ERR_UNSUPPORTED,
-                        "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax%s%lld");
+                        "tensor-core engine covers N = 64, 128, 256 with S <= N/16, exact argmax%s%lld");
         if (n == 0) return PCL_OK;
         if ((s = ensure_ws(ctx, tc_workspace(n)))) return s;
         e = launch_tc(*P, *a, *b, d_pairs, n, dn, d_out, ctx->ws, ctx->ws_bytes, ctx->num_sms, ctx->d_err,

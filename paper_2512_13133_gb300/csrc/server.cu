@@ -277,7 +277,7 @@ pcl_status pcl_server_create_classes(pcl_ctx *ctx, const pcl_params *params, con
             } else if (tc) {
                 if (!pcl::tc_supported(g) || P->shift_rule != PCL_SHIFT_EXACT_ARGMAX)
                     return fail(ctx, PCL_ERR_UNSUPPORTED,
-                                who + "tensor-core engine covers (N, S) = (64, 4), (128, 8), (256, 16), exact argmax");
+                                who + "tensor-core engine covers N = 64, 128, 256 with S <= N/16, exact argmax");
                 engine = kTc;
             } else {
                 if (P->cos_engine != PCL_ENGINE_FFT_PCM)

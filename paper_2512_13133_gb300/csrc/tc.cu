@@ -732,7 +732,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int b = col / nbp, n = col - b * nbp;
                     const int dx = -S + gg + 16 * (b % C::NBX);
                     const int dy = -S + rr + 8 * (b / C::NBX);
-                    const bool valid = dx <= S;
+                    // the kernel's window is S = N/16; a smaller marker (g.S < S)
+                    // keeps the shifts within it
+                    const bool valid = dx <= S && abs(dx) <= g.S && abs(dy) <= g.S;
                     const unsigned long long k =
                         warp_max64(valid ? shift_key((uint32_t)__uint_as_float(v[q]), dx, dy, S) : 0ull);
                     if (lane == 0 && n < (int)item.count) atomicMax(keys + n, k);
@@ -762,12 +764,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bcol = __reduce_add_sync(0xffffffffu, bcol);
                 const uint64_t *bbits = B.bits + (size_t)bi * N * NW;
                 unsigned long long k = kc;
-                if (brow >= cstar) {
+                // the rest lies at |dy| = S or |dx| = S: outside a smaller window
+                if (g.S == S && brow >= cstar) {
                     const unsigned long long r = rest_row_key<S, NW, C::DYL>(abits, bbits, lane);
                     k = r > k ? r : k;
                 }
                 if constexpr (C::COL) {
-                    if (bcol >= cstar) {
+                    if (g.S == S && bcol >= cstar) {
                         const unsigned long long r = rest_col_key<S, NW, C::DXL>(abits, bbits, lane);
                         k = r > k ? r : k;
                     }
@@ -916,9 +919,9 @@ __global__ void tc_items_kernel(const uint32_t *head, const uint32_t *hpos, cons
 
 }  // namespace
 
-bool tc_supported(const Geo &g) {
-    return (g.N == 64 && g.S == 4) || (g.N == 128 && g.S == 8) || (g.N == 256 && g.S == 16);
-}
+// rasters of 64^2, 128^2 or 256^2 px with S <= N/16: the kernel of that size
+// (window S = N/16) keeps the shifts of the smaller window
+bool tc_supported(const Geo &g) { return (g.N == 64 || g.N == 128 || g.N == 256) && g.S >= 0 && g.S <= g.N / 16; }
 
 size_t tc_workspace(uint64_t n) { return 4 * (3 * (size_t)n + 8) + sizeof(TcItem) * (size_t)(n + 1) + 256; }
 
@@ -967,7 +970,7 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     const int op = prm.cos_engine == PCL_ENGINE_TC_DIRECT_FP8   ? kOpE4M3
                    : prm.cos_engine == PCL_ENGINE_TC_DIRECT_BF16 ? kOpBF16
                                                                  : kOpF16;
-    const int NB = g.S == 4 ? members_of<4, 1>() : g.S == 8 ? members_of<8, 2>() : members_of<16, 4>();
+    const int NB = g.N == 64 ? members_of<4, 1>() : g.N == 128 ? members_of<8, 2>() : members_of<16, 4>();
     char *w = static_cast<char *>(ws);
     uint32_t *keep = reinterpret_cast<uint32_t *>(w);
     uint32_t *pos = keep + n;           // n + 1
@@ -985,9 +988,9 @@ cudaError_t launch_tc(const pcl_params &prm, const pcl_clipset &a, const pcl_cli
     tc_seg_kernel<<<num_sms * 4, 256, 0, st>>>(pairs, surv, pos + n, keep);
     tc_items_kernel<<<num_sms * 4, 256, 0, st>>>(keep, nullptr, pos + n, NB, items, n_items, (uint32_t)n + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    switch (g.S) {
-        case 4: return launch_corr_op<4, 1>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
-        case 8: return launch_corr_op<8, 2>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+    switch (g.N) {
+        case 64: return launch_corr_op<4, 1>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
+        case 128: return launch_corr_op<8, 2>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
         default: return launch_corr_op<16, 4>(op, prm, a, b, pairs, surv, items, n_items, out, num_sms, d_err, wait_ns, st);
     }
 }

@@ -110,7 +110,7 @@ def test_tc_rejects_uncovered_geometry(torch_cuda):
     import paper_2512_13133_gb300 as pcl
     wl = synth.preset("scale", seed=9, n_clips=20, n_seeds=4, n_copies=10)
     ctx = pcl.Context(0)
-    P = pcl.params(wl.window_dbu, wl.pitch_dbu, 32, cos_engine=pcl.ENGINE_TC_DIRECT)  # N = 256, S = 8
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, 80, cos_engine=pcl.ENGINE_TC_DIRECT)  # N = 256, S = 20 > N/16
     cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects)
     pcl.pcl_rasterize(ctx, P, cs)
     tp = torch_cuda.from_numpy(np.array([[0, 1]], dtype=np.int32)).cuda()
@@ -151,4 +151,38 @@ def test_tc_wait_limit_times_out_and_context_recovers(torch_cuda):
     for f in ("dx_dbu", "dy_dbu"):
         np.testing.assert_array_equal(g[f], o[f])
     np.testing.assert_array_equal(g["score"].astype(np.int64), o["score"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,S", [(64, 2), (128, 5), (256, 7), (256, 11), (256, 0)])
+@pytest.mark.parametrize("engine", ["f16", "e4m3"])
+def test_tc_engine_smaller_markers(torch_cuda, N, S, engine):
+    """Markers below N/16: the kernel of the size correlates its full window
+    and the argmax keeps the shifts |dx|, |dy| <= S; shift, overlap and
+    decision equal the oracle's at that marker (and the FFT engine's)."""
+    import paper_2512_13133_gb300 as pcl
+    kind = {64: "n64", 128: "n128", 256: "n256"}[N]
+    wl = _workload(kind)
+    M = S * wl.pitch_dbu
+    rng = np.random.default_rng(N + S)
+    pairs = _pairs(wl, rng, 400)
+    eng = {"f16": pcl.ENGINE_TC_DIRECT, "e4m3": pcl.ENGINE_TC_DIRECT_FP8}[engine]
+    ctx = pcl.Context(0)
+    Pt = pcl.params(wl.window_dbu, wl.pitch_dbu, M, cos_engine=eng, flags=pcl.P_NO_GATES)
+    Pf = pcl.params(wl.window_dbu, wl.pitch_dbu, M, flags=pcl.P_NO_GATES)
+    cs = pcl.alloc_clipset(Pf, wl.rect_off, wl.rects)
+    pcl.pcl_rasterize(ctx, Pf, cs)
+    tp = torch_cuda.from_numpy(pairs.astype(np.int32)).cuda()
+    gt = pcl.records_to_numpy(pcl.match(ctx, Pt, pcl.MODE_COSINE, cs, cs, tp))
+    assert pcl.pcl_device_error(ctx) == 0
+    o = oracle.ClipSet(wl, marker_dbu=M).match(pairs, oracle.MODE_COSINE, use_gates=False)
+    assert np.abs(gt["dx_dbu"]).max() <= M and np.abs(gt["dy_dbu"]).max() <= M
+    for f in ("dx_dbu", "dy_dbu", "pass_"):
+        np.testing.assert_array_equal(gt[f], o[f])
+    np.testing.assert_array_equal(gt["score"].astype(np.int64), o["score"])
+    assert np.abs(gt["sim"].astype(np.float64) - o["sim"]).max() <= 1e-5
+    if S > 0:
+        gf = pcl.records_to_numpy(pcl.match(ctx, Pf, pcl.MODE_COSINE, cs, cs, tp))
+        for f in ("dx_dbu", "dy_dbu", "score", "pass_"):
+            np.testing.assert_array_equal(gt[f], gf[f])
     ctx.close()
