@@ -272,9 +272,10 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
    the union of the shards' outputs is exactly pcl_candidates' output and the
    shards' gate counts sum to its counts.  The subsets depend on clip indices
    only (every caller holds the whole clip set, in the same order):
-     COSINE  pairs (a, b) with (a + b) mod S = s (the band join still walks
-             every band, testing only its shard's members; the G1 count is
-             the shard's pair count minus the pairs it enumerated);
+     COSINE  pairs a < b with a mod S = s (the band join walks the
+             two-sided area band of the representatives a = s, s + S, ...
+             only, keeping the members b > a; the G1 count is the shard's
+             pair count minus the pairs it enumerated);
      EDGE    the tiles s, s + S, s + 2S, ... of the screen's tile numbering
              (32 row clips i x 256 column clips j with i < j, numbered column
              block after column block: column block y holds row tiles

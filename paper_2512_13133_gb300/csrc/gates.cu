@@ -19,9 +19,12 @@
 // (p, end_p) with end_p = #{clips with area <= floor((den^2 a_p - 1)/num^2)}.
 // Warps take positions p from a global counter and test G3 and G2 on every
 // band member with the whole warp.  A shard s of S (several GPUs sharing one
-// self-join) keeps the pairs (a, b) with (a + b) mod S = s: a partition that
-// depends on the clip indices only, not on the order the counting sort gives
-// clips of equal area.
+// self-join) keeps the pairs a < b with a mod S = s: its warps take the
+// representatives a = s, s + S, ... and walk their two-sided band (the clips
+// whose areas pass G1 with a's, found from the counting sort's bucket
+// offsets), keeping the members b > a -- a partition that depends on the clip
+// indices only, not on the order the counting sort gives clips of equal
+// area, and each shard walks 1/S of the representatives.
 #include <climits>
 
 #include "gates.cuh"
@@ -118,18 +121,25 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
     const int nb2 = g.nb * g.nb, words = nb2 / 2;
     const uint64_t num2 = (uint64_t)prm.cos_num * prm.cos_num, den2 = (uint64_t)prm.cos_den * prm.cos_den;
     unsigned long long kept = 0, g2 = 0, g3 = 0;
+    const bool sharded = n_shards > 1;
     for (;;) {
         uint32_t p = 0;
         if (lane == 0) p = atomicAdd(next_pos, 1u);
         p = __shfl_sync(0xffffffffu, p, 0);
-        if (p >= n) break;
-        const uint32_t a = order[p];
-        const uint32_t kp = spop[p];
+        // the representative: the clip at sorted position p, or with shards
+        // the clip of index shard + p S
+        const uint64_t ai = sharded ? (uint64_t)shard + (uint64_t)p * n_shards : p;
+        if (ai >= n) break;
+        const uint32_t a = sharded ? (uint32_t)ai : order[p];
+        const uint32_t kp = sharded ? cs.pop[a] : spop[p];
         const uint64_t pa = kp % V;
         const uint32_t base = kp - (uint32_t)pa;  // first key of the class
         uint64_t vmax = pa == 0 ? 0 : (den2 * pa - 1) / num2;
         if (vmax > vmax_all) vmax = vmax_all;
         const uint32_t end = cum[base + vmax + 1];
+        // forward band from p + 1, or the two-sided band from the smallest
+        // area that passes G1 with pa (num^2 pa < den^2 pb)
+        const uint32_t start = sharded ? cum[base + (pa == 0 ? 0 : (num2 * pa) / den2 + 1)] : p + 1;
         const uint32_t *cwa = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)a * 2 * nb2);
         uint32_t ca[WPL], da[WPL];
 #pragma unroll
@@ -139,9 +149,9 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             da[c] = t < words ? cwa[words + t] : 0u;
         }
         if (pa == 0) {  // the band holds the other empty clips only: similar by definition
-            for (uint32_t q0 = p + 1; q0 < end; q0 += 32) {
+            for (uint32_t q0 = start; q0 < end; q0 += 32) {
                 const uint32_t bq = q0 + lane < end ? order[q0 + lane] : 0u;
-                const bool v = q0 + lane < end && ((uint64_t)a + bq) % n_shards == shard;
+                const bool v = q0 + lane < end && (!sharded || bq > a);
                 const unsigned m = __ballot_sync(0xffffffffu, v);
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(m));
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
         // band members 32 at a time: lane l sets up member q0 + l (index,
         // thresholds; members of a non-empty representative are non-empty),
         // then the warp tests them one after the other
-        for (uint32_t q0 = p + 1; q0 < end; q0 += 32) {
+        for (uint32_t q0 = start; q0 < end; q0 += 32) {
             const uint32_t q = q0 + lane;
             uint32_t b = 0;
             int tA = 0, tB = 0;  // areas are below 2^31, so are the thresholds (clamped below)
@@ -167,8 +177,8 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                 tB = (int)max((int64_t)pb - um, (int64_t)INT_MIN);
             }
             int cnt = (int)min(32u, end - q0);
-            if (n_shards > 1) {  // this shard's members only, moved to the low lanes in order
-                const unsigned mem = __ballot_sync(0xffffffffu, q < end && ((uint64_t)a + b) % n_shards == shard);
+            if (sharded) {  // the members b > a only, moved to the low lanes in order
+                const unsigned mem = __ballot_sync(0xffffffffu, q < end && b > a);
                 const int src = nth_set_bit(mem, lane);  // lane of this lane's member
                 const int from = src >= 0 ? src : lane;
                 b = __shfl_sync(0xffffffffu, b, from);
@@ -278,15 +288,11 @@ size_t band_join_workspace(const Geo &g, uint32_t n, bool topo) {
     return 4 * (2 * Vt + (topo ? 3 : 2) * (size_t)n) + 8 * 16 + 64;
 }
 
-// pairs i < j < n with (i + j) mod S = s: for each i, the j in (i, n) of one residue
+// pairs i < j < n with i mod S = s: n - 1 - i for each such i
 uint64_t shard_pairs(uint64_t n, uint32_t s, uint32_t S) {
     if (S <= 1) return n * (n ? n - 1 : 0) / 2;
-    auto below = [S](uint64_t x, uint64_t r) { return x > r ? (x - r + S - 1) / S : 0; };  // #{j < x : j % S == r}
     uint64_t t = 0;
-    for (uint64_t i = 0; i + 1 < n; ++i) {
-        const uint64_t r = (s + S - i % S) % S;
-        t += below(n, r) - below(i + 1, r);
-    }
+    for (uint64_t i = s; i < n; i += S) t += n - 1 - i;
     return t;
 }
 

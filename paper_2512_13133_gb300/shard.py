@@ -41,12 +41,12 @@ def _tiles_before(by: np.ndarray, nbx: int) -> np.ndarray:
 def pair_shard(pairs, n: int, mode: int, n_shards: int) -> np.ndarray:
     """Shard (0 .. n_shards - 1) that owns each pair (a, b), a != b, of a
     self-join of n clips, as pcl_candidates_shard partitions them: COSINE by
-    (a + b) mod S, EDGE by the screen tile of (min, max) modulo S."""
+    min(a, b) mod S, EDGE by the screen tile of (min, max) modulo S."""
     p = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
     if n_shards == 1:
         return np.zeros(len(p), np.int64)
     if mode == MODE_COSINE:
-        return (p[:, 0] + p[:, 1]) % n_shards
+        return p.min(axis=1) % n_shards
     if mode != MODE_EDGE:
         raise ValueError("mode must be COSINE or EDGE")
     i, j = p.min(axis=1), p.max(axis=1)

@@ -44,7 +44,7 @@ def test_every_pair_in_exactly_one_shard(mode, S):
     assert s.min() >= 0 and s.max() < S
     counts = np.bincount(s, minlength=S)
     assert counts.sum() == n * (n - 1) // 2
-    if S > 1 and mode == shard.MODE_COSINE:  # (a + b) mod S spreads the pairs evenly
+    if S > 1 and mode == shard.MODE_COSINE:  # min(a, b) mod S: shards within n pairs of each other
         assert counts.max() - counts.min() <= n
 
 
