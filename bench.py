@@ -90,9 +90,9 @@ def peaks():
 # DRAM bytes (read + write) per launch of the kernels on the default scale
 # workload, from single-pass ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum) of `bench.py --only edge|band` at 100,000 clips
-# (profiles/dram_scale_100k.md) and of `bench.py --only fft --clips 10000`
-# (profiles/pair_fft_10k.md; the FFT figure is per pair: every pair reads
-# its member's spectrum, so a launch's traffic grows with its pairs).  A
+# and of `bench.py --only fft --clips 10000` (the FFT figure is per pair:
+# every pair reads its member's spectrum, so a launch's traffic grows with
+# its pairs).  A
 # figure counts only while the kernel's sources hash as they did when it was
 # taken; otherwise the bench reports null.
 TRAFFIC = {
