@@ -166,6 +166,19 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
             ca[c] = w < words ? cwa[w] : 0u;
             da[c] = w < words ? cwa[words + w] : 0u;
         }
+        // small rasters (one word of block counts per lane: N <= 128): the
+        // query's profiles in registers for G2, which decides most band pairs
+        uint32_t ar[4] = {0u, 0u, 0u, 0u}, ac[4] = {0u, 0u, 0u, 0u};
+        if constexpr (WPL == 1) {
+            const uint16_t *pq = Q.prof + (size_t)q * 2 * g.N;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < g.N / 32) {
+                    ar[u] = pq[lane + 32 * u];
+                    ac[u] = pq[g.N + lane + 32 * u];
+                }
+            }
+        }
         // members 32 at a time: lane l sets up member q0 + l (index, the
         // thresholds of the exact rule; G1 passes, so neither is clamped),
         // then the warp tests them one after the other
@@ -188,8 +201,18 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
                     ++g3;
                     continue;
                 }
-                if (warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N, g.S,
-                                         (int64_t)pa - tAk, lane)) {
+                bool g2r;
+                if constexpr (WPL == 1) {
+                    extern __shared__ uint16_t g2_scratch[];
+                    uint16_t *sc = g2_scratch + (threadIdx.x >> 5) * 2 * (g.N + 2 * g.S);
+                    const uint16_t *pbk = L.prof + (size_t)bk * 2 * g.N;
+                    g2r = g.N == 64 ? warp_g2_rejects_reg<2>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc)
+                                    : warp_g2_rejects_reg<4>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc);
+                } else {
+                    g2r = warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N,
+                                               g.S, (int64_t)pa - tAk, lane);
+                }
+                if (g2r) {
                     ++g2;
                     continue;
                 }
@@ -257,7 +280,8 @@ cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const
         cross_chunks_kernel<<<(n_ch + 255) / 256, 256, 0, st>>>(beg, endp, nq, n_ch, qlo, cnt);
         scan_items_kernel<<<1, 1024, 0, st>>>(cnt, n_ch, item_off);
         switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
-            case 1: cross_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,
+            case 1: cross_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, Q, L, lib_order,
+                                                                      lib_spop, qorder, qspop,
                                                                       beg, endp, qlo, item_off, n_ch, out, cap,
                                                                       count, local, next_item); break;
             case 4: cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,

@@ -148,6 +148,20 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             ca[c] = t < words ? cwa[t] : 0u;
             da[c] = t < words ? cwa[words + t] : 0u;
         }
+        // small rasters (one word of block counts per lane: N <= 128): the
+        // representative's profiles in registers for G2, which decides most
+        // band pairs there
+        uint32_t ar[4] = {0u, 0u, 0u, 0u}, ac[4] = {0u, 0u, 0u, 0u};
+        if constexpr (WPL == 1) {
+            const uint16_t *pr = cs.prof + (size_t)a * 2 * g.N;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < g.N / 32) {
+                    ar[u] = pr[lane + 32 * u];
+                    ac[u] = pr[g.N + lane + 32 * u];
+                }
+            }
+        }
         if (pa == 0) {  // the band holds the other empty clips only: similar by definition
             for (uint32_t q0 = start; q0 < end; q0 += 32) {
                 const uint32_t bq = q0 + lane < end ? order[q0 + lane] : 0u;
@@ -194,8 +208,18 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                     return;
                 }
                 // G2 with the same threshold (tA = pa - um; never clamped in a band)
-                if (warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N, g.S,
-                                         (int64_t)pa - tAk, lane)) {
+                bool g2r;
+                if constexpr (WPL == 1) {
+                    extern __shared__ uint16_t g2_scratch[];
+                    uint16_t *sc = g2_scratch + (threadIdx.x >> 5) * 2 * (g.N + 2 * g.S);
+                    const uint16_t *pbk = cs.prof + (size_t)bk * 2 * g.N;
+                    g2r = g.N == 64 ? warp_g2_rejects_reg<2>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc)
+                                    : warp_g2_rejects_reg<4>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc);
+                } else {
+                    g2r = warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N,
+                                               g.S, (int64_t)pa - tAk, lane);
+                }
+                if (g2r) {
                     ++g2;
                     return;
                 }
@@ -332,7 +356,8 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     scatter_kernel<<<num_sms * 4, 256, 0, st>>>(k, n, cum, fill, order, spop);
     const uint32_t vall = (uint32_t)g.N * g.N;
     switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
-        case 1: band_join_kernel<1><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
+        case 1: band_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, cs, order, spop, cum, V,
+                                                                                       vall, out, cap, count,
                                                                  local, next_pos, shard, n_shards); break;
         case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
                                                                  local, next_pos, shard, n_shards); break;

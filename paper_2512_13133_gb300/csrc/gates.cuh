@@ -140,6 +140,44 @@ __device__ __forceinline__ bool warp_g2_rejects_smem(const uint16_t *__restrict_
 // shared-memory G2 scratch per warp (u16 elements) for rasters up to N = 512
 constexpr int kG2Scratch = 2 * (512 + 2 * 64);
 
+// G2 for a band walk over small rasters (N = 32 NPL <= 128, where the density
+// bound of 16-px blocks dilated by a block is loose and G2 decides most band
+// pairs): the representative's row and column counts are held in registers
+// for the whole walk (ar, ac: value of index lane + 32 u), the member's are
+// staged per pair in the warp's shared scratch (2 (N + 2S) u16, zero padded by
+// S on both sides).  The same decision as warp_g2_rejects_lite: rejected when
+// the largest row sum or the largest column sum over |d| <= S is <= um.
+template <int NPL>
+__device__ __forceinline__ bool warp_g2_rejects_reg(const uint32_t (&ar)[4], const uint32_t (&ac)[4],
+                                                    const uint16_t *__restrict__ pb, int S, int64_t um, int lane,
+                                                    uint16_t *scratch) {
+    constexpr int N = 32 * NPL;
+    const int L = N + 2 * S;
+    __syncwarp();  // the previous pair's reads of scratch are done
+    for (int k = lane; k < 2 * L; k += 32) {
+        const int ax = k >= L, i = k - ax * L - S;
+        scratch[k] = (i >= 0 && i < N) ? __ldg(pb + ax * N + i) : (uint16_t)0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const uint16_t *Bs = scratch + ax * L + S;  // Bs[k] = prof_B(k) for -S <= k < N + S
+        bool above = false;
+        for (int i = 0; i <= 2 * S && !above; ++i) {
+            const int d = (i & 1) ? (i + 1) >> 1 : -(i >> 1);
+            uint32_t t = 0;
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) t += min(ax ? ac[u] : ar[u], (uint32_t)Bs[lane + 32 * u - d]);
+            above = (int64_t)__reduce_add_sync(0xffffffffu, t) > um;
+        }
+        if (!above) return true;
+    }
+    return false;
+}
+
+// bytes of the per-warp G2 scratch of a 256-thread band walk over N <= 128
+__host__ __device__ inline int band_g2_smem(int N, int S) { return N <= 128 ? 8 * 2 * (N + 2 * S) * 2 : 0; }
+
 // The same decision with every profile value loaded where it is used and no
 // early exit: fewer registers, for callers where G2 is rare and register
 // pressure matters more than its speed.
