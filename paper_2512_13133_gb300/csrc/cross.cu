@@ -167,17 +167,13 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
             da[c] = w < words ? cwa[words + w] : 0u;
         }
         // small rasters (one word of block counts per lane: N <= 128): the
-        // query's profiles in registers for G2, which decides most band pairs
-        uint32_t ar[4] = {0u, 0u, 0u, 0u}, ac[4] = {0u, 0u, 0u, 0u};
+        // query's profiles and their dilated maxima in the warp's scratch for
+        // G2, which decides most band pairs
+        uint16_t *g2s = nullptr;
         if constexpr (WPL == 1) {
-            const uint16_t *pq = Q.prof + (size_t)q * 2 * g.N;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u < g.N / 32) {
-                    ar[u] = pq[lane + 32 * u];
-                    ac[u] = pq[g.N + lane + 32 * u];
-                }
-            }
+            extern __shared__ uint16_t g2_scratch[];
+            g2s = g2_scratch + (threadIdx.x >> 5) * band_g2_warp(g.N, g.S);
+            g2_rep_setup(Q.prof + (size_t)q * 2 * g.N, g.N, g.S, lane, g2s);
         }
         // members 32 at a time: lane l sets up member q0 + l (index, the
         // thresholds of the exact rule; G1 passes, so neither is clamped),
@@ -203,11 +199,8 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
                 }
                 bool g2r;
                 if constexpr (WPL == 1) {
-                    extern __shared__ uint16_t g2_scratch[];
-                    uint16_t *sc = g2_scratch + (threadIdx.x >> 5) * 2 * (g.N + 2 * g.S);
                     const uint16_t *pbk = L.prof + (size_t)bk * 2 * g.N;
-                    g2r = g.N == 64 ? warp_g2_rejects_reg<2>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc)
-                                    : warp_g2_rejects_reg<4>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc);
+                    g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
                 } else {
                     g2r = warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N,
                                                g.S, (int64_t)pa - tAk, lane);

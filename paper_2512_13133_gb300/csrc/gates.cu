@@ -149,18 +149,13 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             da[c] = t < words ? cwa[words + t] : 0u;
         }
         // small rasters (one word of block counts per lane: N <= 128): the
-        // representative's profiles in registers for G2, which decides most
-        // band pairs there
-        uint32_t ar[4] = {0u, 0u, 0u, 0u}, ac[4] = {0u, 0u, 0u, 0u};
+        // representative's profiles and their dilated maxima in the warp's
+        // scratch for G2, which decides most band pairs there
+        uint16_t *g2s = nullptr;
         if constexpr (WPL == 1) {
-            const uint16_t *pr = cs.prof + (size_t)a * 2 * g.N;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u < g.N / 32) {
-                    ar[u] = pr[lane + 32 * u];
-                    ac[u] = pr[g.N + lane + 32 * u];
-                }
-            }
+            extern __shared__ uint16_t g2_scratch[];
+            g2s = g2_scratch + (threadIdx.x >> 5) * band_g2_warp(g.N, g.S);
+            g2_rep_setup(cs.prof + (size_t)a * 2 * g.N, g.N, g.S, lane, g2s);
         }
         if (pa == 0) {  // the band holds the other empty clips only: similar by definition
             for (uint32_t q0 = start; q0 < end; q0 += 32) {
@@ -210,11 +205,8 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                 // G2 with the same threshold (tA = pa - um; never clamped in a band)
                 bool g2r;
                 if constexpr (WPL == 1) {
-                    extern __shared__ uint16_t g2_scratch[];
-                    uint16_t *sc = g2_scratch + (threadIdx.x >> 5) * 2 * (g.N + 2 * g.S);
                     const uint16_t *pbk = cs.prof + (size_t)bk * 2 * g.N;
-                    g2r = g.N == 64 ? warp_g2_rejects_reg<2>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc)
-                                    : warp_g2_rejects_reg<4>(ar, ac, pbk, g.S, (int64_t)pa - tAk, lane, sc);
+                    g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
                 } else {
                     g2r = warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N,
                                                g.S, (int64_t)pa - tAk, lane);

@@ -140,34 +140,56 @@ __device__ __forceinline__ bool warp_g2_rejects_smem(const uint16_t *__restrict_
 // shared-memory G2 scratch per warp (u16 elements) for rasters up to N = 512
 constexpr int kG2Scratch = 2 * (512 + 2 * 64);
 
-// G2 for a band walk over small rasters (N = 32 NPL <= 128, where the density
-// bound of 16-px blocks dilated by a block is loose and G2 decides most band
-// pairs): the representative's row and column counts are held in registers
-// for the whole walk (ar, ac: value of index lane + 32 u), the member's are
-// staged per pair in the warp's shared scratch (2 (N + 2S) u16, zero padded by
-// S on both sides).  The same decision as warp_g2_rejects_lite: rejected when
-// the largest row sum or the largest column sum over |d| <= S is <= um.
-template <int NPL>
-__device__ __forceinline__ bool warp_g2_rejects_reg(const uint32_t (&ar)[4], const uint32_t (&ac)[4],
-                                                    const uint16_t *__restrict__ pb, int S, int64_t um, int lane,
-                                                    uint16_t *scratch) {
-    constexpr int N = 32 * NPL;
-    const int L = N + 2 * S;
-    __syncwarp();  // the previous pair's reads of scratch are done
-    for (int k = lane; k < 2 * L; k += 32) {
-        const int ax = k >= L, i = k - ax * L - S;
-        scratch[k] = (i >= 0 && i < N) ? __ldg(pb + ax * N + i) : (uint16_t)0;
+// G2 for a band walk over small rasters (N <= 128, where the density bound of
+// 16-px blocks dilated by a block is loose and G2 decides most band pairs).
+// Per representative, in the warp's scratch: its row and column counts (As,
+// 2N u16) and their maxima over |d| <= S, the dilated profiles rmax(z) = max
+// r_A(z + d) (Am, 2N u16).  Since each row sum sum_y min(r_A(y), r_B(y - d))
+// is at most sum_z min(rmax(z), r_B(z)), one pass over the member's profiles
+// without shifts decides G2 whenever that bound (or the columns') is <= um;
+// otherwise the member's profiles are staged (Bs, 2 (N + 2S) u16, zero padded
+// by S) and every shift is summed.  The decision is warp_g2_rejects_lite's.
+__device__ __forceinline__ void g2_rep_setup(const uint16_t *__restrict__ pr, int N, int S, int lane, uint16_t *As) {
+    uint16_t *Am = As + 2 * N;
+    __syncwarp();  // the previous representative's reads are done
+    for (int k = lane; k < 2 * N; k += 32) As[k] = __ldg(pr + k);
+    __syncwarp();
+    for (int k = lane; k < 2 * N; k += 32) {
+        const int ax = k >= N, j = k - ax * N, lo = j - S < 0 ? 0 : j - S, hi = j + S >= N ? N - 1 : j + S;
+        uint32_t m = 0;
+        for (int t = lo; t <= hi; ++t) m = max(m, (uint32_t)As[ax * N + t]);
+        Am[k] = (uint16_t)m;
     }
     __syncwarp();
-#pragma unroll
+}
+
+__device__ __forceinline__ bool g2_rejects_small(uint16_t *As, const uint16_t *__restrict__ pb, int N, int S,
+                                                 int64_t um, int lane) {
+    const uint16_t *Am = As + 2 * N;
+    uint16_t *Bs = As + 4 * N;
+    // both dilated bounds in one reduction (each at most N^2 <= 16384)
+    uint32_t tr = 0, tc = 0;
+    for (int j = lane; j < N; j += 32) {
+        tr += min((uint32_t)Am[j], (uint32_t)__ldg(pb + j));
+        tc += min((uint32_t)Am[N + j], (uint32_t)__ldg(pb + N + j));
+    }
+    const uint32_t sr = __reduce_add_sync(0xffffffffu, tr | (tc << 16));
+    if ((int64_t)(sr & 0xffffu) <= um || (int64_t)(sr >> 16) <= um) return true;
+    const int L = N + 2 * S;
+    __syncwarp();  // the previous pair's reads of Bs are done
+    for (int k = lane; k < 2 * L; k += 32) {
+        const int ax = k >= L, i = k - ax * L - S;
+        Bs[k] = (i >= 0 && i < N) ? __ldg(pb + ax * N + i) : (uint16_t)0;
+    }
+    __syncwarp();
     for (int ax = 0; ax < 2; ++ax) {
-        const uint16_t *Bs = scratch + ax * L + S;  // Bs[k] = prof_B(k) for -S <= k < N + S
+        const uint16_t *B = Bs + ax * L + S;  // B[k] = prof_B(k) for -S <= k < N + S
+        const uint16_t *A = As + ax * N;
         bool above = false;
         for (int i = 0; i <= 2 * S && !above; ++i) {
             const int d = (i & 1) ? (i + 1) >> 1 : -(i >> 1);
             uint32_t t = 0;
-#pragma unroll
-            for (int u = 0; u < NPL; ++u) t += min(ax ? ac[u] : ar[u], (uint32_t)Bs[lane + 32 * u - d]);
+            for (int j = lane; j < N; j += 32) t += min((uint32_t)A[j], (uint32_t)B[j - d]);
             above = (int64_t)__reduce_add_sync(0xffffffffu, t) > um;
         }
         if (!above) return true;
@@ -175,8 +197,10 @@ __device__ __forceinline__ bool warp_g2_rejects_reg(const uint32_t (&ar)[4], con
     return false;
 }
 
-// bytes of the per-warp G2 scratch of a 256-thread band walk over N <= 128
-__host__ __device__ inline int band_g2_smem(int N, int S) { return N <= 128 ? 8 * 2 * (N + 2 * S) * 2 : 0; }
+// per-warp G2 scratch (u16) of a band walk over N <= 128: As, Am, then Bs
+__host__ __device__ inline int band_g2_warp(int N, int S) { return 4 * N + 2 * (N + 2 * S); }
+// bytes of that scratch for a 256-thread block
+__host__ __device__ inline int band_g2_smem(int N, int S) { return N <= 128 ? 8 * band_g2_warp(N, S) * 2 : 0; }
 
 // The same decision with every profile value loaded where it is used and no
 // early exit: fewer registers, for callers where G2 is rare and register
