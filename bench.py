@@ -102,10 +102,10 @@ TRAFFIC = {
                               "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
                   "bytes": 1.85e9 + 25.19e6},
     "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
-                             "4e861a2f716a4094c65e1eebb9f9d1677406b28b1febc936393931652685d793",
+                             "dc554a4f79339cd5c7cd35ce946a1b563f687cb35839033eee1dc35e43062f77",
                              "paper_2512_13133_gb300/csrc/gates.cuh":
-                             "adc2c8cb55cdf1852c51c72423a8c5db0fb50baece80cf4b0416d36c2b505b4f"},
-                 "bytes": 189.63e6 + 3.93e6},
+                             "27cfb97ec504eeca8efb64f578a3bc60ed3bfc995d6e5d9af9d959353fa0c13d"},
+                 "bytes": 189.05e6 + 3.97e6},
     "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
                              "177f4ab710f11721ca4eafa1eb5504eab2340ddff890639dd517e226bbcea14a",
                              "paper_2512_13133_gb300/csrc/fft_dev.cuh":
