@@ -1122,7 +1122,8 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.empty_cache()
         if args.library_clips and args.config == "scale":
             # a resident library of the serving form's size: rasters and
-            # signatures only (the tensor-core engine needs no spectra)
+            # signatures only (the tensor-core and exact-scan engines need no
+            # spectra)
             import synth
             t0 = time.time()
             k = args.library_clips
@@ -1136,6 +1137,10 @@ def run_ours(args, rank, world, local_rank):
                                                        cs_lib.rorder)) / 1e9,
                              "setup_s": time.time() - t0,
                              "cosine": run_serving(pcl, ctx, Ptc, cs_lib, lib, cand_per_query=256),
+                             "cosine_exact_scan": run_serving(
+                                 pcl, ctx, pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, COS_NUM, COS_DEN,
+                                                      TOL, cos_engine=pcl.ENGINE_EXACT_SCAN),
+                                 cs_lib, lib, cand_per_query=256),
                              "edge": run_serving(pcl, ctx, P, cs_lib, lib, mode=pcl.MODE_EDGE,
                                                  cand_per_query=8192)}
             del cs_lib, lib
