@@ -107,8 +107,10 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
 
 // spop holds the sorted keys: the area, or with the topological pre-screen
 // class * V + area (V = N^2 + 2), so that a band never leaves its class
-template <int WPL>
-__global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
+// LP: the lane-per-member first chunk of G3 (WPL > 1, blk 16-byte aligned;
+// band_lp_smem() bytes of dynamic shared memory)
+template <int WPL, bool LP = false>
+__global__ void __launch_bounds__(256, LP ? 6 : 8) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
                                                         const uint32_t *spop, const uint32_t *cum, uint32_t V,
                                                         uint32_t vmax_all, pcl_pair *out, uint64_t cap,
                                                         unsigned long long *count,
@@ -157,6 +159,16 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             g2s = g2_scratch + (threadIdx.x >> 5) * band_g2_warp(g.N, g.S);
             g2_rep_setup(cs.prof + (size_t)a * 2 * g.N, g.N, g.S, lane, g2s);
         }
+        uint32_t *lrep = nullptr;  // LP: the representative's first-chunk words, then the member rows
+        if constexpr (LP) {
+            static_assert(WPL > 1, "the first chunk is 32 words");
+            extern __shared__ __align__(16) uint32_t bj_lp[];
+            lrep = bj_lp + (threadIdx.x >> 5) * kBjWarpWords;
+            __syncwarp();  // the previous representative's words are no longer read
+            lrep[lane] = ca[0];
+            lrep[32 + lane] = da[0];
+            __syncwarp();
+        }
         if (pa == 0) {  // the band holds the other empty clips only: similar by definition
             for (uint32_t q0 = start; q0 < end; q0 += 32) {
                 const uint32_t bq = q0 + lane < end ? order[q0 + lane] : 0u;
@@ -171,6 +183,27 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
             }
             continue;
         }
+        // G2 and the output for member bk once G3 keeps it
+        auto after_g3 = [&](uint32_t bk, int tAk) {
+            // G2 with the same threshold (tA = pa - um; never clamped in a band)
+            bool g2r;
+            if constexpr (WPL == 1) {
+                const uint16_t *pbk = cs.prof + (size_t)bk * 2 * g.N;
+                g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
+            } else {
+                g2r = warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N,
+                                           g.S, (int64_t)pa - tAk, lane);
+            }
+            if (g2r) {
+                ++g2;
+                return;
+            }
+            ++kept;
+            if (lane == 0) {
+                const unsigned long long idx = atomicAdd(count, 1ull);
+                if (idx < cap) out[idx] = pcl_pair{min(a, bk), max(a, bk)};
+            }
+        };
         // band members 32 at a time: lane l sets up member q0 + l (index,
         // thresholds; members of a non-empty representative are non-empty),
         // then the warp tests them one after the other
@@ -202,25 +235,43 @@ __global__ void __launch_bounds__(256, 8) band_join_kernel(pcl_params prm, pcl_c
                     ++g3;
                     return;
                 }
-                // G2 with the same threshold (tA = pa - um; never clamped in a band)
-                bool g2r;
-                if constexpr (WPL == 1) {
-                    const uint16_t *pbk = cs.prof + (size_t)bk * 2 * g.N;
-                    g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
-                } else {
-                    g2r = warp_g2_rejects_lite(cs.prof + (size_t)a * 2 * g.N, cs.prof + (size_t)bk * 2 * g.N, g.N,
-                                               g.S, (int64_t)pa - tAk, lane);
-                }
-                if (g2r) {
-                    ++g2;
-                    return;
-                }
-                ++kept;
-                if (lane == 0) {
-                    const unsigned long long idx = atomicAdd(count, 1ull);
-                    if (idx < cap) out[idx] = pcl_pair{min(a, bk), max(a, bk)};
-                }
+                after_g3(bk, tAk);
             };
+            if constexpr (LP) {
+                // each lane sums its member's first chunk of both deficits
+                // (A's first: on its own it rejects most band pairs); the
+                // members left take the other chunks with the whole warp
+                const bool mine = lane < cnt;
+                uint32_t *rows = lrep + 64;
+                bj_stage(rows, cs.blk, nb2, b, __ballot_sync(0xffffffffu, mine), words, lane);  // neighbourhood sums
+                int DA = 0, DB = 0;
+                bool rej = false;
+                if (mine) {
+                    DA = bj_deficit<false>(rows + 32 * lane, lane, lrep);
+                    rej = DA >= tA;
+                }
+                const unsigned keep_a = __ballot_sync(0xffffffffu, mine && !rej);
+                if (keep_a) {
+                    bj_stage(rows, cs.blk, nb2, b, keep_a, 0, lane);  // block counts
+                    if (mine && !rej) {
+                        DB = bj_deficit<true>(rows + 32 * lane, lane, lrep + 32);
+                        rej = DB >= tB;
+                    }
+                }
+                g3 += __popc(__ballot_sync(0xffffffffu, mine && rej));
+                unsigned left = __ballot_sync(0xffffffffu, mine && !rej);
+                while (left) {
+                    const int k = __ffs(left) - 1;
+                    left &= left - 1u;
+                    const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                    const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+                    const int DAk = __shfl_sync(0xffffffffu, DA, k), DBk = __shfl_sync(0xffffffffu, DB, k);
+                    const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)bk * 2 * nb2);
+                    if (g3_rest_rejects<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, DAk, DBk, lane)) ++g3;
+                    else after_g3(bk, tAk);
+                }
+                continue;
+            }
             // Pre-screen two members at a time: the representative's deficit
             // over the first 64 blocks against each member (the test that
             // alone rejects most band pairs), both sums in one reduction (each
@@ -347,14 +398,25 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     scan_kernel<<<1, 1024, 0, st>>>(cum, Vt);
     scatter_kernel<<<num_sms * 4, 256, 0, st>>>(k, n, cum, fill, order, spop);
     const uint32_t vall = (uint32_t)g.N * g.N;
+    const bool lp = (reinterpret_cast<uintptr_t>(cs.blk) & 15u) == 0;  // 16-byte copies of block rows
     switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
         case 1: band_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, cs, order, spop, cum, V,
                                                                                        vall, out, cap, count,
                                                                  local, next_pos, shard, n_shards); break;
-        case 4: band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
-                                                                 local, next_pos, shard, n_shards); break;
-        case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap,
-                                                                   count, local, next_pos, shard, n_shards); break;
+        case 4:
+            if (lp) band_join_kernel<4, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(prm, cs, order, spop, cum, V,
+                                                                                     vall, out, cap, count, local,
+                                                                                     next_pos, shard, n_shards);
+            else band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
+                                                                  local, next_pos, shard, n_shards);
+            break;
+        case 16:
+            if (lp) band_join_kernel<16, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(prm, cs, order, spop, cum, V,
+                                                                                      vall, out, cap, count, local,
+                                                                                      next_pos, shard, n_shards);
+            else band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap,
+                                                                   count, local, next_pos, shard, n_shards);
+            break;
         default: return cudaErrorInvalidValue;
     }
     const unsigned long long total = shard_pairs(n, shard, n_shards);

@@ -233,6 +233,11 @@ __device__ __forceinline__ bool warp_g2_rejects_lite(const uint16_t *__restrict_
 // first chunk A's deficit is summed and tested before B's: on its own it
 // rejects most pairs of a band.
 template <int WPL>
+__device__ __forceinline__ bool g3_rest_rejects(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+                                                const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
+                                                int words, int tA, int tB, int DA, int DB, int lane);
+
+template <int WPL>
 __device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
                                                const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
                                                int words, int tA, int tB, int lane) {
@@ -242,8 +247,17 @@ __device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const 
     int DA = (int)((sr & 0xffffu) + (sr >> 16));
     if (DA >= tA) return true;
     sr = __reduce_add_sync(0xffffffffu, b0 - __vminu2(b0, da[0]));
-    int DB = (int)((sr & 0xffffu) + (sr >> 16));
+    const int DB = (int)((sr & 0xffffu) + (sr >> 16));
     if (DB >= tB) return true;
+    return g3_rest_rejects<WPL>(ca, da, cb, db, words, tA, tB, DA, DB, lane);
+}
+
+// G3 from the second 32-lane chunk on, the first chunk's deficits DA and DB
+// (neither at its threshold) already summed: the rest of g3_rejects_thr.
+template <int WPL>
+__device__ __forceinline__ bool g3_rest_rejects(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+                                                const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
+                                                int words, int tA, int tB, int DA, int DB, int lane) {
 #pragma unroll
     for (int c = 1; c < WPL; ++c) {
         const int t = c * 32 + lane;
@@ -259,6 +273,67 @@ __device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const 
         if (DA >= tA || DB >= tB) return true;
     }
     return false;
+}
+
+// ---- lane-per-member first chunk (N >= 256: 32 or more u32 words of block
+// counts per clip).  In the band join each lane takes one of up to 32 band
+// members and sums the member's first-chunk deficits (the first 64 blocks,
+// spread over the raster) itself, from member words staged in the warp's
+// shared memory by 16-byte asynchronous copies: the test that decides about
+// four fifths of band pairs costs a few instructions per pair instead of a
+// warp reduction per member.  Per warp: the representative's first 32 words
+// of block counts and of neighbourhood sums, then one 32-word row per member.
+constexpr int kBjWarpWords = 64 + 32 * 32;
+__host__ __device__ inline int band_lp_smem() { return 8 * kBjWarpWords * 4; }  // 8 warps per CTA
+
+__device__ __forceinline__ void cp_async16(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stage words [off, off + 32) of the block row of each member m in mask
+// (lane m holds its clip index bm) into row m of rows.  16-byte chunk j of
+// row m sits at chunk position j ^ (m & 7), so that 8 lanes reading 16-byte
+// vectors of their own rows meet 8 different bank groups.  blk must be
+// 16-byte aligned (the caller checks).
+__device__ __forceinline__ void bj_stage(uint32_t *rows, const uint16_t *blk, int nb2, uint32_t bm, unsigned mask,
+                                         int off, int lane) {
+    __syncwarp();  // the rows' previous contents are no longer read
+    const int g = lane >> 3, j = lane & 7;
+    for (int m0 = 0; m0 < 32; m0 += 4) {
+        if (((mask >> m0) & 0xfu) == 0u) continue;  // warp-uniform
+        const int m = m0 + g;
+        const uint32_t b = __shfl_sync(0xffffffffu, bm, m);
+        if ((mask >> m) & 1u)
+            cp_async16(rows + 32 * m + 4 * (j ^ (m & 7)),
+                       reinterpret_cast<const uint32_t *>(blk + (size_t)b * 2 * nb2) + off + 4 * j);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+// Sum over the 32 words of x - min(x, y), both 16-bit halves added: x from the
+// lane's member row m and y from the representative's words (MEMBER_FIRST),
+// or the other way round.  Each half of a term is at most 256 (a block
+// count), so each half of the running sum stays below 32 * 256.
+template <bool MEMBER_FIRST>
+__device__ __forceinline__ int bj_deficit(const uint32_t *row, int m, const uint32_t *rep) {
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(row + 4 * (j ^ (m & 7)));
+        const uint4 r = *reinterpret_cast<const uint4 *>(rep + 4 * j);
+        if constexpr (MEMBER_FIRST) {
+            acc += (u.x - __vminu2(u.x, r.x)) + (u.y - __vminu2(u.y, r.y));
+            acc += (u.z - __vminu2(u.z, r.z)) + (u.w - __vminu2(u.w, r.w));
+        } else {
+            acc += (r.x - __vminu2(r.x, u.x)) + (r.y - __vminu2(r.y, u.y));
+            acc += (r.z - __vminu2(r.z, u.z)) + (r.w - __vminu2(r.w, u.w));
+        }
+    }
+    return (int)((acc & 0xffffu) + (acc >> 16));
 }
 
 // cosine gates of one pair (warp-uniform result): PCL_GATE_* or 0.  scratch
