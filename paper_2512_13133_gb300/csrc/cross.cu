@@ -107,9 +107,12 @@ __global__ void __launch_bounds__(1024) scan_items_kernel(const uint32_t *v, uin
     if (threadIdx.x == 1023) out[m] = run;
 }
 
-// WPL: u32 words of block counts per lane (the query's are held in registers)
-template <int WPL>
-__global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
+// WPL: u32 words of block counts per lane (the query's are held in registers).
+// LP: the lane-per-member first chunk of G3, as in the self-join (WPL > 1,
+// the library's blk 16-byte aligned; band_lp_smem() bytes of dynamic shared
+// memory)
+template <int WPL, bool LP = false>
+__global__ void __launch_bounds__(256, LP ? 6 : 1) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
                                                          const uint32_t *lib_order, const uint32_t *lib_spop,
                                                          const uint32_t *qorder, const uint32_t *qspop,
                                                          const uint32_t *beg, const uint32_t *end,
@@ -175,6 +178,36 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
             g2s = g2_scratch + (threadIdx.x >> 5) * band_g2_warp(g.N, g.S);
             g2_rep_setup(Q.prof + (size_t)q * 2 * g.N, g.N, g.S, lane, g2s);
         }
+        uint32_t *lrep = nullptr;  // LP: the query's first-chunk words, then the member rows
+        if constexpr (LP) {
+            static_assert(WPL > 1, "the first chunk is 32 words");
+            extern __shared__ __align__(16) uint32_t bj_lp[];
+            lrep = bj_lp + (threadIdx.x >> 5) * kBjWarpWords;
+            __syncwarp();  // the previous query's words are no longer read
+            lrep[lane] = ca[0];
+            lrep[32 + lane] = da[0];
+            __syncwarp();
+        }
+        // G2 and the output for library clip bk once G3 keeps it
+        auto after_g3 = [&](uint32_t bk, int tAk) {
+            bool g2r;
+            if constexpr (WPL == 1) {
+                const uint16_t *pbk = L.prof + (size_t)bk * 2 * g.N;
+                g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
+            } else {
+                g2r = warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N, g.S,
+                                           (int64_t)pa - tAk, lane);
+            }
+            if (g2r) {
+                ++g2;
+                return;
+            }
+            ++kept;
+            if (lane == 0) {
+                const unsigned long long idx = atomicAdd(count, 1ull);
+                if (idx < cap) out[idx] = pcl_pair{q, bk};
+            }
+        };
         // members 32 at a time: lane l sets up member q0 + l (index, the
         // thresholds of the exact rule; G1 passes, so neither is clamped),
         // then the warp tests them one after the other
@@ -189,6 +222,40 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
                 tB = (int)((int64_t)pb - um);
             }
             const int cnt = (int)min(32u, p1 - q0);
+            if constexpr (LP) {
+                // each lane sums its member's first chunk of both deficits; the
+                // members left take the other chunks with the whole warp
+                const bool mine = lane < cnt;
+                uint32_t *rows = lrep + 64;
+                bj_stage(rows, L.blk, nb2, b, __ballot_sync(0xffffffffu, mine), words, lane);  // neighbourhood sums
+                int DA = 0, DB = 0;
+                bool rej = false;
+                if (mine) {
+                    DA = bj_deficit<false>(rows + 32 * lane, lane, lrep);
+                    rej = DA >= tA;
+                }
+                const unsigned keep_a = __ballot_sync(0xffffffffu, mine && !rej);
+                if (keep_a) {
+                    bj_stage(rows, L.blk, nb2, b, keep_a, 0, lane);  // block counts
+                    if (mine && !rej) {
+                        DB = bj_deficit<true>(rows + 32 * lane, lane, lrep + 32);
+                        rej = DB >= tB;
+                    }
+                }
+                g3 += __popc(__ballot_sync(0xffffffffu, mine && rej));
+                unsigned left = __ballot_sync(0xffffffffu, mine && !rej);
+                while (left) {
+                    const int k = __ffs(left) - 1;
+                    left &= left - 1u;
+                    const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                    const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+                    const int DAk = __shfl_sync(0xffffffffu, DA, k), DBk = __shfl_sync(0xffffffffu, DB, k);
+                    const uint32_t *cwb = reinterpret_cast<const uint32_t *>(L.blk + (size_t)bk * 2 * nb2);
+                    if (g3_rest_rejects<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, DAk, DBk, lane)) ++g3;
+                    else after_g3(bk, tAk);
+                }
+                continue;
+            }
             for (int k = 0; k < cnt; ++k) {
                 const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
                 const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
@@ -197,23 +264,7 @@ __global__ void __launch_bounds__(256) cross_join_kernel(pcl_params prm, pcl_cli
                     ++g3;
                     continue;
                 }
-                bool g2r;
-                if constexpr (WPL == 1) {
-                    const uint16_t *pbk = L.prof + (size_t)bk * 2 * g.N;
-                    g2r = g2_rejects_small(g2s, pbk, g.N, g.S, (int64_t)pa - tAk, lane);
-                } else {
-                    g2r = warp_g2_rejects_lite(Q.prof + (size_t)q * 2 * g.N, L.prof + (size_t)bk * 2 * g.N, g.N,
-                                               g.S, (int64_t)pa - tAk, lane);
-                }
-                if (g2r) {
-                    ++g2;
-                    continue;
-                }
-                ++kept;
-                if (lane == 0) {
-                    const unsigned long long idx = atomicAdd(count, 1ull);
-                    if (idx < cap) out[idx] = pcl_pair{q, bk};
-                }
+                after_g3(bk, tAk);
             }
         }
     }
@@ -272,17 +323,28 @@ cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const
                                                              prm.cos_den, beg, endp);
         cross_chunks_kernel<<<(n_ch + 255) / 256, 256, 0, st>>>(beg, endp, nq, n_ch, qlo, cnt);
         scan_items_kernel<<<1, 1024, 0, st>>>(cnt, n_ch, item_off);
+        const bool lp = (reinterpret_cast<uintptr_t>(L.blk) & 15u) == 0;  // 16-byte copies of block rows
         switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
             case 1: cross_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, Q, L, lib_order,
                                                                       lib_spop, qorder, qspop,
                                                                       beg, endp, qlo, item_off, n_ch, out, cap,
                                                                       count, local, next_item); break;
-            case 4: cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,
-                                                                      beg, endp, qlo, item_off, n_ch, out, cap,
-                                                                      count, local, next_item); break;
-            case 16: cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder,
+            case 4:
+                if (lp) cross_join_kernel<4, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(
+                    prm, Q, L, lib_order, lib_spop, qorder, qspop, beg, endp, qlo, item_off, n_ch, out, cap, count,
+                    local, next_item);
+                else cross_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder, qspop,
+                                                                       beg, endp, qlo, item_off, n_ch, out, cap,
+                                                                       count, local, next_item);
+                break;
+            case 16:
+                if (lp) cross_join_kernel<16, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(
+                    prm, Q, L, lib_order, lib_spop, qorder, qspop, beg, endp, qlo, item_off, n_ch, out, cap, count,
+                    local, next_item);
+                else cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder,
                                                                         qspop, beg, endp, qlo, item_off, n_ch, out,
-                                                                        cap, count, local, next_item); break;
+                                                                        cap, count, local, next_item);
+                break;
             default: return cudaErrorInvalidValue;
         }
     }

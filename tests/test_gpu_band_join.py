@@ -97,3 +97,25 @@ def test_band_join_shards_512(ctx, torch_cuda, n_shards):
         counts += gates.cpu().numpy()
     assert got == set(map(tuple, op.astype(np.int64).tolist()))
     np.testing.assert_array_equal(counts[:6], ocounts[:6].astype(np.int64))
+
+
+@pytest.mark.parametrize("window_dbu,na,nb", [(1024, 60, 1500), (2048, 40, 400)])
+def test_cross_join_matches_oracle(ctx, torch_cuda, window_dbu, na, nb):
+    """Query x library candidates (the cross join of the serving loop, also
+    lane-per-member in its first chunk) at 256² and 512², with the library's
+    block array aligned and not: the oracle's exhaustive two-set screen."""
+    import paper_2512_13133_gb300 as pcl
+    wl = _workload(na + nb, window_dbu)
+    wa, wb = wl.subset(np.arange(0, na)), wl.subset(np.arange(na, na + nb))
+    P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80)
+    ca = pcl.alloc_clipset(P, wa.rect_off, wa.rects, with_spec=False)
+    cb = pcl.alloc_clipset(P, wb.rect_off, wb.rects, with_spec=False)
+    pcl.pcl_rasterize(ctx, P, ca)
+    pcl.pcl_rasterize(ctx, P, cb)
+    op, oc = oracle.ClipSet(synth.concat(wa, wb)).candidates_ab(na, pcl.MODE_COSINE, cos_num=80)
+    assert oc[pcl.GATE_G3_DENSITY] > 1000
+    want = set(map(tuple, op.astype(np.int64).tolist()))
+    for lib in (cb, _misaligned_blk(torch_cuda, cb)):
+        gp, gc = pcl.candidates(ctx, P, pcl.MODE_COSINE, ca, b=lib)
+        assert set(map(tuple, gp.cpu().numpy().astype(np.int64).tolist())) == want
+        np.testing.assert_array_equal(gc[:6], oc[:6].astype(np.int64))
