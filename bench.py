@@ -102,10 +102,10 @@ TRAFFIC = {
                               "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
                   "bytes": 1.85e9 + 25.19e6},
     "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
-                             "1158754a98ae9ab6eb5b97fcabe67b2a8cfb6d1433cc9cbff87692ae0eeb0d50",
+                             "761390a890765e2051712e727c67a8275db754aa8334c35045d9ba3fbb8da76a",
                              "paper_2512_13133_gb300/csrc/gates.cuh":
                              "e5b5c89e0881023dbee5ed0a6342c15ae8890a53ab02ca05081cd08f65cf7e61"},
-                 "bytes": 186.43e6 + 3.53e6},
+                 "bytes": 186.22e6 + 3.54e6},
     "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
                              "177f4ab710f11721ca4eafa1eb5504eab2340ddff890639dd517e226bbcea14a",
                              "paper_2512_13133_gb300/csrc/fft_dev.cuh":

@@ -108,11 +108,12 @@ __global__ void __launch_bounds__(1024) scan_items_kernel(const uint32_t *v, uin
 }
 
 // WPL: u32 words of block counts per lane (the query's are held in registers).
-// LP: the lane-per-member first chunk of G3, as in the self-join (WPL > 1,
+// LP: the lane-per-member first chunk of G3, as in the self-join (WPL = 4,
 // the library's blk 16-byte aligned; band_lp_smem() bytes of dynamic shared
-// memory)
+// memory).  Without LP the minimum of blocks per SM is left unset (0): the
+// compiler's own register choice, which a hint of 1 would raise.
 template <int WPL, bool LP = false>
-__global__ void __launch_bounds__(256, LP ? 6 : 1) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
+__global__ void __launch_bounds__(256, LP ? 6 : 0) cross_join_kernel(pcl_params prm, pcl_clipset Q, pcl_clipset L,
                                                          const uint32_t *lib_order, const uint32_t *lib_spop,
                                                          const uint32_t *qorder, const uint32_t *qspop,
                                                          const uint32_t *beg, const uint32_t *end,
@@ -254,17 +255,17 @@ __global__ void __launch_bounds__(256, LP ? 6 : 1) cross_join_kernel(pcl_params 
                     if (g3_rest_rejects<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, DAk, DBk, lane)) ++g3;
                     else after_g3(bk, tAk);
                 }
-                continue;
-            }
-            for (int k = 0; k < cnt; ++k) {
-                const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
-                const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
-                const uint32_t *cwb = reinterpret_cast<const uint32_t *>(L.blk + (size_t)bk * 2 * nb2);
-                if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
-                    ++g3;
-                    continue;
+            } else {
+                for (int k = 0; k < cnt; ++k) {
+                    const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
+                    const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
+                    const uint32_t *cwb = reinterpret_cast<const uint32_t *>(L.blk + (size_t)bk * 2 * nb2);
+                    if (g3_rejects_thr<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, lane)) {
+                        ++g3;
+                        continue;
+                    }
+                    after_g3(bk, tAk);
                 }
-                after_g3(bk, tAk);
             }
         }
     }
@@ -323,6 +324,7 @@ cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const
                                                              prm.cos_den, beg, endp);
         cross_chunks_kernel<<<(n_ch + 255) / 256, 256, 0, st>>>(beg, endp, nq, n_ch, qlo, cnt);
         scan_items_kernel<<<1, 1024, 0, st>>>(cnt, n_ch, item_off);
+        // the lane-per-member first chunk at 256² only, as in the self-join
         const bool lp = (reinterpret_cast<uintptr_t>(L.blk) & 15u) == 0;  // 16-byte copies of block rows
         switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
             case 1: cross_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, Q, L, lib_order,
@@ -337,14 +339,9 @@ cudaError_t launch_cross_join(const pcl_params &prm, const pcl_clipset &Q, const
                                                                        beg, endp, qlo, item_off, n_ch, out, cap,
                                                                        count, local, next_item);
                 break;
-            case 16:
-                if (lp) cross_join_kernel<16, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(
-                    prm, Q, L, lib_order, lib_spop, qorder, qspop, beg, endp, qlo, item_off, n_ch, out, cap, count,
-                    local, next_item);
-                else cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder,
+            case 16: cross_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, Q, L, lib_order, lib_spop, qorder,
                                                                         qspop, beg, endp, qlo, item_off, n_ch, out,
-                                                                        cap, count, local, next_item);
-                break;
+                                                                        cap, count, local, next_item); break;
             default: return cudaErrorInvalidValue;
         }
     }

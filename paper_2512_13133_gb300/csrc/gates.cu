@@ -107,7 +107,7 @@ __global__ void scatter_kernel(const uint32_t *pop, uint32_t n, const uint32_t *
 
 // spop holds the sorted keys: the area, or with the topological pre-screen
 // class * V + area (V = N^2 + 2), so that a band never leaves its class
-// LP: the lane-per-member first chunk of G3 (WPL > 1, blk 16-byte aligned;
+// LP: the lane-per-member first chunk of G3 (WPL = 4, blk 16-byte aligned;
 // band_lp_smem() bytes of dynamic shared memory)
 template <int WPL, bool LP = false>
 __global__ void __launch_bounds__(256, LP ? 6 : 8) band_join_kernel(pcl_params prm, pcl_clipset cs, const uint32_t *order,
@@ -398,6 +398,8 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
     scan_kernel<<<1, 1024, 0, st>>>(cum, Vt);
     scatter_kernel<<<num_sms * 4, 256, 0, st>>>(k, n, cum, fill, order, spop);
     const uint32_t vall = (uint32_t)g.N * g.N;
+    // the lane-per-member first chunk at 256² (4 words per lane; at 512² the
+    // first 64 of 1,024 blocks decide too few pairs to pay for the staging)
     const bool lp = (reinterpret_cast<uintptr_t>(cs.blk) & 15u) == 0;  // 16-byte copies of block rows
     switch ((g.nb * g.nb / 2 + 31) / 32) {  // u32 words of block counts per lane
         case 1: band_join_kernel<1><<<num_sms * 8, 256, band_g2_smem(g.N, g.S), st>>>(prm, cs, order, spop, cum, V,
@@ -410,13 +412,8 @@ cudaError_t launch_band_join(const pcl_params &prm, const pcl_clipset &cs, void 
             else band_join_kernel<4><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap, count,
                                                                   local, next_pos, shard, n_shards);
             break;
-        case 16:
-            if (lp) band_join_kernel<16, true><<<num_sms * 6, 256, band_lp_smem(), st>>>(prm, cs, order, spop, cum, V,
-                                                                                      vall, out, cap, count, local,
-                                                                                      next_pos, shard, n_shards);
-            else band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap,
-                                                                   count, local, next_pos, shard, n_shards);
-            break;
+        case 16: band_join_kernel<16><<<num_sms * 8, 256, 0, st>>>(prm, cs, order, spop, cum, V, vall, out, cap,
+                                                                   count, local, next_pos, shard, n_shards); break;
         default: return cudaErrorInvalidValue;
     }
     const unsigned long long total = shard_pairs(n, shard, n_shards);

@@ -1,5 +1,5 @@
-"""The cosine band join at 256² and 512² rasters, where each lane of a warp
-sums the first chunk of the G3 density bound for its own band member (member
+"""The cosine band join at 256² and 512² rasters (at 256² each lane of a warp
+sums the first chunk of the G3 density bound for its own band member, member
 block words staged in shared memory by 16-byte copies), against the oracle's
 exhaustive screen: candidate sets and gate counts exact, at two thresholds
 (T = 0.80 gives bands of hundreds of members, so full and partial groups of 32
@@ -72,13 +72,14 @@ def test_band_join_matches_oracle(ctx, torch_cuda, window_dbu, n, cos_num):
         assert gcounts[:6].sum() == n * (n - 1) // 2
 
 
+@pytest.mark.parametrize("window_dbu", [1024, 2048])
 @pytest.mark.parametrize("n_shards", [1, 3])
-def test_band_join_shards_512(ctx, torch_cuda, n_shards):
-    """Shards of the 512² band join (members b > a of representatives a = s +
-    k S, compacted to the low lanes before the lane-per-member chunk) add up
-    to the self-join, with the oracle's gate counts."""
+def test_band_join_shards(ctx, torch_cuda, window_dbu, n_shards):
+    """Shards of the band join (members b > a of representatives a = s + k S,
+    compacted to the low lanes before the lane-per-member chunk at 256²) add
+    up to the self-join, with the oracle's gate counts."""
     import paper_2512_13133_gb300 as pcl
-    wl = _workload(200, 2048)
+    wl = _workload(200, window_dbu)
     P = pcl.params(wl.window_dbu, wl.pitch_dbu, wl.marker_dbu, cos_num=80)
     cs = pcl.alloc_clipset(P, wl.rect_off, wl.rects, with_spec=False)
     pcl.pcl_rasterize(ctx, P, cs)
