@@ -248,7 +248,12 @@ pcl_status pcl_spectra(pcl_ctx *ctx, const pcl_params *P, pcl_clipset *cs, const
    incremented: [0] survivors, [g] pairs rejected by gate g (their sum is
    the number of pairs screened).  COSINE uses the context workspace (two
    sets: about 16 (N^2 + 2) + 16 |a| + 8 |b| bytes for the area orders of
-   both sets and the bands of a's clips).
+   both sets and the bands of a's clips).  EDGE uses it for the list of pairs
+   whose polygons all meet occupied cells, which a second kernel checks for
+   the exact correspondence: 16 bytes per entry, one entry per 256 pairs
+   screened, at least 65,536 and at most 2^24 entries (pairs past the list
+   are checked inside the screen).  Calls that use the context workspace run
+   in stream order on one stream at a time.
    With P->flags & PCL_P_TOPO_HASH (self-join only) a lossy topological
    pre-screen runs first (Sec. 3.1 stage 1 filters with topological hashing
    before the exact tests): a pair is kept only if both clips have the same

@@ -13,10 +13,13 @@ cudaError_t launch_raster(const pcl_params &, const pcl_clipset &, cudaStream_t)
 size_t band_join_workspace(const Geo &, uint32_t, bool);
 cudaError_t launch_band_join(const pcl_params &, const pcl_clipset &, void *, size_t, pcl_pair *, uint64_t,
                              unsigned long long *, unsigned long long *, int, cudaStream_t, uint32_t, uint32_t);
+size_t edge_checks_workspace(uint64_t);
 cudaError_t launch_edge_screen(const pcl_params &, const pcl_clipset &, pcl_pair *, uint64_t,
-                               unsigned long long *, unsigned long long *, cudaStream_t, uint32_t, uint32_t);
+                               unsigned long long *, unsigned long long *, cudaStream_t, uint32_t, uint32_t, void *,
+                               size_t, int);
 cudaError_t launch_edge_screen_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *,
-                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t);
+                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t, void *,
+                                     size_t, int);
 cudaError_t launch_area_sort(const uint32_t *, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                              int, cudaStream_t);
 size_t cross_join_workspace(const Geo &, uint32_t, uint32_t);
@@ -254,7 +257,9 @@ pcl_status pcl_candidates(pcl_ctx *ctx, const pcl_params *P, uint32_t mode, cons
     auto *cnt = reinterpret_cast<unsigned long long *>(d_count);
     auto *gates = reinterpret_cast<unsigned long long *>(d_gate_counts);
     if (edge) {
-        e = launch_edge_screen_cross(*P, *a, *b, d_out, cap, cnt, gates, st);
+        // the workspace holds the list of pairs for the correspondence check
+        if ((s = ensure_ws(ctx, edge_checks_workspace((uint64_t)a->n_clips * b->n_clips)))) return s;
+        e = launch_edge_screen_cross(*P, *a, *b, d_out, cap, cnt, gates, st, ctx->ws, ctx->ws_bytes, ctx->num_sms);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge screen (two sets)");
     }
     const Geo g = make_geo(*P);
@@ -300,7 +305,10 @@ pcl_status pcl_candidates_shard(pcl_ctx *ctx, const pcl_params *P, uint32_t mode
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "band join");
     }
     if (mode == PCL_MODE_EDGE) {
-        e = launch_edge_screen(*P, *cs, d_out, cap, cnt, gates, st, shard, n_shards);
+        const uint64_t n = cs->n_clips;
+        if ((s = ensure_ws(ctx, edge_checks_workspace(n * (n - (n > 0)) / 2 / n_shards)))) return s;
+        e = launch_edge_screen(*P, *cs, d_out, cap, cnt, gates, st, shard, n_shards, ctx->ws, ctx->ws_bytes,
+                               ctx->num_sms);
         return e == cudaSuccess ? PCL_OK : cuda_fail(ctx, e, "edge screen");
     }
     return fail(ctx, PCL_ERR_INVALID, "unknown mode%s %lld", "", mode);

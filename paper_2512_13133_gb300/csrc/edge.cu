@@ -3,15 +3,24 @@
 //
 // edge_screen_kernel: the self-join screen of all pairs i < j through E2 and
 // E1 (tiles of 32 row clips x 256 column clips; the cheap occupancy-grid
-// tests of E1 run one pair per lane, the exact correspondence of the few
-// survivors one pair per warp).  edge_match_kernel: the Min-Max record of
-// each listed pair, one pair per warp (lanes hold the polygons).
+// tests of E1 run one pair per lane; the few survivors go to a list whose
+// exact correspondence edge_check_kernel checks afterwards, one pair per
+// warp).  edge_match_kernel: the Min-Max record of each listed pair, one pair
+// per warp (lanes hold the polygons).
 #include "edge_dev.cuh"
 
 namespace pcl {
 
 namespace {
 using namespace edge_dev;
+
+// the screen's list of pairs for the exact correspondence check (device
+// memory; cap 0: every such pair is checked inside the screen)
+struct EdgeChecks {
+    int4 *list;
+    uint64_t cap;
+    unsigned long long *count;
+};
 
 __device__ __forceinline__ void emit_pair(pcl_pair *out, uint64_t cap, unsigned long long *count,
                                           bool keep, uint32_t a, uint32_t b) {
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
                                                           pcl_pair *out, uint64_t cap,
                                                           unsigned long long *count,
                                                           unsigned long long *gates, uint32_t shard,
-                                                          uint32_t n_shards) {
+                                                          uint32_t n_shards, EdgeChecks chk) {
     const pcl_clipset &RW = CROSS ? RS : CS;  // the row clips (the same set in the self-join)
     const uint32_t nr = RW.n_clips, n = CS.n_clips;  // rows, columns
     uint32_t bx, by;
@@ -274,11 +283,27 @@ __global__ void __launch_bounds__(256, 4) edge_screen_kernel(pcl_params prm, pcl
         __syncwarp();
         fn = 0;
     };
-    // tag: row | col << 8 | small_is_a << 16 of the pair
+    // tag: row | col << 8 | small_is_a << 16 of the pair.  The pairs go to
+    // the check list while it has room, else to this warp's queue.
     auto push_full = [&](bool p, int tag, int s0x, int s0y) {
         const unsigned m = __ballot_sync(0xffffffffu, p);
-        if (p) fq[warp][fn + __popc(m & lt)] = make_int4(tag, s0x, s0y, 0);
-        fn += __popc(m);
+        if (!m) return;
+        bool here = p;
+        if (chk.cap) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(chk.count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            const unsigned long long idx = base + __popc(m & lt);
+            if (p && idx < chk.cap) {
+                chk.list[idx] = make_int4((int)(i0 + (tag & 0xff)), (int)(jblk + ((tag >> 8) & 0xff)), s0x,
+                                          s0y * 2 + ((tag >> 16) & 1));
+                here = false;
+            }
+        }
+        const unsigned mh = __ballot_sync(0xffffffffu, here);
+        if (here) fq[warp][fn + __popc(mh & lt)] = make_int4(tag, s0x, s0y, 0);
+        fn += __popc(mh);
         __syncwarp();
         if (fn >= 32) run_full();  // keeps fn below 32 between pushes
     };
@@ -409,7 +434,71 @@ __global__ void __launch_bounds__(256) edge_match_kernel(pcl_params prm, pcl_cli
     }
 }
 
+// The exact correspondence (Sec. 2.2.2 condition 1) of the pairs the screen
+// listed: entry {i, j, tx, 2 ty + small_is_a} (i a row clip of RW, j a
+// column clip of CS, (tx, ty) the shift as the screen's queue holds it).
+// Warps take 32 consecutive entries at a time (grid-stride) and emit the
+// pairs that pass with one atomic per batch; counters go to gates (E1 for
+// the pairs that fail, [0] for the others).
+template <bool CROSS>
+__global__ void __launch_bounds__(256) edge_check_kernel(pcl_clipset RS, pcl_clipset CS, EdgeChecks chk,
+                                                         pcl_pair *out, uint64_t cap, unsigned long long *count,
+                                                         unsigned long long *gates) {
+    const pcl_clipset &RW = CROSS ? RS : CS;
+    const int4 *rrects = reinterpret_cast<const int4 *>(RW.rects), *crects = reinterpret_cast<const int4 *>(CS.rects);
+    unsigned long long n = *chk.count;
+    if (n > chk.cap) n = chk.cap;
+    const int lane = threadIdx.x & 31;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long kept = 0, e1 = 0;
+    for (uint64_t t0 = w0 * 32; t0 < n; t0 += nw * 32) {  // warp-uniform
+        const int m = (int)(n - t0 < 32 ? n - t0 : 32);
+        const int4 mine = lane < m ? chk.list[t0 + lane] : make_int4(0, 0, 0, 0);
+        unsigned ok = 0u;
+        for (int q = 0; q < m; ++q) {
+            const uint32_t i = (uint32_t)__shfl_sync(0xffffffffu, mine.x, q);
+            const uint32_t j = (uint32_t)__shfl_sync(0xffffffffu, mine.y, q);
+            const int tx = __shfl_sync(0xffffffffu, mine.z, q), tw = __shfl_sync(0xffffffffu, mine.w, q);
+            const bool sa = tw & 1;
+            const int ty = tw >> 1;
+            const int offa = (int)__ldg(RW.rect_off + i), na = __ldg(RW.esig + (size_t)i * 8);
+            const int offb = (int)__ldg(CS.rect_off + j), nb = __ldg(CS.esig + (size_t)j * 8);
+            const int4 *sr = sa ? rrects + offa : crects + offb, *lr = sa ? crects + offb : rrects + offa;
+            const uint16_t *so = sa ? RW.rorder + offa : CS.rorder + offb;
+            if (warp_correspond(sr, so, sa ? na : nb, lr, sa ? nb : na, sa, tx, ty, lane)) ok |= 1u << q;
+        }
+        const bool keep = (ok >> lane) & 1u;
+        emit_pair(out, cap, count, keep, (uint32_t)mine.x, (uint32_t)mine.y);
+        kept += (unsigned long long)__popc(ok);
+        e1 += (unsigned long long)(m - __popc(ok));
+    }
+    if (lane == 0 && gates) {
+        if (kept) atomicAdd(gates + 0, kept);
+        if (e1) atomicAdd(gates + PCL_GATE_E1_MATCH, e1);
+    }
+}
+
 }  // namespace
+
+// bytes of the check list for a screen of `pairs` pairs: a count, then
+// entries for one pair in 256 (at least 65,536 and at most 2^24 entries);
+// pairs past the list are checked inside the screen
+uint64_t edge_checks_capacity(uint64_t pairs) {
+    const uint64_t c = pairs / 256;
+    return c < (1ull << 16) ? (1ull << 16) : c > (1ull << 24) ? (1ull << 24) : c;
+}
+size_t edge_checks_workspace(uint64_t pairs) { return 16 + 16 * (size_t)edge_checks_capacity(pairs); }
+
+static EdgeChecks edge_checks(void *ws, size_t ws_bytes) {
+    EdgeChecks c{nullptr, 0, nullptr};
+    if (ws && ws_bytes >= 16 + 16) {
+        c.count = static_cast<unsigned long long *>(ws);
+        c.list = reinterpret_cast<int4 *>(static_cast<char *>(ws) + 16);
+        c.cap = (ws_bytes - 16) / 16;
+    }
+    return c;
+}
 
 // shard s of S (several GPUs sharing one self-join) screens the tiles
 // s, s + S, s + 2S, ... of the 1-D tile numbering: a partition by clip index
@@ -420,7 +509,8 @@ uint64_t edge_screen_tiles(uint32_t n) {
 
 cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl_pair *out,
                                uint64_t cap, unsigned long long *count, unsigned long long *gates,
-                               cudaStream_t st, uint32_t shard, uint32_t n_shards) {
+                               cudaStream_t st, uint32_t shard, uint32_t n_shards, void *ws, size_t ws_bytes,
+                               int num_sms) {
     if (n_shards == 0 || shard >= n_shards) return cudaErrorInvalidValue;
     // only the tiles that hold pairs i < j (about half of them)
     const uint64_t tiles = edge_screen_tiles(cs.n_clips);
@@ -429,32 +519,51 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
     const unsigned grid = (unsigned)((tiles - shard + n_shards - 1) / n_shards);
     const int csz = prm.window_dbu / 64;
     const bool p2 = (csz & (csz - 1)) == 0, topo = (prm.flags & PCL_P_TOPO_HASH) != 0;
+    const EdgeChecks chk = edge_checks(ws, ws_bytes);
+    if (chk.cap) {
+        const cudaError_t e = cudaMemsetAsync(chk.count, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+    }
     if (topo && p2)
         edge_screen_kernel<true, false, true><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard,
-                                                                    n_shards);
+                                                                    n_shards, chk);
     else if (topo)
         edge_screen_kernel<false, false, true><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard,
-                                                                     n_shards);
+                                                                     n_shards, chk);
     else if (p2)
-        edge_screen_kernel<true, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
+        edge_screen_kernel<true, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards,
+                                                              chk);
     else
-        edge_screen_kernel<false, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard, n_shards);
+        edge_screen_kernel<false, false><<<grid, 256, 0, st>>>(prm, cs, cs, out, cap, count, gates, shard,
+                                                               n_shards, chk);
+    if (chk.cap) edge_check_kernel<false><<<num_sms * 8, 256, 0, st>>>(cs, cs, chk, out, cap, count, gates);
     return cudaGetLastError();
 }
 
 // query x library screen (serving): every (q, l) pair through E2 and E1, the
-// survivors written as (q, l); tiles of 32 queries x 256 library clips
+// survivors written as (q, l); tiles of 32 queries x 256 library clips.  With
+// no workspace (ws NULL: the server's slots) every pair is checked inside the
+// screen.
 cudaError_t launch_edge_screen_cross(const pcl_params &prm, const pcl_clipset &q, const pcl_clipset &lib,
                                      pcl_pair *out, uint64_t cap, unsigned long long *count,
-                                     unsigned long long *gates, cudaStream_t st) {
+                                     unsigned long long *gates, cudaStream_t st, void *ws, size_t ws_bytes,
+                                     int num_sms) {
     if (q.n_clips == 0 || lib.n_clips == 0) return cudaSuccess;
     const uint64_t tiles = (uint64_t)((q.n_clips + 31) / 32) * ((lib.n_clips + kColsB - 1) / kColsB);
     if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     const int csz = prm.window_dbu / 64;
+    const EdgeChecks chk = edge_checks(ws, ws_bytes);
+    if (chk.cap) {
+        const cudaError_t e = cudaMemsetAsync(chk.count, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+    }
     if ((csz & (csz - 1)) == 0)
-        edge_screen_kernel<true, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1);
+        edge_screen_kernel<true, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1,
+                                                                        chk);
     else
-        edge_screen_kernel<false, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1);
+        edge_screen_kernel<false, true><<<(unsigned)tiles, 256, 0, st>>>(prm, q, lib, out, cap, count, gates, 0, 1,
+                                                                         chk);
+    if (chk.cap) edge_check_kernel<true><<<num_sms * 8, 256, 0, st>>>(q, lib, chk, out, cap, count, gates);
     return cudaGetLastError();
 }
 

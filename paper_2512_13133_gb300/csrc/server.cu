@@ -50,7 +50,8 @@ cudaError_t launch_tc(const pcl_params &, const pcl_clipset &, const pcl_clipset
                       const unsigned long long *, pcl_record *, void *, size_t, int, int *, unsigned long long,
                       cudaStream_t);
 cudaError_t launch_edge_screen_cross(const pcl_params &, const pcl_clipset &, const pcl_clipset &, pcl_pair *,
-                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t);
+                                     uint64_t, unsigned long long *, unsigned long long *, cudaStream_t, void *,
+                                     size_t, int);
 cudaError_t launch_edge_match(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const pcl_pair *, uint64_t,
                               const unsigned long long *, pcl_record *, int, cudaStream_t);
 cudaError_t launch_cross_join(const pcl_params &, const pcl_clipset &, const pcl_clipset &, const uint32_t *,
@@ -406,7 +407,8 @@ pcl_status pcl_server_submit_class(pcl_server *s, uint32_t cls, const uint32_t *
         // of the self-join, rows = queries, columns = library clips), then
         // the Min-Max record of each survivor, one pair per warp
         if (e == cudaSuccess)
-            e = pcl::launch_edge_screen_cross(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, nullptr, st);
+            e = pcl::launch_edge_screen_cross(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, nullptr, st,
+                                              nullptr, 0, ctx->num_sms);
         if (e == cudaSuccess)
             e = pcl::launch_edge_match(k.P, sl->q, k.lib, sl->cand, cap, sl->counts + 0, sl->rec, ctx->num_sms, st);
     } else {
