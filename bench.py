@@ -97,10 +97,11 @@ def peaks():
 # taken; otherwise the bench reports null.
 TRAFFIC = {
     "cand_edge": {"sources": {"paper_2512_13133_gb300/csrc/edge.cu":
-                              "f8428a4d07647d91cb8b9a30511f40f9963539da9033c77e9e6c5c1e814b5d4d",
+                              "24881dc859f2e04454e884f6b59bac034f3cc09715159213c296f31d42bc90e2",
                               "paper_2512_13133_gb300/csrc/edge_dev.cuh":
                               "91b43fe9f14b6cc097d8b42b10055358e7d3ba02c7518a45ff01bacbb54247c7"},
-                  "bytes": 1.85e9 + 25.19e6},
+                  # the screen (1.63 GB + 202.12 MB) and its list's check (257.90 + 16.14 MB)
+                  "bytes": 1.63e9 + 202.12e6 + 257.90e6 + 16.14e6},
     "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
                              "761390a890765e2051712e727c67a8275db754aa8334c35045d9ba3fbb8da76a",
                              "paper_2512_13133_gb300/csrc/gates.cuh":
@@ -1297,9 +1298,10 @@ def run_ours(args, rank, world, local_rank):
         "topo_prescreen": topo,
         "next": nxt,
     }
-    # kernels launched per step: raster 1, band join 5, edge screen 1, cosine match 4
-    # (mark, two spectra sweeps counted once for a self-join, pair) -> 3, edge match 1, compact 2
-    line["gpu_launches"] = args.steps * (1 + 5 + 1 + 3 + 1 + 2)
+    # kernels launched per step: raster 1, band join 5, edge screen 2 (the screen and the
+    # correspondence check of its list), cosine match 4 (mark, two spectra sweeps counted
+    # once for a self-join, pair) -> 3, edge match 1, compact 2
+    line["gpu_launches"] = args.steps * (1 + 5 + 2 + 3 + 1 + 2)
     if not args.no_cpu_baseline and world == 1:
         n_s = args.cpu_sample or default_sample(args.config)
         a, t, thr = oracle_sample(wl, n_s)
