@@ -490,12 +490,14 @@ uint64_t edge_checks_capacity(uint64_t pairs) {
 }
 size_t edge_checks_workspace(uint64_t pairs) { return 16 + 16 * (size_t)edge_checks_capacity(pairs); }
 
-static EdgeChecks edge_checks(void *ws, size_t ws_bytes) {
+// the check list of a screen of `pairs` pairs at the start of the workspace
+// (none if the workspace is missing or smaller than edge_checks_workspace)
+static EdgeChecks edge_checks(void *ws, size_t ws_bytes, uint64_t pairs) {
     EdgeChecks c{nullptr, 0, nullptr};
-    if (ws && ws_bytes >= 16 + 16) {
+    if (ws && ws_bytes >= edge_checks_workspace(pairs)) {
         c.count = static_cast<unsigned long long *>(ws);
         c.list = reinterpret_cast<int4 *>(static_cast<char *>(ws) + 16);
-        c.cap = (ws_bytes - 16) / 16;
+        c.cap = edge_checks_capacity(pairs);
     }
     return c;
 }
@@ -519,7 +521,8 @@ cudaError_t launch_edge_screen(const pcl_params &prm, const pcl_clipset &cs, pcl
     const unsigned grid = (unsigned)((tiles - shard + n_shards - 1) / n_shards);
     const int csz = prm.window_dbu / 64;
     const bool p2 = (csz & (csz - 1)) == 0, topo = (prm.flags & PCL_P_TOPO_HASH) != 0;
-    const EdgeChecks chk = edge_checks(ws, ws_bytes);
+    const uint64_t n = cs.n_clips;
+    const EdgeChecks chk = edge_checks(ws, ws_bytes, n * (n - (n > 0)) / 2 / n_shards);
     if (chk.cap) {
         const cudaError_t e = cudaMemsetAsync(chk.count, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
@@ -552,7 +555,7 @@ cudaError_t launch_edge_screen_cross(const pcl_params &prm, const pcl_clipset &q
     const uint64_t tiles = (uint64_t)((q.n_clips + 31) / 32) * ((lib.n_clips + kColsB - 1) / kColsB);
     if (tiles > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     const int csz = prm.window_dbu / 64;
-    const EdgeChecks chk = edge_checks(ws, ws_bytes);
+    const EdgeChecks chk = edge_checks(ws, ws_bytes, (uint64_t)q.n_clips * lib.n_clips);
     if (chk.cap) {
         const cudaError_t e = cudaMemsetAsync(chk.count, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
