@@ -103,10 +103,10 @@ TRAFFIC = {
                   # the screen (1.63 GB + 201.62 MB) and its list's check (257.92 + 16.15 MB)
                   "bytes": 1.63e9 + 201.62e6 + 257.92e6 + 16.15e6},
     "cand_cos": {"sources": {"paper_2512_13133_gb300/csrc/gates.cu":
-                             "761390a890765e2051712e727c67a8275db754aa8334c35045d9ba3fbb8da76a",
+                             "5935883332fb8b84d06ddb62a40a0e119ddaeb97da669f62ebc438834c34e99b",
                              "paper_2512_13133_gb300/csrc/gates.cuh":
-                             "e5b5c89e0881023dbee5ed0a6342c15ae8890a53ab02ca05081cd08f65cf7e61"},
-                 "bytes": 186.22e6 + 3.54e6},
+                             "7383112e07955c850196dd11d6cdf0d93e2e08c1eab2c834c73868a92928f7d0"},
+                 "bytes": 185.34e6 + 4.26e6},
     "fft_pair": {"sources": {"paper_2512_13133_gb300/csrc/fft.cu":
                              "177f4ab710f11721ca4eafa1eb5504eab2340ddff890639dd517e226bbcea14a",
                              "paper_2512_13133_gb300/csrc/fft_dev.cuh":

@@ -260,14 +260,30 @@ __global__ void __launch_bounds__(256, LP ? 6 : 8) band_join_kernel(pcl_params p
                 }
                 g3 += __popc(__ballot_sync(0xffffffffu, mine && rej));
                 unsigned left = __ballot_sync(0xffffffffu, mine && !rej);
+                // the members left, one after the other with the whole warp; the
+                // next one's second-chunk words load while the current one is tested
+                uint32_t b1 = 0u, d1 = 0u;
+                if (left) {
+                    const uint32_t *cw = reinterpret_cast<const uint32_t *>(
+                        cs.blk + (size_t)__shfl_sync(0xffffffffu, b, __ffs(left) - 1) * 2 * nb2);
+                    b1 = __ldg(cw + 32 + lane);
+                    d1 = __ldg(cw + words + 32 + lane);
+                }
                 while (left) {
                     const int k = __ffs(left) - 1;
                     left &= left - 1u;
                     const uint32_t bk = __shfl_sync(0xffffffffu, b, k);
                     const int tAk = __shfl_sync(0xffffffffu, tA, k), tBk = __shfl_sync(0xffffffffu, tB, k);
                     const int DAk = __shfl_sync(0xffffffffu, DA, k), DBk = __shfl_sync(0xffffffffu, DB, k);
+                    const uint32_t cb1 = b1, cd1 = d1;
+                    if (left) {
+                        const uint32_t *cw = reinterpret_cast<const uint32_t *>(
+                            cs.blk + (size_t)__shfl_sync(0xffffffffu, b, __ffs(left) - 1) * 2 * nb2);
+                        b1 = __ldg(cw + 32 + lane);
+                        d1 = __ldg(cw + words + 32 + lane);
+                    }
                     const uint32_t *cwb = reinterpret_cast<const uint32_t *>(cs.blk + (size_t)bk * 2 * nb2);
-                    if (g3_rest_rejects<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, DAk, DBk, lane)) ++g3;
+                    if (g3_rest_pre<WPL>(ca, da, cwb, cwb + words, words, tAk, tBk, DAk, DBk, cb1, cd1, lane)) ++g3;
                     else after_g3(bk, tAk);
                 }
                 continue;

@@ -252,6 +252,35 @@ __device__ __forceinline__ bool g3_rejects_thr(const uint32_t (&ca)[WPL], const 
     return g3_rest_rejects<WPL>(ca, da, cb, db, words, tA, tB, DA, DB, lane);
 }
 
+// g3_rest_rejects with the second chunk's words of the member (cb, db at
+// 32 + lane) already loaded into b1 and d1 (WPL > 1)
+template <int WPL>
+__device__ __forceinline__ bool g3_rest_pre(const uint32_t (&ca)[WPL], const uint32_t (&da)[WPL],
+                                            const uint32_t *__restrict__ cb, const uint32_t *__restrict__ db,
+                                            int words, int tA, int tB, int DA, int DB, uint32_t b1, uint32_t d1,
+                                            int lane) {
+    const uint32_t sa = __reduce_add_sync(0xffffffffu, ca[1] - __vminu2(ca[1], d1));
+    const uint32_t sb = __reduce_add_sync(0xffffffffu, b1 - __vminu2(b1, da[1]));
+    DA += (int)((sa & 0xffffu) + (sa >> 16));
+    DB += (int)((sb & 0xffffu) + (sb >> 16));
+    if (DA >= tA || DB >= tB) return true;
+#pragma unroll
+    for (int c = 2; c < WPL; ++c) {
+        const int t = c * 32 + lane;
+        uint32_t pda = 0u, pdb = 0u;
+        if (t < words) {
+            const uint32_t b = __ldg(cb + t);
+            pda = ca[c] - __vminu2(ca[c], __ldg(db + t));
+            pdb = b - __vminu2(b, da[c]);
+        }
+        const uint32_t ra = __reduce_add_sync(0xffffffffu, pda), rb = __reduce_add_sync(0xffffffffu, pdb);
+        DA += (int)((ra & 0xffffu) + (ra >> 16));
+        DB += (int)((rb & 0xffffu) + (rb >> 16));
+        if (DA >= tA || DB >= tB) return true;
+    }
+    return false;
+}
+
 // G3 from the second 32-lane chunk on, the first chunk's deficits DA and DB
 // (neither at its threshold) already summed: the rest of g3_rejects_thr.
 template <int WPL>
